@@ -1,0 +1,402 @@
+"""Seeded synthetic scenes: the inputs both the CUDA solver and the CPU oracle read.
+
+The paper evaluates on TDOM/DSM benchmarks and learned feature pyramids that are not
+available here (Sec. III-B, Sec. V-A).  This module stands in for them with seeded
+synthetic frames of the same structure:
+
+* a DSM crop (sum of Gaussian hills plus box buildings) lifted to 3D geo-anchors
+  P_j = (x_j, y_j, D(x_j, y_j)), one per crop cell (Supp. "Geo-anchor Construction");
+* a 3-level query feature pyramid with C channels, L2-normalised per pixel
+  (Supp. "Network Architecture": descriptors are L2-normalised along channels);
+* reference descriptors f_l^r(p_j) obtained by reading the query pyramid at the
+  ground-truth projection of each anchor, plus Gaussian noise;
+* pose hypotheses in (x, y, yaw) around the ground truth (Sec. IV-E), an IMU gravity
+  measurement (Eq. 3) and a single-point laser range along the optical axis (Eq. 4-6).
+
+This module only *synthesises data*.  It contains none of the solver: no residual,
+Jacobian, robust weight, normal equation or pose update.  The ground-truth rendering
+of reference descriptors uses a 3x4 projection matrix and scipy's
+``ndimage.map_coordinates`` (order 1), i.e. an implementation independent of both the
+oracle and the CUDA path, so that "the oracle's cost vanishes at the ground truth" is
+a real check of the oracle's projection and sampling conventions.
+
+Conventions (shared by every consumer of these arrays):
+  * world frame ENU (x east, y north, z up), gravity direction gamma^W = (0, 0, -1);
+  * camera frame x right, y down, z forward; a pose is T_cw = [R | t] (world->camera),
+    stored row-major as 12 float64 values;
+  * pixel i covers [i, i+1) (corner convention); the principal point of level 0 is
+    (W0/2, H0/2) and level l uses K scaled by 2^-l;
+  * DSM cell (r, c) is centred at (x0 + (c + 1/2) gsd, y0 + (r + 1/2) gsd);
+  * every coordinate is expressed in the frame's local metric frame whose origin is the
+    crop centre (the map origin is not needed by the solver).
+"""
+from __future__ import annotations
+
+import dataclasses
+from dataclasses import dataclass, field
+
+import numpy as np
+from scipy import ndimage
+from scipy.spatial.transform import Rotation
+
+
+GRAVITY_WORLD = np.array([0.0, 0.0, -1.0])
+
+
+@dataclass
+class SceneConfig:
+    """Recipe of one synthetic frame.  Defaults follow the 256^2-crop, C=32 workload."""
+
+    crop_side: int = 256                  # anchors per crop side (N = crop_side^2)
+    gsd: float = 0.5                      # metres per DSM cell
+    n_hills: int = 8
+    hill_sigma: float = 10.0              # metres
+    hill_amp: tuple = (0.0, 15.0)         # metres
+    n_boxes: int = 4
+    box_height: tuple = (5.0, 40.0)       # metres
+    box_side: tuple = (6.0, 16.0)         # metres
+    channels: int = 32
+    levels: tuple = ((480, 640), (240, 320), (120, 160))   # (H, W), level 0 finest
+    f0: float = 600.0                     # level-0 focal length in pixels (fx = fy)
+    blur_sigma: float = 2.0               # pixels, at each level's own resolution
+    n_blobs: int = 8                      # Gaussian blobs per channel
+    blob_sigma: tuple = (6.0, 20.0)       # pixels
+    blob_amp: tuple = (-2.0, 2.0)
+    altitude: tuple = (120.0, 300.0)      # camera height above the datum, metres
+    pitch_deg: tuple = (30.0, 70.0)       # depression of the optical axis below horizon
+    ref_noise: float = 0.01               # std of the noise added to reference descriptors
+    n_hyps: int = 64
+    hyp_mode: str = "xy_yaw"              # "xy_yaw": U(+-dxy, +-dxy, +-dyaw); "rot_trans": exact angle/offset
+    hyp_xy: float = 10.0                  # metres
+    hyp_yaw_deg: float = 5.0              # degrees
+    hyp_rot_deg: float = 3.0              # rot_trans mode: rotation angle about a random axis
+    hyp_trans: float = 5.0                # rot_trans mode: translation length
+    use_gravity: bool = True
+    gravity_noise_deg: float = 0.2
+    w_grav: float = 1e2
+    use_range: bool = True
+    range_noise: float = 0.1              # metres
+    w_range: float = 1e1
+
+
+def config_small_plain() -> SceneConfig:
+    """Plain single frame: 64x64 DSM at 1 m, C=16, one 120x160 level, 1 hypothesis
+    perturbed by exactly 3 deg / 5 m, no priors (the small parity workload)."""
+    return SceneConfig(crop_side=64, gsd=1.0, box_height=(5.0, 30.0), channels=16,
+                       levels=((120, 160),), f0=150.0, altitude=(150.0, 150.0),
+                       pitch_deg=(45.0, 45.0), n_hyps=1, hyp_mode="rot_trans",
+                       use_gravity=False, use_range=False)
+
+
+def config_full_frame(n_hyps: int = 64) -> SceneConfig:
+    """Full single frame: 256x256 crop at 0.5 m, C=32, 3 levels 480x640/240x320/120x160,
+    fx=600, 64 hypotheses within +-10 m / +-5 deg, gravity and range priors on."""
+    return SceneConfig(n_hyps=n_hyps)
+
+
+def config_reduced_frame(crop_side: int = 70, n_hyps: int = 6, channels: int = 32,
+                         levels=((120, 160), (60, 80), (30, 40)), f0: float = 150.0,
+                         gsd: float = 1.0) -> SceneConfig:
+    """The full-frame recipe shrunk so that the FP64 oracle finishes in seconds, while
+    still spanning several point tiles and a ragged tail (70^2 = 4900 anchors)."""
+    return SceneConfig(crop_side=crop_side, gsd=gsd, channels=channels, levels=levels,
+                       f0=f0, n_hyps=n_hyps)
+
+
+@dataclass
+class Frame:
+    """One synthetic frame.  Arrays are C-contiguous numpy arrays."""
+
+    points: np.ndarray            # (3, N) float32, SoA: x, y, z in the local frame
+    point_valid: np.ndarray       # (N,) uint8
+    point_weight: np.ndarray      # (N,) float32 (ones)
+    ref_feat: list                # L arrays (N, C) float32
+    qry_feat: list                # L arrays (H_l, W_l, C) float32, NHWC
+    fx: float
+    fy: float
+    cx: float
+    cy: float
+    T_hyps: np.ndarray            # (M, 12) float64, rows [R | t] row-major
+    T_gt: np.ndarray              # (12,) float64
+    use_gravity: bool
+    gravity_cam: np.ndarray       # (3,)
+    gravity_world: np.ndarray     # (3,)
+    w_grav: float
+    use_range: bool
+    range_m: float
+    w_range: float
+    dsm: np.ndarray               # (H_D, W_D) float32
+    dsm_x0: float
+    dsm_y0: float
+    dsm_gsd: float
+    seed: int = 0
+    meta: dict = field(default_factory=dict)
+
+    @property
+    def N(self) -> int:
+        return self.points.shape[1]
+
+    @property
+    def M(self) -> int:
+        return self.T_hyps.shape[0]
+
+    @property
+    def C(self) -> int:
+        return self.qry_feat[0].shape[2]
+
+    @property
+    def L(self) -> int:
+        return len(self.qry_feat)
+
+    def replace(self, **kw) -> "Frame":
+        return dataclasses.replace(self, **kw)
+
+
+# ----------------------------------------------------------------------------- DSM
+
+def _make_dsm(cfg: SceneConfig, rng: np.random.Generator):
+    S, gsd = cfg.crop_side, cfg.gsd
+    half = 0.5 * S * gsd
+    x0 = y0 = -half
+    xs = x0 + (np.arange(S) + 0.5) * gsd
+    ys = y0 + (np.arange(S) + 0.5) * gsd
+    X, Y = np.meshgrid(xs, ys)                       # row = y, column = x
+    Z = np.zeros((S, S))
+    for _ in range(cfg.n_hills):
+        cx_, cy_ = rng.uniform(-half, half, 2)
+        amp = rng.uniform(*cfg.hill_amp)
+        Z += amp * np.exp(-((X - cx_) ** 2 + (Y - cy_) ** 2) / (2 * cfg.hill_sigma ** 2))
+    for _ in range(cfg.n_boxes):
+        cx_, cy_ = rng.uniform(-half, half, 2)
+        sx, sy = rng.uniform(*cfg.box_side, 2)
+        h = rng.uniform(*cfg.box_height)
+        inside = (np.abs(X - cx_) <= sx / 2) & (np.abs(Y - cy_) <= sy / 2)
+        Z = np.where(inside, np.maximum(Z, h), Z)
+    return Z.astype(np.float32), x0, y0, X, Y
+
+
+def dsm_height(dsm: np.ndarray, x0: float, y0: float, gsd: float, x, y):
+    """Bilinear DSM height at world (x, y) via scipy (cell centres at x0 + (c+1/2) gsd).
+    Outside the raster the nearest edge value is used (only for ground-truth synthesis)."""
+    cc = (np.asarray(x, float) - x0) / gsd - 0.5
+    rr = (np.asarray(y, float) - y0) / gsd - 0.5
+    return ndimage.map_coordinates(dsm.astype(np.float64), [np.atleast_1d(rr), np.atleast_1d(cc)],
+                                   order=1, mode="nearest")
+
+
+# ------------------------------------------------------------------------ features
+
+def _make_feature_map(H: int, W: int, C: int, cfg: SceneConfig, rng: np.random.Generator):
+    maps = np.empty((H, W, C), np.float64)
+    yy = np.arange(H) + 0.5
+    xx = np.arange(W) + 0.5
+    for c in range(C):
+        m = ndimage.gaussian_filter(rng.standard_normal((H, W)), cfg.blur_sigma, mode="reflect")
+        for _ in range(cfg.n_blobs):
+            bx, by = rng.uniform(0, W), rng.uniform(0, H)
+            s = rng.uniform(*cfg.blob_sigma)
+            a = rng.uniform(*cfg.blob_amp)
+            m += a * np.outer(np.exp(-(yy - by) ** 2 / (2 * s * s)),
+                              np.exp(-(xx - bx) ** 2 / (2 * s * s)))
+        maps[:, :, c] = m
+    maps /= np.linalg.norm(maps, axis=2, keepdims=True) + 1e-12
+    return maps.astype(np.float32)
+
+
+# ---------------------------------------------------------------------------- pose
+
+def look_pose(C_world: np.ndarray, yaw: float, pitch: float) -> np.ndarray:
+    """World->camera pose (12 values) of a camera at C_world heading `yaw` (radians from
+    east, counter-clockwise) with its optical axis `pitch` radians below the horizon."""
+    h = np.array([np.cos(yaw), np.sin(yaw), 0.0])
+    d = np.cos(pitch) * h + np.sin(pitch) * np.array([0.0, 0.0, -1.0])
+    right = np.array([np.sin(yaw), -np.cos(yaw), 0.0])
+    down = np.cross(d, right)
+    R_wc = np.stack([right, down, d], axis=1)        # columns: camera axes in world
+    R_cw = R_wc.T
+    t = -R_cw @ C_world
+    return np.concatenate([np.hstack([R_cw, t[:, None]]).ravel()])
+
+
+def pose_parts(T: np.ndarray):
+    T = np.asarray(T, float).reshape(3, 4)
+    return T[:, :3], T[:, 3]
+
+
+def camera_centre(T: np.ndarray) -> np.ndarray:
+    R, t = pose_parts(T)
+    return -R.T @ t
+
+
+def compose_pose(R_cw: np.ndarray, C_world: np.ndarray) -> np.ndarray:
+    t = -R_cw @ C_world
+    return np.hstack([R_cw, t[:, None]]).ravel()
+
+
+def _perturb_xy_yaw(T_gt, dx, dy, dyaw):
+    """Shift the camera centre by (dx, dy, 0) and rotate it about the world z axis
+    through the camera centre by dyaw (the (x, y, psi) hypothesis space, Sec. IV-E)."""
+    R, _ = pose_parts(T_gt)
+    C = camera_centre(T_gt)
+    Rz = Rotation.from_rotvec([0.0, 0.0, dyaw]).as_matrix()
+    R_wc = Rz @ R.T
+    return compose_pose(R_wc.T, C + np.array([dx, dy, 0.0]))
+
+
+def _perturb_rot_trans(T_gt, axis, angle, direction, length):
+    R, _ = pose_parts(T_gt)
+    C = camera_centre(T_gt)
+    Rw = Rotation.from_rotvec(axis * angle).as_matrix()
+    R_wc = Rw @ R.T
+    return compose_pose(R_wc.T, C + direction * length)
+
+
+def _unit(rng):
+    v = rng.standard_normal(3)
+    return v / np.linalg.norm(v)
+
+
+# -------------------------------------------------------------------- ground truth
+
+def project_gt(points_xyz: np.ndarray, T: np.ndarray, f: float, cx: float, cy: float):
+    """Ground-truth pixel coordinates of world points via the 3x4 matrix K [R | t]."""
+    P = np.array([[f, 0.0, cx], [0.0, f, cy], [0.0, 0.0, 1.0]]) @ np.asarray(T, float).reshape(3, 4)
+    Xh = np.vstack([points_xyz.astype(np.float64), np.ones((1, points_xyz.shape[1]))])
+    uvw = P @ Xh
+    return uvw[0] / uvw[2], uvw[1] / uvw[2], uvw[2]
+
+
+def read_map(fmap: np.ndarray, u: np.ndarray, v: np.ndarray) -> np.ndarray:
+    """Read an (H, W, C) map at continuous pixel coordinates (corner convention) with
+    scipy's linear interpolation.  Returns (len(u), C) float64."""
+    coords = [v - 0.5, u - 0.5]
+    out = np.empty((u.size, fmap.shape[2]))
+    for c in range(fmap.shape[2]):
+        out[:, c] = ndimage.map_coordinates(fmap[:, :, c].astype(np.float64), coords,
+                                            order=1, mode="nearest")
+    return out
+
+
+def _ray_to_dsm(C, d, dsm, x0, y0, gsd, step=0.05, s_max=5000.0):
+    """Distance along the ray C + s d to its first crossing of the bilinear DSM surface
+    (march, then bisection to 1e-9 m)."""
+    def above(s):
+        p = C + s * d
+        return p[2] - dsm_height(dsm, x0, y0, gsd, p[0], p[1])[0]
+
+    s_lo, s = 0.0, step
+    f_lo = above(0.0)
+    if f_lo <= 0:
+        raise ValueError("camera below the surface")
+    while s < s_max:
+        if above(s) <= 0:
+            break
+        s_lo, s = s, s + step
+    else:
+        raise ValueError("ray does not reach the surface")
+    lo, hi = s_lo, s
+    while hi - lo > 1e-9:
+        mid = 0.5 * (lo + hi)
+        if above(mid) > 0:
+            lo = mid
+        else:
+            hi = mid
+    return 0.5 * (lo + hi)
+
+
+# ------------------------------------------------------------------------- frames
+
+def make_frame(cfg: SceneConfig, seed: int) -> Frame:
+    """Build one seeded frame from `cfg`.  Independent sub-streams (SeedSequence children)
+    drive the DSM, each pyramid level, the pose, the noise and the hypotheses."""
+    ss = np.random.SeedSequence(seed)
+    kids = ss.spawn(8 + len(cfg.levels))
+    r_dsm, r_pose, r_ref, r_hyp, r_grav, r_rng = (np.random.default_rng(k) for k in kids[:6])
+    r_lev = [np.random.default_rng(k) for k in kids[8:]]
+
+    dsm, x0, y0, X, Y = _make_dsm(cfg, r_dsm)
+    S, gsd = cfg.crop_side, cfg.gsd
+    points = np.stack([X.ravel(), Y.ravel(), dsm.astype(np.float64).ravel()]).astype(np.float32)
+
+    H0, W0 = cfg.levels[0]
+    cx0, cy0 = W0 / 2.0, H0 / 2.0
+
+    # ground-truth pose: optical axis through the crop centre's surface point
+    alt = r_pose.uniform(*cfg.altitude)
+    pitch = np.deg2rad(r_pose.uniform(*cfg.pitch_deg))
+    yaw = r_pose.uniform(0.0, 2.0 * np.pi)
+    target = np.array([0.0, 0.0, dsm_height(dsm, x0, y0, gsd, 0.0, 0.0)[0]])
+    d = np.cos(pitch) * np.array([np.cos(yaw), np.sin(yaw), 0.0]) + np.sin(pitch) * np.array([0, 0, -1.0])
+    dist = (alt - target[2]) / np.sin(pitch)
+    C_gt = target - dist * d
+    T_gt = look_pose(C_gt, yaw, pitch)
+
+    qry, refs = [], []
+    valid = np.ones(points.shape[1], bool)
+    for lvl, (H, W) in enumerate(cfg.levels):
+        qry.append(_make_feature_map(H, W, cfg.channels, cfg, r_lev[lvl]))
+    for lvl, (H, W) in enumerate(cfg.levels):
+        s = 2.0 ** -lvl
+        u, v, z = project_gt(points, T_gt, cfg.f0 * s, cx0 * s, cy0 * s)
+        vis = (z > 0.1) & (u - 0.5 >= 0) & (u - 0.5 <= W - 1) & (v - 0.5 >= 0) & (v - 0.5 <= H - 1)
+        valid &= vis
+        f = read_map(qry[lvl], u, v)
+        f += cfg.ref_noise * r_ref.standard_normal(f.shape)
+        refs.append(f.astype(np.float32))
+    for f in refs:
+        f[~valid] = 0.0
+
+    # hypotheses
+    M = cfg.n_hyps
+    hyps = np.empty((M, 12))
+    for m in range(M):
+        if cfg.hyp_mode == "xy_yaw":
+            dx, dy = r_hyp.uniform(-cfg.hyp_xy, cfg.hyp_xy, 2)
+            dpsi = np.deg2rad(r_hyp.uniform(-cfg.hyp_yaw_deg, cfg.hyp_yaw_deg))
+            hyps[m] = _perturb_xy_yaw(T_gt, dx, dy, dpsi)
+        elif cfg.hyp_mode == "rot_trans":
+            hyps[m] = _perturb_rot_trans(T_gt, _unit(r_hyp), np.deg2rad(cfg.hyp_rot_deg),
+                                         _unit(r_hyp), cfg.hyp_trans)
+        else:
+            raise ValueError(cfg.hyp_mode)
+
+    # IMU gravity in the camera frame, tilted by a small angle about a perpendicular axis
+    R_gt, _ = pose_parts(T_gt)
+    g_cam = R_gt @ GRAVITY_WORLD
+    a = np.cross(g_cam, _unit(r_grav))
+    a /= np.linalg.norm(a)
+    g_meas = Rotation.from_rotvec(a * np.deg2rad(cfg.gravity_noise_deg)).as_matrix() @ g_cam
+
+    # laser range along the optical axis (the principal point is the image centre)
+    rng_true = _ray_to_dsm(C_gt, d, dsm, x0, y0, gsd)
+    rng_meas = rng_true + cfg.range_noise * r_rng.standard_normal()
+
+    return Frame(points=np.ascontiguousarray(points), point_valid=valid.astype(np.uint8),
+                 point_weight=np.ones(points.shape[1], np.float32), ref_feat=refs,
+                 qry_feat=qry, fx=cfg.f0, fy=cfg.f0, cx=cx0, cy=cy0,
+                 T_hyps=hyps, T_gt=T_gt, use_gravity=cfg.use_gravity,
+                 gravity_cam=g_meas, gravity_world=GRAVITY_WORLD.copy(), w_grav=cfg.w_grav,
+                 use_range=cfg.use_range, range_m=float(rng_meas), w_range=cfg.w_range,
+                 dsm=dsm, dsm_x0=x0, dsm_y0=y0, dsm_gsd=gsd, seed=seed,
+                 meta=dict(alt=alt, pitch_deg=float(np.rad2deg(pitch)), yaw_deg=float(np.rad2deg(yaw)),
+                           range_true=float(rng_true), crop_side=S))
+
+
+def frame_seed(workload: int, index: int) -> int:
+    """Seed of frame `index` of workload number `workload` (1_000_000 * workload + index)."""
+    return 1_000_000 * workload + index
+
+
+# ------------------------------------------------------------------- error metrics
+
+def rotation_error_deg(Ta, Tb) -> float:
+    """Angle of R_a^T R_b in degrees (arccos of the clamped trace formula)."""
+    Ra, _ = pose_parts(Ta)
+    Rb, _ = pose_parts(Tb)
+    c = (np.trace(Ra.T @ Rb) - 1.0) / 2.0
+    return float(np.rad2deg(np.arccos(np.clip(c, -1.0, 1.0))))
+
+
+def translation_error_m(Ta, Tb) -> float:
+    """Distance between camera centres in metres."""
+    return float(np.linalg.norm(camera_centre(Ta) - camera_centre(Tb)))
