@@ -1,0 +1,341 @@
+"""Throughput of the multi-hypothesis featuremetric LM pose solver on GB300.
+
+Metric: hypothesis x LM-iterations per second on the full single-frame workload
+(256^2-anchor TDOM/DSM crop at 0.5 m, C = 32 FP32 descriptors, 3-level query pyramid
+480x640 / 240x320 / 120x160, 64 hypotheses, 10 LM iterations per level, gravity and
+laser-range priors on).  One step = one whole solve of one frame: every level, every
+iteration, every hypothesis, the priors, the damped solves and the final selection.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+`value` is measured with the frame resident in device memory (CUDA events around each
+solve on the solve's stream, L2 flushed by a 512 MiB write between steps, outside the
+events).  `e2e` is the same metric through the C-ABI with page-locked HOST buffers, the
+host->device copies of the frame and the device->host copy of the results inside the
+timed region.  `--impl reference` times the FP64 CPU oracle on the host cores on a
+bounded sample of the same workload.  Under torchrun every rank solves its own frame
+(independent replicas, no collective on the data path); rank 0 prints one JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "hypothesis·LM-iters/sec (256² crop, C=32)"
+UNIT = "hyp*iter/s"
+WORKLOAD = ("full single frame: 256x256 anchors at 0.5 m, C=32, 3 levels 480x640/240x320/120x160, "
+            "64 hypotheses, 10 LM iterations per level, gravity + range priors")
+MEASURED_PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "build_kernel_traffic.json")
+BUILD_SRC = os.path.join(ROOT, "paper_2606_31098_gb300", "csrc", "pilot_build_impl.cuh")
+SM_COUNT = 152
+FP32_LANES_PER_SM = 128
+
+
+def flops_per_unit(C: int) -> int:
+    """Algorithmic FP32 flops of one (anchor, hypothesis) evaluation of the build pass:
+    25 per channel (bilinear value + 2 gradients 12, residual 1, six sums 12) plus 200 per
+    anchor (transform 18, projection 10, Huber 6, Jacobian rows 12, M A 36, weights 12,
+    21 H entries 84, 6 g entries 24)."""
+    return 25 * C + 200
+
+
+def gather_bytes_per_unit(C: int, elem: int) -> int:
+    """Bytes of the 4-tap bilinear gather of one (anchor, hypothesis) evaluation."""
+    return 4 * C * elem
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=60)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--seed-index", type=int, default=0)
+    return ap.parse_args()
+
+
+def dist_env():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.out = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.out, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.out.close()
+        rows = []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                rows.append(dict(sm=float(parts[1]), smax=float(parts[2]), power=float(parts[3]),
+                                 hw=parts[5], hw_thermal=parts[6], sw_thermal=parts[7], sw_power=parts[8]))
+            except ValueError:
+                continue
+        os.unlink(self.path)
+        if not rows:
+            return None
+        reasons = set()
+        for r in rows:
+            for key, name in (("hw", "hw_slowdown"), ("hw_thermal", "hw_thermal_slowdown"),
+                              ("sw_thermal", "sw_thermal_slowdown"), ("sw_power", "sw_power_cap")):
+                if r[key].lower() == "active":
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(r["sm"] for r in rows), "sm_max_mhz": max(r["smax"] for r in rows),
+                "power_w_max": max(r["power"] for r in rows), "samples": len(rows), "reasons": sorted(reasons)}
+
+
+def load_peaks():
+    try:
+        return json.load(open(MEASURED_PEAKS))
+    except Exception:
+        return None
+
+
+def build_src_hash() -> str:
+    return hashlib.sha256(open(BUILD_SRC, "rb").read()).hexdigest()[:16]
+
+
+def traffic_per_launch(units_per_launch: int):
+    """DRAM bytes per build launch from the committed ncu summary, scaled to the units of
+    one launch; None when the kernel source changed since the counters were taken."""
+    try:
+        t = json.load(open(TRAFFIC_FILE))
+    except Exception:
+        return None
+    if t.get("build_src_sha256_16") != build_src_hash():
+        return None
+    return t["dram_bytes_per_unit"] * units_per_launch
+
+
+def cpu_cores() -> int:
+    try:
+        return len(os.sched_getaffinity(0))
+    except Exception:
+        return os.cpu_count() or 1
+
+
+def run_oracle_sample(frame, n_hyps: int, threads: int):
+    """Solve `n_hyps` hypotheses of the frame with the FP64 oracle; returns
+    (hyp_iters, seconds)."""
+    from oracle import oracle as O
+    t0 = time.perf_counter()
+    r = O.solve(frame, O.SolverOptions(iters=(10, 10, 10, 0)), T_hyps=frame.T_hyps[:n_hyps], n_threads=threads)
+    return r.hyp_iters, time.perf_counter() - t0
+
+
+def oracle_hyps_for(threads: int) -> int:
+    # about 2 hypotheses per thread (~1.7 s of CPU per hypothesis on one core), so one
+    # sample is 10-30 s of CPU work
+    return max(2, 2 * threads)
+
+
+# --------------------------------------------------------------------- reference arm
+
+def run_reference(args):
+    world, rank, _ = dist_env()
+    if rank != 0:
+        return 0
+    from paper_2606_31098_gb300 import scenes as S
+    from oracle import build_oracle
+    build_oracle.build()
+    frame = S.make_frame(S.config_full_frame(), S.frame_seed(2, args.seed_index))
+    threads = cpu_cores()
+    nh = oracle_hyps_for(threads)
+    for _ in range(args.warmup):
+        run_oracle_sample(frame, nh, threads)
+    total_units, total_s = 0, 0.0
+    for _ in range(args.steps):
+        u, s = run_oracle_sample(frame, nh, threads)
+        total_units += u
+        total_s += s
+    value = total_units / total_s
+    sample = f"{nh} of the 64 hypotheses of the full frame per step (all 3 levels x 10 iterations)"
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total_s / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic (seeded scene generator)",
+            "config": {"workload": WORKLOAD, "reference": "FP64 CPU oracle (plain C, OpenMP over hypotheses)"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# --------------------------------------------------------------------------- our arm
+
+def run_ours(args):
+    import torch
+    world, rank, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    torch.cuda.set_device(local)
+
+    from paper_2606_31098_gb300 import binding as B
+    from paper_2606_31098_gb300 import build_ext
+    from paper_2606_31098_gb300 import scenes as S
+
+    build_ext.build()
+    B.load()
+    frame = S.make_frame(S.config_full_frame(), S.frame_seed(2, args.seed_index + rank))
+    opts = B.Options(iters=(10, 10, 10, 0), max_points=frame.N, max_hyps=frame.M, max_channels=32, profile=1)
+    solver = B.Solver(opts)
+    stream = torch.cuda.current_stream()
+    dev = B.FrameArgs(frame, B.device_arrays(frame), is_device=True)
+    host = B.FrameArgs(frame, B.host_arrays(frame, pinned=True), is_device=False)
+    flush = torch.empty(512 * 1024 * 1024, dtype=torch.uint8, device="cuda")
+
+    def barrier():
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+
+    def timed(fa, steps):
+        times, build_ms, build_n, launches, units = [], 0.0, 0, 0, 0
+        for _ in range(steps):
+            flush.zero_()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            r = solver.solve(fa, stream)
+            e1.record(stream)
+            e1.synchronize()
+            times.append(e0.elapsed_time(e1))
+            ms, nb, nt = solver.profile()
+            build_ms += ms
+            build_n += nb
+            launches += nt
+            units += r.hyp_iters
+        return times, build_ms, build_n, launches, units, r
+
+    for _ in range(args.warmup):
+        solver.solve(dev, stream)
+        solver.solve(host, stream)
+    torch.cuda.synchronize()
+
+    clocks = ClockSampler(local)
+    clocks.start()
+    barrier()
+    torch.cuda.synchronize()
+    times, build_ms, build_n, launches, units, res = timed(dev, args.steps)
+    torch.cuda.synchronize()
+    barrier()
+    e2e_times, _, _, _, e2e_units, _ = timed(host, args.steps)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+
+    total_ms = sum(times)
+    e2e_ms = sum(e2e_times)
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([total_ms, e2e_ms], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms, e2e_ms = t.tolist()
+    value = world * units / (total_ms / 1e3)
+    e2e_value = world * e2e_units / (e2e_ms / 1e3)
+
+    # roofline of the dominant kernel (the build pass)
+    C, elem = frame.C, 4
+    units_per_launch = frame.N * frame.M          # no pruning: every launch runs all hypotheses
+    avg_launch_ms = build_ms / max(build_n, 1)
+    achieved_tflops = units_per_launch * flops_per_unit(C) / (avg_launch_ms * 1e-3) / 1e12
+    sm_max = (clk or {}).get("sm_max_mhz") or (load_peaks() or {}).get("sm_max_mhz", 2070.0)
+    peak_tflops = SM_COUNT * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
+    gather_gbs = units_per_launch * gather_bytes_per_unit(C, elem) / (avg_launch_ms * 1e-3) / 1e9
+    traffic = traffic_per_launch(units_per_launch)
+
+    h2d = sum(a.nbytes for k, v in B.host_arrays(frame).items() for a in (v if isinstance(v, list) else [v]))
+    d2h = frame.M * (12 * 8 + 8 + 4 + 4) + 16
+
+    cpu = None
+    if rank == 0:
+        threads = cpu_cores()
+        nh = oracle_hyps_for(threads)
+        u, s = run_oracle_sample(frame, nh, threads)
+        cpu = {"value": u / s, "unit": UNIT, "cores": threads, "kind": "oracle",
+               "sample": f"{nh} of the 64 hypotheses of the same frame, all 3 levels x 10 iterations "
+                         f"({u} hyp*iter in {s:.1f} s)"}
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic (seeded scene generator)",
+                "config": {"workload": WORKLOAD, "points": frame.N, "hypotheses": frame.M, "channels": C,
+                           "levels": [list(q.shape[:2]) for q in frame.qry_feat], "iters_per_level": [10, 10, 10],
+                           "feature_dtype": "f32", "form": "plain single frame, one stream",
+                           "l2": "flushed between steps (512 MiB write)", "replicas": world},
+                "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+                        "d2h_bytes_per_step": int(d2h), "ms_per_step": e2e_ms / args.steps},
+                "gpu_launches": int(launches),
+                "roofline": {"bound": "alu", "kernel": "build pass (pilot::build_kernel<f32, 32>)",
+                             "achieved": achieved_tflops, "peak": peak_tflops, "unit": "TFLOP/s",
+                             "frac": achieved_tflops / peak_tflops, "traffic": traffic,
+                             "peak_basis": f"FP32 FMA: {SM_COUNT} SMs x {FP32_LANES_PER_SM} lanes x 2 x {sm_max:.0f} MHz",
+                             "flops_per_unit": flops_per_unit(C), "units_per_launch": units_per_launch,
+                             "avg_launch_ms": avg_launch_ms, "launches": build_n,
+                             "gather_bytes_per_unit": gather_bytes_per_unit(C, elem), "gather_GBps": gather_gbs,
+                             "build_share_of_step": build_ms / total_ms},
+                "clocks": clk,
+                "cpu_baseline": cpu}
+        print(json.dumps(line), flush=True)
+    solver.close()
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,179 @@
+/*
+ * pilot_align.h -- C-ABI of the GB300 featuremetric multi-hypothesis LM pose solver.
+ *
+ * The solver estimates the world->camera pose of a query frame by aligning its feature
+ * pyramid with 3D geo-anchors lifted from a TDOM/DSM crop (problem statement, Sec. IV).
+ * For every anchor P_j and pose hypothesis T it projects P_j into the query pyramid,
+ * bilinearly samples C channels, forms the photo residual (Eq. 1) under a Huber loss
+ * (Eq. 2), adds the IMU gravity residual (Eq. 3) and the single-point laser range
+ * residual (Eq. 4-6) to the total objective (Eq. 7), and takes damped Gauss-Newton
+ * (Levenberg-Marquardt) steps (Eq. 8) with the left SE(3) update (Eq. 9), coarse to
+ * fine over the pyramid, for many hypotheses at once (Sec. IV-E and Supp.
+ * "Multi-Hypothesis Refinement"); the output is the hypothesis of lowest objective.
+ *
+ * Conventions shared by every entry point:
+ *   - No C++ exception crosses this boundary.  Every call returns a pilot_status; the
+ *     detail of the last failure on the calling thread is in pilot_align_last_error().
+ *   - Inputs are never modified.  Output buffers belong to the caller.
+ *   - A handle owns its device workspace (sized at create from the config's max_*
+ *     fields); frames larger than that are rejected with PILOT_EINVAL.  A handle is not
+ *     re-entrant: use one handle per host thread.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = the legacy default stream).
+ *     Every call that takes a stream has returned all results to host memory, and has
+ *     finished using the caller's input buffers, when it returns.
+ *   - Per-hypothesis failures (too few visible anchors, a singular damped system,
+ *     non-finite values) are reported as per-hypothesis statuses, not as errors.
+ *   - Readings where the paper is silent (documented at each field):
+ *       pose state T_cw = [R | t] world->camera, row-major 3x4, FP64; the LM update is
+ *       T <- exp(dxi) T with dxi = (nu, omega), translation first;
+ *       pixel i covers [i, i+1); level l intrinsics are K_0 scaled by 2^-l;
+ *       Huber acts on the squared norm: rho(s) = s for s <= delta^2, else
+ *       2 delta sqrt(s) - delta^2, and the anchor weight sits inside: rho(w ||r||^2);
+ *       a step is accepted iff it lowers the objective and keeps at least
+ *       min_valid_frac of the valid anchors visible; lambda x10 / /10 clamped to
+ *       [1e-12, 1e12], reset to lambda0 at every level; rejected steps still count
+ *       as iterations (a fixed number of iterations per level, no early exit).
+ */
+#ifndef PILOT_ALIGN_H
+#define PILOT_ALIGN_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define PILOT_MAX_LEVELS 4
+
+typedef enum {
+    PILOT_OK = 0,
+    PILOT_EINVAL = -1,    /* malformed config/frame/result, or a size beyond the handle's */
+    PILOT_ENOMEM = -2,    /* device or pinned host allocation failed */
+    PILOT_ECUDA = -3,     /* a CUDA runtime call or kernel launch failed */
+    PILOT_ETIMEOUT = -4,  /* a bounded device-side wait gave up */
+    PILOT_EBUSY = -5      /* serving: not admitted yet (no slot or memory free) */
+} pilot_status;
+
+/* Storage type of the feature pyramids (query maps and reference descriptors).
+ * Arithmetic is always FP32; values are (stored value) x (per-channel scale). */
+typedef enum {
+    PILOT_F32 = 0,
+    PILOT_BF16 = 1,
+    PILOT_F16 = 2,
+    PILOT_FP8E4M3 = 3
+} pilot_dtype;
+
+typedef enum {
+    PILOT_HYP_OK = 0,
+    PILOT_HYP_FEW_VALID = 1,  /* final n_valid below min_valid_frac x valid anchors */
+    PILOT_HYP_NOT_PD = 2,     /* the last attempted damped solve was not positive definite */
+    PILOT_HYP_NONFINITE = 3,  /* final objective or pose not finite */
+    PILOT_HYP_PRUNED = 4      /* dropped by keep_top_k after a coarser level */
+} pilot_hyp_status;
+
+/* Solver options.  A zero-initialised struct means the defaults noted here. */
+typedef struct {
+    int iters_per_level[PILOT_MAX_LEVELS]; /* LM iterations at level l (0 = finest) */
+    double lambda0;          /* initial damping; 0 -> 1e-3 */
+    int damping_mode;        /* 0: H + lambda I (Eq. 8); 1: H + lambda diag(H) */
+    double huber_photo;      /* delta of the photo Huber (Eq. 2); 0 -> 0.1 */
+    double huber_grav;       /* delta of the gravity Huber (Eq. 7); 0 -> 0.1 */
+    double huber_range;      /* delta of the range Huber, metres (Eq. 7); 0 -> 1.0 */
+    int keep_top_k[PILOT_MAX_LEVELS]; /* after level l > 0 keep the K lowest objectives
+                                         for the finer levels; 0 = keep all */
+    double min_valid_frac;   /* acceptance / status threshold, fraction of valid anchors;
+                                negative -> 0.05 */
+    int max_points;          /* workspace sizing: largest N, M, C the handle accepts */
+    int max_hyps;
+    int max_channels;
+    int profile;             /* 1: time every build-pass launch with CUDA events */
+} pilot_align_config;
+
+/* One query frame.  All pointers are owned by the caller and are either all device
+ * pointers (is_device = 1) or all host pointers (is_device = 0; the solver copies them to
+ * its workspace).  Every coordinate is in one local metric frame (e.g. centred on the
+ * crop); x east, y north, z up; gravity points along -z in the world. */
+typedef struct {
+    int is_device;
+    int N;                          /* anchors (geo-anchors P_j, Supp. geo-anchor lift) */
+    const float* points;            /* 3 x N SoA: x[N], y[N], z[N] */
+    const float* point_weight;      /* N or NULL (= 1): w_l(j) of Eq. 2 */
+    const uint8_t* point_valid;     /* N or NULL (= all valid); 0 = anchor unused */
+    int C;                          /* channels: 4, 8, 16, 32 or 64 */
+    int L;                          /* pyramid levels, 1..PILOT_MAX_LEVELS */
+    pilot_dtype feat_dtype;
+    const void* ref_feat[PILOT_MAX_LEVELS];   /* f_l^r(p_j): N x C per level */
+    const float* ref_scale[PILOT_MAX_LEVELS]; /* C per level or NULL (= 1) */
+    const void* qry_feat[PILOT_MAX_LEVELS];   /* f_l^q: H_l x W_l x C (NHWC) per level */
+    const float* qry_scale[PILOT_MAX_LEVELS]; /* C per level or NULL (= 1) */
+    int H[PILOT_MAX_LEVELS], W[PILOT_MAX_LEVELS]; /* each >= 2 */
+    double fx, fy, cx, cy;          /* level-0 pinhole intrinsics in pixels */
+    int M;                          /* hypotheses */
+    const double* T_cw;             /* M x 12 initial hypotheses [R | t], world->camera */
+    int use_gravity;                /* Eq. 3 */
+    double gravity_cam[3];          /* gamma^imu: measured gravity direction, camera frame */
+    double gravity_world[3];        /* gamma^W, world frame (normally (0, 0, -1)) */
+    double w_grav;                  /* lambda_imu */
+    int use_range;                  /* Eq. 4-6 */
+    double range_m;                 /* d^range along the ray through pixel (W_0/2, H_0/2) */
+    double w_range;                 /* lambda_range */
+    const float* dsm;               /* dsm_H x dsm_W heights; cell (r, c) is centred at */
+    int dsm_H, dsm_W;               /* (dsm_x0 + (c + 1/2) gsd, dsm_y0 + (r + 1/2) gsd)  */
+    double dsm_x0, dsm_y0, dsm_gsd;
+} pilot_frame;
+
+/* Caller-owned HOST output buffers.  Any pointer may be NULL to skip that output. */
+typedef struct {
+    double* T_cw;          /* M x 12 final poses */
+    double* cost;          /* M final objective (pruned: at the level they were pruned) */
+    int* n_valid;          /* M visible anchors at the final evaluation */
+    int* hyp_status;       /* M pilot_hyp_status */
+    int* best;             /* 1: index of the lowest objective among OK hypotheses, or -1 */
+    long long* hyp_iters;  /* 1: sum over levels of (hypotheses run) x (iterations) */
+} pilot_result;
+
+typedef struct pilot_align_handle pilot_align_handle;
+
+/* Create a solver handle and its device workspace on the current CUDA device.
+ * cfg: options (copied).  out: receives the handle.  Returns PILOT_EINVAL for bad
+ * options, PILOT_ENOMEM / PILOT_ECUDA if the workspace cannot be allocated. */
+pilot_status pilot_align_create(const pilot_align_config* cfg, pilot_align_handle** out);
+
+/* Check a frame against a config without touching the GPU (host logic only).
+ * Returns PILOT_OK or PILOT_EINVAL with the reason in pilot_align_last_error(). */
+pilot_status pilot_align_validate(const pilot_align_config* cfg, const pilot_frame* frame);
+
+/* Run the whole multi-hypothesis coarse-to-fine LM solve of one frame (Sec. IV-E):
+ * levels L-1 .. 0, iters_per_level[l] iterations each, optional top-K between levels,
+ * selection of the lowest objective (Sec. IV-E, last paragraph).  Synchronous on
+ * `stream` when it returns.  M = 0 returns PILOT_OK with best = -1. */
+pilot_status pilot_align_solve(pilot_align_handle* h, const pilot_frame* frame,
+                               pilot_result* result, void* stream);
+
+/* Evaluate the normal equations of the total objective (Eq. 7, Eq. 8) at the given
+ * poses on one level, without any LM step: out29 (HOST, M x 29 doubles) receives per
+ * pose the 21 upper-triangle entries of J^T W J (row-major), the 6 entries of J^T W r,
+ * the objective, and the number of visible anchors.  T_cw (HOST, M x 12) overrides
+ * frame->T_cw.  This is the parity hook of the build pass. */
+pilot_status pilot_align_debug_normal_eq(pilot_align_handle* h, const pilot_frame* frame,
+                                         int level, const double* T_cw, double* out29,
+                                         void* stream);
+
+/* Timing of the last solve when cfg.profile = 1: total device time of the build-pass
+ * launches (milliseconds, CUDA events on the solve's stream), their number, and the
+ * number of kernels of this library launched by that solve. */
+pilot_status pilot_align_profile(const pilot_align_handle* h, double* build_ms,
+                                 int* build_launches, int* total_launches);
+
+/* Release the handle and its device workspace.  NULL is ignored. */
+void pilot_align_destroy(pilot_align_handle* h);
+
+/* Message describing the last failure on the calling thread ("" if none). */
+const char* pilot_align_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PILOT_ALIGN_H */

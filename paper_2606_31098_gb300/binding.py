@@ -1,0 +1,293 @@
+"""ctypes binding of include/pilot_align.h (argument marshalling only).
+
+Every step of the solve runs in the CUDA library libpilot_align.so; this module only
+fills the C structures.  PyTorch serves as the owner of device memory and streams.
+There is no fallback: if the library is missing, loading raises.
+"""
+from __future__ import annotations
+
+import ctypes as ct
+import os
+from dataclasses import dataclass
+
+import numpy as np
+
+MAX_LEVELS = 4
+PILOT_OK, PILOT_EINVAL, PILOT_ENOMEM, PILOT_ECUDA, PILOT_ETIMEOUT, PILOT_EBUSY = 0, -1, -2, -3, -4, -5
+F32, BF16, F16, FP8E4M3 = 0, 1, 2, 3
+HYP_OK, HYP_FEW_VALID, HYP_NOT_PD, HYP_NONFINITE, HYP_PRUNED = range(5)
+DTYPE_NAMES = {F32: "f32", BF16: "bf16", F16: "f16", FP8E4M3: "fp8e4m3"}
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_lib", "libpilot_align.so")
+
+_vp = ct.c_void_p
+
+
+class pilot_align_config(ct.Structure):
+    _fields_ = [
+        ("iters_per_level", ct.c_int * MAX_LEVELS), ("lambda0", ct.c_double),
+        ("damping_mode", ct.c_int), ("huber_photo", ct.c_double), ("huber_grav", ct.c_double),
+        ("huber_range", ct.c_double), ("keep_top_k", ct.c_int * MAX_LEVELS),
+        ("min_valid_frac", ct.c_double), ("max_points", ct.c_int), ("max_hyps", ct.c_int),
+        ("max_channels", ct.c_int), ("profile", ct.c_int),
+    ]
+
+
+class pilot_frame(ct.Structure):
+    _fields_ = [
+        ("is_device", ct.c_int), ("N", ct.c_int), ("points", _vp), ("point_weight", _vp),
+        ("point_valid", _vp), ("C", ct.c_int), ("L", ct.c_int), ("feat_dtype", ct.c_int),
+        ("ref_feat", _vp * MAX_LEVELS), ("ref_scale", _vp * MAX_LEVELS),
+        ("qry_feat", _vp * MAX_LEVELS), ("qry_scale", _vp * MAX_LEVELS),
+        ("H", ct.c_int * MAX_LEVELS), ("W", ct.c_int * MAX_LEVELS),
+        ("fx", ct.c_double), ("fy", ct.c_double), ("cx", ct.c_double), ("cy", ct.c_double),
+        ("M", ct.c_int), ("T_cw", _vp),
+        ("use_gravity", ct.c_int), ("gravity_cam", ct.c_double * 3), ("gravity_world", ct.c_double * 3),
+        ("w_grav", ct.c_double), ("use_range", ct.c_int), ("range_m", ct.c_double),
+        ("w_range", ct.c_double), ("dsm", _vp), ("dsm_H", ct.c_int), ("dsm_W", ct.c_int),
+        ("dsm_x0", ct.c_double), ("dsm_y0", ct.c_double), ("dsm_gsd", ct.c_double),
+    ]
+
+
+class pilot_result(ct.Structure):
+    _fields_ = [("T_cw", _vp), ("cost", _vp), ("n_valid", _vp), ("hyp_status", _vp),
+                ("best", _vp), ("hyp_iters", _vp)]
+
+
+_lib = None
+
+# name -> (restype, argtypes), in the order include/pilot_align.h declares them
+SIGNATURES = {
+    "pilot_align_create": (ct.c_int, [ct.POINTER(pilot_align_config), ct.POINTER(_vp)]),
+    "pilot_align_validate": (ct.c_int, [ct.POINTER(pilot_align_config), ct.POINTER(pilot_frame)]),
+    "pilot_align_solve": (ct.c_int, [_vp, ct.POINTER(pilot_frame), ct.POINTER(pilot_result), _vp]),
+    "pilot_align_debug_normal_eq": (ct.c_int, [_vp, ct.POINTER(pilot_frame), ct.c_int, _vp, _vp, _vp]),
+    "pilot_align_profile": (ct.c_int, [_vp, ct.POINTER(ct.c_double), ct.POINTER(ct.c_int), ct.POINTER(ct.c_int)]),
+    "pilot_align_destroy": (None, [_vp]),
+    "pilot_align_last_error": (ct.c_char_p, []),
+}
+
+
+def load(path: str = LIB_PATH):
+    """Load the CUDA library (build it first with build_ext.build()).  Raises if absent."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(path):
+            raise RuntimeError(f"CUDA library not built: {path} is missing (run build_ext.build())")
+        L = ct.CDLL(path)
+        for name, (res, args) in SIGNATURES.items():
+            fn = getattr(L, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = L
+    return _lib
+
+
+class PilotError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"status {status}: {msg}")
+        self.status = status
+
+
+def check(status: int):
+    if status != PILOT_OK:
+        raise PilotError(status, load().pilot_align_last_error().decode())
+    return status
+
+
+def pilot_align_last_error() -> str:
+    return load().pilot_align_last_error().decode()
+
+
+@dataclass
+class Options:
+    iters: tuple = (10, 10, 10, 0)
+    lambda0: float = 1e-3
+    damping_mode: int = 0
+    huber_photo: float = 0.1
+    huber_grav: float = 0.1
+    huber_range: float = 1.0
+    keep_top_k: tuple = (0, 0, 0, 0)
+    min_valid_frac: float = 0.05
+    max_points: int = 1 << 18
+    max_hyps: int = 256
+    max_channels: int = 32
+    profile: int = 0
+
+    def to_c(self) -> pilot_align_config:
+        c = pilot_align_config()
+        c.iters_per_level[:] = list(self.iters) + [0] * (MAX_LEVELS - len(self.iters))
+        c.lambda0 = self.lambda0
+        c.damping_mode = self.damping_mode
+        c.huber_photo, c.huber_grav, c.huber_range = self.huber_photo, self.huber_grav, self.huber_range
+        c.keep_top_k[:] = list(self.keep_top_k) + [0] * (MAX_LEVELS - len(self.keep_top_k))
+        c.min_valid_frac = self.min_valid_frac
+        c.max_points, c.max_hyps, c.max_channels = self.max_points, self.max_hyps, self.max_channels
+        c.profile = self.profile
+        return c
+
+
+def _ptr(x) -> int | None:
+    """Address of a torch tensor or numpy array (None for None)."""
+    if x is None:
+        return None
+    if hasattr(x, "data_ptr"):
+        return x.data_ptr()
+    return x.ctypes.data
+
+
+class FrameArgs:
+    """A pilot_frame over arrays that stay alive as long as this object.
+
+    `arrays` maps field names to numpy arrays (host frame, is_device = 0) or torch CUDA
+    tensors (device frame, is_device = 1): points (3, N) f32, point_weight (N,) f32,
+    point_valid (N,) u8, ref_feat / qry_feat lists, optional ref_scale / qry_scale lists,
+    T_cw (M, 12) f64, dsm (H_D, W_D) f32.  Scalars come from `frame` (a scenes.Frame).
+    """
+
+    def __init__(self, frame, arrays: dict, is_device: bool, dtype: int = F32):
+        self.arrays = arrays
+        f = pilot_frame()
+        f.is_device = int(is_device)
+        pts = arrays["points"]
+        f.N = int(pts.shape[1])
+        f.points = _ptr(pts)
+        f.point_weight = _ptr(arrays.get("point_weight"))
+        f.point_valid = _ptr(arrays.get("point_valid"))
+        qry = arrays["qry_feat"]
+        ref = arrays["ref_feat"]
+        f.L = len(qry)
+        f.C = int(qry[0].shape[2])
+        f.feat_dtype = dtype
+        qs = arrays.get("qry_scale") or [None] * f.L
+        rs = arrays.get("ref_scale") or [None] * f.L
+        for l in range(f.L):
+            f.qry_feat[l] = _ptr(qry[l])
+            f.ref_feat[l] = _ptr(ref[l])
+            f.qry_scale[l] = _ptr(qs[l])
+            f.ref_scale[l] = _ptr(rs[l])
+            f.H[l], f.W[l] = int(qry[l].shape[0]), int(qry[l].shape[1])
+        f.fx, f.fy, f.cx, f.cy = frame.fx, frame.fy, frame.cx, frame.cy
+        T = arrays["T_cw"]
+        f.M = int(T.shape[0])
+        f.T_cw = _ptr(T)
+        f.use_gravity = int(frame.use_gravity)
+        f.gravity_cam[:] = [float(v) for v in frame.gravity_cam]
+        f.gravity_world[:] = [float(v) for v in frame.gravity_world]
+        f.w_grav = frame.w_grav
+        f.use_range = int(frame.use_range)
+        f.range_m = frame.range_m
+        f.w_range = frame.w_range
+        dsm = arrays["dsm"]
+        f.dsm = _ptr(dsm)
+        f.dsm_H, f.dsm_W = int(dsm.shape[0]), int(dsm.shape[1])
+        f.dsm_x0, f.dsm_y0, f.dsm_gsd = frame.dsm_x0, frame.dsm_y0, frame.dsm_gsd
+        self.c = f
+
+    @property
+    def M(self) -> int:
+        return self.c.M
+
+
+def host_arrays(frame, T_hyps=None, pinned: bool = False) -> dict:
+    """Host (numpy, optionally page-locked torch CPU) arrays of an FP32 frame."""
+    T = np.ascontiguousarray(frame.T_hyps if T_hyps is None else T_hyps, np.float64).reshape(-1, 12)
+    arrs = dict(points=np.ascontiguousarray(frame.points, np.float32),
+                point_weight=np.ascontiguousarray(frame.point_weight, np.float32),
+                point_valid=np.ascontiguousarray(frame.point_valid, np.uint8),
+                ref_feat=[np.ascontiguousarray(r, np.float32) for r in frame.ref_feat],
+                qry_feat=[np.ascontiguousarray(q, np.float32) for q in frame.qry_feat],
+                T_cw=T, dsm=np.ascontiguousarray(frame.dsm, np.float32))
+    if pinned:
+        import torch
+        pin = lambda a: torch.from_numpy(a).pin_memory()
+        arrs = {k: ([pin(x) for x in v] if isinstance(v, list) else pin(v)) for k, v in arrs.items()}
+    return arrs
+
+
+def device_arrays(frame, T_hyps=None, device="cuda") -> dict:
+    """Device (torch CUDA) copies of an FP32 frame's arrays."""
+    import torch
+    h = host_arrays(frame, T_hyps)
+    to = lambda a: torch.from_numpy(a).to(device)
+    return {k: ([to(x) for x in v] if isinstance(v, list) else to(v)) for k, v in h.items()}
+
+
+@dataclass
+class Result:
+    T_cw: np.ndarray
+    cost: np.ndarray
+    n_valid: np.ndarray
+    status: np.ndarray
+    best: int
+    hyp_iters: int
+
+
+class Solver:
+    """Owns one pilot_align_handle."""
+
+    def __init__(self, opts: Options | None = None):
+        self.opts = opts or Options()
+        lib = load()
+        self._cfg = self.opts.to_c()
+        h = _vp()
+        check(lib.pilot_align_create(ct.byref(self._cfg), ct.byref(h)))
+        self.h = h
+
+    def close(self):
+        if getattr(self, "h", None) is not None and self.h.value:
+            load().pilot_align_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @staticmethod
+    def _stream(stream) -> int | None:
+        if stream is None:
+            try:
+                import torch
+                if torch.cuda.is_available():
+                    return torch.cuda.current_stream().cuda_stream
+            except Exception:
+                pass
+            return None
+        return stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)
+
+    def solve(self, fa: FrameArgs, stream=None) -> Result:
+        M = fa.M
+        T = np.zeros((M, 12))
+        cost = np.zeros(M)
+        nv = np.zeros(M, np.int32)
+        st = np.zeros(M, np.int32)
+        best = np.zeros(1, np.int32)
+        hi = np.zeros(1, np.int64)
+        r = pilot_result(T.ctypes.data, cost.ctypes.data, nv.ctypes.data, st.ctypes.data,
+                         best.ctypes.data, hi.ctypes.data)
+        check(load().pilot_align_solve(self.h, ct.byref(fa.c), ct.byref(r), self._stream(stream)))
+        return Result(T, cost, nv, st, int(best[0]), int(hi[0]))
+
+    def normal_eq(self, fa: FrameArgs, level: int, T_cw, stream=None) -> np.ndarray:
+        T = np.ascontiguousarray(T_cw, np.float64).reshape(-1, 12)
+        assert T.shape[0] == fa.M
+        out = np.zeros((fa.M, 29))
+        check(load().pilot_align_debug_normal_eq(self.h, ct.byref(fa.c), int(level), T.ctypes.data,
+                                                 out.ctypes.data, self._stream(stream)))
+        return out
+
+    def profile(self):
+        ms = ct.c_double()
+        nb = ct.c_int()
+        nt = ct.c_int()
+        check(load().pilot_align_profile(self.h, ct.byref(ms), ct.byref(nb), ct.byref(nt)))
+        return ms.value, nb.value, nt.value
+
+
+def validate(opts: Options, fa: FrameArgs) -> tuple[int, str]:
+    cfg = opts.to_c()
+    st = load().pilot_align_validate(ct.byref(cfg), ct.byref(fa.c))
+    return st, pilot_align_last_error()

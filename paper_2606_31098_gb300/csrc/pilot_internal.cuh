@@ -1,0 +1,124 @@
+// Internal declarations shared by the CUDA library's translation units (not installed).
+//
+// Device data layout (one frame):
+//   anchors      SoA FP32  x[N] y[N] z[N]            (coalesced per-anchor reads)
+//   ref features N x C per level, storage dtype       (one contiguous row per anchor)
+//   query maps   H x W x C per level (NHWC)           (one tap = C contiguous values)
+//   hypotheses   HypState[M], FP64 LM state per hypothesis
+//   candidates   pose32[M][12], FP32 [R | t] the build pass evaluates
+//   partials     partial[slot][tile][32] FP32: 21 H + 6 g + cost + n_valid (+3 pad)
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "pilot_align.h"
+
+namespace pilot {
+
+constexpr int kAcc = 32;           // padded width of one partial-sum record
+constexpr int kNumSums = 29;       // 21 H + 6 g + cost + n_valid
+constexpr int kBuildThreads = 256;
+constexpr float kZNear = 0.1f;
+
+// FP64 Levenberg-Marquardt state of one hypothesis.
+struct HypState {
+    double T[12];      // accepted pose [R | t], world -> camera
+    double Tc[12];     // candidate pose awaiting evaluation
+    double H[21];      // J^T W J at T (upper triangle, row-major)
+    double g[6];       // J^T W r at T
+    double cost;       // objective at T
+    double lambda;     // LM damping
+    int n_valid;       // visible anchors at T
+    int has_cand;      // 1: Tc must be evaluated by the next build pass
+    int last_fail;     // 1: the last damped solve was not positive definite
+    int active;        // 0: pruned
+    int status;        // pilot_hyp_status (final)
+    int pad;
+};
+
+// Inputs of one build pass (one level of one frame).
+struct BuildParams {
+    const float* px;
+    const float* py;
+    const float* pz;
+    const float* weight;       // N or nullptr
+    const uint8_t* valid;      // N or nullptr
+    const void* qry;           // H x W x C
+    const void* ref;           // N x C
+    const float* qscale;       // C or nullptr
+    const float* rscale;       // C or nullptr
+    int N, C, H, W;
+    float fx, fy, cx, cy;      // level intrinsics
+    float huber;               // photo Huber delta
+    const float* pose32;       // [M][12]
+    const int* active_idx;     // [n_active] hypothesis index of each slot
+    const HypState* state;     // has_cand flags
+    float* partial;            // [n_active][n_tiles][kAcc]
+    int n_active;
+    int n_tiles;
+    int tile;                  // anchors per tile
+};
+
+// Prior terms (Eq. 3-6), FP64.
+struct PriorParams {
+    int use_gravity;
+    double g_cam[3], g_world[3], w_grav, huber_grav;
+    int use_range;
+    double q[3];               // d^range * v (Eq. 4 ray scaled by the range), camera frame
+    double w_range, huber_range;
+    const float* dsm;
+    int dsm_H, dsm_W;
+    double dsm_x0, dsm_y0, dsm_gsd;
+};
+
+enum EpilogueMode { kEpiInit = 0, kEpiStep = 1, kEpiEval = 2 };
+
+struct EpilogueParams {
+    HypState* state;
+    float* pose32;
+    const float* partial;
+    const int* active_idx;
+    int n_active, n_tiles;
+    int mode;                  // EpilogueMode
+    int solve_next;            // 1: compute the next candidate after this evaluation
+    double lambda0;
+    int damping_mode;
+    PriorParams prior;
+    double* eval_out;          // kEpiEval: [slot][29]
+};
+
+// Result block copied to the host in one transfer.
+struct ResultLayout {
+    size_t off_T, off_cost, off_nvalid, off_status, off_best, bytes;
+    static ResultLayout make(int M) {
+        ResultLayout r;
+        r.off_T = 0;
+        r.off_cost = r.off_T + sizeof(double) * 12 * (size_t)M;
+        r.off_nvalid = r.off_cost + sizeof(double) * (size_t)M;
+        r.off_status = r.off_nvalid + sizeof(int) * (size_t)M;
+        r.off_best = r.off_status + sizeof(int) * (size_t)M;
+        r.bytes = r.off_best + 16;
+        return r;
+    }
+};
+
+// ---- launchers (each returns the cudaError_t of its launch) ----
+cudaError_t launch_epilogue(const EpilogueParams& p, const double* min_valid, cudaStream_t s);
+cudaError_t launch_level_init(HypState* st, float* pose32, const int* active_idx, int n_active,
+                              double lambda0, cudaStream_t s);
+cudaError_t launch_hyp_init(HypState* st, const double* T_cw, int* active_idx, int M,
+                            cudaStream_t s);
+cudaError_t launch_set_poses(HypState* st, float* pose32, const double* T_cw, int* active_idx,
+                             int M, cudaStream_t s);
+cudaError_t launch_prune(HypState* st, const int* active_in, int* active_out, int n_active,
+                         int keep, const double* min_valid, cudaStream_t s);
+cudaError_t launch_count_valid(const uint8_t* valid, int N, double frac, double* min_valid,
+                               cudaStream_t s);
+cudaError_t launch_finalize(HypState* st, int M, const double* min_valid, unsigned char* result,
+                            ResultLayout lay, cudaStream_t s);
+
+template <pilot_dtype DT>
+cudaError_t launch_build_dtype(const BuildParams& p, cudaStream_t s);
+
+}  // namespace pilot

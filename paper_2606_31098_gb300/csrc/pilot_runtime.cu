@@ -1,0 +1,560 @@
+// Host runtime of the C-ABI declared in include/pilot_align.h: validation, workspace,
+// input staging, and the per-level launch sequence of the LM solve.
+//
+// One solve of one frame (Sec. IV-E, Eq. 7-9), all on the caller's stream:
+//   count_valid  (min_valid = frac x valid anchors)    hyp_init (FP64 state from T_cw)
+//   for l = L-1 .. 0:
+//     level_init (lambda = lambda0, candidate = T)
+//     build(l) -> epilogue(init: store E(T), solve first candidate)
+//     repeat iters[l] times: build(l) at the candidates -> epilogue(step: accept or
+//       reject, solve the next candidate)
+//     optional prune (keep_top_k[l])
+//   finalize (statuses, argmin) -> one device-to-host copy of the result block
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <string>
+#include <vector>
+
+#include "pilot_internal.cuh"
+
+using namespace pilot;
+
+namespace {
+
+thread_local std::string g_last_error;
+
+pilot_status fail(pilot_status st, const char* fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_last_error = buf;
+    return st;
+}
+
+pilot_status cuda_fail(cudaError_t e, const char* what) {
+    return fail(e == cudaErrorMemoryAllocation ? PILOT_ENOMEM : PILOT_ECUDA, "%s: %s (%s)", what,
+                cudaGetErrorString(e), cudaGetErrorName(e));
+}
+
+#define PILOT_CUDA(expr, what)                              \
+    do {                                                    \
+        cudaError_t e_ = (expr);                            \
+        if (e_ != cudaSuccess) return cuda_fail(e_, what);  \
+    } while (0)
+
+constexpr int kTile = 1024;          // anchors per build-pass tile
+
+bool channels_supported(int C) { return C == 4 || C == 8 || C == 16 || C == 32 || C == 64; }
+
+size_t dtype_size(pilot_dtype dt) {
+    switch (dt) {
+        case PILOT_F32: return 4;
+        case PILOT_BF16:
+        case PILOT_F16: return 2;
+        case PILOT_FP8E4M3: return 1;
+    }
+    return 0;
+}
+
+pilot_align_config with_defaults(const pilot_align_config& in) {
+    pilot_align_config c = in;
+    if (c.lambda0 == 0.0) c.lambda0 = 1e-3;
+    if (c.huber_photo == 0.0) c.huber_photo = 0.1;
+    if (c.huber_grav == 0.0) c.huber_grav = 0.1;
+    if (c.huber_range == 0.0) c.huber_range = 1.0;
+    if (c.max_points == 0) c.max_points = 1 << 18;
+    if (c.max_hyps == 0) c.max_hyps = 256;
+    if (c.max_channels == 0) c.max_channels = 32;
+    return c;
+}
+
+pilot_status validate_config(const pilot_align_config& c) {
+    for (int l = 0; l < PILOT_MAX_LEVELS; ++l) {
+        if (c.iters_per_level[l] < 0 || c.iters_per_level[l] > 100000)
+            return fail(PILOT_EINVAL, "iters_per_level[%d] = %d out of [0, 100000]", l, c.iters_per_level[l]);
+        if (c.keep_top_k[l] < 0) return fail(PILOT_EINVAL, "keep_top_k[%d] < 0", l);
+    }
+    if (!(c.lambda0 > 0.0) || !isfinite(c.lambda0)) return fail(PILOT_EINVAL, "lambda0 must be > 0");
+    if (c.damping_mode != 0 && c.damping_mode != 1) return fail(PILOT_EINVAL, "damping_mode must be 0 or 1");
+    if (!(c.huber_photo > 0.0) || !(c.huber_grav > 0.0) || !(c.huber_range > 0.0))
+        return fail(PILOT_EINVAL, "Huber thresholds must be > 0");
+    if (!(c.min_valid_frac >= 0.0 && c.min_valid_frac <= 1.0))
+        return fail(PILOT_EINVAL, "min_valid_frac must be in [0, 1]");
+    if (c.max_points < 0 || c.max_hyps < 1) return fail(PILOT_EINVAL, "max_points >= 0 and max_hyps >= 1 required");
+    if (!channels_supported(c.max_channels))
+        return fail(PILOT_EINVAL, "max_channels must be one of 4, 8, 16, 32, 64");
+    return PILOT_OK;
+}
+
+bool aligned(const void* p, size_t a) { return ((uintptr_t)p % a) == 0; }
+
+pilot_status validate_frame(const pilot_align_config& c, const pilot_frame* f) {
+    if (!f) return fail(PILOT_EINVAL, "frame is NULL");
+    if (f->N < 0 || f->N > c.max_points)
+        return fail(PILOT_EINVAL, "N = %d outside [0, max_points = %d]", f->N, c.max_points);
+    if (f->M < 0 || f->M > c.max_hyps) return fail(PILOT_EINVAL, "M = %d outside [0, max_hyps = %d]", f->M, c.max_hyps);
+    if (!channels_supported(f->C)) return fail(PILOT_EINVAL, "C = %d unsupported (4, 8, 16, 32, 64)", f->C);
+    if (f->C > c.max_channels) return fail(PILOT_EINVAL, "C = %d above max_channels = %d", f->C, c.max_channels);
+    if (f->L < 1 || f->L > PILOT_MAX_LEVELS) return fail(PILOT_EINVAL, "L = %d outside [1, %d]", f->L, PILOT_MAX_LEVELS);
+    const size_t es = dtype_size(f->feat_dtype);
+    if (es == 0) return fail(PILOT_EINVAL, "feat_dtype %d unknown", (int)f->feat_dtype);
+    if (f->N > 0 && !f->points) return fail(PILOT_EINVAL, "points is NULL");
+    if (f->M > 0 && !f->T_cw) return fail(PILOT_EINVAL, "T_cw is NULL");
+    if (!(f->fx > 0.0 && f->fy > 0.0 && isfinite(f->fx) && isfinite(f->fy) && isfinite(f->cx) && isfinite(f->cy)))
+        return fail(PILOT_EINVAL, "intrinsics must be finite with fx, fy > 0");
+    for (int l = 0; l < f->L; ++l) {
+        if (f->H[l] < 2 || f->W[l] < 2) return fail(PILOT_EINVAL, "level %d map %dx%d: both sides must be >= 2", l, f->H[l], f->W[l]);
+        if ((double)f->H[l] * f->W[l] * f->C >= 2147483647.0)
+            return fail(PILOT_EINVAL, "level %d map has 2^31 or more elements", l);
+        if (!f->qry_feat[l]) return fail(PILOT_EINVAL, "qry_feat[%d] is NULL", l);
+        if (f->N > 0 && !f->ref_feat[l]) return fail(PILOT_EINVAL, "ref_feat[%d] is NULL", l);
+        if (!aligned(f->qry_feat[l], 4 * es) || (f->ref_feat[l] && !aligned(f->ref_feat[l], 4 * es)))
+            return fail(PILOT_EINVAL, "level %d feature pointers must be aligned to 4 elements (%zu bytes)", l, 4 * es);
+        if ((f->qry_scale[l] && !aligned(f->qry_scale[l], 16)) || (f->ref_scale[l] && !aligned(f->ref_scale[l], 16)))
+            return fail(PILOT_EINVAL, "level %d scale pointers must be 16-byte aligned", l);
+    }
+    if (f->use_gravity) {
+        for (int i = 0; i < 3; ++i)
+            if (!isfinite(f->gravity_cam[i]) || !isfinite(f->gravity_world[i]))
+                return fail(PILOT_EINVAL, "gravity vectors must be finite");
+        if (!(f->w_grav >= 0.0)) return fail(PILOT_EINVAL, "w_grav must be >= 0");
+    }
+    if (f->use_range) {
+        if (!f->dsm || f->dsm_H < 2 || f->dsm_W < 2) return fail(PILOT_EINVAL, "range prior needs a DSM of at least 2x2");
+        if (!(f->dsm_gsd > 0.0) || !isfinite(f->dsm_x0) || !isfinite(f->dsm_y0))
+            return fail(PILOT_EINVAL, "DSM geometry must be finite with gsd > 0");
+        if (!isfinite(f->range_m) || !(f->w_range >= 0.0)) return fail(PILOT_EINVAL, "range_m finite and w_range >= 0 required");
+    }
+    return PILOT_OK;
+}
+
+struct DevBuf {
+    void* ptr = nullptr;
+    size_t bytes = 0;
+};
+
+enum StageSlot { kStPoints, kStWeight, kStValid, kStT, kStDsm, kStRef0, kStQry0 = kStRef0 + PILOT_MAX_LEVELS,
+                 kStRs0 = kStQry0 + PILOT_MAX_LEVELS, kStQs0 = kStRs0 + PILOT_MAX_LEVELS,
+                 kStCount = kStQs0 + PILOT_MAX_LEVELS };
+
+}  // namespace
+
+struct pilot_align_handle {
+    pilot_align_config cfg{};
+    int device = 0;
+    int max_tiles = 0;
+    HypState* state = nullptr;
+    float* pose32 = nullptr;
+    float* partial = nullptr;
+    int* active[2] = {nullptr, nullptr};
+    double* Tin = nullptr;
+    double* eval_out = nullptr;
+    double* min_valid = nullptr;
+    float* ones = nullptr;
+    unsigned char* res_dev = nullptr;
+    unsigned char* res_host = nullptr;
+    DevBuf stage[kStCount];
+    std::vector<cudaEvent_t> events;
+    int build_launches = 0;
+    int total_launches = 0;
+    double build_ms = 0.0;
+};
+
+namespace {
+
+// Device view of a frame: caller pointers (is_device) or staged copies.
+struct DevFrame {
+    const float* points = nullptr;
+    const float* weight = nullptr;
+    const uint8_t* valid = nullptr;
+    const double* T = nullptr;
+    const float* dsm = nullptr;
+    const void* ref[PILOT_MAX_LEVELS] = {};
+    const void* qry[PILOT_MAX_LEVELS] = {};
+    const float* rs[PILOT_MAX_LEVELS] = {};
+    const float* qs[PILOT_MAX_LEVELS] = {};
+};
+
+pilot_status stage_copy(pilot_align_handle* h, int slot, const void* src, size_t bytes,
+                        cudaStream_t s, const void** out) {
+    if (!src || bytes == 0) {
+        *out = nullptr;
+        return PILOT_OK;
+    }
+    DevBuf& b = h->stage[slot];
+    if (b.bytes < bytes) {
+        if (b.ptr) cudaFree(b.ptr);
+        b.ptr = nullptr;
+        b.bytes = 0;
+        PILOT_CUDA(cudaMalloc(&b.ptr, bytes), "staging allocation");
+        b.bytes = bytes;
+    }
+    PILOT_CUDA(cudaMemcpyAsync(b.ptr, src, bytes, cudaMemcpyHostToDevice, s), "host-to-device copy");
+    *out = b.ptr;
+    return PILOT_OK;
+}
+
+pilot_status bind_frame(pilot_align_handle* h, const pilot_frame* f, cudaStream_t s, DevFrame* d,
+                        bool copy_T) {
+    const size_t es = dtype_size(f->feat_dtype);
+    const size_t N = (size_t)f->N, C = (size_t)f->C;
+    if (f->is_device) {
+        d->points = f->points;
+        d->weight = f->point_weight;
+        d->valid = f->point_valid;
+        d->T = f->T_cw;
+        d->dsm = f->use_range ? f->dsm : nullptr;
+        for (int l = 0; l < f->L; ++l) {
+            d->ref[l] = f->ref_feat[l];
+            d->qry[l] = f->qry_feat[l];
+            d->rs[l] = f->ref_scale[l];
+            d->qs[l] = f->qry_scale[l];
+        }
+        return PILOT_OK;
+    }
+    pilot_status st;
+    const void* p;
+#define STAGE(slot, src, bytes, dst, type)                                  \
+    if ((st = stage_copy(h, slot, src, bytes, s, &p)) != PILOT_OK) return st; \
+    dst = static_cast<type>(p);
+    STAGE(kStPoints, f->points, sizeof(float) * 3 * N, d->points, const float*);
+    STAGE(kStWeight, f->point_weight, sizeof(float) * N, d->weight, const float*);
+    STAGE(kStValid, f->point_valid, N, d->valid, const uint8_t*);
+    if (copy_T) {
+        STAGE(kStT, f->T_cw, sizeof(double) * 12 * (size_t)f->M, d->T, const double*);
+    }
+    if (f->use_range) {
+        STAGE(kStDsm, f->dsm, sizeof(float) * (size_t)f->dsm_H * f->dsm_W, d->dsm, const float*);
+    }
+    for (int l = 0; l < f->L; ++l) {
+        STAGE(kStRef0 + l, f->ref_feat[l], es * N * C, d->ref[l], const void*);
+        STAGE(kStQry0 + l, f->qry_feat[l], es * (size_t)f->H[l] * f->W[l] * C, d->qry[l], const void*);
+        STAGE(kStRs0 + l, f->ref_scale[l], sizeof(float) * C, d->rs[l], const float*);
+        STAGE(kStQs0 + l, f->qry_scale[l], sizeof(float) * C, d->qs[l], const float*);
+    }
+#undef STAGE
+    return PILOT_OK;
+}
+
+BuildParams build_params(pilot_align_handle* h, const pilot_frame* f, const DevFrame& d, int level,
+                         int n_active, const int* active) {
+    BuildParams b{};
+    const size_t N = (size_t)f->N;
+    b.px = d.points;
+    b.py = d.points ? d.points + N : nullptr;
+    b.pz = d.points ? d.points + 2 * N : nullptr;
+    b.weight = d.weight;
+    b.valid = d.valid;
+    b.qry = d.qry[level];
+    b.ref = d.ref[level];
+    // scales: both or neither (a missing one reads as ones)
+    if (d.qs[level] || d.rs[level]) {
+        b.qscale = d.qs[level] ? d.qs[level] : h->ones;
+        b.rscale = d.rs[level] ? d.rs[level] : h->ones;
+    }
+    b.N = f->N;
+    b.C = f->C;
+    b.H = f->H[level];
+    b.W = f->W[level];
+    const double s = ldexp(1.0, -level);      // K_l = diag(2^-l, 2^-l, 1) K_0
+    b.fx = (float)(f->fx * s);
+    b.fy = (float)(f->fy * s);
+    b.cx = (float)(f->cx * s);
+    b.cy = (float)(f->cy * s);
+    b.huber = (float)h->cfg.huber_photo;
+    b.pose32 = h->pose32;
+    b.active_idx = active;
+    b.state = h->state;
+    b.partial = h->partial;
+    b.n_active = n_active;
+    b.tile = kTile;
+    b.n_tiles = f->N > 0 ? (f->N + kTile - 1) / kTile : 1;
+    return b;
+}
+
+PriorParams prior_params(const pilot_align_config& c, const pilot_frame* f, const DevFrame& d) {
+    PriorParams pp{};
+    pp.use_gravity = f->use_gravity;
+    for (int i = 0; i < 3; ++i) {
+        pp.g_cam[i] = f->gravity_cam[i];
+        pp.g_world[i] = f->gravity_world[i];
+    }
+    pp.w_grav = f->w_grav;
+    pp.huber_grav = c.huber_grav;
+    pp.use_range = f->use_range;
+    if (f->use_range) {
+        // Eq. 4: v = K^-1 p_c / ||K^-1 p_c||, p_c the level-0 image centre
+        const double k[3] = {(0.5 * f->W[0] - f->cx) / f->fx, (0.5 * f->H[0] - f->cy) / f->fy, 1.0};
+        const double nk = sqrt(k[0] * k[0] + k[1] * k[1] + k[2] * k[2]);
+        for (int i = 0; i < 3; ++i) pp.q[i] = f->range_m * k[i] / nk;
+    }
+    pp.w_range = f->w_range;
+    pp.huber_range = c.huber_range;
+    pp.dsm = d.dsm;
+    pp.dsm_H = f->dsm_H;
+    pp.dsm_W = f->dsm_W;
+    pp.dsm_x0 = f->dsm_x0;
+    pp.dsm_y0 = f->dsm_y0;
+    pp.dsm_gsd = f->dsm_gsd;
+    return pp;
+}
+
+cudaError_t dispatch_build(pilot_dtype dt, const BuildParams& b, cudaStream_t s) {
+    switch (dt) {
+        case PILOT_F32: return launch_build_dtype<PILOT_F32>(b, s);
+        case PILOT_BF16: return launch_build_dtype<PILOT_BF16>(b, s);
+        case PILOT_F16: return launch_build_dtype<PILOT_F16>(b, s);
+        case PILOT_FP8E4M3: return launch_build_dtype<PILOT_FP8E4M3>(b, s);
+    }
+    return cudaErrorInvalidValue;
+}
+
+pilot_status run_build(pilot_align_handle* h, pilot_dtype dt, const BuildParams& b, cudaStream_t s) {
+    const bool prof = h->cfg.profile != 0;
+    size_t k = 2 * (size_t)h->build_launches;
+    if (prof) {
+        while (h->events.size() < k + 2) {
+            cudaEvent_t e;
+            PILOT_CUDA(cudaEventCreate(&e), "event create");
+            h->events.push_back(e);
+        }
+        PILOT_CUDA(cudaEventRecord(h->events[k], s), "event record");
+    }
+    PILOT_CUDA(dispatch_build(dt, b, s), "build-pass launch");
+    if (prof) PILOT_CUDA(cudaEventRecord(h->events[k + 1], s), "event record");
+    ++h->build_launches;
+    ++h->total_launches;
+    return PILOT_OK;
+}
+
+struct DeviceGuard {
+    int prev = -1;
+    explicit DeviceGuard(int dev) {
+        if (cudaGetDevice(&prev) == cudaSuccess && prev != dev) cudaSetDevice(dev);
+        else prev = -1;
+    }
+    ~DeviceGuard() {
+        if (prev >= 0) cudaSetDevice(prev);
+    }
+};
+
+void release(pilot_align_handle* h) {
+    if (!h) return;
+    cudaFree(h->state);
+    cudaFree(h->pose32);
+    cudaFree(h->partial);
+    cudaFree(h->active[0]);
+    cudaFree(h->active[1]);
+    cudaFree(h->Tin);
+    cudaFree(h->eval_out);
+    cudaFree(h->min_valid);
+    cudaFree(h->ones);
+    cudaFree(h->res_dev);
+    if (h->res_host) cudaFreeHost(h->res_host);
+    for (auto& b : h->stage)
+        if (b.ptr) cudaFree(b.ptr);
+    for (auto e : h->events) cudaEventDestroy(e);
+    delete h;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* pilot_align_last_error(void) { return g_last_error.c_str(); }
+
+pilot_status pilot_align_validate(const pilot_align_config* cfg_in, const pilot_frame* frame) {
+    if (!cfg_in) return fail(PILOT_EINVAL, "config is NULL");
+    const pilot_align_config cfg = with_defaults(*cfg_in);
+    pilot_status st = validate_config(cfg);
+    if (st != PILOT_OK) return st;
+    return validate_frame(cfg, frame);
+}
+
+pilot_status pilot_align_create(const pilot_align_config* cfg_in, pilot_align_handle** out) {
+    if (!cfg_in || !out) return fail(PILOT_EINVAL, "config or out is NULL");
+    *out = nullptr;
+    const pilot_align_config cfg = with_defaults(*cfg_in);
+    pilot_status st = validate_config(cfg);
+    if (st != PILOT_OK) return st;
+    pilot_align_handle* h = new pilot_align_handle();
+    h->cfg = cfg;
+    cudaError_t e = cudaGetDevice(&h->device);
+    if (e != cudaSuccess) {
+        delete h;
+        return cuda_fail(e, "cudaGetDevice");
+    }
+    const size_t M = (size_t)cfg.max_hyps;
+    h->max_tiles = cfg.max_points > 0 ? (cfg.max_points + kTile - 1) / kTile : 1;
+    const ResultLayout lay = ResultLayout::make(cfg.max_hyps);
+    std::vector<float> ones(cfg.max_channels, 1.0f);
+#define ALLOC(ptr, bytes)                                      \
+    if ((e = cudaMalloc((void**)&(ptr), (bytes))) != cudaSuccess) { \
+        release(h);                                            \
+        return cuda_fail(e, "workspace allocation");           \
+    }
+    ALLOC(h->state, sizeof(HypState) * M);
+    ALLOC(h->pose32, sizeof(float) * 12 * M);
+    ALLOC(h->partial, sizeof(float) * kAcc * M * (size_t)h->max_tiles);
+    ALLOC(h->active[0], sizeof(int) * M);
+    ALLOC(h->active[1], sizeof(int) * M);
+    ALLOC(h->Tin, sizeof(double) * 12 * M);
+    ALLOC(h->eval_out, sizeof(double) * kNumSums * M);
+    ALLOC(h->min_valid, sizeof(double));
+    ALLOC(h->ones, sizeof(float) * cfg.max_channels);
+    ALLOC(h->res_dev, lay.bytes);
+#undef ALLOC
+    if ((e = cudaMallocHost((void**)&h->res_host, lay.bytes)) != cudaSuccess) {
+        release(h);
+        return cuda_fail(e, "pinned result buffer");
+    }
+    if ((e = cudaMemcpy(h->ones, ones.data(), sizeof(float) * cfg.max_channels, cudaMemcpyHostToDevice)) != cudaSuccess) {
+        release(h);
+        return cuda_fail(e, "workspace init");
+    }
+    *out = h;
+    return PILOT_OK;
+}
+
+void pilot_align_destroy(pilot_align_handle* h) {
+    if (!h) return;
+    DeviceGuard g(h->device);
+    cudaDeviceSynchronize();
+    release(h);
+}
+
+pilot_status pilot_align_solve(pilot_align_handle* h, const pilot_frame* f, pilot_result* res,
+                               void* stream) {
+    if (!h || !res) return fail(PILOT_EINVAL, "handle or result is NULL");
+    pilot_status st = validate_frame(h->cfg, f);
+    if (st != PILOT_OK) return st;
+    h->build_launches = 0;
+    h->total_launches = 0;
+    h->build_ms = 0.0;
+    long long hyp_iters = 0;
+    if (f->M == 0) {
+        if (res->best) *res->best = -1;
+        if (res->hyp_iters) *res->hyp_iters = 0;
+        return PILOT_OK;
+    }
+    DeviceGuard guard(h->device);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const pilot_align_config& c = h->cfg;
+    DevFrame d;
+    if ((st = bind_frame(h, f, s, &d, true)) != PILOT_OK) return st;
+    const int M = f->M;
+
+    PILOT_CUDA(launch_count_valid(d.valid, f->N, c.min_valid_frac, h->min_valid, s), "count_valid launch");
+    PILOT_CUDA(launch_hyp_init(h->state, d.T, h->active[0], M, s), "hyp_init launch");
+    h->total_launches += 2;
+    int cur = 0, n_active = M;
+    const PriorParams prior = prior_params(c, f, d);
+
+    for (int level = f->L - 1; level >= 0; --level) {
+        const int iters = c.iters_per_level[level];
+        BuildParams b = build_params(h, f, d, level, n_active, h->active[cur]);
+        EpilogueParams ep{};
+        ep.state = h->state;
+        ep.pose32 = h->pose32;
+        ep.partial = h->partial;
+        ep.active_idx = h->active[cur];
+        ep.n_active = n_active;
+        ep.n_tiles = b.n_tiles;
+        ep.lambda0 = c.lambda0;
+        ep.damping_mode = c.damping_mode;
+        ep.prior = prior;
+        PILOT_CUDA(launch_level_init(h->state, h->pose32, h->active[cur], n_active, c.lambda0, s), "level_init launch");
+        ++h->total_launches;
+        for (int k = 0; k <= iters; ++k) {
+            if ((st = run_build(h, f->feat_dtype, b, s)) != PILOT_OK) return st;
+            ep.mode = (k == 0) ? kEpiInit : kEpiStep;
+            ep.solve_next = k < iters;
+            PILOT_CUDA(launch_epilogue(ep, h->min_valid, s), "epilogue launch");
+            ++h->total_launches;
+        }
+        hyp_iters += (long long)n_active * iters;
+        const int K = c.keep_top_k[level];
+        if (level > 0 && K > 0 && K < n_active) {
+            PILOT_CUDA(launch_prune(h->state, h->active[cur], h->active[cur ^ 1], n_active, K, h->min_valid, s),
+                       "prune launch");
+            ++h->total_launches;
+            cur ^= 1;
+            n_active = K;
+        }
+    }
+    const ResultLayout lay = ResultLayout::make(M);
+    PILOT_CUDA(launch_finalize(h->state, M, h->min_valid, h->res_dev, lay, s), "finalize launch");
+    ++h->total_launches;
+    PILOT_CUDA(cudaMemcpyAsync(h->res_host, h->res_dev, lay.bytes, cudaMemcpyDeviceToHost, s), "result copy");
+    PILOT_CUDA(cudaStreamSynchronize(s), "solve");
+    if (c.profile) {
+        double total = 0.0;
+        for (int i = 0; i < h->build_launches; ++i) {
+            float ms = 0.f;
+            PILOT_CUDA(cudaEventElapsedTime(&ms, h->events[2 * i], h->events[2 * i + 1]), "event timing");
+            total += ms;
+        }
+        h->build_ms = total;
+    }
+    const unsigned char* r = h->res_host;
+    if (res->T_cw) memcpy(res->T_cw, r + lay.off_T, sizeof(double) * 12 * M);
+    if (res->cost) memcpy(res->cost, r + lay.off_cost, sizeof(double) * M);
+    if (res->n_valid) memcpy(res->n_valid, r + lay.off_nvalid, sizeof(int) * M);
+    if (res->hyp_status) memcpy(res->hyp_status, r + lay.off_status, sizeof(int) * M);
+    if (res->best) memcpy(res->best, r + lay.off_best, sizeof(int));
+    if (res->hyp_iters) *res->hyp_iters = hyp_iters;
+    return PILOT_OK;
+}
+
+pilot_status pilot_align_debug_normal_eq(pilot_align_handle* h, const pilot_frame* f, int level,
+                                         const double* T_cw, double* out29, void* stream) {
+    if (!h || !out29 || !T_cw) return fail(PILOT_EINVAL, "handle, T_cw or out29 is NULL");
+    pilot_status st = validate_frame(h->cfg, f);
+    if (st != PILOT_OK) return st;
+    if (level < 0 || level >= f->L) return fail(PILOT_EINVAL, "level %d outside [0, %d)", level, f->L);
+    const int M = f->M;
+    if (M == 0) return PILOT_OK;
+    DeviceGuard guard(h->device);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    h->build_launches = 0;
+    h->total_launches = 0;
+    DevFrame d;
+    if ((st = bind_frame(h, f, s, &d, false)) != PILOT_OK) return st;
+    PILOT_CUDA(cudaMemcpyAsync(h->Tin, T_cw, sizeof(double) * 12 * M, cudaMemcpyHostToDevice, s), "pose copy");
+    PILOT_CUDA(launch_set_poses(h->state, h->pose32, h->Tin, h->active[0], M, s), "set_poses launch");
+    BuildParams b = build_params(h, f, d, level, M, h->active[0]);
+    if ((st = run_build(h, f->feat_dtype, b, s)) != PILOT_OK) return st;
+    EpilogueParams ep{};
+    ep.state = h->state;
+    ep.pose32 = h->pose32;
+    ep.partial = h->partial;
+    ep.active_idx = h->active[0];
+    ep.n_active = M;
+    ep.n_tiles = b.n_tiles;
+    ep.mode = kEpiEval;
+    ep.prior = prior_params(h->cfg, f, d);
+    ep.eval_out = h->eval_out;
+    PILOT_CUDA(launch_epilogue(ep, h->min_valid, s), "epilogue launch");
+    h->total_launches += 2;
+    PILOT_CUDA(cudaMemcpyAsync(out29, h->eval_out, sizeof(double) * kNumSums * M, cudaMemcpyDeviceToHost, s),
+               "normal-equation copy");
+    PILOT_CUDA(cudaStreamSynchronize(s), "debug_normal_eq");
+    return PILOT_OK;
+}
+
+pilot_status pilot_align_profile(const pilot_align_handle* h, double* build_ms, int* build_launches,
+                                 int* total_launches) {
+    if (!h) return fail(PILOT_EINVAL, "handle is NULL");
+    if (build_ms) *build_ms = h->build_ms;
+    if (build_launches) *build_launches = h->build_launches;
+    if (total_launches) *total_launches = h->total_launches;
+    return PILOT_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,132 @@
+"""Helpers shared by the GPU tests: fixtures, tolerance checks, boundary masks.
+
+Tolerances (FP32 build pass against the FP64 oracle):
+  * normal equations: |dH_ab| <= 1e-5 sqrt(H_aa H_bb), |dg_a| <= 1e-5 sqrt(H_aa cost),
+    |dcost| <= 1e-5 cost, n_valid exact.  Both bounds are scale-aware: by Cauchy-Schwarz
+    |H_ab| <= sqrt(H_aa H_bb) and |g_a| <= sqrt(H_aa cost), so 1e-5 of those bounds is
+    the spec relative tolerance applied to each entry's natural magnitude.
+    Anchors whose sampling position lies within 1e-3 px of a cell edge (or whose depth is
+    within 1e-3 of the near plane) are set aside first: there the FP32 and FP64 readings
+    of the cell / visibility decision may both be right (the interpolant's gradient is
+    discontinuous across cell edges), and 1e-3 px is ~20x the FP32 position error.
+  * final poses: rotation within 1e-3 deg and camera centre within 1 mm.
+"""
+from __future__ import annotations
+
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_2606_31098_gb300 import binding as B
+from paper_2606_31098_gb300 import build_ext
+from paper_2606_31098_gb300 import scenes as S
+
+NE_TOL = 1e-5
+ROT_TOL_DEG = 1e-3
+TRANS_TOL_M = 1e-3
+MARGIN_PX = 1e-3
+
+
+def require_cuda():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    build_ext.build()
+    B.load()
+    return torch
+
+
+def to_oracle_opts(opts: B.Options) -> O.SolverOptions:
+    return O.SolverOptions(iters=tuple(opts.iters), lambda0=opts.lambda0, damping_mode=opts.damping_mode,
+                           huber_photo=opts.huber_photo, huber_grav=opts.huber_grav,
+                           huber_range=opts.huber_range, keep_top_k=tuple(opts.keep_top_k),
+                           min_valid_frac=opts.min_valid_frac)
+
+
+def boundary_mask(frame, levels, poses) -> np.ndarray:
+    """point_valid with every anchor that is ambiguous at any (level, pose) cleared."""
+    keep = frame.point_valid.astype(bool).copy()
+    for level in levels:
+        for T in poses:
+            keep &= O.point_margins(frame, level, T) > MARGIN_PX
+    return keep.astype(np.uint8)
+
+
+def assert_normal_eq_close(gpu29, ora29, tol=NE_TOL, what=""):
+    gpu29 = np.asarray(gpu29)
+    ora29 = np.asarray(ora29)
+    Hg, Ho = O.unpack_H(gpu29[:21]), O.unpack_H(ora29[:21])
+    d = np.sqrt(np.maximum(np.diag(Ho), 0.0))
+    scale = np.outer(d, d) + 1e-300
+    errH = np.abs(Hg - Ho) / scale
+    cost = max(ora29[27], 1e-300)
+    errg = np.abs(gpu29[21:27] - ora29[21:27]) / (d * np.sqrt(cost) + 1e-300)
+    errc = abs(gpu29[27] - ora29[27]) / cost
+    msg = f"{what} H {errH.max():.2e} g {errg.max():.2e} cost {errc:.2e} n {gpu29[28]} vs {ora29[28]}"
+    assert gpu29[28] == ora29[28], msg
+    assert errH.max() <= tol and errg.max() <= tol and errc <= tol, msg
+    return errH.max(), errg.max(), errc
+
+
+def pose_errors(Ta, Tb):
+    return S.rotation_error_deg(Ta, Tb), S.translation_error_m(Ta, Tb)
+
+
+def assert_pose_close(Tg, To, what=""):
+    er, et = pose_errors(Tg, To)
+    assert er <= ROT_TOL_DEG and et <= TRANS_TOL_M, f"{what} rot {er:.2e} deg trans {et:.2e} m"
+    return er, et
+
+
+def device_frame(frame, T_hyps=None, **over):
+    arrs = B.device_arrays(frame, T_hyps)
+    arrs.update(over)
+    return B.FrameArgs(frame, arrs, is_device=True)
+
+
+CONVERGED_STEP = 1e-5
+
+
+def converged(frame, oo, T) -> bool:
+    """A hypothesis has converged when the undamped Gauss-Newton step of the FP64
+    objective at its final pose (finest level) is below 1e-5 (m and rad).  Only then is
+    its end point unique; otherwise it depends on the path LM took."""
+    E = O.evaluate(frame, oo, 0, T)
+    H = O.unpack_H(E[:21])
+    try:
+        dx = np.linalg.solve(H, -E[21:27])
+    except np.linalg.LinAlgError:
+        return False
+    return bool(np.all(np.isfinite(dx)) and np.abs(dx).max() < CONVERGED_STEP)
+
+
+def assert_solutions_agree(frame, opts, g, o, idx=None, min_converged=1):
+    """Compare a GPU solve with the oracle's: statuses equal; converged hypotheses and
+    the selected pose within 1e-3 deg / 1 mm with costs within 1e-5; every other final
+    pose is a valid LM end point (its reported objective is the oracle's objective there)."""
+    oo = to_oracle_opts(opts)
+    idx = list(range(len(o.status))) if idx is None else list(idx)
+    n_conv = 0
+    for k, m in enumerate(idx):
+        assert g.status[m] == o.status[k], f"hyp {m}: status {g.status[m]} vs {o.status[k]}"
+        if o.status[k] == O.HYP_PRUNED:
+            continue
+        if o.status[k] == O.HYP_OK and converged(frame, oo, o.T_cw[k]):
+            n_conv += 1
+            assert_pose_close(g.T_cw[m], o.T_cw[k], what=f"hyp {m}")
+            assert g.cost[m] == pytest.approx(o.cost[k], rel=1e-5)
+        elif o.status[k] == O.HYP_OK:
+            E = O.evaluate(frame, oo, 0, g.T_cw[m])
+            assert g.cost[m] == pytest.approx(E[27], rel=1e-4), f"hyp {m}: reported objective"
+    assert n_conv >= min_converged, f"only {n_conv} converged hypotheses"
+    return n_conv
+
+
+def assert_selection_agrees(frame, opts, g, o, idx=None):
+    idx = list(range(len(o.status))) if idx is None else list(idx)
+    assert (g.best >= 0) == (o.best >= 0)
+    if o.best < 0:
+        return
+    assert converged(frame, to_oracle_opts(opts), o.T_cw[o.best]), "oracle's selection not converged"
+    assert_pose_close(g.T_cw[g.best], o.T_cw[o.best], what="selected pose")
+    assert g.cost[g.best] == pytest.approx(o.cost[o.best], rel=1e-5)

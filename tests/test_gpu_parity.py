@@ -1,0 +1,261 @@
+"""Parity of the CUDA path (through the C-ABI) with the FP64 oracle.
+
+Build pass: normal equations of the total objective (Eq. 7, Eq. 8) at identical inputs,
+every level, element by element under the scale-aware 1e-5 tolerance.  Whole solve
+(Eq. 8-9, Sec. IV-E): final poses within 1e-3 deg / 1 mm, statuses equal.  Sizes span
+several 1024-anchor tiles with a ragged tail (70^2 = 4900), odd hypothesis counts, and
+the full 256^2-crop, C = 32, 3-level workload on sampled hypotheses.
+"""
+import dataclasses
+
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_2606_31098_gb300 import binding as B
+from paper_2606_31098_gb300 import scenes as S
+
+from gpu_support import (assert_normal_eq_close, assert_pose_close, assert_selection_agrees,
+                         assert_solutions_agree, boundary_mask, converged, device_frame, pose_errors,
+                         require_cuda, to_oracle_opts)
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def torch():
+    return require_cuda()
+
+
+def random_poses(T_ref, n, seed, trans=3.0, rot_deg=2.0):
+    rng = np.random.default_rng(seed)
+    return [O.pose_update(np.concatenate([rng.uniform(-trans, trans, 3),
+                                          np.deg2rad(rng.uniform(-rot_deg, rot_deg, 3))]), T_ref)
+            for _ in range(n)]
+
+
+def check_normal_eq(frame, opts, levels, poses):
+    valid = boundary_mask(frame, levels, poses)
+    fm = frame.replace(point_valid=valid)
+    fa = device_frame(fm, np.array(poses))
+    solver = B.Solver(opts)
+    oo = to_oracle_opts(opts)
+    worst = np.zeros(3)
+    for level in levels:
+        gpu = solver.normal_eq(fa, level, np.array(poses))
+        for m, T in enumerate(poses):
+            ora = O.evaluate(fm, oo, level, T)
+            worst = np.maximum(worst, assert_normal_eq_close(gpu[m], ora, what=f"level {level} pose {m}"))
+    solver.close()
+    return worst
+
+
+# ----------------------------------------------------------------- normal equations
+
+def test_normal_equations_small_plain_frame(torch):
+    f = S.make_frame(S.config_small_plain(), S.frame_seed(1, 0))
+    poses = [f.T_gt, *f.T_hyps, *random_poses(f.T_gt, 5, 1)]
+    check_normal_eq(f, B.Options(iters=(20, 0, 0, 0), max_channels=32), [0], poses)
+
+
+def test_normal_equations_reduced_frame_every_level_with_priors(torch):
+    f = S.make_frame(S.config_reduced_frame(), S.frame_seed(2, 100))
+    poses = [f.T_gt, *f.T_hyps, *random_poses(f.T_gt, 3, 2)]
+    check_normal_eq(f, B.Options(), [0, 1, 2], poses)
+
+
+@pytest.mark.parametrize("C", [4, 8, 16, 64])
+def test_normal_equations_other_channel_counts(torch, C):
+    cfg = dataclasses.replace(S.config_reduced_frame(crop_side=37, n_hyps=3, channels=C))
+    f = S.make_frame(cfg, 300 + C)
+    poses = [f.T_gt, *f.T_hyps]
+    check_normal_eq(f, B.Options(max_channels=64), [0, 2], poses)
+
+
+def test_normal_equations_with_weights_and_both_huber_branches(torch):
+    f = S.make_frame(S.config_reduced_frame(crop_side=45, n_hyps=3), 777)
+    rng = np.random.default_rng(3)
+    f = f.replace(point_weight=rng.uniform(0.2, 3.0, f.N).astype(np.float32))
+    poses = [f.T_gt, *f.T_hyps]
+    check_normal_eq(f, B.Options(huber_photo=0.05, huber_grav=0.001, huber_range=0.05), [0, 1, 2], poses)
+
+
+def test_normal_equations_full_size_sampled(torch):
+    f = S.make_frame(S.config_full_frame(), S.frame_seed(2, 0))
+    poses = [f.T_gt, f.T_hyps[0], f.T_hyps[31], f.T_hyps[63]]
+    check_normal_eq(f, B.Options(), [0, 1, 2], poses)
+
+
+def test_unmasked_normal_equations_differ_only_through_edge_anchors(torch):
+    """Without setting edge anchors aside, the FP32/FP64 difference stays within what
+    the few ambiguous anchors can contribute (well under 1e-3 of the natural scale)."""
+    f = S.make_frame(S.config_full_frame(n_hyps=4), S.frame_seed(2, 1))
+    fa = device_frame(f)
+    solver = B.Solver(B.Options())
+    oo = to_oracle_opts(B.Options())
+    for level in (0, 2):
+        gpu = solver.normal_eq(fa, level, f.T_hyps)
+        for m in range(f.M):
+            ora = O.evaluate(f, oo, level, f.T_hyps[m])
+            assert abs(gpu[m][28] - ora[28]) <= 0.001 * ora[28]
+            Ho = O.unpack_H(ora[:21])
+            d = np.sqrt(np.diag(Ho))
+            assert np.max(np.abs(O.unpack_H(gpu[m][:21]) - Ho) / np.outer(d, d)) < 1e-3
+    solver.close()
+
+
+# ------------------------------------------------------------------- whole solves
+
+def compare_solves(frame, opts, n_threads=0, hyps=None, T_hyps=None):
+    fa = device_frame(frame, T_hyps)
+    solver = B.Solver(opts)
+    g = solver.solve(fa)
+    solver.close()
+    idx = list(range(fa.M)) if hyps is None else list(hyps)
+    Tsub = (frame.T_hyps if T_hyps is None else T_hyps)[idx]
+    o = O.solve(frame, to_oracle_opts(opts), T_hyps=Tsub, n_threads=n_threads)
+    return g, o, idx
+
+
+def test_solve_small_plain_frame(torch):
+    f = S.make_frame(S.config_small_plain(), S.frame_seed(1, 0))
+    opts = B.Options(iters=(20, 0, 0, 0), max_channels=32)
+    g, o, _ = compare_solves(f, opts)
+    assert g.status[0] == o.status[0] == B.HYP_OK
+    assert g.best == o.best == 0
+    assert g.hyp_iters == o.hyp_iters == 20
+    assert_pose_close(g.T_cw[0], o.T_cw[0])
+    assert g.cost[0] == pytest.approx(o.cost[0], rel=1e-5)
+
+
+@pytest.mark.parametrize("seed", [0, 1, 2])
+def test_solve_reduced_frame_all_hypotheses(torch, seed):
+    """Converged hypotheses and the selected pose agree with the oracle; hypotheses still
+    moving after the last iteration end at valid points of their own path."""
+    f = S.make_frame(S.config_reduced_frame(n_hyps=7), S.frame_seed(2, 200 + seed))
+    opts = B.Options()
+    g, o, _ = compare_solves(f, opts)
+    assert g.hyp_iters == o.hyp_iters == 7 * 30
+    assert_solutions_agree(f, opts, g, o, min_converged=2)
+    assert_selection_agrees(f, opts, g, o)
+
+
+def test_solve_full_size_sampled_hypotheses(torch):
+    """The full 256^2 x C=32 x 3-level frame with 64 hypotheses on the GPU; the oracle
+    re-solves a sample of them (hypotheses are independent without pruning)."""
+    f = S.make_frame(S.config_full_frame(), S.frame_seed(2, 0))
+    opts = B.Options()
+    fa = device_frame(f)
+    solver = B.Solver(opts)
+    g = solver.solve(fa)
+    solver.close()
+    assert g.hyp_iters == 64 * 30
+    assert g.best >= 0 and g.status[g.best] == B.HYP_OK
+    sample = sorted({0, g.best, 17, 42})
+    o = O.solve(f, to_oracle_opts(opts), T_hyps=f.T_hyps[sample])
+    sub = B.Result(g.T_cw, g.cost, g.n_valid, g.status, g.best, g.hyp_iters)
+    assert_solutions_agree(f, opts, sub, o, idx=sample, min_converged=1)
+    k = sample.index(g.best)
+    assert converged(f, to_oracle_opts(opts), o.T_cw[k])
+    assert_pose_close(g.T_cw[g.best], o.T_cw[k], what="selected pose")
+    # the selected pose is close to the ground truth of the synthetic scene
+    er, et = pose_errors(g.T_cw[g.best], f.T_gt)
+    assert er < 0.1 and et < 0.5
+
+
+def test_pruning_keeps_a_valid_top_k(torch):
+    """Top-K after the coarse level only (Supp. "Multi-Hypothesis Refinement").  With no
+    iterations at the finer levels every final pose is the hypothesis' coarse end pose,
+    so the FP64 coarse objective at those poses ranks them: the GPU must keep exactly K,
+    all among the K lowest up to 1e-5 (near-ties may go either way), and each pruned
+    hypothesis reports its coarse objective."""
+    f = S.make_frame(S.config_reduced_frame(n_hyps=9), S.frame_seed(2, 300))
+    K = 4
+    opts = B.Options(iters=(0, 0, 6, 0), keep_top_k=(0, 0, K, 0))
+    oo = to_oracle_opts(opts)
+    g = B.Solver(opts).solve(device_frame(f))
+    assert g.hyp_iters == 9 * 6
+    coarse = np.array([O.evaluate(f, oo, 2, g.T_cw[m])[27] for m in range(f.M)])
+    kth = np.sort(coarse)[K - 1]
+    kept = np.flatnonzero(g.status != B.HYP_PRUNED)
+    assert len(kept) == K
+    for m in kept:
+        assert coarse[m] <= kth * (1 + 1e-5)
+    for m in np.flatnonzero(g.status == B.HYP_PRUNED):
+        assert coarse[m] >= kth * (1 - 1e-5)
+        assert g.cost[m] == pytest.approx(coarse[m], rel=1e-5)
+
+
+def test_solve_with_two_prunes_selects_the_same_pose(torch):
+    f = S.make_frame(S.config_reduced_frame(n_hyps=9), S.frame_seed(2, 301))
+    opts = B.Options(iters=(10, 10, 10, 0), keep_top_k=(0, 3, 5, 0))
+    g, o, _ = compare_solves(f, opts)
+    assert g.hyp_iters == o.hyp_iters == 9 * 10 + 5 * 10 + 3 * 10
+    assert (g.status == B.HYP_PRUNED).sum() == (o.status == O.HYP_PRUNED).sum() == 6
+    assert_selection_agrees(f, opts, g, o)
+
+
+def test_solve_with_diag_damping_and_weights(torch):
+    f = S.make_frame(S.config_reduced_frame(n_hyps=5), S.frame_seed(2, 400))
+    rng = np.random.default_rng(4)
+    f = f.replace(point_weight=rng.uniform(0.5, 2.0, f.N).astype(np.float32))
+    opts = B.Options(damping_mode=1, lambda0=1e-2)
+    g, o, _ = compare_solves(f, opts)
+    assert_solutions_agree(f, opts, g, o, min_converged=1)
+    assert_selection_agrees(f, opts, g, o)
+
+
+# -------------------------------------------------------------------- edge cases
+
+def test_zero_hypotheses(torch):
+    f = S.make_frame(S.config_reduced_frame(n_hyps=2), 5)
+    fa = device_frame(f, np.zeros((0, 12)))
+    r = B.Solver(B.Options()).solve(fa)
+    assert r.best == -1 and r.hyp_iters == 0
+
+
+def test_priors_only_no_anchors(torch):
+    f = S.make_frame(S.config_reduced_frame(n_hyps=3), 6)
+    empty = f.replace(points=np.zeros((3, 0), np.float32), point_valid=np.zeros(0, np.uint8),
+                      point_weight=np.zeros(0, np.float32),
+                      ref_feat=[np.zeros((0, f.C), np.float32) for _ in range(f.L)])
+    opts = B.Options(min_valid_frac=0.0)
+    g, o, _ = compare_solves(empty, opts)
+    np.testing.assert_array_equal(g.status, o.status)
+    for m in range(f.M):
+        np.testing.assert_allclose(g.T_cw[m], o.T_cw[m], atol=1e-9)
+        assert g.cost[m] == pytest.approx(o.cost[m], rel=1e-9, abs=1e-12)
+
+
+def test_all_anchors_invisible_and_nan_maps(torch):
+    f = S.make_frame(S.config_reduced_frame(n_hyps=2), 7)
+    T = f.T_hyps.copy()
+    T[:, 3] += 1e4
+    g, o, _ = compare_solves(f, B.Options(), T_hyps=T)
+    assert np.all(g.status == B.HYP_FEW_VALID) and np.all(o.status == O.HYP_FEW_VALID)
+    assert g.best == o.best == -1
+    nan_maps = [np.full_like(q, np.nan) for q in f.qry_feat]
+    g, o, _ = compare_solves(f.replace(qry_feat=nan_maps), B.Options())
+    assert np.all(g.status == B.HYP_NONFINITE) and np.all(o.status == O.HYP_NONFINITE)
+
+
+def test_host_frame_equals_device_frame_and_is_deterministic(torch):
+    f = S.make_frame(S.config_reduced_frame(n_hyps=5), 8)
+    solver = B.Solver(B.Options())
+    a = solver.solve(device_frame(f))
+    b = solver.solve(B.FrameArgs(f, B.host_arrays(f), is_device=False))
+    c = solver.solve(device_frame(f))
+    for x in (b, c):
+        np.testing.assert_array_equal(a.T_cw, x.T_cw)
+        np.testing.assert_array_equal(a.cost, x.cost)
+        np.testing.assert_array_equal(a.status, x.status)
+
+
+def test_hypothesis_permutation_invariance(torch):
+    f = S.make_frame(S.config_reduced_frame(n_hyps=6), 9)
+    solver = B.Solver(B.Options())
+    a = solver.solve(device_frame(f))
+    perm = np.array([3, 5, 0, 1, 4, 2])
+    b = solver.solve(device_frame(f, f.T_hyps[perm]))
+    np.testing.assert_array_equal(a.T_cw[perm], b.T_cw)
+    np.testing.assert_array_equal(a.cost[perm], b.cost)
