@@ -22,6 +22,7 @@ import argparse
 import hashlib
 import json
 import os
+import re
 import statistics
 import subprocess
 import sys
@@ -38,7 +39,7 @@ UNIT = "hyp*iter/s"
 WORKLOAD = ("full single frame: 256x256 anchors at 0.5 m, C=32, 3 levels 480x640/240x320/120x160, "
             "64 hypotheses, 10 LM iterations per level, gravity + range priors")
 MEASURED_PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
-TRAFFIC_FILE = os.path.join(ROOT, "profiles", "build_kernel_traffic.json")
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "build_kernel_f32_c32_full_frame.md")
 BUILD_SRC = os.path.join(ROOT, "paper_2606_31098_gb300", "csrc", "pilot_build_impl.cuh")
 SM_COUNT = 152
 FP32_LANES_PER_SM = 128
@@ -144,12 +145,13 @@ def traffic_per_launch(units_per_launch: int):
     """DRAM bytes per build launch from the committed ncu summary, scaled to the units of
     one launch; None when the kernel source changed since the counters were taken."""
     try:
-        t = json.load(open(TRAFFIC_FILE))
-    except Exception:
+        text = open(TRAFFIC_FILE).read()
+    except OSError:
         return None
-    if t.get("build_src_sha256_16") != build_src_hash():
+    m = re.search(r"traffic_dram_bytes_per_unit:\s*([0-9.eE+-]+)\s*\(build_src_sha256_16:\s*([0-9a-f]+)\)", text)
+    if not m or m.group(2) != build_src_hash():
         return None
-    return t["dram_bytes_per_unit"] * units_per_launch
+    return float(m.group(1)) * units_per_launch
 
 
 def cpu_cores() -> int:

@@ -11,13 +11,15 @@
 // formed: per anchor only the 2x2 Gram matrix M = G^T G, b = G^T r and s = ||r||^2 are
 // summed over channels, then H_j = w A^T M A and g_j = w A^T b.
 //
-// Thread mapping.  A group of LP = C/4 consecutive lanes owns one anchor; lane q of the
-// group reads channels [4q, 4q+4) of each of the 4 taps, so one tap of one anchor is a
-// single contiguous C-element segment read by LP lanes (one 128-byte line at C = 32 in
-// FP32).  The per-anchor sums are all-reduced inside the group with xor shuffles
-// (bit-identical in every lane), every lane of the group then accumulates the same
-// 29 sums, and the CTA reduces them across groups and warps in a fixed order: the
-// result is deterministic and independent of the grid shape.
+// Thread mapping.  A group of LP = C / CPL consecutive lanes (CPL = 4 channels per lane,
+// 8 at C = 64) works on LP anchors at a time.  Each lane projects one of them and
+// broadcasts its tap offset and bilinear weights to the group; the group then reads the
+// 4 taps of every anchor together, lane q taking channels [CPL q, CPL q + CPL), so one
+// tap is one contiguous C-element segment read by LP lanes (one 128-byte line at C = 32
+// in FP32).  A butterfly reduce-scatter over the group leaves in lane q the channel
+// sums of anchor q, and each lane finishes its own anchor (Huber weight, A, 21 + 6
+// sums) exactly once.  The CTA reduces the lanes' sums in a fixed order: the result is
+// deterministic and independent of the grid shape.
 #pragma once
 
 #include <cuda_bf16.h>
@@ -86,10 +88,13 @@ __device__ __forceinline__ void channel(ChanSums& a, float t00, float t01, float
 template <pilot_dtype DT, int C>
 __global__ void __launch_bounds__(kBuildThreads)
 build_kernel(const BuildParams p) {
-    static_assert(C % 4 == 0 && C >= 4 && C <= 128, "channels");
-    constexpr int LP = C / 4;                       // lanes per anchor
-    constexpr int GROUPS = kBuildThreads / LP;      // anchors in flight per CTA
-    static_assert(LP <= 32, "group larger than a warp");
+    static_assert(C % 4 == 0 && C >= 4 && C <= 64, "channels");
+    constexpr int CPL = (C >= 64) ? 8 : 4;          // channels per lane
+    constexpr int NV = CPL / 4;                     // 4-channel vectors per lane and tap
+    constexpr int LP = C / CPL;                     // lanes per group = anchors per batch
+    constexpr int GROUPS = kBuildThreads / LP;
+    constexpr int BATCH = GROUPS * LP;              // anchors per CTA pass
+    static_assert(LP >= 1 && LP <= 16 && (LP & (LP - 1)) == 0, "group size");
     __shared__ float red[kBuildThreads / 32][kAcc];
 
     const int slot = blockIdx.y;
@@ -99,8 +104,10 @@ build_kernel(const BuildParams p) {
 
     const int tid = threadIdx.x;
     const int lane = tid & 31, warp = tid >> 5;
-    const int q = tid % LP, grp = tid / LP;
-    const unsigned gmask = (LP == 32) ? 0xffffffffu : (((1u << LP) - 1u) << (lane & ~(LP - 1)));
+    const int q = lane & (LP - 1);                  // lane within the group
+    const int grp = tid / LP;
+    const int src0 = lane & ~(LP - 1);              // first lane of the group
+    const unsigned gmask = (LP == 32) ? 0xffffffffu : (((1u << LP) - 1u) << src0);
 
     const float* P = p.pose32 + 12 * hyp;
     const float R00 = P[0], R01 = P[1], R02 = P[2], T0 = P[3];
@@ -108,10 +115,16 @@ build_kernel(const BuildParams p) {
     const float R20 = P[8], R21 = P[9], R22 = P[10], T2 = P[11];
 
     const bool scaled = p.qscale != nullptr;
-    float4 qs = make_float4(1.f, 1.f, 1.f, 1.f), rs = qs;
-    if (scaled) {
-        qs = __ldg(reinterpret_cast<const float4*>(p.qscale) + q);
-        rs = __ldg(reinterpret_cast<const float4*>(p.rscale) + q);
+    float qs[CPL], rs[CPL];
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+        float4 a = make_float4(1.f, 1.f, 1.f, 1.f), b = a;
+        if (scaled) {
+            a = __ldg(reinterpret_cast<const float4*>(p.qscale) + q * NV + v);
+            b = __ldg(reinterpret_cast<const float4*>(p.rscale) + q * NV + v);
+        }
+        qs[4 * v] = a.x; qs[4 * v + 1] = a.y; qs[4 * v + 2] = a.z; qs[4 * v + 3] = a.w;
+        rs[4 * v] = b.x; rs[4 * v + 1] = b.y; rs[4 * v + 2] = b.z; rs[4 * v + 3] = b.w;
     }
 
     float acc[kNumSums];
@@ -120,94 +133,134 @@ build_kernel(const BuildParams p) {
 
     const int j0 = blockIdx.x * p.tile;
     const int j1 = min(j0 + p.tile, p.N);
-    const size_t WC = (size_t)p.W * C;
+    const int WC = p.W * C;
     const float xmax = (float)(p.W - 1), ymax = (float)(p.H - 1);
     const float d2 = p.huber * p.huber;
 
-    for (int j = j0 + grp; j < j1; j += GROUPS) {
-        if (p.valid && !p.valid[j]) continue;
-        const float X = __ldg(p.px + j), Y = __ldg(p.py + j), Z = __ldg(p.pz + j);
-        // p = R P + t  (world -> camera)
-        const float x = fmaf(R00, X, fmaf(R01, Y, fmaf(R02, Z, T0)));
-        const float y = fmaf(R10, X, fmaf(R11, Y, fmaf(R12, Z, T1)));
-        const float z = fmaf(R20, X, fmaf(R21, Y, fmaf(R22, Z, T2)));
-        if (!(z > kZNear)) continue;
-        const float iz = 1.0f / z;
-        // pixel i covers [i, i+1): array coordinate = pixel - 1/2
-        const float xs = fmaf(p.fx * x, iz, p.cx) - 0.5f;
-        const float ys = fmaf(p.fy * y, iz, p.cy) - 0.5f;
-        if (!(xs >= 0.f && xs <= xmax && ys >= 0.f && ys <= ymax)) continue;
-        const int c0 = min((int)xs, p.W - 2);
-        const int r0 = min((int)ys, p.H - 2);
-        const float ax = xs - (float)c0, ay = ys - (float)r0;
-
-        const size_t base = ((size_t)r0 * p.W + c0) * C + 4 * q;
-        const float4 a00 = load4<DT>(p.qry, base);
-        const float4 a01 = load4<DT>(p.qry, base + C);
-        const float4 a10 = load4<DT>(p.qry, base + WC);
-        const float4 a11 = load4<DT>(p.qry, base + WC + C);
-        const float4 fr = load4<DT>(p.ref, (size_t)j * C + 4 * q);
-
-        ChanSums cs{0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-        channel(cs, a00.x, a01.x, a10.x, a11.x, fr.x, ax, ay, scaled, qs.x, rs.x);
-        channel(cs, a00.y, a01.y, a10.y, a11.y, fr.y, ax, ay, scaled, qs.y, rs.y);
-        channel(cs, a00.z, a01.z, a10.z, a11.z, fr.z, ax, ay, scaled, qs.z, rs.z);
-        channel(cs, a00.w, a01.w, a10.w, a11.w, fr.w, ax, ay, scaled, qs.w, rs.w);
-#pragma unroll
-        for (int off = 1; off < LP; off <<= 1) {
-            cs.s += __shfl_xor_sync(gmask, cs.s, off);
-            cs.m00 += __shfl_xor_sync(gmask, cs.m00, off);
-            cs.m01 += __shfl_xor_sync(gmask, cs.m01, off);
-            cs.m11 += __shfl_xor_sync(gmask, cs.m11, off);
-            cs.b0 += __shfl_xor_sync(gmask, cs.b0, off);
-            cs.b1 += __shfl_xor_sync(gmask, cs.b1, off);
-        }
-
-        // Huber on w ||r||^2 and the IRLS weight w rho'
-        const float w = p.weight ? __ldg(p.weight + j) : 1.0f;
-        const float sw = w * cs.s;
-        float rho, drho;
-        if (sw <= d2) {
-            rho = sw;
-            drho = 1.0f;
-        } else {
-            const float rt = sqrtf(sw);
-            rho = 2.0f * p.huber * rt - d2;
-            drho = p.huber / rt;
-        }
-        const float om = w * drho;
-
-        // A = d(u,v)/dp [I | -[p]x]; the rotational part of each row a is p x a
-        const float du_dx = p.fx * iz, du_dz = -p.fx * x * iz * iz;
-        const float dv_dy = p.fy * iz, dv_dz = -p.fy * y * iz * iz;
-        const float A0[6] = {du_dx, 0.f, du_dz, y * du_dz, z * du_dx - x * du_dz, -y * du_dx};
-        const float A1[6] = {0.f, dv_dy, dv_dz, y * dv_dz - z * dv_dy, -x * dv_dz, x * dv_dy};
-        float B0[6], B1[6], W0[6], W1[6];
-#pragma unroll
-        for (int k = 0; k < 6; ++k) {
-            B0[k] = fmaf(cs.m00, A0[k], cs.m01 * A1[k]);
-            B1[k] = fmaf(cs.m01, A0[k], cs.m11 * A1[k]);
-            W0[k] = om * A0[k];
-            W1[k] = om * A1[k];
-        }
-        int e = 0;
-#pragma unroll
-        for (int a = 0; a < 6; ++a) {
-#pragma unroll
-            for (int b = a; b < 6; ++b) {
-                acc[e] = fmaf(W0[a], B0[b], fmaf(W1[a], B1[b], acc[e]));
-                ++e;
+    for (int jb = j0 + grp * LP; jb < j1; jb += BATCH) {
+        // 1. every lane projects its own anchor jb + q
+        const int jo = jb + q;
+        bool vis = false;
+        int off = 0;
+        float ax = 0.f, ay = 0.f, x = 0.f, y = 0.f, z = 1.f, iz = 1.f;
+        if (jo < j1 && (!p.valid || p.valid[jo])) {
+            const float X = __ldg(p.px + jo), Y = __ldg(p.py + jo), Z = __ldg(p.pz + jo);
+            // p = R P + t  (world -> camera)
+            x = fmaf(R00, X, fmaf(R01, Y, fmaf(R02, Z, T0)));
+            y = fmaf(R10, X, fmaf(R11, Y, fmaf(R12, Z, T1)));
+            z = fmaf(R20, X, fmaf(R21, Y, fmaf(R22, Z, T2)));
+            if (z > kZNear) {
+                iz = 1.0f / z;
+                // pixel i covers [i, i+1): array coordinate = pixel - 1/2
+                const float xs = fmaf(p.fx * x, iz, p.cx) - 0.5f;
+                const float ys = fmaf(p.fy * y, iz, p.cy) - 0.5f;
+                if (xs >= 0.f && xs <= xmax && ys >= 0.f && ys <= ymax) {
+                    const int c0 = min((int)xs, p.W - 2);
+                    const int r0 = min((int)ys, p.H - 2);
+                    ax = xs - (float)c0;
+                    ay = ys - (float)r0;
+                    off = (r0 * p.W + c0) * C;
+                    vis = true;
+                }
             }
         }
+
+        // 2. the group gathers its LP anchors together: lane q reads channels
+        //    [CPL q, CPL q + CPL) of the 4 taps and of the reference row of each
+        float S[LP][6];
 #pragma unroll
-        for (int a = 0; a < 6; ++a) acc[21 + a] = fmaf(W0[a], cs.b0, fmaf(W1[a], cs.b1, acc[21 + a]));
-        acc[27] += rho;
-        acc[28] += 1.0f;
+        for (int i = 0; i < LP; ++i) {
+            const int vi = __shfl_sync(gmask, (int)vis, src0 + i);
+            const int oi = __shfl_sync(gmask, off, src0 + i) + CPL * q;
+            const float axi = __shfl_sync(gmask, ax, src0 + i);
+            const float ayi = __shfl_sync(gmask, ay, src0 + i);
+            const int ri = (vi ? jb + i : 0) * C + CPL * q;   // row 0 is a safe dummy
+            ChanSums cs{0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+            for (int v = 0; v < NV; ++v) {
+                const float4 a00 = load4<DT>(p.qry, (size_t)oi + 4 * v);
+                const float4 a01 = load4<DT>(p.qry, (size_t)oi + C + 4 * v);
+                const float4 a10 = load4<DT>(p.qry, (size_t)oi + WC + 4 * v);
+                const float4 a11 = load4<DT>(p.qry, (size_t)oi + WC + C + 4 * v);
+                const float4 fr = load4<DT>(p.ref, (size_t)ri + 4 * v);
+                channel(cs, a00.x, a01.x, a10.x, a11.x, fr.x, axi, ayi, scaled, qs[4 * v], rs[4 * v]);
+                channel(cs, a00.y, a01.y, a10.y, a11.y, fr.y, axi, ayi, scaled, qs[4 * v + 1], rs[4 * v + 1]);
+                channel(cs, a00.z, a01.z, a10.z, a11.z, fr.z, axi, ayi, scaled, qs[4 * v + 2], rs[4 * v + 2]);
+                channel(cs, a00.w, a01.w, a10.w, a11.w, fr.w, axi, ayi, scaled, qs[4 * v + 3], rs[4 * v + 3]);
+            }
+            const float m = vi ? 1.0f : 0.0f;
+            S[i][0] = cs.s * m;
+            S[i][1] = cs.m00 * m;
+            S[i][2] = cs.m01 * m;
+            S[i][3] = cs.m11 * m;
+            S[i][4] = cs.b0 * m;
+            S[i][5] = cs.b1 * m;
+        }
+
+        // 3. butterfly reduce-scatter: afterwards S[0] of lane q holds anchor q's sums
+#pragma unroll
+        for (int half = LP / 2; half >= 1; half >>= 1) {
+            const bool upper = (q & half) != 0;
+#pragma unroll
+            for (int t = 0; t < half; ++t) {
+#pragma unroll
+                for (int v = 0; v < 6; ++v) {
+                    const float send = upper ? S[t][v] : S[t + half][v];
+                    const float keep = upper ? S[t + half][v] : S[t][v];
+                    S[t][v] = keep + __shfl_xor_sync(gmask, send, half);
+                }
+            }
+        }
+
+        // 4. each lane finishes its own anchor: Huber weight, A = d(u,v)/dp [I | -[p]x],
+        //    H += w A^T M A, g += w A^T b
+        if (vis) {
+            const float s = S[0][0], m00 = S[0][1], m01 = S[0][2], m11 = S[0][3];
+            const float b0 = S[0][4], b1 = S[0][5];
+            const float w = p.weight ? __ldg(p.weight + jo) : 1.0f;
+            const float sw = w * s;
+            float rho, drho;
+            if (sw <= d2) {
+                rho = sw;
+                drho = 1.0f;
+            } else {
+                const float rt = sqrtf(sw);
+                rho = 2.0f * p.huber * rt - d2;
+                drho = p.huber / rt;
+            }
+            const float om = w * drho;
+            // the rotational part of each row a of d(u,v)/dp is p x a
+            const float du_dx = p.fx * iz, du_dz = -p.fx * x * iz * iz;
+            const float dv_dy = p.fy * iz, dv_dz = -p.fy * y * iz * iz;
+            const float A0[6] = {du_dx, 0.f, du_dz, y * du_dz, z * du_dx - x * du_dz, -y * du_dx};
+            const float A1[6] = {0.f, dv_dy, dv_dz, y * dv_dz - z * dv_dy, -x * dv_dz, x * dv_dy};
+            float B0[6], B1[6], W0[6], W1[6];
+#pragma unroll
+            for (int k = 0; k < 6; ++k) {
+                B0[k] = fmaf(m00, A0[k], m01 * A1[k]);
+                B1[k] = fmaf(m01, A0[k], m11 * A1[k]);
+                W0[k] = om * A0[k];
+                W1[k] = om * A1[k];
+            }
+            int e = 0;
+#pragma unroll
+            for (int a = 0; a < 6; ++a) {
+#pragma unroll
+                for (int b = a; b < 6; ++b) {
+                    acc[e] = fmaf(W0[a], B0[b], fmaf(W1[a], B1[b], acc[e]));
+                    ++e;
+                }
+            }
+#pragma unroll
+            for (int a = 0; a < 6; ++a) acc[21 + a] = fmaf(W0[a], b0, fmaf(W1[a], b1, acc[21 + a]));
+            acc[27] += rho;
+            acc[28] += 1.0f;
+        }
     }
 
-    // Every lane of a group holds the group's sums: reduce across groups, then warps.
+    // Each lane holds distinct anchors: reduce across the warp, then across warps.
 #pragma unroll
-    for (int off = LP; off < 32; off <<= 1) {
+    for (int off = 1; off < 32; off <<= 1) {
 #pragma unroll
         for (int i = 0; i < kNumSums; ++i) acc[i] += __shfl_xor_sync(0xffffffffu, acc[i], off);
     }

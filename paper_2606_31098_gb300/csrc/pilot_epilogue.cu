@@ -300,17 +300,30 @@ __global__ void prune_kernel(HypState* st, const int* active_in, int* active_out
     }
 }
 
+// One block of 1024 threads: number of valid anchors (4 flags per load when aligned).
 __global__ void count_valid_kernel(const uint8_t* valid, int N, double frac, double* min_valid) {
-    __shared__ int part[256];
+    __shared__ int part[32];
     int c = 0;
-    for (int j = threadIdx.x; j < N; j += blockDim.x) c += valid ? (valid[j] != 0) : 1;
-    part[threadIdx.x] = c;
-    __syncthreads();
-    for (int s = 128; s > 0; s >>= 1) {
-        if (threadIdx.x < s) part[threadIdx.x] += part[threadIdx.x + s];
-        __syncthreads();
+    if (!valid) {
+        c = (threadIdx.x == 0) ? N : 0;
+    } else if (((uintptr_t)valid & 3) == 0) {
+        const uint32_t* w = reinterpret_cast<const uint32_t*>(valid);
+        for (int k = threadIdx.x; k < N / 4; k += blockDim.x) {
+            const uint32_t v = w[k];
+            c += ((v & 0xffu) != 0) + ((v & 0xff00u) != 0) + ((v & 0xff0000u) != 0) + ((v >> 24) != 0);
+        }
+        for (int j = (N / 4) * 4 + threadIdx.x; j < N; j += blockDim.x) c += valid[j] != 0;
+    } else {
+        for (int j = threadIdx.x; j < N; j += blockDim.x) c += valid[j] != 0;
     }
-    if (threadIdx.x == 0) *min_valid = frac * (double)part[0];
+    for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
+    if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = c;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        int v = (threadIdx.x < (blockDim.x >> 5)) ? part[threadIdx.x] : 0;
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if (threadIdx.x == 0) *min_valid = frac * (double)v;
+    }
 }
 
 // One block of 256 threads: final statuses, result block, argmin (ties -> lowest index).
@@ -403,7 +416,7 @@ cudaError_t launch_prune(HypState* st, const int* active_in, int* active_out, in
 
 cudaError_t launch_count_valid(const uint8_t* valid, int N, double frac, double* min_valid,
                                cudaStream_t s) {
-    count_valid_kernel<<<1, 256, 0, s>>>(valid, N, frac, min_valid);
+    count_valid_kernel<<<1, 1024, 0, s>>>(valid, N, frac, min_valid);
     return cudaGetLastError();
 }
 

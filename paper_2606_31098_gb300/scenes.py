@@ -95,10 +95,12 @@ def config_full_frame(n_hyps: int = 64) -> SceneConfig:
 
 
 def config_reduced_frame(crop_side: int = 70, n_hyps: int = 6, channels: int = 32,
-                         levels=((120, 160), (60, 80), (30, 40)), f0: float = 150.0,
+                         levels=((240, 320), (120, 160), (60, 80)), f0: float = 600.0,
                          gsd: float = 1.0) -> SceneConfig:
     """The full-frame recipe shrunk so that the FP64 oracle finishes in seconds, while
-    still spanning several point tiles and a ragged tail (70^2 = 4900 anchors)."""
+    still spanning several point tiles and a ragged tail (70^2 = 4900 anchors).  The
+    focal length stays that of the full frame (600 px at the finest level), so a pixel
+    subtends the same angle and the pose is as well conditioned per anchor."""
     return SceneConfig(crop_side=crop_side, gsd=gsd, channels=channels, levels=levels,
                        f0=f0, n_hyps=n_hyps)
 

@@ -1,10 +1,14 @@
 """Helpers shared by the GPU tests: fixtures, tolerance checks, boundary masks.
 
 Tolerances (FP32 build pass against the FP64 oracle):
-  * normal equations: |dH_ab| <= 1e-5 sqrt(H_aa H_bb), |dg_a| <= 1e-5 sqrt(H_aa cost),
-    |dcost| <= 1e-5 cost, n_valid exact.  Both bounds are scale-aware: by Cauchy-Schwarz
-    |H_ab| <= sqrt(H_aa H_bb) and |g_a| <= sqrt(H_aa cost), so 1e-5 of those bounds is
-    the spec relative tolerance applied to each entry's natural magnitude.
+  * normal equations, compared at the pose the build pass evaluates (the FP32 rounding
+    of the FP64 hypothesis, step A2 of the path): |dH_ab| <= 1e-5 sqrt(H_aa H_bb),
+    |dg_a| <= 1e-5 sqrt(H_aa F), |dcost| <= 1e-5 max(cost, 1e-3 F), n_valid exact, where
+    F = sum_j w_j ||f_j||^2 = the number of visible anchors for L2-normalised descriptors
+    (weights 1).  By Cauchy-Schwarz |H_ab| <= sqrt(H_aa H_bb) and the FP32 sums behind g
+    and the cost are bounded by sqrt(H_aa F) and F: the benchmark spec's 1e-5 relative
+    tolerance is applied to the magnitude of what FP32 actually sums (at the optimum the
+    residuals, and g, are only descriptor noise, so a residual-based scale would vanish).
     Anchors whose sampling position lies within 1e-3 px of a cell edge (or whose depth is
     within 1e-3 of the near plane) are set aside first: there the FP32 and FP64 readings
     of the cell / visibility decision may both be right (the interpolant's gradient is
@@ -52,16 +56,21 @@ def boundary_mask(frame, levels, poses) -> np.ndarray:
     return keep.astype(np.uint8)
 
 
-def assert_normal_eq_close(gpu29, ora29, tol=NE_TOL, what=""):
+def fp32_pose(T):
+    """The pose the build pass evaluates: the FP32 rounding of an FP64 pose."""
+    return np.asarray(T, np.float64).astype(np.float32).astype(np.float64)
+
+
+def assert_normal_eq_close(gpu29, ora29, tol=NE_TOL, what="", F=None):
     gpu29 = np.asarray(gpu29)
     ora29 = np.asarray(ora29)
     Hg, Ho = O.unpack_H(gpu29[:21]), O.unpack_H(ora29[:21])
+    F = max(float(ora29[28]) if F is None else F, 1.0)
     d = np.sqrt(np.maximum(np.diag(Ho), 0.0))
     scale = np.outer(d, d) + 1e-300
     errH = np.abs(Hg - Ho) / scale
-    cost = max(ora29[27], 1e-300)
-    errg = np.abs(gpu29[21:27] - ora29[21:27]) / (d * np.sqrt(cost) + 1e-300)
-    errc = abs(gpu29[27] - ora29[27]) / cost
+    errg = np.abs(gpu29[21:27] - ora29[21:27]) / (d * np.sqrt(F) + 1e-300)
+    errc = abs(gpu29[27] - ora29[27]) / max(ora29[27], 1e-3 * F)
     msg = f"{what} H {errH.max():.2e} g {errg.max():.2e} cost {errc:.2e} n {gpu29[28]} vs {ora29[28]}"
     assert gpu29[28] == ora29[28], msg
     assert errH.max() <= tol and errg.max() <= tol and errc <= tol, msg
@@ -84,46 +93,61 @@ def device_frame(frame, T_hyps=None, **over):
     return B.FrameArgs(frame, arrs, is_device=True)
 
 
-CONVERGED_STEP = 1e-5
+CONVERGED_TRANS_M = 2e-4
+CONVERGED_ROT_RAD = 3.5e-6
 
 
-def converged(frame, oo, T) -> bool:
-    """A hypothesis has converged when the undamped Gauss-Newton step of the FP64
-    objective at its final pose (finest level) is below 1e-5 (m and rad).  Only then is
-    its end point unique; otherwise it depends on the path LM took."""
+def gn_step(frame, oo, T):
+    """Undamped Gauss-Newton step of the FP64 objective at T (finest level): its size is
+    the distance of T from the local optimum of the quadratic model."""
     E = O.evaluate(frame, oo, 0, T)
     H = O.unpack_H(E[:21])
     try:
         dx = np.linalg.solve(H, -E[21:27])
     except np.linalg.LinAlgError:
-        return False
-    return bool(np.all(np.isfinite(dx)) and np.abs(dx).max() < CONVERGED_STEP)
+        return np.inf, np.inf
+    if not np.all(np.isfinite(dx)):
+        return np.inf, np.inf
+    return float(np.linalg.norm(dx[:3])), float(np.linalg.norm(dx[3:]))
+
+
+def converged(frame, oo, T) -> bool:
+    """An end point is converged when it is within 0.2 mm and 2e-4 deg of the optimum of
+    the FP64 quadratic model (5x inside the pose tolerance).  Only then is it unique; an
+    end point still moving after the last iteration depends on the path LM took."""
+    t, r = gn_step(frame, oo, T)
+    return t < CONVERGED_TRANS_M and r < CONVERGED_ROT_RAD
 
 
 def assert_solutions_agree(frame, opts, g, o, idx=None, min_converged=1):
-    """Compare a GPU solve with the oracle's: statuses equal; converged hypotheses and
-    the selected pose within 1e-3 deg / 1 mm with costs within 1e-5; every other final
-    pose is a valid LM end point (its reported objective is the oracle's objective there)."""
+    """Compare a GPU solve with the oracle's.  Statuses must be equal.  Every hypothesis
+    whose FP64 end point is converged is unique and the GPU must reach it: pose within
+    1e-3 deg / 1 mm, objective within 1e-5.  A hypothesis still moving after its last
+    iteration ends at a path-dependent point (an FP32 accept/reject decision on a cost
+    change below FP32 resolution changes lambda and the path); there the GPU's end point
+    is checked to be valid: its reported objective is the FP64 objective at that pose."""
     oo = to_oracle_opts(opts)
     idx = list(range(len(o.status))) if idx is None else list(idx)
     n_conv = 0
     for k, m in enumerate(idx):
         assert g.status[m] == o.status[k], f"hyp {m}: status {g.status[m]} vs {o.status[k]}"
-        if o.status[k] == O.HYP_PRUNED:
+        if o.status[k] != O.HYP_OK:
             continue
-        if o.status[k] == O.HYP_OK and converged(frame, oo, o.T_cw[k]):
+        if converged(frame, oo, o.T_cw[k]):
             n_conv += 1
             assert_pose_close(g.T_cw[m], o.T_cw[k], what=f"hyp {m}")
             assert g.cost[m] == pytest.approx(o.cost[k], rel=1e-5)
-        elif o.status[k] == O.HYP_OK:
+        else:
             E = O.evaluate(frame, oo, 0, g.T_cw[m])
             assert g.cost[m] == pytest.approx(E[27], rel=1e-4), f"hyp {m}: reported objective"
     assert n_conv >= min_converged, f"only {n_conv} converged hypotheses"
     return n_conv
 
 
-def assert_selection_agrees(frame, opts, g, o, idx=None):
-    idx = list(range(len(o.status))) if idx is None else list(idx)
+def assert_selection_agrees(frame, opts, g, o):
+    """The selected pose (Sec. IV-E) is the method's output: it must agree with the
+    oracle's within 1e-3 deg / 1 mm (many hypotheses share the optimum, so the indices
+    may differ)."""
     assert (g.best >= 0) == (o.best >= 0)
     if o.best < 0:
         return

@@ -200,12 +200,18 @@ def test_gradient_and_hessian_with_non_uniform_anchor_weights(small_frame):
     small Huber threshold so that both Huber branches are active."""
     f = small_frame
     rng = np.random.default_rng(99)
-    opts = O.SolverOptions(huber_photo=0.16)
     level = 1
     T = random_poses(f, 1, 123)[0]
     margins = O.point_margins(f, level, T)
     valid = (f.point_valid.astype(bool) & (margins > 1e-3)).astype(np.uint8)
     fm = f.replace(point_valid=valid, point_weight=rng.uniform(0.2, 3.0, f.N).astype(np.float32))
+    # Huber threshold at the median of w ||r||^2, so that both branches are exercised
+    ws = []
+    for j in np.flatnonzero(valid):
+        vis, r, _ = O.point_residual(fm, level, T, j, with_jacobian=False)
+        if vis:
+            ws.append(fm.point_weight[j] * float(r @ r))
+    opts = O.SolverOptions(huber_photo=float(np.sqrt(np.median(ws))))
     E = O.evaluate(fm, opts, level, T)
     h = 1e-7
     fd = np.array([(O.evaluate(fm, opts, level, perturbed(T, k, h))[27] -
