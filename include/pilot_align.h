@@ -19,8 +19,9 @@
  *     fields); frames larger than that are rejected with PILOT_EINVAL.  A handle is not
  *     re-entrant: use one handle per host thread.
  *   - `stream` is a cudaStream_t passed as void* (NULL = the legacy default stream).
- *     Every call that takes a stream has returned all results to host memory, and has
- *     finished using the caller's input buffers, when it returns.
+ *     Every call that takes a stream, except pilot_align_normal_eq_noalloc (which only
+ *     enqueues), has returned all results to host memory, and has finished using the
+ *     caller's input buffers, when it returns.
  *   - Per-hypothesis failures (too few visible anchors, a singular damped system,
  *     non-finite values) are reported as per-hypothesis statuses, not as errors.
  *   - Readings where the paper is silent (documented at each field):
@@ -165,6 +166,28 @@ pilot_status pilot_align_debug_normal_eq(pilot_align_handle* h, const pilot_fram
  * number of kernels of this library launched by that solve. */
 pilot_status pilot_align_profile(const pilot_align_handle* h, double* build_ms,
                                  int* build_launches, int* total_launches);
+
+/* Normal equations at given poses, like pilot_align_debug_normal_eq, for callers that
+ * cannot allocate device memory.  (The paper has no counterpart: this is a deployment
+ * variant of the build-pass evaluation.)  Some callers may not call cudaMalloc: a process
+ * whose device memory is handed out by an external pool it must go through, or a
+ * latency-bound loop that cannot risk an allocation's implicit device synchronisation.
+ * This call allocates nothing and needs no handle; its scratch is a fixed array of about
+ * 2.3 MB that every GPU loading this library holds until the process exits.
+ *   cfg:    options (only the Huber thresholds are used; 0 means the default)
+ *   frame:  a DEVICE frame (is_device = 1, else PILOT_EINVAL), N <= 65536 anchors
+ *   level:  pyramid level to evaluate
+ *   T_cw:   DEVICE pointer, frame->M x 12 poses (frame->T_cw is ignored), M <= 256
+ *   out29:  DEVICE pointer, frame->M x 29 doubles, written like debug_normal_eq's out29
+ *   stream: cudaStream_t as void*; the call only enqueues work: out29 is ready when the
+ *           stream reaches that point.
+ * Sizes beyond the limits return PILOT_EINVAL with the limit in pilot_align_last_error().
+ * The first call on a device looks up the scratch address for that device (make that first
+ * call before any stream capture).  All calls share the one scratch array: calls whose work
+ * overlaps on the GPU race on it, so the caller must serialise them. */
+pilot_status pilot_align_normal_eq_noalloc(const pilot_align_config* cfg, const pilot_frame* frame,
+                                           int level, const double* T_cw, double* out29,
+                                           void* stream);
 
 /* Release the handle and its device workspace.  NULL is ignored. */
 void pilot_align_destroy(pilot_align_handle* h);

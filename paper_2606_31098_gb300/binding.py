@@ -64,6 +64,8 @@ SIGNATURES = {
     "pilot_align_solve": (ct.c_int, [_vp, ct.POINTER(pilot_frame), ct.POINTER(pilot_result), _vp]),
     "pilot_align_debug_normal_eq": (ct.c_int, [_vp, ct.POINTER(pilot_frame), ct.c_int, _vp, _vp, _vp]),
     "pilot_align_profile": (ct.c_int, [_vp, ct.POINTER(ct.c_double), ct.POINTER(ct.c_int), ct.POINTER(ct.c_int)]),
+    "pilot_align_normal_eq_noalloc": (ct.c_int, [ct.POINTER(pilot_align_config), ct.POINTER(pilot_frame), ct.c_int,
+                                                  _vp, _vp, _vp]),
     "pilot_align_destroy": (None, [_vp]),
     "pilot_align_last_error": (ct.c_char_p, []),
 }
@@ -285,6 +287,14 @@ class Solver:
         nt = ct.c_int()
         check(load().pilot_align_profile(self.h, ct.byref(ms), ct.byref(nb), ct.byref(nt)))
         return ms.value, nb.value, nt.value
+
+
+def normal_eq_noalloc(opts: Options, fa: FrameArgs, level: int, T_cw_dev, out29_dev, stream=None) -> int:
+    """pilot_align_normal_eq_noalloc: device poses in, device M x 29 out, no allocation.
+    Returns the status (the work is only enqueued on `stream`)."""
+    cfg = opts.to_c()
+    return load().pilot_align_normal_eq_noalloc(ct.byref(cfg), ct.byref(fa.c), int(level), _ptr(T_cw_dev),
+                                                 _ptr(out29_dev), Solver._stream(stream))
 
 
 def validate(opts: Options, fa: FrameArgs) -> tuple[int, str]:

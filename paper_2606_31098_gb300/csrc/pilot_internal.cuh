@@ -121,4 +121,7 @@ cudaError_t launch_finalize(HypState* st, int M, const double* min_valid, unsign
 template <pilot_dtype DT>
 cudaError_t launch_build_dtype(const BuildParams& p, cudaStream_t s);
 
+// Sets the message pilot_align_last_error() returns on the calling thread.
+void record_error(const char* msg);
+
 }  // namespace pilot

@@ -365,6 +365,10 @@ void release(pilot_align_handle* h) {
 
 }  // namespace
 
+namespace pilot {
+void record_error(const char* msg) { g_last_error = msg; }
+}  // namespace pilot
+
 extern "C" {
 
 const char* pilot_align_last_error(void) { return g_last_error.c_str(); }
