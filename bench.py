@@ -314,7 +314,7 @@ def run_ours(args):
                 "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
                         "d2h_bytes_per_step": int(d2h), "ms_per_step": e2e_ms / args.steps},
                 "gpu_launches": int(launches),
-                "roofline": {"bound": "alu", "kernel": "build pass (pilot::build_kernel<f32, 32>)",
+                "roofline": {"bound": "alu", "kernel": "build pass with fused FP64 step (pilot::build_fused_kernel<f32, 32>)",
                              "achieved": achieved_tflops, "peak": peak_tflops, "unit": "TFLOP/s",
                              "frac": achieved_tflops / peak_tflops, "traffic": traffic,
                              "peak_basis": f"FP32 FMA: {SM_COUNT} SMs x {FP32_LANES_PER_SM} lanes x 2 x {sm_max:.0f} MHz",

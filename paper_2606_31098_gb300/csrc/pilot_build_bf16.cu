@@ -4,4 +4,5 @@
 
 namespace pilot {
 template cudaError_t launch_build_dtype<PILOT_BF16>(const BuildParams&, cudaStream_t);
+template cudaError_t launch_build_fused_dtype<PILOT_BF16>(const FusedBuildParams&, cudaStream_t);
 }  // namespace pilot

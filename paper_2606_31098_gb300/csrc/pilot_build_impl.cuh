@@ -11,48 +11,86 @@
 // formed: per anchor only the 2x2 Gram matrix M = G^T G, b = G^T r and s = ||r||^2 are
 // summed over channels, then H_j = w A^T M A and g_j = w A^T b.
 //
-// Thread mapping.  A group of LP = C / CPL consecutive lanes (CPL = 4 channels per lane,
-// 8 at C = 64) works on LP anchors at a time.  Each lane projects one of them and
-// broadcasts its tap offset and bilinear weights to the group; the group then reads the
-// 4 taps of every anchor together, lane q taking channels [CPL q, CPL q + CPL), so one
-// tap is one contiguous C-element segment read by LP lanes (one 128-byte line at C = 32
-// in FP32).  A butterfly reduce-scatter over the group leaves in lane q the channel
-// sums of anchor q, and each lane finishes its own anchor (Huber weight, A, 21 + 6
-// sums) exactly once.  The CTA reduces the lanes' sums in a fixed order: the result is
-// deterministic and independent of the grid shape.
+// Thread mapping.  A group of LP consecutive lanes works on LP anchors at a time, LP
+// chosen so that one 16-byte load per lane covers a whole tap (LP = C x element size /
+// 16, at most 8: 8 lanes for FP32 at C = 32, 4 for BF16, 2 for FP8), i.e. one L1
+// wavefront per anchor and tap.  Each lane projects one anchor and broadcasts its tap
+// offset and bilinear weights to the group; the group then reads the 4 taps and the
+// reference row of every anchor together (vector k of lane q holds channels
+// VW (q + k LP) .. + VW).  A butterfly reduce-scatter over the group
+// leaves in lane q the channel sums of anchor q, and each lane finishes its own anchor
+// (Huber weight, A, 21 + 6 sums) exactly once.  An invisible anchor's partial sums stay
+// in its own reduce-scatter slot and are discarded by its owner.  The CTA reduces the
+// lanes' sums in a fixed order: the result is deterministic and independent of the
+// grid shape.
 #pragma once
 
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 #include <cuda_fp8.h>
 
+#include "pilot_fp64.cuh"
 #include "pilot_internal.cuh"
 
 namespace pilot {
 
-// Load 4 consecutive channels starting at element `idx` and widen them to FP32.
-template <pilot_dtype DT>
-__device__ __forceinline__ float4 load4(const void* base, size_t idx) {
+template <pilot_dtype DT> struct Storage;
+template <> struct Storage<PILOT_F32> { using T = float; static constexpr int VEC = 4; };
+template <> struct Storage<PILOT_BF16> { using T = uint16_t; static constexpr int VEC = 8; };
+template <> struct Storage<PILOT_F16> { using T = uint16_t; static constexpr int VEC = 8; };
+template <> struct Storage<PILOT_FP8E4M3> { using T = uint8_t; static constexpr int VEC = 16; };
+
+// Load W (4, 8 or 16) consecutive channels at p and widen them to FP32 (one 4-, 8- or
+// 16-byte load).
+template <pilot_dtype DT, int W>
+__device__ __forceinline__ void load_vec(const typename Storage<DT>::T* p, float* out) {
+    static_assert(W == 4 || W == 8 || W == 16, "vector width");
     if constexpr (DT == PILOT_F32) {
-        return __ldg(reinterpret_cast<const float4*>(static_cast<const float*>(base) + idx));
-    } else if constexpr (DT == PILOT_BF16) {
-        // bfloat16 is the upper half of an IEEE binary32: widening is a 16-bit shift
-        const uint2 r = __ldg(reinterpret_cast<const uint2*>(static_cast<const uint16_t*>(base) + idx));
-        return make_float4(__uint_as_float(r.x << 16), __uint_as_float(r.x & 0xffff0000u),
-                           __uint_as_float(r.y << 16), __uint_as_float(r.y & 0xffff0000u));
-    } else if constexpr (DT == PILOT_F16) {
-        const uint2 r = __ldg(reinterpret_cast<const uint2*>(static_cast<const uint16_t*>(base) + idx));
-        __half2 h0, h1;
-        memcpy(&h0, &r.x, 4);
-        memcpy(&h1, &r.y, 4);
-        const float2 a = __half22float2(h0), b = __half22float2(h1);
-        return make_float4(a.x, a.y, b.x, b.y);
+        static_assert(W == 4, "FP32 vectors are 4 wide");
+        const float4 v = __ldg(reinterpret_cast<const float4*>(p));
+        out[0] = v.x; out[1] = v.y; out[2] = v.z; out[3] = v.w;
+    } else if constexpr (DT == PILOT_BF16 || DT == PILOT_F16) {
+        static_assert(W <= 8, "16-bit vectors are at most 8 wide");
+        uint32_t w[W / 2];
+        if constexpr (W == 8) {
+            const uint4 r = __ldg(reinterpret_cast<const uint4*>(p));
+            w[0] = r.x; w[1] = r.y; w[2] = r.z; w[3] = r.w;
+        } else {
+            const uint2 r = __ldg(reinterpret_cast<const uint2*>(p));
+            w[0] = r.x; w[1] = r.y;
+        }
+#pragma unroll
+        for (int k = 0; k < W / 2; ++k) {
+            if constexpr (DT == PILOT_BF16) {
+                // bfloat16 is the upper half of an IEEE binary32: widening is a 16-bit shift
+                out[2 * k] = __uint_as_float(w[k] << 16);
+                out[2 * k + 1] = __uint_as_float(w[k] & 0xffff0000u);
+            } else {
+                __half2 h;
+                memcpy(&h, &w[k], 4);
+                const float2 f = __half22float2(h);
+                out[2 * k] = f.x;
+                out[2 * k + 1] = f.y;
+            }
+        }
     } else {
-        const uint32_t r = __ldg(reinterpret_cast<const uint32_t*>(static_cast<const uint8_t*>(base) + idx));
-        const __half2_raw lo = __nv_cvt_fp8x2_to_halfraw2((__nv_fp8x2_storage_t)(r & 0xffffu), __NV_E4M3);
-        const __half2_raw hi = __nv_cvt_fp8x2_to_halfraw2((__nv_fp8x2_storage_t)(r >> 16), __NV_E4M3);
-        const float2 a = __half22float2(__half2(lo)), b = __half22float2(__half2(hi));
-        return make_float4(a.x, a.y, b.x, b.y);
+        uint32_t w[W / 4];
+        if constexpr (W == 16) {
+            const uint4 r = __ldg(reinterpret_cast<const uint4*>(p));
+            w[0] = r.x; w[1] = r.y; w[2] = r.z; w[3] = r.w;
+        } else if constexpr (W == 8) {
+            const uint2 r = __ldg(reinterpret_cast<const uint2*>(p));
+            w[0] = r.x; w[1] = r.y;
+        } else {
+            w[0] = __ldg(reinterpret_cast<const uint32_t*>(p));
+        }
+#pragma unroll
+        for (int k = 0; k < W / 4; ++k) {
+            const __half2_raw lo = __nv_cvt_fp8x2_to_halfraw2((__nv_fp8x2_storage_t)(w[k] & 0xffffu), __NV_E4M3);
+            const __half2_raw hi = __nv_cvt_fp8x2_to_halfraw2((__nv_fp8x2_storage_t)(w[k] >> 16), __NV_E4M3);
+            const float2 a = __half22float2(__half2(lo)), b = __half22float2(__half2(hi));
+            out[4 * k] = a.x; out[4 * k + 1] = a.y; out[4 * k + 2] = b.x; out[4 * k + 3] = b.y;
+        }
     }
 }
 
@@ -61,16 +99,16 @@ struct ChanSums {
 };
 
 // One channel: bilinear value and in-cell gradient, residual, and the six sums.
+template <bool SCALED>
 __device__ __forceinline__ void channel(ChanSums& a, float t00, float t01, float t10, float t11,
-                                        float fr, float ax, float ay, bool scaled, float sq,
-                                        float sr) {
+                                        float fr, float ax, float ay, float sq, float sr) {
     const float bq = t01 - t00;              // d/dx along the upper row
     const float cq = t10 - t00;              // d/dy along the left column
     const float dq = (t11 - t10) - bq;       // bilinear cross term
     float fu = fmaf(dq, ay, bq);             // df/du inside the cell
     float fv = fmaf(dq, ax, cq);             // df/dv inside the cell
     float f = fmaf(ax, fu, fmaf(ay, cq, t00));
-    if (scaled) {
+    if constexpr (SCALED) {
         f *= sq;
         fu *= sq;
         fv *= sq;
@@ -85,66 +123,78 @@ __device__ __forceinline__ void channel(ChanSums& a, float t00, float t01, float
     a.b1 = fmaf(fv, r, a.b1);
 }
 
-template <pilot_dtype DT, int C>
-__global__ void __launch_bounds__(kBuildThreads)
-build_kernel(const BuildParams p) {
-    static_assert(C % 4 == 0 && C >= 4 && C <= 64, "channels");
-    constexpr int CPL = (C >= 64) ? 8 : 4;          // channels per lane
-    constexpr int NV = CPL / 4;                     // 4-channel vectors per lane and tap
-    constexpr int LP = C / CPL;                     // lanes per group = anchors per batch
-    constexpr int GROUPS = kBuildThreads / LP;
-    constexpr int BATCH = GROUPS * LP;              // anchors per CTA pass
-    static_assert(LP >= 1 && LP <= 16 && (LP & (LP - 1)) == 0, "group size");
-    __shared__ float red[kBuildThreads / 32][kAcc];
+// The level-specific inputs of the anchor loop.
+struct LevelView {
+    const float* px;
+    const float* py;
+    const float* pz;
+    const float* weight;
+    const uint8_t* valid;
+    const void* qry;
+    const void* ref;
+    const float* qscale;
+    const float* rscale;
+    int H, W;
+    float fx, fy, cx, cy, huber;
+};
 
-    const int slot = blockIdx.y;
-    const int hyp = p.active_idx[slot];
-    float* out = p.partial + ((size_t)slot * p.n_tiles + blockIdx.x) * kAcc;
-    if (!p.state[hyp].has_cand) return;            // uniform over the CTA
+__device__ __forceinline__ LevelView level_view(const BuildParams& p) {
+    return LevelView{p.px, p.py, p.pz, p.weight, p.valid, p.qry, p.ref, p.qscale, p.rscale,
+                     p.H, p.W, p.fx, p.fy, p.cx, p.cy, p.huber};
+}
+
+// Accumulate anchors [j_begin, j_end) at pose P (12 FP32 values) into this lane's 29
+// sums.  Every thread of the CTA calls it with the same range; threads are grouped as
+// described at the top of the file.
+template <pilot_dtype DT, int C, bool SCALED, int NTHREADS>
+__device__ __forceinline__ void accumulate_anchors(const LevelView& v, const float* P, int j_begin,
+                                                   int j_end, float* acc) {
+    using Elem = typename Storage<DT>::T;
+    constexpr int VEC = Storage<DT>::VEC;            // channels per 16-byte vector
+    constexpr int VW = (C < VEC) ? C : VEC;          // channels per vector load
+    constexpr int LP = (C / VW < 8) ? C / VW : 8;    // lanes per group = anchors per batch
+    constexpr int CPL = C / LP;                      // channels per lane
+    constexpr int NV = CPL / VW;                     // vector loads per lane and tap
+    constexpr int GROUPS = NTHREADS / LP;
+    constexpr int BATCH = GROUPS * LP;
+    static_assert(C % 4 == 0 && C >= 4 && C <= 64 && LP >= 1 && LP <= 8, "channels");
 
     const int tid = threadIdx.x;
-    const int lane = tid & 31, warp = tid >> 5;
-    const int q = lane & (LP - 1);                  // lane within the group
+    const int lane = tid & 31;
+    const int q = lane & (LP - 1);
     const int grp = tid / LP;
-    const int src0 = lane & ~(LP - 1);              // first lane of the group
-    const unsigned gmask = (LP == 32) ? 0xffffffffu : (((1u << LP) - 1u) << src0);
+    const int src0 = lane & ~(LP - 1);
+    const unsigned gmask = (((1u << LP) - 1u) << src0);
 
-    const float* P = p.pose32 + 12 * hyp;
     const float R00 = P[0], R01 = P[1], R02 = P[2], T0 = P[3];
     const float R10 = P[4], R11 = P[5], R12 = P[6], T1 = P[7];
     const float R20 = P[8], R21 = P[9], R22 = P[10], T2 = P[11];
 
-    const bool scaled = p.qscale != nullptr;
+    // channels owned by this lane: vector k covers VW (q + k LP) .. + VW
     float qs[CPL], rs[CPL];
 #pragma unroll
-    for (int v = 0; v < NV; ++v) {
-        float4 a = make_float4(1.f, 1.f, 1.f, 1.f), b = a;
-        if (scaled) {
-            a = __ldg(reinterpret_cast<const float4*>(p.qscale) + q * NV + v);
-            b = __ldg(reinterpret_cast<const float4*>(p.rscale) + q * NV + v);
-        }
-        qs[4 * v] = a.x; qs[4 * v + 1] = a.y; qs[4 * v + 2] = a.z; qs[4 * v + 3] = a.w;
-        rs[4 * v] = b.x; rs[4 * v + 1] = b.y; rs[4 * v + 2] = b.z; rs[4 * v + 3] = b.w;
-    }
-
-    float acc[kNumSums];
+    for (int k = 0; k < NV; ++k)
 #pragma unroll
-    for (int i = 0; i < kNumSums; ++i) acc[i] = 0.f;
+        for (int e = 0; e < VW; ++e) {
+            const int ch = VW * (q + k * LP) + e;
+            qs[k * VW + e] = SCALED ? __ldg(v.qscale + ch) : 1.0f;
+            rs[k * VW + e] = SCALED ? __ldg(v.rscale + ch) : 1.0f;
+        }
 
-    const int j0 = blockIdx.x * p.tile;
-    const int j1 = min(j0 + p.tile, p.N);
-    const int WC = p.W * C;
-    const float xmax = (float)(p.W - 1), ymax = (float)(p.H - 1);
-    const float d2 = p.huber * p.huber;
+    const Elem* qry = static_cast<const Elem*>(v.qry);
+    const Elem* ref = static_cast<const Elem*>(v.ref);
+    const int WC = v.W * C;
+    const float xmax = (float)(v.W - 1), ymax = (float)(v.H - 1);
+    const float d2 = v.huber * v.huber;
 
-    for (int jb = j0 + grp * LP; jb < j1; jb += BATCH) {
+    for (int jb = j_begin + grp * LP; jb < j_end; jb += BATCH) {
         // 1. every lane projects its own anchor jb + q
         const int jo = jb + q;
         bool vis = false;
         int off = 0;
         float ax = 0.f, ay = 0.f, x = 0.f, y = 0.f, z = 1.f, iz = 1.f;
-        if (jo < j1 && (!p.valid || p.valid[jo])) {
-            const float X = __ldg(p.px + jo), Y = __ldg(p.py + jo), Z = __ldg(p.pz + jo);
+        if (jo < j_end && (!v.valid || v.valid[jo])) {
+            const float X = __ldg(v.px + jo), Y = __ldg(v.py + jo), Z = __ldg(v.pz + jo);
             // p = R P + t  (world -> camera)
             x = fmaf(R00, X, fmaf(R01, Y, fmaf(R02, Z, T0)));
             y = fmaf(R10, X, fmaf(R11, Y, fmaf(R12, Z, T1)));
@@ -152,62 +202,89 @@ build_kernel(const BuildParams p) {
             if (z > kZNear) {
                 iz = 1.0f / z;
                 // pixel i covers [i, i+1): array coordinate = pixel - 1/2
-                const float xs = fmaf(p.fx * x, iz, p.cx) - 0.5f;
-                const float ys = fmaf(p.fy * y, iz, p.cy) - 0.5f;
+                const float xs = fmaf(v.fx * x, iz, v.cx) - 0.5f;
+                const float ys = fmaf(v.fy * y, iz, v.cy) - 0.5f;
                 if (xs >= 0.f && xs <= xmax && ys >= 0.f && ys <= ymax) {
-                    const int c0 = min((int)xs, p.W - 2);
-                    const int r0 = min((int)ys, p.H - 2);
+                    const int c0 = min((int)xs, v.W - 2);
+                    const int r0 = min((int)ys, v.H - 2);
                     ax = xs - (float)c0;
                     ay = ys - (float)r0;
-                    off = (r0 * p.W + c0) * C;
+                    off = (r0 * v.W + c0) * C;
                     vis = true;
                 }
             }
         }
 
-        // 2. the group gathers its LP anchors together: lane q reads channels
-        //    [CPL q, CPL q + CPL) of the 4 taps and of the reference row of each
-        float S[LP][6];
+        // 2. the group reads the taps of its LP anchors together, two at a time: anchors
+        //    t and t + LP/2 are read, then the first butterfly round (xor LP/2) keeps in
+        //    each lane only the half it owns, so only LP/2 partial records stay live
+        constexpr int HALF = (LP > 1) ? LP / 2 : 1;
+        float S[HALF][6];
 #pragma unroll
-        for (int i = 0; i < LP; ++i) {
-            const int vi = __shfl_sync(gmask, (int)vis, src0 + i);
-            const int oi = __shfl_sync(gmask, off, src0 + i) + CPL * q;
-            const float axi = __shfl_sync(gmask, ax, src0 + i);
-            const float ayi = __shfl_sync(gmask, ay, src0 + i);
-            const int ri = (vi ? jb + i : 0) * C + CPL * q;   // row 0 is a safe dummy
-            ChanSums cs{0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+        for (int t = 0; t < HALF; ++t) {
+            float P2[2][6];
 #pragma unroll
-            for (int v = 0; v < NV; ++v) {
-                const float4 a00 = load4<DT>(p.qry, (size_t)oi + 4 * v);
-                const float4 a01 = load4<DT>(p.qry, (size_t)oi + C + 4 * v);
-                const float4 a10 = load4<DT>(p.qry, (size_t)oi + WC + 4 * v);
-                const float4 a11 = load4<DT>(p.qry, (size_t)oi + WC + C + 4 * v);
-                const float4 fr = load4<DT>(p.ref, (size_t)ri + 4 * v);
-                channel(cs, a00.x, a01.x, a10.x, a11.x, fr.x, axi, ayi, scaled, qs[4 * v], rs[4 * v]);
-                channel(cs, a00.y, a01.y, a10.y, a11.y, fr.y, axi, ayi, scaled, qs[4 * v + 1], rs[4 * v + 1]);
-                channel(cs, a00.z, a01.z, a10.z, a11.z, fr.z, axi, ayi, scaled, qs[4 * v + 2], rs[4 * v + 2]);
-                channel(cs, a00.w, a01.w, a10.w, a11.w, fr.w, axi, ayi, scaled, qs[4 * v + 3], rs[4 * v + 3]);
+            for (int u = 0; u < ((LP > 1) ? 2 : 1); ++u) {
+                const int i = t + u * HALF;
+                int vi = (int)vis, oi = off;
+                float axi = ax, ayi = ay;
+                if constexpr (LP > 1) {
+                    vi = __shfl_sync(gmask, (int)vis, src0 + i);
+                    oi = __shfl_sync(gmask, off, src0 + i);
+                    axi = __shfl_sync(gmask, ax, src0 + i);
+                    ayi = __shfl_sync(gmask, ay, src0 + i);
+                }
+                const int ri = (vi ? jb + i : 0) * C;    // row 0 is a safe dummy
+                const Elem* t00 = qry + oi;
+                const Elem* t10 = t00 + WC;
+                const Elem* fr = ref + ri;
+                ChanSums cs{0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+                for (int k = 0; k < NV; ++k) {
+                    const int c = VW * (q + k * LP);
+                    float a00[VW], a01[VW], a10[VW], a11[VW], rr[VW];
+                    load_vec<DT, VW>(t00 + c, a00);
+                    load_vec<DT, VW>(t00 + c + C, a01);
+                    load_vec<DT, VW>(t10 + c, a10);
+                    load_vec<DT, VW>(t10 + c + C, a11);
+                    load_vec<DT, VW>(fr + c, rr);
+#pragma unroll
+                    for (int e = 0; e < VW; ++e)
+                        channel<SCALED>(cs, a00[e], a01[e], a10[e], a11[e], rr[e], axi, ayi,
+                                        qs[k * VW + e], rs[k * VW + e]);
+                }
+                P2[u][0] = cs.s;
+                P2[u][1] = cs.m00;
+                P2[u][2] = cs.m01;
+                P2[u][3] = cs.m11;
+                P2[u][4] = cs.b0;
+                P2[u][5] = cs.b1;
             }
-            const float m = vi ? 1.0f : 0.0f;
-            S[i][0] = cs.s * m;
-            S[i][1] = cs.m00 * m;
-            S[i][2] = cs.m01 * m;
-            S[i][3] = cs.m11 * m;
-            S[i][4] = cs.b0 * m;
-            S[i][5] = cs.b1 * m;
+            if constexpr (LP > 1) {
+                const bool upper = (q & HALF) != 0;
+#pragma unroll
+                for (int k = 0; k < 6; ++k) {
+                    const float send = upper ? P2[0][k] : P2[1][k];
+                    const float keep = upper ? P2[1][k] : P2[0][k];
+                    S[t][k] = keep + __shfl_xor_sync(gmask, send, HALF);
+                }
+            } else {
+#pragma unroll
+                for (int k = 0; k < 6; ++k) S[t][k] = P2[0][k];
+            }
         }
 
-        // 3. butterfly reduce-scatter: afterwards S[0] of lane q holds anchor q's sums
+        // 3. remaining butterfly rounds: afterwards S[0] of lane q holds anchor q's sums
 #pragma unroll
-        for (int half = LP / 2; half >= 1; half >>= 1) {
+        for (int half = HALF / 2; half >= 1; half >>= 1) {
             const bool upper = (q & half) != 0;
 #pragma unroll
             for (int t = 0; t < half; ++t) {
 #pragma unroll
-                for (int v = 0; v < 6; ++v) {
-                    const float send = upper ? S[t][v] : S[t + half][v];
-                    const float keep = upper ? S[t + half][v] : S[t][v];
-                    S[t][v] = keep + __shfl_xor_sync(gmask, send, half);
+                for (int k = 0; k < 6; ++k) {
+                    const float send = upper ? S[t][k] : S[t + half][k];
+                    const float keep = upper ? S[t + half][k] : S[t][k];
+                    S[t][k] = keep + __shfl_xor_sync(gmask, send, half);
                 }
             }
         }
@@ -217,7 +294,7 @@ build_kernel(const BuildParams p) {
         if (vis) {
             const float s = S[0][0], m00 = S[0][1], m01 = S[0][2], m11 = S[0][3];
             const float b0 = S[0][4], b1 = S[0][5];
-            const float w = p.weight ? __ldg(p.weight + jo) : 1.0f;
+            const float w = v.weight ? __ldg(v.weight + jo) : 1.0f;
             const float sw = w * s;
             float rho, drho;
             if (sw <= d2) {
@@ -225,13 +302,13 @@ build_kernel(const BuildParams p) {
                 drho = 1.0f;
             } else {
                 const float rt = sqrtf(sw);
-                rho = 2.0f * p.huber * rt - d2;
-                drho = p.huber / rt;
+                rho = 2.0f * v.huber * rt - d2;
+                drho = v.huber / rt;
             }
             const float om = w * drho;
             // the rotational part of each row a of d(u,v)/dp is p x a
-            const float du_dx = p.fx * iz, du_dz = -p.fx * x * iz * iz;
-            const float dv_dy = p.fy * iz, dv_dz = -p.fy * y * iz * iz;
+            const float du_dx = v.fx * iz, du_dz = -v.fx * x * iz * iz;
+            const float dv_dy = v.fy * iz, dv_dz = -v.fy * y * iz * iz;
             const float A0[6] = {du_dx, 0.f, du_dz, y * du_dz, z * du_dx - x * du_dz, -y * du_dx};
             const float A1[6] = {0.f, dv_dy, dv_dz, y * dv_dz - z * dv_dy, -x * dv_dz, x * dv_dy};
             float B0[6], B1[6], W0[6], W1[6];
@@ -257,8 +334,12 @@ build_kernel(const BuildParams p) {
             acc[28] += 1.0f;
         }
     }
+}
 
-    // Each lane holds distinct anchors: reduce across the warp, then across warps.
+// Fixed-order CTA reduction of the lanes' 29 sums; thread t < kAcc returns sum t (0 pads).
+template <int NTHREADS>
+__device__ __forceinline__ float cta_reduce(float* acc, float (*red)[kAcc]) {
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
 #pragma unroll
     for (int off = 1; off < 32; off <<= 1) {
 #pragma unroll
@@ -269,20 +350,101 @@ build_kernel(const BuildParams p) {
         for (int i = 0; i < kNumSums; ++i) red[warp][i] = acc[i];
     }
     __syncthreads();
-    if (tid < kAcc) {
-        float v = 0.f;
-        if (tid < kNumSums) {
+    float v = 0.f;
+    if (tid < kNumSums) {
 #pragma unroll
-            for (int w = 0; w < kBuildThreads / 32; ++w) v += red[w][tid];
-        }
-        out[tid] = v;
+        for (int w = 0; w < NTHREADS / 32; ++w) v += red[w][tid];
+    }
+    return v;
+}
+
+template <pilot_dtype DT, int C, bool SCALED>
+__global__ void __launch_bounds__(kBuildThreads)
+build_kernel(const BuildParams p) {
+    __shared__ float red[kBuildThreads / 32][kAcc];
+    const int slot = blockIdx.y;
+    const int hyp = p.active_idx[slot];
+    float* out = p.partial + ((size_t)slot * p.n_tiles + blockIdx.x) * kAcc;
+    if (!p.state[hyp].has_cand) return;            // uniform over the CTA
+    float acc[kNumSums];
+#pragma unroll
+    for (int i = 0; i < kNumSums; ++i) acc[i] = 0.f;
+    const int j0 = blockIdx.x * p.tile;
+    accumulate_anchors<DT, C, SCALED, kBuildThreads>(level_view(p), p.pose32 + 12 * hyp, j0,
+                                                     min(j0 + p.tile, p.N), acc);
+    const float v = cta_reduce<kBuildThreads>(acc, red);
+    if (threadIdx.x < kAcc) out[threadIdx.x] = v;
+}
+
+// The same pass with the per-hypothesis FP64 step fused in: the CTA that takes the last
+// ticket of its hypothesis sums the tile records (FP64, 8 chains per value, fixed order)
+// and runs lm_step.  A hypothesis without a candidate runs its step in tile 0's CTA.
+template <pilot_dtype DT, int C, bool SCALED>
+__global__ void __launch_bounds__(kBuildThreads)
+build_fused_kernel(const FusedBuildParams fp) {
+    const BuildParams& p = fp.b;
+    __shared__ float red[kBuildThreads / 32][kAcc];
+    __shared__ double part[8][kAcc];
+    __shared__ double E[kAcc];
+    __shared__ int s_last;
+    const int slot = blockIdx.y;
+    const int hyp = p.active_idx[slot];
+    const int tid = threadIdx.x;
+    if (!p.state[hyp].has_cand) {                  // uniform over the CTA
+        if (blockIdx.x == 0 && tid == 0) lm_step(fp.ep, slot, E, *fp.min_valid);
+        return;
+    }
+    float acc[kNumSums];
+#pragma unroll
+    for (int i = 0; i < kNumSums; ++i) acc[i] = 0.f;
+    const int j0 = blockIdx.x * p.tile;
+    accumulate_anchors<DT, C, SCALED, kBuildThreads>(level_view(p), p.pose32 + 12 * hyp, j0,
+                                                     min(j0 + p.tile, p.N), acc);
+    const float v = cta_reduce<kBuildThreads>(acc, red);
+    float* out = p.partial + ((size_t)slot * p.n_tiles + blockIdx.x) * kAcc;
+    if (tid < kAcc) out[tid] = v;
+    __threadfence();
+    __syncthreads();
+    if (tid == 0) s_last = (atomicAdd(fp.tickets + slot, 1u) == (unsigned)(p.n_tiles - 1));
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
+    const int vi = tid & 31, c = tid >> 5;
+    const float* src = p.partial + (size_t)slot * p.n_tiles * kAcc + vi;
+    double a = 0.0;
+    for (int t = c; t < p.n_tiles; t += 8) a += (double)__ldcg(src + (size_t)t * kAcc);
+    part[c][vi] = a;
+    __syncthreads();
+    if (tid < kAcc) {
+        double sum = 0.0;
+#pragma unroll
+        for (int k = 0; k < 8; ++k) sum += part[k][tid];
+        E[tid] = sum;
+    }
+    __syncthreads();
+    if (tid == 0) {
+        lm_step(fp.ep, slot, E, *fp.min_valid);
+        fp.tickets[slot] = 0u;
     }
 }
 
 template <pilot_dtype DT, int C>
 cudaError_t launch_build_typed(const BuildParams& p, cudaStream_t s) {
     dim3 grid(p.n_tiles, p.n_active);
-    build_kernel<DT, C><<<grid, kBuildThreads, 0, s>>>(p);
+    if (p.qscale)
+        build_kernel<DT, C, true><<<grid, kBuildThreads, 0, s>>>(p);
+    else
+        build_kernel<DT, C, false><<<grid, kBuildThreads, 0, s>>>(p);
+    return cudaGetLastError();
+}
+
+template <pilot_dtype DT, int C>
+cudaError_t launch_build_fused_typed(const FusedBuildParams& p, cudaStream_t s) {
+    dim3 grid(p.b.n_tiles, p.b.n_active);
+    if (p.b.qscale)
+        build_fused_kernel<DT, C, true><<<grid, kBuildThreads, 0, s>>>(p);
+    else
+        build_fused_kernel<DT, C, false><<<grid, kBuildThreads, 0, s>>>(p);
     return cudaGetLastError();
 }
 
@@ -294,6 +456,18 @@ cudaError_t launch_build_dtype(const BuildParams& p, cudaStream_t s) {
         case 16: return launch_build_typed<DT, 16>(p, s);
         case 32: return launch_build_typed<DT, 32>(p, s);
         case 64: return launch_build_typed<DT, 64>(p, s);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+template <pilot_dtype DT>
+cudaError_t launch_build_fused_dtype(const FusedBuildParams& p, cudaStream_t s) {
+    switch (p.b.C) {
+        case 4: return launch_build_fused_typed<DT, 4>(p, s);
+        case 8: return launch_build_fused_typed<DT, 8>(p, s);
+        case 16: return launch_build_fused_typed<DT, 16>(p, s);
+        case 32: return launch_build_fused_typed<DT, 32>(p, s);
+        case 64: return launch_build_fused_typed<DT, 64>(p, s);
         default: return cudaErrorInvalidValue;
     }
 }

@@ -88,6 +88,15 @@ struct EpilogueParams {
     double* eval_out;          // kEpiEval: [slot][29]
 };
 
+// A build pass whose last CTA per hypothesis runs the FP64 LM step itself (the CTA that
+// takes the last ticket of its hypothesis sums the tile records and calls lm_step).
+struct FusedBuildParams {
+    BuildParams b;
+    EpilogueParams ep;
+    unsigned* tickets;         // [n_active], zero between launches
+    const double* min_valid;
+};
+
 // Result block copied to the host in one transfer.
 struct ResultLayout {
     size_t off_T, off_cost, off_nvalid, off_status, off_best, bytes;
@@ -120,6 +129,8 @@ cudaError_t launch_finalize(HypState* st, int M, const double* min_valid, unsign
 
 template <pilot_dtype DT>
 cudaError_t launch_build_dtype(const BuildParams& p, cudaStream_t s);
+template <pilot_dtype DT>
+cudaError_t launch_build_fused_dtype(const FusedBuildParams& p, cudaStream_t s);
 
 // Sets the message pilot_align_last_error() returns on the calling thread.
 void record_error(const char* msg);

@@ -5,9 +5,9 @@
 //   count_valid  (min_valid = frac x valid anchors)    hyp_init (FP64 state from T_cw)
 //   for l = L-1 .. 0:
 //     level_init (lambda = lambda0, candidate = T)
-//     build(l) -> epilogue(init: store E(T), solve first candidate)
-//     repeat iters[l] times: build(l) at the candidates -> epilogue(step: accept or
-//       reject, solve the next candidate)
+//     build(l) with the FP64 step fused (init: store E(T), solve the first candidate)
+//     repeat iters[l] times: build(l) at the candidates, fused step (accept or reject,
+//       solve the next candidate)
 //     optional prune (keep_top_k[l])
 //   finalize (statuses, argmin) -> one device-to-host copy of the result block
 #include <cuda_runtime.h>
@@ -114,8 +114,8 @@ pilot_status validate_frame(const pilot_align_config& c, const pilot_frame* f) {
             return fail(PILOT_EINVAL, "level %d map has 2^31 or more elements", l);
         if (!f->qry_feat[l]) return fail(PILOT_EINVAL, "qry_feat[%d] is NULL", l);
         if (f->N > 0 && !f->ref_feat[l]) return fail(PILOT_EINVAL, "ref_feat[%d] is NULL", l);
-        if (!aligned(f->qry_feat[l], 4 * es) || (f->ref_feat[l] && !aligned(f->ref_feat[l], 4 * es)))
-            return fail(PILOT_EINVAL, "level %d feature pointers must be aligned to 4 elements (%zu bytes)", l, 4 * es);
+        if (!aligned(f->qry_feat[l], 16) || (f->ref_feat[l] && !aligned(f->ref_feat[l], 16)))
+            return fail(PILOT_EINVAL, "level %d feature pointers must be 16-byte aligned", l);
         if ((f->qry_scale[l] && !aligned(f->qry_scale[l], 16)) || (f->ref_scale[l] && !aligned(f->ref_scale[l], 16)))
             return fail(PILOT_EINVAL, "level %d scale pointers must be 16-byte aligned", l);
     }
@@ -156,6 +156,7 @@ struct pilot_align_handle {
     double* Tin = nullptr;
     double* eval_out = nullptr;
     double* min_valid = nullptr;
+    unsigned* tickets = nullptr;
     float* ones = nullptr;
     unsigned char* res_dev = nullptr;
     unsigned char* res_host = nullptr;
@@ -315,7 +316,19 @@ cudaError_t dispatch_build(pilot_dtype dt, const BuildParams& b, cudaStream_t s)
     return cudaErrorInvalidValue;
 }
 
-pilot_status run_build(pilot_align_handle* h, pilot_dtype dt, const BuildParams& b, cudaStream_t s) {
+cudaError_t dispatch_build_fused(pilot_dtype dt, const FusedBuildParams& b, cudaStream_t s) {
+    switch (dt) {
+        case PILOT_F32: return launch_build_fused_dtype<PILOT_F32>(b, s);
+        case PILOT_BF16: return launch_build_fused_dtype<PILOT_BF16>(b, s);
+        case PILOT_F16: return launch_build_fused_dtype<PILOT_F16>(b, s);
+        case PILOT_FP8E4M3: return launch_build_fused_dtype<PILOT_FP8E4M3>(b, s);
+    }
+    return cudaErrorInvalidValue;
+}
+
+// One build launch, plain (ep == nullptr) or with the FP64 step fused in.
+pilot_status run_build(pilot_align_handle* h, pilot_dtype dt, const BuildParams& b, cudaStream_t s,
+                       const EpilogueParams* ep = nullptr) {
     const bool prof = h->cfg.profile != 0;
     size_t k = 2 * (size_t)h->build_launches;
     if (prof) {
@@ -326,7 +339,12 @@ pilot_status run_build(pilot_align_handle* h, pilot_dtype dt, const BuildParams&
         }
         PILOT_CUDA(cudaEventRecord(h->events[k], s), "event record");
     }
-    PILOT_CUDA(dispatch_build(dt, b, s), "build-pass launch");
+    if (ep) {
+        FusedBuildParams fb{b, *ep, h->tickets, h->min_valid};
+        PILOT_CUDA(dispatch_build_fused(dt, fb, s), "fused build-pass launch");
+    } else {
+        PILOT_CUDA(dispatch_build(dt, b, s), "build-pass launch");
+    }
     if (prof) PILOT_CUDA(cudaEventRecord(h->events[k + 1], s), "event record");
     ++h->build_launches;
     ++h->total_launches;
@@ -354,6 +372,7 @@ void release(pilot_align_handle* h) {
     cudaFree(h->Tin);
     cudaFree(h->eval_out);
     cudaFree(h->min_valid);
+    cudaFree(h->tickets);
     cudaFree(h->ones);
     cudaFree(h->res_dev);
     if (h->res_host) cudaFreeHost(h->res_host);
@@ -411,6 +430,7 @@ pilot_status pilot_align_create(const pilot_align_config* cfg_in, pilot_align_ha
     ALLOC(h->Tin, sizeof(double) * 12 * M);
     ALLOC(h->eval_out, sizeof(double) * kNumSums * M);
     ALLOC(h->min_valid, sizeof(double));
+    ALLOC(h->tickets, sizeof(unsigned) * M);
     ALLOC(h->ones, sizeof(float) * cfg.max_channels);
     ALLOC(h->res_dev, lay.bytes);
 #undef ALLOC
@@ -418,7 +438,8 @@ pilot_status pilot_align_create(const pilot_align_config* cfg_in, pilot_align_ha
         release(h);
         return cuda_fail(e, "pinned result buffer");
     }
-    if ((e = cudaMemcpy(h->ones, ones.data(), sizeof(float) * cfg.max_channels, cudaMemcpyHostToDevice)) != cudaSuccess) {
+    if ((e = cudaMemcpy(h->ones, ones.data(), sizeof(float) * cfg.max_channels, cudaMemcpyHostToDevice)) != cudaSuccess ||
+        (e = cudaMemset(h->tickets, 0, sizeof(unsigned) * M)) != cudaSuccess) {
         release(h);
         return cuda_fail(e, "workspace init");
     }
@@ -454,6 +475,7 @@ pilot_status pilot_align_solve(pilot_align_handle* h, const pilot_frame* f, pilo
     if ((st = bind_frame(h, f, s, &d, true)) != PILOT_OK) return st;
     const int M = f->M;
 
+    PILOT_CUDA(cudaMemsetAsync(h->tickets, 0, sizeof(unsigned) * M, s), "ticket reset");
     PILOT_CUDA(launch_count_valid(d.valid, f->N, c.min_valid_frac, h->min_valid, s), "count_valid launch");
     PILOT_CUDA(launch_hyp_init(h->state, d.T, h->active[0], M, s), "hyp_init launch");
     h->total_launches += 2;
@@ -476,11 +498,9 @@ pilot_status pilot_align_solve(pilot_align_handle* h, const pilot_frame* f, pilo
         PILOT_CUDA(launch_level_init(h->state, h->pose32, h->active[cur], n_active, c.lambda0, s), "level_init launch");
         ++h->total_launches;
         for (int k = 0; k <= iters; ++k) {
-            if ((st = run_build(h, f->feat_dtype, b, s)) != PILOT_OK) return st;
             ep.mode = (k == 0) ? kEpiInit : kEpiStep;
             ep.solve_next = k < iters;
-            PILOT_CUDA(launch_epilogue(ep, h->min_valid, s), "epilogue launch");
-            ++h->total_launches;
+            if ((st = run_build(h, f->feat_dtype, b, s, &ep)) != PILOT_OK) return st;
         }
         hyp_iters += (long long)n_active * iters;
         const int K = c.keep_top_k[level];
