@@ -271,6 +271,16 @@ def run_ours(args):
     torch.cuda.synchronize()
     clk = clocks.stop()
 
+    # the same plain form on reduced-precision storage (GPU-quantised maps, FP32 math)
+    precision = {}
+    for dt in (B.BF16, B.FP8E4M3):
+        qa = B.FrameArgs(frame, B.quantized_device_arrays(frame, dt), is_device=True, dtype=dt)
+        for _ in range(2):
+            solver.solve(qa, stream)
+        qt, qb, qn, _, qu, _ = timed(qa, max(3, args.steps // 3))
+        precision[B.DTYPE_NAMES[dt]] = {"value": world * qu / (sum(qt) / 1e3), "unit": UNIT,
+                                        "ms_per_step": sum(qt) / len(qt), "build_avg_launch_ms": qb / max(qn, 1)}
+
     total_ms = sum(times)
     e2e_ms = sum(e2e_times)
     if world > 1:
@@ -322,6 +332,7 @@ def run_ours(args):
                              "avg_launch_ms": avg_launch_ms, "launches": build_n,
                              "gather_bytes_per_unit": gather_bytes_per_unit(C, elem), "gather_GBps": gather_gbs,
                              "build_share_of_step": build_ms / total_ms},
+                "precision_forms": precision,
                 "clocks": clk,
                 "cpu_baseline": cpu}
         print(json.dumps(line), flush=True)

@@ -189,6 +189,20 @@ pilot_status pilot_align_normal_eq_noalloc(const pilot_align_config* cfg, const 
                                            int level, const double* T_cw, double* out29,
                                            void* stream);
 
+/* Quantise feature rows for reduced-precision storage (the precision form of the path:
+ * feature pyramids in BF16, FP16 or FP8-E4M3 with FP32 arithmetic).  DEVICE pointers:
+ *   src   rows x C FP32 (16-byte aligned), e.g. an H x W x C map (rows = H W) or an
+ *         N x C reference block
+ *   dst   rows x C elements of `dtype` (BF16, F16 or FP8E4M3)
+ *   scale C FP32 per-channel scales, written: s_c = absmax_c / q_max when per_channel = 1
+ *         or dtype = FP8E4M3 (q_max = 448 for E4M3, 65504 for F16, 1 for BF16), else 1;
+ *         a channel whose absmax is 0 gets s_c = 1
+ * dst = round(src / s_c) (FP32 product with the reciprocal of s_c), rounded to nearest
+ * even, E4M3 saturating at +-448.  The value the solver uses is dst x s_c: pass `scale` as
+ * the frame's qry_scale / ref_scale.  Only enqueues work on `stream`; allocates nothing. */
+pilot_status pilot_quantize_features(const float* src, long long rows, int C, pilot_dtype dtype,
+                                     int per_channel, void* dst, float* scale, void* stream);
+
 /* Release the handle and its device workspace.  NULL is ignored. */
 void pilot_align_destroy(pilot_align_handle* h);
 

@@ -66,6 +66,7 @@ SIGNATURES = {
     "pilot_align_profile": (ct.c_int, [_vp, ct.POINTER(ct.c_double), ct.POINTER(ct.c_int), ct.POINTER(ct.c_int)]),
     "pilot_align_normal_eq_noalloc": (ct.c_int, [ct.POINTER(pilot_align_config), ct.POINTER(pilot_frame), ct.c_int,
                                                   _vp, _vp, _vp]),
+    "pilot_quantize_features": (ct.c_int, [_vp, ct.c_longlong, ct.c_int, ct.c_int, ct.c_int, _vp, _vp, _vp]),
     "pilot_align_destroy": (None, [_vp]),
     "pilot_align_last_error": (ct.c_char_p, []),
 }
@@ -295,6 +296,36 @@ def normal_eq_noalloc(opts: Options, fa: FrameArgs, level: int, T_cw_dev, out29_
     cfg = opts.to_c()
     return load().pilot_align_normal_eq_noalloc(ct.byref(cfg), ct.byref(fa.c), int(level), _ptr(T_cw_dev),
                                                  _ptr(out29_dev), Solver._stream(stream))
+
+
+def quantize_features(src, dtype: int, per_channel: bool = False, stream=None):
+    """pilot_quantize_features on a contiguous FP32 CUDA tensor (..., C): returns the
+    quantised tensor (torch bfloat16 / float16 / uint8 bytes for E4M3) and the C scales."""
+    import torch
+    src = src.contiguous()
+    C = int(src.shape[-1])
+    rows = src.numel() // C
+    tdt = {BF16: torch.bfloat16, F16: torch.float16, FP8E4M3: torch.uint8}[dtype]
+    dst = torch.empty(src.shape, dtype=tdt, device=src.device)
+    scale = torch.empty(C, dtype=torch.float32, device=src.device)
+    check(load().pilot_quantize_features(src.data_ptr(), rows, C, dtype, int(per_channel), dst.data_ptr(),
+                                         scale.data_ptr(), Solver._stream(stream)))
+    return dst, scale
+
+
+def quantized_device_arrays(frame, dtype: int, per_channel: bool = False, T_hyps=None, device="cuda") -> dict:
+    """Device arrays of a frame with the query maps and reference descriptors quantised on
+    the GPU (each map and each reference block with its own per-channel scales)."""
+    arrs = device_arrays(frame, T_hyps, device)
+    if dtype == F32:
+        return arrs
+    qf, qs, rf, rs = [], [], [], []
+    for q, r in zip(arrs["qry_feat"], arrs["ref_feat"]):
+        a, sa = quantize_features(q, dtype, per_channel)
+        b, sb = quantize_features(r, dtype, per_channel) if r.numel() else (r.to(a.dtype), sa.clone())
+        qf.append(a); qs.append(sa); rf.append(b); rs.append(sb)
+    arrs.update(qry_feat=qf, qry_scale=qs, ref_feat=rf, ref_scale=rs)
+    return arrs
 
 
 def validate(opts: Options, fa: FrameArgs) -> tuple[int, str]:
