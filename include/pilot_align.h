@@ -89,6 +89,8 @@ typedef struct {
     int max_hyps;
     int max_channels;
     int profile;             /* 1: time every build-pass launch with CUDA events */
+    int max_frames;          /* batched form: largest number of frames per call; 0 -> 64
+                                (max_hyps then bounds the hypotheses of the whole batch) */
 } pilot_align_config;
 
 /* One query frame.  All pointers are owned by the caller and are either all device
@@ -152,6 +154,20 @@ pilot_status pilot_align_validate(const pilot_align_config* cfg, const pilot_fra
 pilot_status pilot_align_solve(pilot_align_handle* h, const pilot_frame* frame,
                                pilot_result* result, void* stream);
 
+/* Batched form: solve n_frames independent frames (uneven N, M, map sizes, intrinsics,
+ * priors) in one pass per pyramid level.  Each level is one persistent launch whose CTAs
+ * pull (frame, hypothesis) jobs, longest first, and run a job's whole LM loop at that
+ * level; the launches, the per-frame top-K and the selection are replayed from a CUDA
+ * graph captured on the first call (and again when the storage type, C or L changes).
+ * Requirements: every frame is a DEVICE frame; all frames share C, L, feat_dtype and the
+ * presence of per-channel scales; n_frames <= max_frames; the hypotheses of all frames
+ * together <= max_hyps, at most 8192 per frame.  results[i] receives frame i's outputs
+ * exactly as pilot_align_solve would (the reduction order is the same, so each frame's
+ * outputs are bitwise those of its own pilot_align_solve, whatever else is in the batch).
+ * Synchronous on `stream`. */
+pilot_status pilot_align_solve_batch(pilot_align_handle* h, const pilot_frame* frames, int n_frames,
+                                     pilot_result* results, void* stream);
+
 /* Evaluate the normal equations of the total objective (Eq. 7, Eq. 8) at the given
  * poses on one level, without any LM step: out29 (HOST, M x 29 doubles) receives per
  * pose the 21 upper-triangle entries of J^T W J (row-major), the 6 entries of J^T W r,
@@ -205,6 +221,50 @@ pilot_status pilot_quantize_features(const float* src, long long rows, int C, pi
 
 /* Release the handle and its device workspace.  NULL is ignored. */
 void pilot_align_destroy(pilot_align_handle* h);
+
+/* ---- Serving: continuous batching of frames from many concurrent streams ----
+ *
+ * A server owns a worker thread and the current CUDA device.  Frames are admitted when a
+ * slot is free, their hypotheses fit in cfg.max_hyps (shared by all admitted frames) and
+ * their data fit in the device arena of hbm_budget bytes; admission copies the frame into
+ * the arena, where its pyramid and LM state stay until it completes.  The worker then runs
+ * rounds: in each round every admitted frame advances one pyramid level, all frames sharing
+ * one persistent launch (replayed from a CUDA graph) whatever level each is at; frames that
+ * arrive meanwhile join at the next round.  A frame's outputs are exactly those
+ * pilot_align_solve gives for it, however many other frames are being served.  All served
+ * frames must share C, L, feat_dtype and the presence of scales (fixed by the first frame). */
+typedef struct pilot_server pilot_server;
+
+typedef struct {
+    long long rounds, admitted, completed, pending, active, peak_active;
+    long long arena_bytes_in_use, arena_bytes_peak;
+} pilot_serve_stats;
+
+/* cfg: solver options (max_hyps bounds the hypotheses of all admitted frames together);
+ * hbm_budget: device bytes reserved for frame data; max_slots: most frames admitted at once. */
+pilot_status pilot_serve_create(const pilot_align_config* cfg, size_t hbm_budget, int max_slots,
+                                pilot_server** out);
+
+/* Queue a frame (host or device pointers, which must stay valid and unchanged until the
+ * ticket is reported done).  Returns PILOT_EBUSY when the pending queue (4 x max_slots + 64)
+ * is full, PILOT_EINVAL for a frame that could never be admitted. */
+pilot_status pilot_serve_submit(pilot_server* s, const pilot_frame* frame, uint64_t* ticket);
+
+/* Non-blocking: *done = 1 once the frame completed; its outputs are then copied into
+ * `result` (may be NULL), *latency_ms (may be NULL) is submit-to-completion wall time, and
+ * the ticket is retired. */
+pilot_status pilot_serve_poll(pilot_server* s, uint64_t ticket, pilot_result* result, int* done,
+                              double* latency_ms);
+
+/* Blocking form of poll; PILOT_ETIMEOUT after timeout_ms. */
+pilot_status pilot_serve_wait(pilot_server* s, uint64_t ticket, pilot_result* result,
+                              double* latency_ms, int timeout_ms);
+
+pilot_status pilot_serve_get_stats(pilot_server* s, pilot_serve_stats* out);
+
+/* Stops the worker after its current round and releases everything; tickets not yet
+ * polled are dropped.  NULL is ignored. */
+void pilot_serve_destroy(pilot_server* s);
 
 /* Message describing the last failure on the calling thread ("" if none). */
 const char* pilot_align_last_error(void);

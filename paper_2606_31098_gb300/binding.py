@@ -30,7 +30,7 @@ class pilot_align_config(ct.Structure):
         ("damping_mode", ct.c_int), ("huber_photo", ct.c_double), ("huber_grav", ct.c_double),
         ("huber_range", ct.c_double), ("keep_top_k", ct.c_int * MAX_LEVELS),
         ("min_valid_frac", ct.c_double), ("max_points", ct.c_int), ("max_hyps", ct.c_int),
-        ("max_channels", ct.c_int), ("profile", ct.c_int),
+        ("max_channels", ct.c_int), ("profile", ct.c_int), ("max_frames", ct.c_int),
     ]
 
 
@@ -62,6 +62,7 @@ SIGNATURES = {
     "pilot_align_create": (ct.c_int, [ct.POINTER(pilot_align_config), ct.POINTER(_vp)]),
     "pilot_align_validate": (ct.c_int, [ct.POINTER(pilot_align_config), ct.POINTER(pilot_frame)]),
     "pilot_align_solve": (ct.c_int, [_vp, ct.POINTER(pilot_frame), ct.POINTER(pilot_result), _vp]),
+    "pilot_align_solve_batch": (ct.c_int, [_vp, _vp, ct.c_int, _vp, _vp]),
     "pilot_align_debug_normal_eq": (ct.c_int, [_vp, ct.POINTER(pilot_frame), ct.c_int, _vp, _vp, _vp]),
     "pilot_align_profile": (ct.c_int, [_vp, ct.POINTER(ct.c_double), ct.POINTER(ct.c_int), ct.POINTER(ct.c_int)]),
     "pilot_align_normal_eq_noalloc": (ct.c_int, [ct.POINTER(pilot_align_config), ct.POINTER(pilot_frame), ct.c_int,
@@ -69,7 +70,19 @@ SIGNATURES = {
     "pilot_quantize_features": (ct.c_int, [_vp, ct.c_longlong, ct.c_int, ct.c_int, ct.c_int, _vp, _vp, _vp]),
     "pilot_align_destroy": (None, [_vp]),
     "pilot_align_last_error": (ct.c_char_p, []),
+    "pilot_serve_create": (ct.c_int, [ct.POINTER(pilot_align_config), ct.c_size_t, ct.c_int, ct.POINTER(_vp)]),
+    "pilot_serve_submit": (ct.c_int, [_vp, ct.POINTER(pilot_frame), ct.POINTER(ct.c_uint64)]),
+    "pilot_serve_poll": (ct.c_int, [_vp, ct.c_uint64, ct.POINTER(pilot_result), ct.POINTER(ct.c_int),
+                                    ct.POINTER(ct.c_double)]),
+    "pilot_serve_wait": (ct.c_int, [_vp, ct.c_uint64, ct.POINTER(pilot_result), ct.POINTER(ct.c_double), ct.c_int]),
+    "pilot_serve_get_stats": (ct.c_int, [_vp, _vp]),
+    "pilot_serve_destroy": (None, [_vp]),
 }
+
+
+class pilot_serve_stats(ct.Structure):
+    _fields_ = [(n, ct.c_longlong) for n in ("rounds", "admitted", "completed", "pending", "active",
+                                             "peak_active", "arena_bytes_in_use", "arena_bytes_peak")]
 
 
 def load(path: str = LIB_PATH):
@@ -117,6 +130,7 @@ class Options:
     max_hyps: int = 256
     max_channels: int = 32
     profile: int = 0
+    max_frames: int = 64
 
     def to_c(self) -> pilot_align_config:
         c = pilot_align_config()
@@ -128,6 +142,7 @@ class Options:
         c.min_valid_frac = self.min_valid_frac
         c.max_points, c.max_hyps, c.max_channels = self.max_points, self.max_hyps, self.max_channels
         c.profile = self.profile
+        c.max_frames = self.max_frames
         return c
 
 
@@ -274,6 +289,24 @@ class Solver:
         check(load().pilot_align_solve(self.h, ct.byref(fa.c), ct.byref(r), self._stream(stream)))
         return Result(T, cost, nv, st, int(best[0]), int(hi[0]))
 
+    def solve_batch(self, fas: list, stream=None) -> list:
+        """pilot_align_solve_batch over a list of device FrameArgs."""
+        n = len(fas)
+        frames = (pilot_frame * max(n, 1))()
+        for i, fa in enumerate(fas):
+            frames[i] = fa.c
+        outs, res = [], (pilot_result * max(n, 1))()
+        for i, fa in enumerate(fas):
+            M = fa.M
+            o = dict(T=np.zeros((M, 12)), cost=np.zeros(M), nv=np.zeros(M, np.int32), st=np.zeros(M, np.int32),
+                     best=np.zeros(1, np.int32), hi=np.zeros(1, np.int64))
+            res[i] = pilot_result(o["T"].ctypes.data, o["cost"].ctypes.data, o["nv"].ctypes.data,
+                                  o["st"].ctypes.data, o["best"].ctypes.data, o["hi"].ctypes.data)
+            outs.append(o)
+        check(load().pilot_align_solve_batch(self.h, ct.cast(frames, _vp), n, ct.cast(res, _vp),
+                                             self._stream(stream)))
+        return [Result(o["T"], o["cost"], o["nv"], o["st"], int(o["best"][0]), int(o["hi"][0])) for o in outs]
+
     def normal_eq(self, fa: FrameArgs, level: int, T_cw, stream=None) -> np.ndarray:
         T = np.ascontiguousarray(T_cw, np.float64).reshape(-1, 12)
         assert T.shape[0] == fa.M
@@ -332,3 +365,67 @@ def validate(opts: Options, fa: FrameArgs) -> tuple[int, str]:
     cfg = opts.to_c()
     st = load().pilot_align_validate(ct.byref(cfg), ct.byref(fa.c))
     return st, pilot_align_last_error()
+
+
+class Server:
+    """pilot_serve_*: continuous-batching server over one CUDA device."""
+
+    def __init__(self, opts: Options, hbm_budget: int, max_slots: int):
+        lib = load()
+        self._cfg = opts.to_c()
+        h = _vp()
+        check(lib.pilot_serve_create(ct.byref(self._cfg), int(hbm_budget), int(max_slots), ct.byref(h)))
+        self.h = h
+        self._frames = {}
+
+    def submit(self, fa: FrameArgs) -> int:
+        """Queue a frame; returns its ticket (raises PilotError, status PILOT_EBUSY, when the
+        pending queue is full).  `fa` is kept alive until the ticket is collected."""
+        t = ct.c_uint64()
+        check(load().pilot_serve_submit(self.h, ct.byref(fa.c), ct.byref(t)))
+        self._frames[t.value] = fa
+        return t.value
+
+    def _result_bufs(self, M):
+        o = dict(T=np.zeros((M, 12)), cost=np.zeros(M), nv=np.zeros(M, np.int32), st=np.zeros(M, np.int32),
+                 best=np.zeros(1, np.int32), hi=np.zeros(1, np.int64))
+        r = pilot_result(o["T"].ctypes.data, o["cost"].ctypes.data, o["nv"].ctypes.data, o["st"].ctypes.data,
+                         o["best"].ctypes.data, o["hi"].ctypes.data)
+        return o, r
+
+    def poll(self, ticket: int):
+        """(done, Result or None, latency_ms)."""
+        fa = self._frames[ticket]
+        o, r = self._result_bufs(fa.M)
+        done = ct.c_int()
+        lat = ct.c_double()
+        check(load().pilot_serve_poll(self.h, ct.c_uint64(ticket), ct.byref(r), ct.byref(done), ct.byref(lat)))
+        if not done.value:
+            return False, None, None
+        del self._frames[ticket]
+        return True, Result(o["T"], o["cost"], o["nv"], o["st"], int(o["best"][0]), int(o["hi"][0])), lat.value
+
+    def wait(self, ticket: int, timeout_ms: int = 600000):
+        fa = self._frames[ticket]
+        o, r = self._result_bufs(fa.M)
+        lat = ct.c_double()
+        check(load().pilot_serve_wait(self.h, ct.c_uint64(ticket), ct.byref(r), ct.byref(lat), int(timeout_ms)))
+        del self._frames[ticket]
+        return Result(o["T"], o["cost"], o["nv"], o["st"], int(o["best"][0]), int(o["hi"][0])), lat.value
+
+    def stats(self) -> dict:
+        st = pilot_serve_stats()
+        check(load().pilot_serve_get_stats(self.h, ct.cast(ct.byref(st), _vp)))
+        return {n: getattr(st, n) for n, _ in pilot_serve_stats._fields_}
+
+    def close(self):
+        if getattr(self, "h", None) is not None and self.h.value:
+            load().pilot_serve_destroy(self.h)
+            self.h = None
+            self._frames.clear()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -201,7 +201,220 @@ __global__ void finalize_kernel(HypState* st, int M, const double* min_valid_ptr
     if (threadIdx.x == 0) *best = bi[0];
 }
 
+// ---- batched form and serving rounds: one block per frame ----
+
+__device__ void init_frame(const FrameDesc& f, HypState* st, int* active) {
+    for (int m = threadIdx.x; m < f.M; m += blockDim.x) {
+        HypState& s = st[f.hyp_offset + m];
+        for (int i = 0; i < 12; ++i) s.T[i] = s.Tc[i] = f.T_cw[12 * m + i];
+        for (int i = 0; i < 21; ++i) s.H[i] = 0.0;
+        for (int i = 0; i < 6; ++i) s.g[i] = 0.0;
+        s.cost = 0.0;
+        s.lambda = 0.0;
+        s.n_valid = 0;
+        s.has_cand = 0;
+        s.last_fail = 0;
+        s.active = 1;
+        s.status = PILOT_HYP_OK;
+        active[f.hyp_offset + m] = m;
+    }
+}
+
+// min_valid of one frame (block-wide; blockDim.x a multiple of 32, <= 1024)
+__device__ void count_frame(const FrameDesc& f, double frac, double* min_valid) {
+    __shared__ int part[32];
+    int c = 0;
+    for (int j = threadIdx.x; j < f.N; j += blockDim.x) c += f.valid ? (f.valid[j] != 0) : 1;
+    for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
+    if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = c;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        int v = (threadIdx.x < (blockDim.x >> 5)) ? part[threadIdx.x] : 0;
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if (threadIdx.x == 0) *min_valid = frac * (double)v;
+    }
+    __syncthreads();
+}
+
+// Top-K of one frame among its n active hypotheses (same ranking as prune_kernel).  The
+// frame's active list is compacted in place (read fully before any write; at most 8
+// survivors per thread, so blockDim.x x 8 >= n).
+__device__ void prune_frame(const FrameDesc& f, HypState* st, int* active, int n, int K, double mv) {
+    if (K <= 0 || K >= n) return;
+    int* act = active + f.hyp_offset;
+    HypState* S = st + f.hyp_offset;
+    for (int s = threadIdx.x; s < n; s += blockDim.x) {
+        const int m = act[s];
+        int rank = 0;
+        for (int s2 = 0; s2 < n; ++s2) {
+            const int m2 = act[s2];
+            rank += ranks_before(S[m2], m2, S[m], m, mv) ? 1 : 0;
+        }
+        if (rank >= K) {
+            S[m].active = 0;
+            S[m].status = PILOT_HYP_PRUNED;
+        }
+    }
+    __syncthreads();
+    int keep_pos[8];
+    int keep_val[8];
+    int nk = 0;
+    for (int s = threadIdx.x; s < n && nk < 8; s += blockDim.x) {
+        const int m = act[s];
+        if (!S[m].active) continue;
+        int pos = 0;
+        for (int s2 = 0; s2 < s; ++s2) pos += S[act[s2]].active;
+        keep_pos[nk] = pos;
+        keep_val[nk] = m;
+        ++nk;
+    }
+    __syncthreads();
+    for (int i = 0; i < nk; ++i) act[keep_pos[i]] = keep_val[i];
+    __syncthreads();
+}
+
+// Statuses, per-hypothesis outputs (at the global hypothesis index) and the argmin of
+// one frame.  blockDim.x <= 1024, a power of two.
+__device__ void finalize_frame(const FrameDesc& f, int fi, HypState* st, double mv,
+                               unsigned char* res, int max_hyps) {
+    const ResultLayout lay = ResultLayout::make(max_hyps);
+    double* T = reinterpret_cast<double*>(res + lay.off_T);
+    double* cost = reinterpret_cast<double*>(res + lay.off_cost);
+    int* nv = reinterpret_cast<int*>(res + lay.off_nvalid);
+    int* status = reinterpret_cast<int*>(res + lay.off_status);
+    int* best = reinterpret_cast<int*>(res + lay.bytes);      // one int per frame after the block
+    __shared__ double bc[1024];
+    __shared__ int bi[1024];
+    double my_c = 0.0;
+    int my_i = -1;
+    for (int m = threadIdx.x; m < f.M; m += blockDim.x) {
+        const int g = f.hyp_offset + m;
+        HypState& s = st[g];
+        if (s.active) {
+            bool finite = isfinite(s.cost);
+            for (int i = 0; i < 12; ++i) finite = finite && isfinite(s.T[i]);
+            int code;
+            if (!finite) code = PILOT_HYP_NONFINITE;
+            else if (s.n_valid < mv) code = PILOT_HYP_FEW_VALID;
+            else if (s.last_fail) code = PILOT_HYP_NOT_PD;
+            else code = PILOT_HYP_OK;
+            s.status = code;
+        }
+        for (int i = 0; i < 12; ++i) T[12 * (size_t)g + i] = s.T[i];
+        cost[g] = s.cost;
+        nv[g] = s.n_valid;
+        status[g] = s.status;
+        if (s.status == PILOT_HYP_OK && (my_i < 0 || s.cost < my_c)) {
+            my_c = s.cost;
+            my_i = m;
+        }
+    }
+    bc[threadIdx.x] = my_c;
+    bi[threadIdx.x] = my_i;
+    __syncthreads();
+    for (int k = blockDim.x / 2; k > 0; k >>= 1) {
+        if ((int)threadIdx.x < k) {
+            const int j = threadIdx.x + k;
+            const bool take = bi[j] >= 0 &&
+                              (bi[threadIdx.x] < 0 || bc[j] < bc[threadIdx.x] ||
+                               (bc[j] == bc[threadIdx.x] && bi[j] < bi[threadIdx.x]));
+            if (take) {
+                bc[threadIdx.x] = bc[j];
+                bi[threadIdx.x] = bi[j];
+            }
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) best[fi] = bi[0];
+}
+
+__global__ void batch_init_kernel(const BatchHeader* hdr, const FrameDesc* frames, HypState* st,
+                                  int* active) {
+    if ((int)blockIdx.x >= hdr->n_frames) return;
+    init_frame(frames[blockIdx.x], st, active);
+}
+
+__global__ void batch_count_valid_kernel(const BatchHeader* hdr, const FrameDesc* frames, double frac,
+                                         double* min_valid) {
+    if ((int)blockIdx.x >= hdr->n_frames) return;
+    count_frame(frames[blockIdx.x], frac, min_valid + blockIdx.x);
+}
+
+__global__ void batch_prune_kernel(const BatchHeader* hdr, const FrameDesc* frames, HypState* st,
+                                   int* active, const int* n_active, int K, const double* min_valid) {
+    const int fi = blockIdx.x;
+    if (fi >= hdr->n_frames) return;
+    prune_frame(frames[fi], st, active, n_active[fi], K, min_valid[fi]);
+}
+
+__global__ void batch_finalize_kernel(const BatchHeader* hdr, const FrameDesc* frames, HypState* st,
+                                      const double* min_valid, unsigned char* res, int max_hyps) {
+    const int fi = blockIdx.x;
+    if (fi >= hdr->n_frames) return;
+    finalize_frame(frames[fi], fi, st, min_valid[fi], res, max_hyps);
+}
+
+__global__ void round_prepare_kernel(const BatchHeader* hdr, const FrameDesc* frames, HypState* st,
+                                     int* active, double frac, double* min_valid) {
+    const int fi = blockIdx.x;
+    if (fi >= hdr->n_frames) return;
+    const FrameDesc& f = frames[fi];
+    if (!(f.flags & kFlagInit)) return;
+    init_frame(f, st, active);
+    count_frame(f, frac, min_valid + fi);
+}
+
+__global__ void round_finish_kernel(const BatchHeader* hdr, const FrameDesc* frames, HypState* st,
+                                    int* active, const double* min_valid, unsigned char* res,
+                                    int max_hyps) {
+    const int fi = blockIdx.x;
+    if (fi >= hdr->n_frames) return;
+    const FrameDesc& f = frames[fi];
+    if (f.flags & kFlagPrune) prune_frame(f, st, active, f.n_active, f.keep, min_valid[fi]);
+    if (f.flags & kFlagFinalize) finalize_frame(f, fi, st, min_valid[fi], res, max_hyps);
+}
+
 }  // namespace
+
+cudaError_t launch_batch_init(const BatchHeader* hdr, const FrameDesc* frames, HypState* st,
+                              int* active, int max_frames, cudaStream_t s) {
+    batch_init_kernel<<<max_frames, 128, 0, s>>>(hdr, frames, st, active);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_batch_count_valid(const BatchHeader* hdr, const FrameDesc* frames, double frac,
+                                     double* min_valid, int max_frames, cudaStream_t s) {
+    batch_count_valid_kernel<<<max_frames, 1024, 0, s>>>(hdr, frames, frac, min_valid);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_batch_prune(const BatchHeader* hdr, const FrameDesc* frames, HypState* st,
+                               int* active, const int* n_active, int keep, const double* min_valid,
+                               int max_frames, cudaStream_t s) {
+    batch_prune_kernel<<<max_frames, 1024, 0, s>>>(hdr, frames, st, active, n_active, keep, min_valid);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_batch_finalize(const BatchHeader* hdr, const FrameDesc* frames, HypState* st,
+                                  const double* min_valid, unsigned char* result, int max_hyps,
+                                  int max_frames, cudaStream_t s) {
+    batch_finalize_kernel<<<max_frames, 1024, 0, s>>>(hdr, frames, st, min_valid, result, max_hyps);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_round_prepare(const BatchHeader* hdr, const FrameDesc* frames, HypState* st,
+                                 int* active, double frac, double* min_valid, int max_frames,
+                                 cudaStream_t s) {
+    round_prepare_kernel<<<max_frames, 1024, 0, s>>>(hdr, frames, st, active, frac, min_valid);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_round_finish(const BatchHeader* hdr, const FrameDesc* frames, HypState* st,
+                                int* active, const double* min_valid, unsigned char* result,
+                                int max_hyps, int max_frames, cudaStream_t s) {
+    round_finish_kernel<<<max_frames, 1024, 0, s>>>(hdr, frames, st, active, min_valid, result, max_hyps);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_epilogue(const EpilogueParams& p, const double* min_valid, cudaStream_t s) {
     if (p.n_active <= 0) return cudaSuccess;

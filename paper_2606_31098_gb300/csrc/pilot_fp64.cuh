@@ -183,24 +183,25 @@ __device__ __forceinline__ void store_pose32(float* dst, const double* T) {
     for (int i = 0; i < 12; ++i) dst[i] = (float)T[i];
 }
 
-// One hypothesis' FP64 step after its build pass: E (29 sums, photo only on entry) gets
-// the priors at the evaluated pose, then (init) becomes the current state, or (step) is
-// accepted or rejected, then the next candidate is solved for.  Single thread.
-__device__ inline void lm_step(const EpilogueParams& p, int slot, double* E, double min_valid) {
-    const int hyp = p.active_idx[slot];
-    HypState& st = p.state[hyp];
-    const bool evaluated = (p.mode == kEpiStep) ? (st.has_cand != 0) : true;
-    const double* Tev = (p.mode == kEpiStep) ? st.Tc : st.T;
+// One hypothesis' FP64 step after a build pass at its candidate.  E (29 sums, photo term
+// only on entry) gets the priors at the evaluated pose; then (init) it becomes the current
+// state, or (step) the candidate is accepted or rejected; then the next candidate is
+// solved for and, if cand32 is given, written there in FP32.  Single thread.
+__device__ inline void lm_update(HypState& st, int mode, int solve_next, int damping_mode,
+                                 const PriorParams& prior, double* E, double min_valid,
+                                 float* cand32, double* eval_out) {
+    const bool evaluated = (mode == kEpiStep) ? (st.has_cand != 0) : true;
+    const double* Tev = (mode == kEpiStep) ? st.Tc : st.T;
     if (evaluated) {
-        if (p.prior.use_gravity) add_gravity(p.prior, Tev, E);
-        if (p.prior.use_range) add_range(p.prior, Tev, E);
+        if (prior.use_gravity) add_gravity(prior, Tev, E);
+        if (prior.use_range) add_range(prior, Tev, E);
     }
-    if (p.mode == kEpiEval) {
-        for (int i = 0; i < kNumSums; ++i) p.eval_out[(size_t)slot * kNumSums + i] = E[i];
+    if (mode == kEpiEval) {
+        for (int i = 0; i < kNumSums; ++i) eval_out[i] = E[i];
         st.has_cand = 0;
         return;
     }
-    if (p.mode == kEpiInit) {
+    if (mode == kEpiInit) {
         for (int i = 0; i < 21; ++i) st.H[i] = E[i];
         for (int i = 0; i < 6; ++i) st.g[i] = E[21 + i];
         st.cost = E[27];
@@ -218,18 +219,25 @@ __device__ inline void lm_step(const EpilogueParams& p, int slot, double* E, dou
         }
     }
     st.has_cand = 0;
-    if (p.solve_next) {
+    if (solve_next) {
         double dxi[6];
-        if (!damped_solve(st.H, st.g, st.lambda, p.damping_mode, dxi)) {
+        if (!damped_solve(st.H, st.g, st.lambda, damping_mode, dxi)) {
             st.lambda = fmin(st.lambda * 10.0, kLambdaMax);
             st.last_fail = 1;
         } else {
             st.last_fail = 0;
             pose_update(dxi, st.T, st.Tc);
-            store_pose32(p.pose32 + 12 * hyp, st.Tc);
+            if (cand32) store_pose32(cand32, st.Tc);
             st.has_cand = 1;
         }
     }
+}
+
+// lm_update for slot `slot` of a launch described by p (candidate written to p.pose32).
+__device__ inline void lm_step(const EpilogueParams& p, int slot, double* E, double min_valid) {
+    const int hyp = p.active_idx[slot];
+    lm_update(p.state[hyp], p.mode, p.solve_next, p.damping_mode, p.prior, E, min_valid,
+              p.pose32 + 12 * hyp, p.eval_out ? p.eval_out + (size_t)slot * kNumSums : nullptr);
 }
 
 }  // namespace pilot

@@ -97,10 +97,64 @@ struct FusedBuildParams {
     const double* min_valid;
 };
 
+// ---- batched form: many frames, one persistent launch per pyramid level ----
+
+// One frame of a batch, as the device kernels see it.
+struct FrameDesc {
+    const float* px;
+    const float* py;
+    const float* pz;
+    const float* weight;
+    const uint8_t* valid;
+    const void* ref[PILOT_MAX_LEVELS];
+    const void* qry[PILOT_MAX_LEVELS];
+    const float* rscale[PILOT_MAX_LEVELS];
+    const float* qscale[PILOT_MAX_LEVELS];
+    int N, M;
+    int H[PILOT_MAX_LEVELS], W[PILOT_MAX_LEVELS];
+    float fx[PILOT_MAX_LEVELS], fy[PILOT_MAX_LEVELS], cx[PILOT_MAX_LEVELS], cy[PILOT_MAX_LEVELS];
+    const double* T_cw;        // M x 12 initial hypotheses
+    int hyp_offset;            // first global hypothesis (state, active list, results)
+    int level;                 // serving: the level this frame runs in the current round
+    int n_active;              // serving: hypotheses still active at that level
+    int flags;                 // serving: kFlagInit | kFlagPrune | kFlagFinalize
+    int keep;                  // serving: top-K after this level (kFlagPrune)
+    int pad;
+    PriorParams prior;
+};
+
+enum FrameFlags { kFlagInit = 1, kFlagPrune = 2, kFlagFinalize = 4 };
+
+// Batch header, rewritten before every batch (the captured graph reads it).
+struct BatchHeader {
+    int n_frames;
+    int n_jobs[PILOT_MAX_LEVELS];
+    int total_hyps;
+};
+
+// Persistent level kernel arguments.  Job j of level l is (job_frame[j], job_slot[j]):
+// the job_slot-th entry of that frame's active list.
+struct LevelArgs {
+    const BatchHeader* header;
+    const FrameDesc* frames;
+    const int* job_frame;
+    const int* job_slot;
+    const int* active;         // per frame: active[hyp_offset + slot] = local hypothesis
+    HypState* state;           // global hypothesis index
+    const double* min_valid;   // per frame
+    int* counter;              // job counter of this level (zero before the launch)
+    int level;                 // >= 0: every frame runs this level; -1: each its own level
+    int n_jobs_index;          // which header->n_jobs entry counts this launch's jobs
+    int iters[PILOT_MAX_LEVELS];
+    int tile, damping_mode;
+    float huber;
+    double lambda0;
+};
+
 // Result block copied to the host in one transfer.
 struct ResultLayout {
     size_t off_T, off_cost, off_nvalid, off_status, off_best, bytes;
-    static ResultLayout make(int M) {
+    __host__ __device__ static ResultLayout make(int M) {
         ResultLayout r;
         r.off_T = 0;
         r.off_cost = r.off_T + sizeof(double) * 12 * (size_t)M;
@@ -132,7 +186,43 @@ cudaError_t launch_build_dtype(const BuildParams& p, cudaStream_t s);
 template <pilot_dtype DT>
 cudaError_t launch_build_fused_dtype(const FusedBuildParams& p, cudaStream_t s);
 
+template <pilot_dtype DT>
+cudaError_t launch_level_persistent_dtype(int C, bool scaled, const LevelArgs& a, int grid,
+                                          cudaStream_t s);
+template <pilot_dtype DT>
+cudaError_t level_persistent_occupancy(int C, bool scaled, int* ctas_per_sm);
+
+// batch bookkeeping (one block per frame; frames beyond header->n_frames return)
+cudaError_t launch_batch_init(const BatchHeader* hdr, const FrameDesc* frames, HypState* st,
+                              int* active, int max_frames, cudaStream_t s);
+cudaError_t launch_batch_count_valid(const BatchHeader* hdr, const FrameDesc* frames, double frac,
+                                     double* min_valid, int max_frames, cudaStream_t s);
+cudaError_t launch_batch_prune(const BatchHeader* hdr, const FrameDesc* frames, HypState* st,
+                               int* active, const int* n_active, int keep, const double* min_valid,
+                               int max_frames, cudaStream_t s);
+cudaError_t launch_batch_finalize(const BatchHeader* hdr, const FrameDesc* frames, HypState* st,
+                                  const double* min_valid, unsigned char* result, int max_hyps,
+                                  int max_frames, cudaStream_t s);
+// serving rounds: the same steps, each frame doing only what its flags ask for
+cudaError_t launch_round_prepare(const BatchHeader* hdr, const FrameDesc* frames, HypState* st,
+                                 int* active, double frac, double* min_valid, int max_frames,
+                                 cudaStream_t s);
+cudaError_t launch_round_finish(const BatchHeader* hdr, const FrameDesc* frames, HypState* st,
+                                int* active, const double* min_valid, unsigned char* result,
+                                int max_hyps, int max_frames, cudaStream_t s);
+
 // Sets the message pilot_align_last_error() returns on the calling thread.
 void record_error(const char* msg);
+const char* last_error_message();
+
+// host helpers shared by the runtime's translation units
+pilot_align_config config_with_defaults(const pilot_align_config& c);
+pilot_status check_config(const pilot_align_config& c);
+pilot_status check_frame(const pilot_align_config& c, const pilot_frame* f);
+size_t dtype_bytes(pilot_dtype dt);
+PriorParams frame_prior(const pilot_align_config& c, const pilot_frame* f, const float* dsm_dev);
+cudaError_t level_launch(pilot_dtype dt, int C, bool scaled, const LevelArgs& a, int grid, cudaStream_t s);
+cudaError_t level_occupancy_query(pilot_dtype dt, int C, bool scaled, int* n);
+constexpr int kPlainTile = 1024;
 
 }  // namespace pilot

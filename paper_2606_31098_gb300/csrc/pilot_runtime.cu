@@ -16,6 +16,7 @@
 #include <stdio.h>
 #include <string.h>
 
+#include <algorithm>
 #include <string>
 #include <vector>
 
@@ -71,6 +72,7 @@ pilot_align_config with_defaults(const pilot_align_config& in) {
     if (c.max_points == 0) c.max_points = 1 << 18;
     if (c.max_hyps == 0) c.max_hyps = 256;
     if (c.max_channels == 0) c.max_channels = 32;
+    if (c.max_frames == 0) c.max_frames = 64;
     return c;
 }
 
@@ -89,6 +91,7 @@ pilot_status validate_config(const pilot_align_config& c) {
     if (c.max_points < 0 || c.max_hyps < 1) return fail(PILOT_EINVAL, "max_points >= 0 and max_hyps >= 1 required");
     if (!channels_supported(c.max_channels))
         return fail(PILOT_EINVAL, "max_channels must be one of 4, 8, 16, 32, 64");
+    if (c.max_frames < 1 || c.max_frames > 65536) return fail(PILOT_EINVAL, "max_frames must be in [1, 65536]");
     return PILOT_OK;
 }
 
@@ -162,6 +165,21 @@ struct pilot_align_handle {
     unsigned char* res_host = nullptr;
     DevBuf stage[kStCount];
     std::vector<cudaEvent_t> events;
+    // batched form
+    unsigned char* bdesc_dev = nullptr;
+    unsigned char* bdesc_host = nullptr;
+    size_t bdesc_bytes = 0;
+    unsigned char* bres_dev = nullptr;
+    unsigned char* bres_host = nullptr;
+    size_t bres_bytes = 0;
+    int* bactive = nullptr;
+    double* bmin_valid = nullptr;
+    int* bcounters = nullptr;
+    cudaStream_t bstream = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t gexec = nullptr;
+    long long graph_key = -1;
+    int level_grid = 0;
     int build_launches = 0;
     int total_launches = 0;
     double build_ms = 0.0;
@@ -379,6 +397,16 @@ void release(pilot_align_handle* h) {
     for (auto& b : h->stage)
         if (b.ptr) cudaFree(b.ptr);
     for (auto e : h->events) cudaEventDestroy(e);
+    if (h->gexec) cudaGraphExecDestroy(h->gexec);
+    if (h->graph) cudaGraphDestroy(h->graph);
+    cudaFree(h->bdesc_dev);
+    if (h->bdesc_host) cudaFreeHost(h->bdesc_host);
+    cudaFree(h->bres_dev);
+    if (h->bres_host) cudaFreeHost(h->bres_host);
+    cudaFree(h->bactive);
+    cudaFree(h->bmin_valid);
+    cudaFree(h->bcounters);
+    if (h->bstream) cudaStreamDestroy(h->bstream);
     delete h;
 }
 
@@ -386,7 +414,157 @@ void release(pilot_align_handle* h) {
 
 namespace pilot {
 void record_error(const char* msg) { g_last_error = msg; }
+const char* last_error_message() { return g_last_error.c_str(); }
+pilot_align_config config_with_defaults(const pilot_align_config& c) { return with_defaults(c); }
+pilot_status check_config(const pilot_align_config& c) { return validate_config(c); }
+pilot_status check_frame(const pilot_align_config& c, const pilot_frame* f) { return validate_frame(c, f); }
+size_t dtype_bytes(pilot_dtype dt) { return dtype_size(dt); }
+PriorParams frame_prior(const pilot_align_config& c, const pilot_frame* f, const float* dsm_dev) {
+    DevFrame d;
+    d.dsm = f->use_range ? dsm_dev : nullptr;
+    return prior_params(c, f, d);
+}
+cudaError_t level_launch(pilot_dtype dt, int C, bool scaled, const LevelArgs& a, int grid, cudaStream_t s);
+cudaError_t level_occupancy_query(pilot_dtype dt, int C, bool scaled, int* n);
 }  // namespace pilot
+
+namespace {
+
+// Layout of the batch descriptor block (device copy and pinned host staging).
+struct BatchLayout {
+    size_t off_hdr, off_frames, off_nactive, off_job_frame, off_job_slot, bytes;
+    int max_frames, max_jobs;
+    static BatchLayout make(int max_frames, int max_hyps) {
+        auto a256 = [](size_t b) { return (b + 255) / 256 * 256; };
+        BatchLayout l;
+        l.max_frames = max_frames;
+        l.max_jobs = max_hyps;
+        l.off_hdr = 0;
+        l.off_frames = a256(sizeof(BatchHeader));
+        l.off_nactive = a256(l.off_frames + sizeof(FrameDesc) * (size_t)max_frames);
+        l.off_job_frame = a256(l.off_nactive + sizeof(int) * PILOT_MAX_LEVELS * (size_t)max_frames);
+        l.off_job_slot = a256(l.off_job_frame + sizeof(int) * PILOT_MAX_LEVELS * (size_t)max_hyps);
+        l.bytes = a256(l.off_job_slot + sizeof(int) * PILOT_MAX_LEVELS * (size_t)max_hyps);
+        return l;
+    }
+};
+
+pilot_status batch_alloc(pilot_align_handle* h) {
+    if (h->bdesc_dev) return PILOT_OK;
+    const pilot_align_config& c = h->cfg;
+    const BatchLayout lay = BatchLayout::make(c.max_frames, c.max_hyps);
+    h->bdesc_bytes = lay.bytes;
+    h->bres_bytes = ResultLayout::make(c.max_hyps).bytes + sizeof(int) * (size_t)c.max_frames;
+    PILOT_CUDA(cudaMalloc((void**)&h->bdesc_dev, h->bdesc_bytes), "batch descriptor allocation");
+    PILOT_CUDA(cudaMallocHost((void**)&h->bdesc_host, h->bdesc_bytes), "batch descriptor staging");
+    PILOT_CUDA(cudaMalloc((void**)&h->bres_dev, h->bres_bytes), "batch result allocation");
+    PILOT_CUDA(cudaMallocHost((void**)&h->bres_host, h->bres_bytes), "batch result staging");
+    PILOT_CUDA(cudaMalloc((void**)&h->bactive, sizeof(int) * (size_t)c.max_hyps), "batch active lists");
+    PILOT_CUDA(cudaMalloc((void**)&h->bmin_valid, sizeof(double) * (size_t)c.max_frames), "batch thresholds");
+    PILOT_CUDA(cudaMalloc((void**)&h->bcounters, sizeof(int) * PILOT_MAX_LEVELS), "batch counters");
+    PILOT_CUDA(cudaStreamCreateWithFlags(&h->bstream, cudaStreamNonBlocking), "batch stream");
+    return PILOT_OK;
+}
+
+cudaError_t launch_level(pilot_dtype dt, int C, bool scaled, const LevelArgs& a, int grid, cudaStream_t s) {
+    switch (dt) {
+        case PILOT_F32: return launch_level_persistent_dtype<PILOT_F32>(C, scaled, a, grid, s);
+        case PILOT_BF16: return launch_level_persistent_dtype<PILOT_BF16>(C, scaled, a, grid, s);
+        case PILOT_F16: return launch_level_persistent_dtype<PILOT_F16>(C, scaled, a, grid, s);
+        case PILOT_FP8E4M3: return launch_level_persistent_dtype<PILOT_FP8E4M3>(C, scaled, a, grid, s);
+    }
+    return cudaErrorInvalidValue;
+}
+
+cudaError_t level_occupancy(pilot_dtype dt, int C, bool scaled, int* n) {
+    switch (dt) {
+        case PILOT_F32: return level_persistent_occupancy<PILOT_F32>(C, scaled, n);
+        case PILOT_BF16: return level_persistent_occupancy<PILOT_BF16>(C, scaled, n);
+        case PILOT_F16: return level_persistent_occupancy<PILOT_F16>(C, scaled, n);
+        case PILOT_FP8E4M3: return level_persistent_occupancy<PILOT_FP8E4M3>(C, scaled, n);
+    }
+    return cudaErrorInvalidValue;
+}
+
+}  // namespace
+
+namespace pilot {
+cudaError_t level_launch(pilot_dtype dt, int C, bool scaled, const LevelArgs& a, int grid, cudaStream_t s) {
+    return launch_level(dt, C, scaled, a, grid, s);
+}
+cudaError_t level_occupancy_query(pilot_dtype dt, int C, bool scaled, int* n) {
+    return level_occupancy(dt, C, scaled, n);
+}
+}  // namespace pilot
+
+namespace {
+
+// Records the whole batched solve on h->bstream: descriptor upload, per-frame set-up,
+// one persistent launch per level (+ per-frame top-K), selection, result download.
+pilot_status capture_batch_graph(pilot_align_handle* h, pilot_dtype dt, int C, bool scaled, int L) {
+    const pilot_align_config& c = h->cfg;
+    const BatchLayout lay = BatchLayout::make(c.max_frames, c.max_hyps);
+    int dev = 0, sms = 0, per_sm = 0;
+    PILOT_CUDA(cudaGetDevice(&dev), "cudaGetDevice");
+    PILOT_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev), "SM count");
+    PILOT_CUDA(level_occupancy(dt, C, scaled, &per_sm), "occupancy query");
+    h->level_grid = sms * (per_sm > 0 ? per_sm : 1);
+    if (h->gexec) cudaGraphExecDestroy(h->gexec);
+    if (h->graph) cudaGraphDestroy(h->graph);
+    h->gexec = nullptr;
+    h->graph = nullptr;
+    cudaStream_t s = h->bstream;
+    const BatchHeader* hdr = reinterpret_cast<const BatchHeader*>(h->bdesc_dev + lay.off_hdr);
+    const FrameDesc* frames = reinterpret_cast<const FrameDesc*>(h->bdesc_dev + lay.off_frames);
+    const int* nactive = reinterpret_cast<const int*>(h->bdesc_dev + lay.off_nactive);
+    const int* job_frame = reinterpret_cast<const int*>(h->bdesc_dev + lay.off_job_frame);
+    const int* job_slot = reinterpret_cast<const int*>(h->bdesc_dev + lay.off_job_slot);
+    PILOT_CUDA(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal), "graph capture begin");
+    cudaError_t e = cudaMemcpyAsync(h->bdesc_dev, h->bdesc_host, h->bdesc_bytes, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(h->bcounters, 0, sizeof(int) * PILOT_MAX_LEVELS, s);
+    if (e == cudaSuccess) e = launch_batch_init(hdr, frames, h->state, h->bactive, c.max_frames, s);
+    if (e == cudaSuccess)
+        e = launch_batch_count_valid(hdr, frames, c.min_valid_frac, h->bmin_valid, c.max_frames, s);
+    for (int level = L - 1; level >= 0 && e == cudaSuccess; --level) {
+        LevelArgs a{};
+        a.header = hdr;
+        a.frames = frames;
+        a.job_frame = job_frame + (size_t)level * lay.max_jobs;
+        a.job_slot = job_slot + (size_t)level * lay.max_jobs;
+        a.active = h->bactive;
+        a.state = h->state;
+        a.min_valid = h->bmin_valid;
+        a.counter = h->bcounters + level;
+        a.level = level;
+        a.n_jobs_index = level;
+        for (int l = 0; l < PILOT_MAX_LEVELS; ++l) a.iters[l] = c.iters_per_level[l];
+        a.tile = kTile;
+        a.damping_mode = c.damping_mode;
+        a.huber = (float)c.huber_photo;
+        a.lambda0 = c.lambda0;
+        e = launch_level(dt, C, scaled, a, h->level_grid, s);
+        const int K = c.keep_top_k[level];
+        if (e == cudaSuccess && level > 0 && K > 0)
+            e = launch_batch_prune(hdr, frames, h->state, h->bactive, nactive + (size_t)level * lay.max_frames, K,
+                                   h->bmin_valid, c.max_frames, s);
+    }
+    if (e == cudaSuccess)
+        e = launch_batch_finalize(hdr, frames, h->state, h->bmin_valid, h->bres_dev, c.max_hyps, c.max_frames, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(h->bres_host, h->bres_dev, h->bres_bytes, cudaMemcpyDeviceToHost, s);
+    cudaGraph_t g = nullptr;
+    cudaError_t e2 = cudaStreamEndCapture(s, &g);
+    if (e != cudaSuccess) {
+        if (g) cudaGraphDestroy(g);
+        return cuda_fail(e, "batch graph capture");
+    }
+    if (e2 != cudaSuccess) return cuda_fail(e2, "graph capture end");
+    h->graph = g;
+    PILOT_CUDA(cudaGraphInstantiate(&h->gexec, g, 0), "graph instantiate");
+    h->graph_key = ((long long)dt << 32) | ((long long)C << 16) | ((long long)scaled << 8) | (long long)L;
+    return PILOT_OK;
+}
+
+}  // namespace
 
 extern "C" {
 
@@ -569,6 +747,128 @@ pilot_status pilot_align_debug_normal_eq(pilot_align_handle* h, const pilot_fram
     PILOT_CUDA(cudaMemcpyAsync(out29, h->eval_out, sizeof(double) * kNumSums * M, cudaMemcpyDeviceToHost, s),
                "normal-equation copy");
     PILOT_CUDA(cudaStreamSynchronize(s), "debug_normal_eq");
+    return PILOT_OK;
+}
+
+pilot_status pilot_align_solve_batch(pilot_align_handle* h, const pilot_frame* frames, int n,
+                                     pilot_result* results, void* stream) {
+    if (!h || (n > 0 && (!frames || !results))) return fail(PILOT_EINVAL, "handle, frames or results is NULL");
+    const pilot_align_config& c = h->cfg;
+    if (n < 0 || n > c.max_frames) return fail(PILOT_EINVAL, "n_frames = %d outside [0, max_frames = %d]", n, c.max_frames);
+    if (n == 0) return PILOT_OK;
+    pilot_status st;
+    long long total = 0;
+    const pilot_frame& f0 = frames[0];
+    bool scaled = false;
+    for (int i = 0; i < n; ++i) {
+        const pilot_frame* f = frames + i;
+        if ((st = validate_frame(c, f)) != PILOT_OK) return fail(st, "frame %d: %s", i, g_last_error.c_str());
+        if (!f->is_device) return fail(PILOT_EINVAL, "frame %d: the batched form needs device frames", i);
+        if (f->C != f0.C || f->L != f0.L || f->feat_dtype != f0.feat_dtype)
+            return fail(PILOT_EINVAL, "frame %d: C, L and feat_dtype must match frame 0", i);
+        if (f->M > 8192) return fail(PILOT_EINVAL, "frame %d: M = %d above 8192", i, f->M);
+        for (int l = 0; l < f->L; ++l) {
+            const bool sl = f->qry_scale[l] || f->ref_scale[l];
+            if (i == 0 && l == 0) scaled = sl;
+            if (sl != scaled || (sl && (!f->qry_scale[l] || !f->ref_scale[l])))
+                return fail(PILOT_EINVAL, "frame %d level %d: give both scale arrays on every level of every "
+                                          "frame, or none", i, l);
+        }
+        total += f->M;
+    }
+    if (total > c.max_hyps) return fail(PILOT_EINVAL, "batch has %lld hypotheses, above max_hyps = %d", total, c.max_hyps);
+    DeviceGuard guard(h->device);
+    if ((st = batch_alloc(h)) != PILOT_OK) return st;
+    const BatchLayout lay = BatchLayout::make(c.max_frames, c.max_hyps);
+    unsigned char* hb = h->bdesc_host;
+    BatchHeader* hdr = reinterpret_cast<BatchHeader*>(hb + lay.off_hdr);
+    FrameDesc* fds = reinterpret_cast<FrameDesc*>(hb + lay.off_frames);
+    int* nactive = reinterpret_cast<int*>(hb + lay.off_nactive);
+    int* job_frame = reinterpret_cast<int*>(hb + lay.off_job_frame);
+    int* job_slot = reinterpret_cast<int*>(hb + lay.off_job_slot);
+    memset(hdr, 0, sizeof(BatchHeader));
+    hdr->n_frames = n;
+    hdr->total_hyps = (int)total;
+    const int L = f0.L;
+    int off = 0;
+    for (int i = 0; i < n; ++i) {
+        const pilot_frame* f = frames + i;
+        FrameDesc& d = fds[i];
+        memset(&d, 0, sizeof d);
+        const size_t N = (size_t)f->N;
+        d.px = f->points;
+        d.py = f->points ? f->points + N : nullptr;
+        d.pz = f->points ? f->points + 2 * N : nullptr;
+        d.weight = f->point_weight;
+        d.valid = f->point_valid;
+        d.N = f->N;
+        d.M = f->M;
+        for (int l = 0; l < L; ++l) {
+            d.ref[l] = f->ref_feat[l];
+            d.qry[l] = f->qry_feat[l];
+            d.rscale[l] = f->ref_scale[l];
+            d.qscale[l] = f->qry_scale[l];
+            d.H[l] = f->H[l];
+            d.W[l] = f->W[l];
+            const double sc = ldexp(1.0, -l);
+            d.fx[l] = (float)(f->fx * sc);
+            d.fy[l] = (float)(f->fy * sc);
+            d.cx[l] = (float)(f->cx * sc);
+            d.cy[l] = (float)(f->cy * sc);
+        }
+        d.T_cw = f->T_cw;
+        d.hyp_offset = off;
+        DevFrame dv;
+        dv.dsm = f->use_range ? f->dsm : nullptr;
+        d.prior = prior_params(c, f, dv);
+        off += f->M;
+    }
+    // hypotheses per frame and level (top-K is deterministic in count), and the job
+    // tables: frames with more anchors first (longest job first), slots in order
+    std::vector<int> order(n);
+    for (int i = 0; i < n; ++i) order[i] = i;
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return frames[a].N > frames[b].N; });
+    std::vector<long long> hyp_iters(n, 0);
+    std::vector<int> cur(n);
+    for (int i = 0; i < n; ++i) cur[i] = frames[i].M;
+    for (int level = L - 1; level >= 0; --level) {
+        int nj = 0;
+        for (int i = 0; i < n; ++i) nactive[(size_t)level * lay.max_frames + i] = cur[i];
+        for (int oi = 0; oi < n; ++oi) {
+            const int i = order[oi];
+            for (int k = 0; k < cur[i]; ++k) {
+                job_frame[(size_t)level * lay.max_jobs + nj] = i;
+                job_slot[(size_t)level * lay.max_jobs + nj] = k;
+                ++nj;
+            }
+        }
+        hdr->n_jobs[level] = nj;
+        for (int i = 0; i < n; ++i) {
+            hyp_iters[i] += (long long)cur[i] * c.iters_per_level[level];
+            const int K = c.keep_top_k[level];
+            if (level > 0 && K > 0 && K < cur[i]) cur[i] = K;
+        }
+    }
+    const long long key = ((long long)f0.feat_dtype << 32) | ((long long)f0.C << 16) | ((long long)scaled << 8) | (long long)L;
+    if (!h->gexec || h->graph_key != key)
+        if ((st = capture_batch_graph(h, f0.feat_dtype, f0.C, scaled, L)) != PILOT_OK) return st;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    PILOT_CUDA(cudaGraphLaunch(h->gexec, s), "batch graph launch");
+    PILOT_CUDA(cudaStreamSynchronize(s), "batch solve");
+    h->total_launches = 4 + 2 * L + 1;
+    const ResultLayout rl = ResultLayout::make(c.max_hyps);
+    const unsigned char* r = h->bres_host;
+    const int* best = reinterpret_cast<const int*>(r + rl.bytes);
+    for (int i = 0; i < n; ++i) {
+        const int o = fds[i].hyp_offset, M = frames[i].M;
+        pilot_result& out = results[i];
+        if (out.T_cw) memcpy(out.T_cw, r + rl.off_T + sizeof(double) * 12 * (size_t)o, sizeof(double) * 12 * M);
+        if (out.cost) memcpy(out.cost, r + rl.off_cost + sizeof(double) * (size_t)o, sizeof(double) * M);
+        if (out.n_valid) memcpy(out.n_valid, r + rl.off_nvalid + sizeof(int) * (size_t)o, sizeof(int) * M);
+        if (out.hyp_status) memcpy(out.hyp_status, r + rl.off_status + sizeof(int) * (size_t)o, sizeof(int) * M);
+        if (out.best) *out.best = best[i];
+        if (out.hyp_iters) *out.hyp_iters = hyp_iters[i];
+    }
     return PILOT_OK;
 }
 

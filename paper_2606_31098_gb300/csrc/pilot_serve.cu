@@ -1,0 +1,613 @@
+// Serving: a persistent request loop with continuous batching at pyramid-level granularity.
+//
+// Clients submit frames from many concurrent streams (uneven crops, hypothesis counts).
+// A worker thread owns the GPU:
+//   admission  a pending frame is admitted when a slot is free, its hypotheses fit in the
+//              hypothesis state array and its data fit in the device arena (the HBM budget
+//              given at create); admission copies the frame into the arena, where its
+//              pyramid and LM state stay until it completes.
+//   round      every active frame advances by one pyramid level: one graph replay uploads
+//              the round's descriptors, sets up newly admitted frames, runs one persistent
+//              launch in which each frame's hypotheses run that frame's current level
+//              (frames at different levels share the launch), applies per-frame top-K,
+//              finalises frames that finished the finest level and downloads results.
+//   retire     finished frames free their slot, hypotheses and arena space; frames that
+//              arrived meanwhile are admitted before the next round.
+// Each frame's arithmetic is exactly that of pilot_align_solve (same kernels, same
+// reduction order), so a frame's result does not depend on what else is being served.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <string.h>
+
+#include <algorithm>
+#include <chrono>
+#include <condition_variable>
+#include <deque>
+#include <map>
+#include <memory>
+#include <mutex>
+#include <string>
+#include <thread>
+#include <unordered_map>
+#include <vector>
+
+#include "pilot_internal.cuh"
+
+using namespace pilot;
+
+namespace {
+
+double now_ms() {
+    using namespace std::chrono;
+    return duration<double, std::milli>(steady_clock::now().time_since_epoch()).count();
+}
+
+pilot_status sfail(pilot_status st, const std::string& m) {
+    record_error(m.c_str());
+    return st;
+}
+
+// First-fit allocator over [0, capacity) with coalescing free ranges.
+class RangeAllocator {
+  public:
+    void reset(size_t capacity) {
+        free_.clear();
+        if (capacity) free_[0] = capacity;
+        in_use_ = peak_ = 0;
+    }
+    bool alloc(size_t n, size_t* off) {
+        for (auto it = free_.begin(); it != free_.end(); ++it) {
+            if (it->second >= n) {
+                *off = it->first;
+                const size_t rest = it->second - n, start = it->first + n;
+                free_.erase(it);
+                if (rest) free_[start] = rest;
+                in_use_ += n;
+                peak_ = std::max(peak_, in_use_);
+                return true;
+            }
+        }
+        return false;
+    }
+    void release(size_t off, size_t n) {
+        if (!n) return;
+        in_use_ -= n;
+        auto it = free_.emplace(off, n).first;
+        auto nx = std::next(it);
+        if (nx != free_.end() && it->first + it->second == nx->first) {
+            it->second += nx->second;
+            free_.erase(nx);
+        }
+        if (it != free_.begin()) {
+            auto pv = std::prev(it);
+            if (pv->first + pv->second == it->first) {
+                pv->second += it->second;
+                free_.erase(it);
+            }
+        }
+    }
+    size_t in_use() const { return in_use_; }
+    size_t peak() const { return peak_; }
+
+  private:
+    std::map<size_t, size_t> free_;
+    size_t in_use_ = 0, peak_ = 0;
+};
+
+size_t a256(size_t b) { return (b + 255) / 256 * 256; }
+
+// Device bytes a frame occupies in the arena (every array rounded to 256 bytes).
+size_t frame_bytes(const pilot_frame& f) {
+    const size_t es = dtype_bytes(f.feat_dtype), N = f.N, C = f.C;
+    size_t b = a256(sizeof(float) * 3 * N);
+    if (f.point_weight) b += a256(sizeof(float) * N);
+    if (f.point_valid) b += a256(N);
+    for (int l = 0; l < f.L; ++l) {
+        b += a256(es * N * C) + a256(es * (size_t)f.H[l] * f.W[l] * C);
+        if (f.ref_scale[l]) b += a256(sizeof(float) * C);
+        if (f.qry_scale[l]) b += a256(sizeof(float) * C);
+    }
+    b += a256(sizeof(double) * 12 * (size_t)f.M);
+    if (f.use_range) b += a256(sizeof(float) * (size_t)f.dsm_H * f.dsm_W);
+    return b;
+}
+
+enum ReqState { kPending = 0, kActive = 1, kDone = 2, kFailed = 3 };
+
+struct Request {
+    uint64_t ticket = 0;
+    pilot_frame src{};           // the caller's frame (pointers valid until done)
+    pilot_frame dev{};           // the arena copy
+    double t_submit = 0, t_admit = 0, t_done = 0;
+    size_t arena_off = 0, arena_bytes = 0, hyp_off = 0;
+    int slot = -1, level = 0, n_active = 0;
+    bool initialized = false;
+    long long hyp_iters = 0;
+    int state = kPending;
+    std::vector<double> T, cost;
+    std::vector<int> n_valid, status;
+    int best = -1;
+};
+
+}  // namespace
+
+struct pilot_server {
+    pilot_align_config cfg{};
+    int device = 0;
+    size_t budget = 0;
+    int max_slots = 0, max_pending = 0;
+    unsigned char* arena = nullptr;
+    RangeAllocator arena_alloc, hyp_alloc;
+    std::vector<int> free_slots;
+    HypState* state = nullptr;
+    int* active = nullptr;
+    double* min_valid = nullptr;
+    int* counter = nullptr;
+    unsigned char* desc_dev = nullptr;
+    unsigned char* desc_host = nullptr;
+    size_t desc_bytes = 0, off_frames = 0, off_job_frame = 0, off_job_slot = 0;
+    unsigned char* res_dev = nullptr;
+    unsigned char* res_host = nullptr;
+    size_t res_bytes = 0;
+    cudaStream_t stream = nullptr;
+    cudaGraphExec_t gexec = nullptr;
+    cudaGraph_t graph = nullptr;
+    int grid = 0;
+    bool key_set = false;
+    pilot_dtype dt = PILOT_F32;
+    int C = 0, L = 0;
+    bool scaled = false;
+    std::thread worker;
+    std::mutex mu;
+    std::condition_variable cv_work, cv_done;
+    bool stop = false;
+    pilot_status failure = PILOT_OK;
+    std::string failure_msg;
+    std::deque<Request*> pending;
+    std::vector<Request*> running;
+    std::unordered_map<uint64_t, std::unique_ptr<Request>> reqs;
+    uint64_t next_ticket = 1;
+    long long rounds = 0, admitted = 0, completed = 0, peak_active = 0;
+};
+
+namespace {
+
+void release_buffers(pilot_server* s) {
+    if (s->gexec) cudaGraphExecDestroy(s->gexec);
+    if (s->graph) cudaGraphDestroy(s->graph);
+    cudaFree(s->arena);
+    cudaFree(s->state);
+    cudaFree(s->active);
+    cudaFree(s->min_valid);
+    cudaFree(s->counter);
+    cudaFree(s->desc_dev);
+    if (s->desc_host) cudaFreeHost(s->desc_host);
+    cudaFree(s->res_dev);
+    if (s->res_host) cudaFreeHost(s->res_host);
+    if (s->stream) cudaStreamDestroy(s->stream);
+}
+
+// Copy one array into the arena (H2D for host frames, D2D for device frames).
+template <typename T>
+cudaError_t place(pilot_server* s, const Request& r, size_t* cursor, const T* src, size_t bytes,
+                  const T** dst) {
+    if (!src || bytes == 0) {
+        *dst = nullptr;
+        return cudaSuccess;
+    }
+    unsigned char* d = s->arena + r.arena_off + *cursor;
+    *cursor += a256(bytes);
+    *dst = reinterpret_cast<const T*>(d);
+    return cudaMemcpyAsync(d, src, bytes, r.src.is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
+                           s->stream);
+}
+
+cudaError_t stage_frame(pilot_server* s, Request& r) {
+    const pilot_frame& f = r.src;
+    pilot_frame& d = r.dev;
+    d = f;
+    d.is_device = 1;
+    const size_t es = dtype_bytes(f.feat_dtype), N = f.N, C = f.C;
+    size_t cur = 0;
+    cudaError_t e = place(s, r, &cur, f.points, sizeof(float) * 3 * N, &d.points);
+    if (e == cudaSuccess) e = place(s, r, &cur, f.point_weight, sizeof(float) * N, &d.point_weight);
+    if (e == cudaSuccess) e = place(s, r, &cur, f.point_valid, N, &d.point_valid);
+    for (int l = 0; l < f.L && e == cudaSuccess; ++l) {
+        const void* p = nullptr;
+        e = place(s, r, &cur, static_cast<const unsigned char*>(f.ref_feat[l]), es * N * C,
+                  reinterpret_cast<const unsigned char**>(&p));
+        d.ref_feat[l] = p;
+        if (e == cudaSuccess)
+            e = place(s, r, &cur, static_cast<const unsigned char*>(f.qry_feat[l]), es * (size_t)f.H[l] * f.W[l] * C,
+                      reinterpret_cast<const unsigned char**>(&p));
+        d.qry_feat[l] = p;
+        if (e == cudaSuccess) e = place(s, r, &cur, f.ref_scale[l], sizeof(float) * C, &d.ref_scale[l]);
+        if (e == cudaSuccess) e = place(s, r, &cur, f.qry_scale[l], sizeof(float) * C, &d.qry_scale[l]);
+    }
+    if (e == cudaSuccess) e = place(s, r, &cur, f.T_cw, sizeof(double) * 12 * (size_t)f.M, &d.T_cw);
+    if (e == cudaSuccess && f.use_range)
+        e = place(s, r, &cur, f.dsm, sizeof(float) * (size_t)f.dsm_H * f.dsm_W, &d.dsm);
+    return e;
+}
+
+cudaError_t capture_round(pilot_server* s) {
+    if (s->gexec) cudaGraphExecDestroy(s->gexec);
+    if (s->graph) cudaGraphDestroy(s->graph);
+    s->gexec = nullptr;
+    s->graph = nullptr;
+    int sms = 0, per_sm = 0;
+    cudaError_t e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, s->device);
+    if (e == cudaSuccess) e = level_occupancy_query(s->dt, s->C, s->scaled, &per_sm);
+    if (e != cudaSuccess) return e;
+    s->grid = sms * (per_sm > 0 ? per_sm : 1);
+    const BatchHeader* hdr = reinterpret_cast<const BatchHeader*>(s->desc_dev);
+    const FrameDesc* frames = reinterpret_cast<const FrameDesc*>(s->desc_dev + s->off_frames);
+    if ((e = cudaStreamBeginCapture(s->stream, cudaStreamCaptureModeThreadLocal)) != cudaSuccess) return e;
+    e = cudaMemcpyAsync(s->desc_dev, s->desc_host, s->desc_bytes, cudaMemcpyHostToDevice, s->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(s->counter, 0, sizeof(int), s->stream);
+    if (e == cudaSuccess)
+        e = launch_round_prepare(hdr, frames, s->state, s->active, s->cfg.min_valid_frac, s->min_valid,
+                                 s->max_slots, s->stream);
+    if (e == cudaSuccess) {
+        LevelArgs a{};
+        a.header = hdr;
+        a.frames = frames;
+        a.job_frame = reinterpret_cast<const int*>(s->desc_dev + s->off_job_frame);
+        a.job_slot = reinterpret_cast<const int*>(s->desc_dev + s->off_job_slot);
+        a.active = s->active;
+        a.state = s->state;
+        a.min_valid = s->min_valid;
+        a.counter = s->counter;
+        a.level = -1;
+        a.n_jobs_index = 0;
+        for (int l = 0; l < PILOT_MAX_LEVELS; ++l) a.iters[l] = s->cfg.iters_per_level[l];
+        a.tile = kPlainTile;
+        a.damping_mode = s->cfg.damping_mode;
+        a.huber = (float)s->cfg.huber_photo;
+        a.lambda0 = s->cfg.lambda0;
+        e = level_launch(s->dt, s->C, s->scaled, a, s->grid, s->stream);
+    }
+    if (e == cudaSuccess)
+        e = launch_round_finish(hdr, frames, s->state, s->active, s->min_valid, s->res_dev, s->cfg.max_hyps,
+                                s->max_slots, s->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(s->res_host, s->res_dev, s->res_bytes, cudaMemcpyDeviceToHost, s->stream);
+    cudaGraph_t g = nullptr;
+    const cudaError_t e2 = cudaStreamEndCapture(s->stream, &g);
+    if (e != cudaSuccess || e2 != cudaSuccess) {
+        if (g) cudaGraphDestroy(g);
+        return e != cudaSuccess ? e : e2;
+    }
+    s->graph = g;
+    return cudaGraphInstantiate(&s->gexec, g, 0);
+}
+
+// Admit pending frames in arrival order while a slot, hypothesis room and arena space are
+// free (head-of-line: a frame that does not fit yet blocks the ones behind it).
+cudaError_t admit(pilot_server* s) {
+    while (!s->pending.empty() && !s->free_slots.empty()) {
+        Request* r = s->pending.front();
+        size_t aoff = 0, hoff = 0;
+        if (!s->hyp_alloc.alloc((size_t)r->src.M, &hoff)) break;
+        if (!s->arena_alloc.alloc(r->arena_bytes, &aoff)) {
+            s->hyp_alloc.release(hoff, (size_t)r->src.M);
+            break;
+        }
+        s->pending.pop_front();
+        r->arena_off = aoff;
+        r->hyp_off = hoff;
+        r->slot = s->free_slots.back();
+        s->free_slots.pop_back();
+        r->level = r->src.L - 1;
+        r->n_active = r->src.M;
+        r->state = kActive;
+        r->t_admit = now_ms();
+        s->running.push_back(r);
+        ++s->admitted;
+        const cudaError_t e = stage_frame(s, *r);
+        if (e != cudaSuccess) return e;
+    }
+    s->peak_active = std::max<long long>(s->peak_active, (long long)s->running.size());
+    return cudaSuccess;
+}
+
+// Descriptors of one round: every slot gets a FrameDesc (idle slots do nothing); jobs are
+// the active hypotheses of every running frame, frames with more anchors first.
+void write_round(pilot_server* s) {
+    const pilot_align_config& c = s->cfg;
+    BatchHeader* hdr = reinterpret_cast<BatchHeader*>(s->desc_host);
+    FrameDesc* fds = reinterpret_cast<FrameDesc*>(s->desc_host + s->off_frames);
+    int* jf = reinterpret_cast<int*>(s->desc_host + s->off_job_frame);
+    int* js = reinterpret_cast<int*>(s->desc_host + s->off_job_slot);
+    memset(hdr, 0, sizeof(BatchHeader));
+    hdr->n_frames = s->max_slots;
+    memset(fds, 0, sizeof(FrameDesc) * (size_t)s->max_slots);
+    std::vector<Request*> order = s->running;
+    std::stable_sort(order.begin(), order.end(), [](Request* a, Request* b) { return a->src.N > b->src.N; });
+    int nj = 0;
+    for (Request* r : order) {
+        const pilot_frame& f = r->dev;
+        FrameDesc& d = fds[r->slot];
+        const size_t N = (size_t)f.N;
+        d.px = f.points;
+        d.py = f.points ? f.points + N : nullptr;
+        d.pz = f.points ? f.points + 2 * N : nullptr;
+        d.weight = f.point_weight;
+        d.valid = f.point_valid;
+        d.N = f.N;
+        d.M = f.M;
+        for (int l = 0; l < f.L; ++l) {
+            d.ref[l] = f.ref_feat[l];
+            d.qry[l] = f.qry_feat[l];
+            d.rscale[l] = f.ref_scale[l];
+            d.qscale[l] = f.qry_scale[l];
+            d.H[l] = f.H[l];
+            d.W[l] = f.W[l];
+            const double sc = ldexp(1.0, -l);
+            d.fx[l] = (float)(f.fx * sc);
+            d.fy[l] = (float)(f.fy * sc);
+            d.cx[l] = (float)(f.cx * sc);
+            d.cy[l] = (float)(f.cy * sc);
+        }
+        d.T_cw = f.T_cw;
+        d.hyp_offset = (int)r->hyp_off;
+        d.level = r->level;
+        d.n_active = r->n_active;
+        const int K = c.keep_top_k[r->level];
+        d.keep = K;
+        d.flags = (r->initialized ? 0 : kFlagInit) | ((r->level > 0 && K > 0 && K < r->n_active) ? kFlagPrune : 0) |
+                  (r->level == 0 ? kFlagFinalize : 0);
+        d.prior = frame_prior(c, &f, f.dsm);
+        for (int k = 0; k < r->n_active; ++k) {
+            jf[nj] = r->slot;
+            js[nj] = k;
+            ++nj;
+        }
+    }
+    hdr->n_jobs[0] = nj;
+}
+
+// After a round: advance levels, collect finished frames.
+void after_round(pilot_server* s) {
+    const pilot_align_config& c = s->cfg;
+    const ResultLayout rl = ResultLayout::make(c.max_hyps);
+    const unsigned char* res = s->res_host;
+    const int* best = reinterpret_cast<const int*>(res + rl.bytes);
+    std::vector<Request*> still;
+    const double t = now_ms();
+    for (Request* r : s->running) {
+        r->initialized = true;
+        r->hyp_iters += (long long)r->n_active * c.iters_per_level[r->level];
+        const int K = c.keep_top_k[r->level];
+        if (r->level > 0 && K > 0 && K < r->n_active) r->n_active = K;
+        if (r->level > 0) {
+            --r->level;
+            still.push_back(r);
+            continue;
+        }
+        const int M = r->src.M;
+        const size_t o = r->hyp_off;
+        r->T.assign(reinterpret_cast<const double*>(res + rl.off_T) + 12 * o,
+                    reinterpret_cast<const double*>(res + rl.off_T) + 12 * (o + M));
+        r->cost.assign(reinterpret_cast<const double*>(res + rl.off_cost) + o,
+                       reinterpret_cast<const double*>(res + rl.off_cost) + o + M);
+        r->n_valid.assign(reinterpret_cast<const int*>(res + rl.off_nvalid) + o,
+                          reinterpret_cast<const int*>(res + rl.off_nvalid) + o + M);
+        r->status.assign(reinterpret_cast<const int*>(res + rl.off_status) + o,
+                         reinterpret_cast<const int*>(res + rl.off_status) + o + M);
+        r->best = best[r->slot];
+        r->state = kDone;
+        r->t_done = t;
+        s->arena_alloc.release(r->arena_off, r->arena_bytes);
+        s->hyp_alloc.release(r->hyp_off, (size_t)M);
+        s->free_slots.push_back(r->slot);
+        ++s->completed;
+    }
+    s->running.swap(still);
+}
+
+void fail_all(pilot_server* s, cudaError_t e, const char* what) {
+    s->failure = PILOT_ECUDA;
+    s->failure_msg = std::string(what) + ": " + cudaGetErrorString(e);
+    for (Request* r : s->running) r->state = kFailed;
+    for (Request* r : s->pending) r->state = kFailed;
+    s->running.clear();
+    s->pending.clear();
+}
+
+void worker_main(pilot_server* s) {
+    cudaSetDevice(s->device);
+    std::unique_lock<std::mutex> lock(s->mu);
+    while (!s->stop) {
+        if (s->failure == PILOT_OK) {
+            const cudaError_t e = admit(s);
+            if (e != cudaSuccess) {
+                fail_all(s, e, "frame staging");
+                s->cv_done.notify_all();
+                continue;
+            }
+        }
+        if (s->running.empty()) {
+            s->cv_work.wait_for(lock, std::chrono::milliseconds(2));
+            continue;
+        }
+        write_round(s);
+        lock.unlock();
+        cudaError_t e = cudaGraphLaunch(s->gexec, s->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+        lock.lock();
+        ++s->rounds;
+        if (e != cudaSuccess) {
+            fail_all(s, e, "serving round");
+        } else {
+            after_round(s);
+        }
+        s->cv_done.notify_all();
+    }
+}
+
+}  // namespace
+
+extern "C" {
+
+pilot_status pilot_serve_create(const pilot_align_config* cfg_in, size_t hbm_budget, int max_slots,
+                                pilot_server** out) {
+    if (!cfg_in || !out) return sfail(PILOT_EINVAL, "config or out is NULL");
+    *out = nullptr;
+    pilot_align_config cfg = config_with_defaults(*cfg_in);
+    pilot_status st = check_config(cfg);
+    if (st != PILOT_OK) return st;
+    if (max_slots < 1 || max_slots > 4096) return sfail(PILOT_EINVAL, "max_slots must be in [1, 4096]");
+    if (hbm_budget < (1u << 20)) return sfail(PILOT_EINVAL, "hbm_budget below 1 MiB");
+    std::unique_ptr<pilot_server> s(new pilot_server());
+    s->cfg = cfg;
+    s->budget = hbm_budget;
+    s->max_slots = max_slots;
+    s->max_pending = 4 * max_slots + 64;
+    cudaError_t e = cudaGetDevice(&s->device);
+    auto bad = [&](const char* what) {
+        std::string m = std::string(what) + ": " + cudaGetErrorString(e);
+        release_buffers(s.get());
+        return sfail(e == cudaErrorMemoryAllocation ? PILOT_ENOMEM : PILOT_ECUDA, m);
+    };
+    if (e != cudaSuccess) return bad("cudaGetDevice");
+    const size_t H = (size_t)cfg.max_hyps;
+    s->off_frames = a256(sizeof(BatchHeader));
+    s->off_job_frame = a256(s->off_frames + sizeof(FrameDesc) * (size_t)max_slots);
+    s->off_job_slot = a256(s->off_job_frame + sizeof(int) * H);
+    s->desc_bytes = a256(s->off_job_slot + sizeof(int) * H);
+    s->res_bytes = ResultLayout::make(cfg.max_hyps).bytes + sizeof(int) * (size_t)max_slots;
+    if ((e = cudaMalloc((void**)&s->arena, hbm_budget)) != cudaSuccess) return bad("arena allocation");
+    if ((e = cudaMalloc((void**)&s->state, sizeof(HypState) * H)) != cudaSuccess) return bad("state allocation");
+    if ((e = cudaMalloc((void**)&s->active, sizeof(int) * H)) != cudaSuccess) return bad("active lists");
+    if ((e = cudaMalloc((void**)&s->min_valid, sizeof(double) * (size_t)max_slots)) != cudaSuccess) return bad("thresholds");
+    if ((e = cudaMalloc((void**)&s->counter, sizeof(int))) != cudaSuccess) return bad("counter");
+    if ((e = cudaMalloc((void**)&s->desc_dev, s->desc_bytes)) != cudaSuccess) return bad("descriptors");
+    if ((e = cudaMallocHost((void**)&s->desc_host, s->desc_bytes)) != cudaSuccess) return bad("descriptor staging");
+    if ((e = cudaMalloc((void**)&s->res_dev, s->res_bytes)) != cudaSuccess) return bad("results");
+    if ((e = cudaMallocHost((void**)&s->res_host, s->res_bytes)) != cudaSuccess) return bad("result staging");
+    if ((e = cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking)) != cudaSuccess) return bad("stream");
+    s->arena_alloc.reset(hbm_budget);
+    s->hyp_alloc.reset(H);
+    for (int i = max_slots - 1; i >= 0; --i) s->free_slots.push_back(i);
+    pilot_server* raw = s.release();
+    raw->worker = std::thread(worker_main, raw);
+    *out = raw;
+    return PILOT_OK;
+}
+
+pilot_status pilot_serve_submit(pilot_server* s, const pilot_frame* f, uint64_t* ticket) {
+    if (!s || !f || !ticket) return sfail(PILOT_EINVAL, "server, frame or ticket is NULL");
+    pilot_status st = check_frame(s->cfg, f);
+    if (st != PILOT_OK) return st;
+    if (f->M == 0) return sfail(PILOT_EINVAL, "a served frame needs at least one hypothesis");
+    if (f->M > 8192) return sfail(PILOT_EINVAL, "M above 8192");
+    bool scaled = false;
+    for (int l = 0; l < f->L; ++l) {
+        const bool sl = f->qry_scale[l] || f->ref_scale[l];
+        if (l == 0) scaled = sl;
+        if (sl != scaled || (sl && (!f->qry_scale[l] || !f->ref_scale[l])))
+            return sfail(PILOT_EINVAL, "give both scale arrays on every level, or none");
+    }
+    const size_t bytes = frame_bytes(*f);
+    if (bytes > s->budget) return sfail(PILOT_EINVAL, "the frame needs more device memory than the whole budget");
+    std::unique_lock<std::mutex> lock(s->mu);
+    if (s->failure != PILOT_OK) return sfail(s->failure, s->failure_msg);
+    if (!s->key_set) {
+        int prev = -1;
+        cudaGetDevice(&prev);
+        if (prev != s->device) cudaSetDevice(s->device);
+        s->dt = f->feat_dtype;
+        s->C = f->C;
+        s->L = f->L;
+        s->scaled = scaled;
+        const cudaError_t e = capture_round(s);
+        if (prev >= 0 && prev != s->device) cudaSetDevice(prev);
+        if (e != cudaSuccess) return sfail(PILOT_ECUDA, std::string("round graph: ") + cudaGetErrorString(e));
+        s->key_set = true;
+    } else if (f->feat_dtype != s->dt || f->C != s->C || f->L != s->L || scaled != s->scaled) {
+        return sfail(PILOT_EINVAL, "every served frame must share C, L, feat_dtype and scale presence");
+    }
+    if ((int)s->pending.size() >= s->max_pending) return sfail(PILOT_EBUSY, "pending queue full");
+    std::unique_ptr<Request> r(new Request());
+    r->ticket = s->next_ticket++;
+    r->src = *f;
+    r->arena_bytes = bytes;
+    r->t_submit = now_ms();
+    *ticket = r->ticket;
+    s->pending.push_back(r.get());
+    s->reqs.emplace(r->ticket, std::move(r));
+    s->cv_work.notify_one();
+    return PILOT_OK;
+}
+
+pilot_status pilot_serve_poll(pilot_server* s, uint64_t ticket, pilot_result* res, int* done,
+                              double* latency_ms) {
+    if (!s || !done) return sfail(PILOT_EINVAL, "server or done is NULL");
+    std::unique_lock<std::mutex> lock(s->mu);
+    auto it = s->reqs.find(ticket);
+    if (it == s->reqs.end()) return sfail(PILOT_EINVAL, "unknown ticket");
+    Request* r = it->second.get();
+    *done = 0;
+    if (r->state == kFailed) {
+        s->reqs.erase(it);
+        return sfail(PILOT_ECUDA, s->failure_msg);
+    }
+    if (r->state != kDone) return PILOT_OK;
+    *done = 1;
+    if (res) {
+        const int M = r->src.M;
+        if (res->T_cw) memcpy(res->T_cw, r->T.data(), sizeof(double) * 12 * M);
+        if (res->cost) memcpy(res->cost, r->cost.data(), sizeof(double) * M);
+        if (res->n_valid) memcpy(res->n_valid, r->n_valid.data(), sizeof(int) * M);
+        if (res->hyp_status) memcpy(res->hyp_status, r->status.data(), sizeof(int) * M);
+        if (res->best) *res->best = r->best;
+        if (res->hyp_iters) *res->hyp_iters = r->hyp_iters;
+    }
+    if (latency_ms) *latency_ms = r->t_done - r->t_submit;
+    s->reqs.erase(it);
+    return PILOT_OK;
+}
+
+pilot_status pilot_serve_wait(pilot_server* s, uint64_t ticket, pilot_result* res, double* latency_ms,
+                              int timeout_ms) {
+    if (!s) return sfail(PILOT_EINVAL, "server is NULL");
+    const double deadline = now_ms() + timeout_ms;
+    for (;;) {
+        int done = 0;
+        pilot_status st = pilot_serve_poll(s, ticket, res, &done, latency_ms);
+        if (st != PILOT_OK || done) return st;
+        std::unique_lock<std::mutex> lock(s->mu);
+        if (now_ms() >= deadline) return sfail(PILOT_ETIMEOUT, "wait timed out");
+        s->cv_done.wait_for(lock, std::chrono::milliseconds(1));
+    }
+}
+
+pilot_status pilot_serve_get_stats(pilot_server* s, pilot_serve_stats* out) {
+    if (!s || !out) return sfail(PILOT_EINVAL, "server or stats is NULL");
+    std::unique_lock<std::mutex> lock(s->mu);
+    out->rounds = s->rounds;
+    out->admitted = s->admitted;
+    out->completed = s->completed;
+    out->pending = (long long)s->pending.size();
+    out->active = (long long)s->running.size();
+    out->peak_active = s->peak_active;
+    out->arena_bytes_in_use = (long long)s->arena_alloc.in_use();
+    out->arena_bytes_peak = (long long)s->arena_alloc.peak();
+    return PILOT_OK;
+}
+
+void pilot_serve_destroy(pilot_server* s) {
+    if (!s) return;
+    {
+        std::unique_lock<std::mutex> lock(s->mu);
+        s->stop = true;
+        s->cv_work.notify_all();
+    }
+    if (s->worker.joinable()) s->worker.join();
+    cudaSetDevice(s->device);
+    cudaStreamSynchronize(s->stream);
+    release_buffers(s);
+    delete s;
+}
+
+}  // extern "C"

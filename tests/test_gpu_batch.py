@@ -1,0 +1,113 @@
+"""Batched form (pilot_align_solve_batch): uneven frames x hypotheses x iterations in one
+persistent launch per level, replayed from a CUDA graph.
+
+Its reductions follow exactly the plain form's order, so every frame's outputs must be
+bitwise those of its own pilot_align_solve (which is itself checked against the FP64
+oracle in test_gpu_parity.py), whatever else is in the batch.
+"""
+import numpy as np
+import pytest
+
+from paper_2606_31098_gb300 import binding as B
+from paper_2606_31098_gb300 import scenes as S
+
+from gpu_support import require_cuda
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def torch():
+    return require_cuda()
+
+
+def uneven_frames(sides=(40, 55, 70, 30), hyps=(3, 7, 5, 2), base=800):
+    return [S.make_frame(S.config_reduced_frame(crop_side=s, n_hyps=m), S.frame_seed(3, base + i))
+            for i, (s, m) in enumerate(zip(sides, hyps))]
+
+
+def args_for(frames, dt=B.F32):
+    return [B.FrameArgs(f, B.quantized_device_arrays(f, dt), is_device=True, dtype=dt) for f in frames]
+
+
+def assert_same(a, b, what=""):
+    np.testing.assert_array_equal(a.T_cw, b.T_cw, err_msg=what)
+    np.testing.assert_array_equal(a.cost, b.cost, err_msg=what)
+    np.testing.assert_array_equal(a.n_valid, b.n_valid, err_msg=what)
+    np.testing.assert_array_equal(a.status, b.status, err_msg=what)
+    assert a.best == b.best and a.hyp_iters == b.hyp_iters, what
+
+
+@pytest.mark.parametrize("opts", [B.Options(), B.Options(iters=(4, 3, 5, 0), keep_top_k=(0, 2, 3, 0)),
+                                  B.Options(damping_mode=1, lambda0=1e-2, iters=(3, 3, 3, 0))])
+def test_batch_equals_each_frames_plain_solve(torch, opts):
+    frames = uneven_frames()
+    fas = args_for(frames)
+    solver = B.Solver(opts)
+    batch = solver.solve_batch(fas)
+    for i, fa in enumerate(fas):
+        assert_same(batch[i], solver.solve(fa), what=f"frame {i}")
+
+
+def test_frame_alone_equals_frame_in_the_mix(torch):
+    frames = uneven_frames(sides=(64, 33, 48), hyps=(4, 6, 3), base=900)
+    fas = args_for(frames)
+    solver = B.Solver(B.Options())
+    mix = solver.solve_batch(fas)
+    alone = solver.solve_batch([fas[1]])[0]
+    assert_same(mix[1], alone)
+    again = solver.solve_batch([fas[2], fas[0], fas[1]])
+    assert_same(again[2], alone)
+    assert_same(again[1], mix[0])
+
+
+@pytest.mark.parametrize("dt", [B.BF16, B.FP8E4M3])
+def test_reduced_precision_batch_equals_plain(torch, dt):
+    frames = uneven_frames(sides=(50, 36), hyps=(4, 5), base=950)
+    fas = args_for(frames, dt)
+    solver = B.Solver(B.Options())
+    batch = solver.solve_batch(fas)
+    for i, fa in enumerate(fas):
+        assert_same(batch[i], solver.solve(fa), what=f"frame {i}")
+
+
+def test_graph_replay_with_new_frames_and_sizes(torch):
+    solver = B.Solver(B.Options())
+    first = args_for(uneven_frames(sides=(30, 40), hyps=(2, 3), base=970))
+    solver.solve_batch(first)
+    second = args_for(uneven_frames(sides=(60, 25, 45), hyps=(5, 1, 4), base=980))
+    batch = solver.solve_batch(second)
+    for i, fa in enumerate(second):
+        assert_same(batch[i], solver.solve(fa), what=f"frame {i}")
+
+
+def test_full_size_uneven_batch(torch):
+    """Crops of 128^2 .. 384^2 anchors, 16-144 hypotheses, BF16 storage (the batched
+    workload's shape, fewer frames): equal to the plain solve of every frame."""
+    cfgs = [(128, 16), (384, 40), (192, 144), (256, 64)]
+    frames = [S.make_frame(S.SceneConfig(crop_side=s, n_hyps=m), S.frame_seed(3, 1000 + i))
+              for i, (s, m) in enumerate(cfgs)]
+    fas = args_for(frames, B.BF16)
+    solver = B.Solver(B.Options(max_points=384 * 384, max_hyps=512))
+    batch = solver.solve_batch(fas)
+    for i, fa in enumerate(fas):
+        assert_same(batch[i], solver.solve(fa), what=f"frame {i}")
+        assert batch[i].best >= 0
+        er, et = S.rotation_error_deg(batch[i].T_cw[batch[i].best], frames[i].T_gt), \
+            S.translation_error_m(batch[i].T_cw[batch[i].best], frames[i].T_gt)
+        assert er < 0.2 and et < 1.0, (i, er, et)
+
+
+def test_batch_validation(torch):
+    frames = uneven_frames(sides=(20, 20), hyps=(2, 2), base=990)
+    solver = B.Solver(B.Options())
+    a = args_for(frames[:1])[0]
+    host = B.FrameArgs(frames[1], B.host_arrays(frames[1]), is_device=False)
+    with pytest.raises(B.PilotError, match="device frames"):
+        solver.solve_batch([a, host])
+    other = S.make_frame(S.config_reduced_frame(crop_side=20, n_hyps=2, channels=16), 5)
+    with pytest.raises(B.PilotError, match="C, L and feat_dtype"):
+        solver.solve_batch([a, args_for([other])[0]])
+    with pytest.raises(B.PilotError, match="max_frames"):
+        B.Solver(B.Options(max_frames=1)).solve_batch([a, a])
+    assert solver.solve_batch([]) == []

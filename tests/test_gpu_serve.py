@@ -1,0 +1,112 @@
+"""Serving (pilot_serve_*): continuous batching with admission by slots and device memory.
+
+Every served frame's result must be bitwise the result of its own pilot_align_solve
+(which test_gpu_parity.py ties to the FP64 oracle), whether it is served alone or while
+other frames of other sizes are in flight at other pyramid levels.
+"""
+import time
+
+import numpy as np
+import pytest
+
+from paper_2606_31098_gb300 import binding as B
+from paper_2606_31098_gb300 import scenes as S
+
+from gpu_support import require_cuda
+from test_gpu_batch import args_for, assert_same, uneven_frames
+
+pytestmark = pytest.mark.gpu
+
+BUDGET = 2 << 30
+
+
+@pytest.fixture(scope="module")
+def torch():
+    return require_cuda()
+
+
+def test_served_mix_equals_plain_solves(torch):
+    frames = uneven_frames(sides=(40, 55, 70, 30, 62), hyps=(3, 7, 5, 2, 4), base=1100)
+    fas = args_for(frames)
+    opts = B.Options()
+    plain = [B.Solver(opts).solve(fa) for fa in fas]
+    server = B.Server(opts, BUDGET, max_slots=8)
+    tickets = [server.submit(fa) for fa in fas]
+    for i, t in enumerate(tickets):
+        res, lat = server.wait(t)
+        assert_same(res, plain[i], what=f"frame {i}")
+        assert lat > 0
+    st = server.stats()
+    assert st["completed"] == len(fas) and st["active"] == 0 and st["arena_bytes_in_use"] == 0
+    server.close()
+
+
+def test_result_alone_equals_result_in_the_mix(torch):
+    frames = uneven_frames(sides=(48, 66, 35), hyps=(5, 3, 6), base=1200)
+    fas = args_for(frames, B.BF16)
+    opts = B.Options(iters=(4, 4, 4, 0), keep_top_k=(0, 2, 4, 0))
+    server = B.Server(opts, BUDGET, max_slots=4)
+    alone, _ = server.wait(server.submit(fas[1]))
+    # the same frame again, submitted between others while they are in flight
+    t0 = server.submit(fas[0])
+    time.sleep(0.002)
+    t1 = server.submit(fas[1])
+    t2 = server.submit(fas[2])
+    mixed, _ = server.wait(t1)
+    server.wait(t0)
+    server.wait(t2)
+    assert_same(mixed, alone)
+    assert_same(mixed, B.Solver(opts).solve(fas[1]))
+    server.close()
+
+
+def test_admission_by_memory_serialises_frames_that_do_not_fit_together(torch):
+    frames = uneven_frames(sides=(50, 50, 50), hyps=(3, 3, 3), base=1300)
+    fas = args_for(frames)
+    nbytes = sum(a.numel() * a.element_size() for k, v in fas[0].arrays.items()
+                 for a in (v if isinstance(v, list) else [v]) if a is not None)
+    one = int(1.6 * nbytes)          # room for one frame (plus alignment), not for two
+    server = B.Server(B.Options(), one, max_slots=8)
+    tickets = [server.submit(fa) for fa in fas]
+    res = [server.wait(t)[0] for t in tickets]
+    st = server.stats()
+    assert st["peak_active"] == 1
+    assert st["arena_bytes_peak"] <= one
+    for i, fa in enumerate(fas):
+        assert_same(res[i], B.Solver(B.Options()).solve(fa), what=f"frame {i}")
+    server.close()
+
+
+def test_host_frames_are_staged_into_the_arena(torch):
+    f = S.make_frame(S.config_reduced_frame(crop_side=45, n_hyps=4), S.frame_seed(3, 1400))
+    host = B.FrameArgs(f, B.host_arrays(f), is_device=False)
+    server = B.Server(B.Options(), BUDGET, max_slots=2)
+    res, _ = server.wait(server.submit(host))
+    assert_same(res, B.Solver(B.Options()).solve(args_for([f])[0]))
+    server.close()
+
+
+def test_submit_errors(torch):
+    fas = args_for(uneven_frames(sides=(30,), hyps=(2,), base=1500))
+    server = B.Server(B.Options(), BUDGET, max_slots=1)
+    server.wait(server.submit(fas[0]))
+    other = S.make_frame(S.config_reduced_frame(crop_side=20, n_hyps=2, channels=16), 5)
+    with pytest.raises(B.PilotError, match="share C, L"):
+        server.submit(args_for([other])[0])
+    tiny = B.Server(B.Options(), 1 << 20, max_slots=1)
+    with pytest.raises(B.PilotError, match="budget"):
+        tiny.submit(fas[0])
+    # a full pending queue answers EBUSY (the worker is busy with the first frames)
+    busy = 0
+    tickets = []
+    for _ in range(200):
+        try:
+            tickets.append(server.submit(fas[0]))
+        except B.PilotError as e:
+            assert e.status == B.PILOT_EBUSY
+            busy += 1
+    assert busy > 0
+    for t in tickets:
+        server.wait(t)
+    server.close()
+    tiny.close()
