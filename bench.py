@@ -65,6 +65,7 @@ def parse():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--seed-index", type=int, default=0)
+    ap.add_argument("--no-forms", action="store_true", help="skip the batched and served measurements")
     return ap.parse_args()
 
 
@@ -159,6 +160,129 @@ def cpu_cores() -> int:
         return len(os.sched_getaffinity(0))
     except Exception:
         return os.cpu_count() or 1
+
+
+def batched_and_served(args, B, S, torch, world, stream):
+    """The batched form (uneven frames, one persistent launch per level under a graph) and
+    the served form (streams at 30 Hz with exponential inter-arrival times), both on BF16
+    storage.  Four distinct frames (crops 128^2, 192^2, 256^2, 384^2, 144 hypotheses each)
+    are generated once; each batch entry / request takes one of them with its own random
+    hypothesis count in [16, 144]."""
+    import threading
+    rng = np.random.default_rng(12345)
+    sides = (128, 192, 256, 384)
+    distinct = [S.make_frame(S.SceneConfig(crop_side=s_, n_hyps=144), S.frame_seed(3, 5000 + i))
+                for i, s_ in enumerate(sides)]
+    dev = [B.quantized_device_arrays(f, B.BF16) for f in distinct]
+    flush = torch.empty(512 * 1024 * 1024, dtype=torch.uint8, device="cuda")
+
+    def entry(k, m, arrays):
+        a = dict(arrays[k])
+        a["T_cw"] = a["T_cw"][:m].contiguous() if hasattr(a["T_cw"], "contiguous") else np.ascontiguousarray(a["T_cw"][:m])
+        return B.FrameArgs(distinct[k], a, is_device=hasattr(a["points"], "data_ptr") and a["points"].is_cuda, dtype=B.BF16)
+
+    def time_batch(fas, reps):
+        solver = B.Solver(B.Options(max_points=384 * 384, max_hyps=sum(fa.M for fa in fas), max_frames=len(fas)))
+        solver.solve_batch(fas, stream)
+        ts, units = [], 0
+        for _ in range(reps):
+            flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            res = solver.solve_batch(fas, stream)
+            e1.record(stream)
+            e1.synchronize()
+            ts.append(e0.elapsed_time(e1))
+            units += sum(r.hyp_iters for r in res)
+        solver.close()
+        return world * units / (sum(ts) / 1e3), sum(ts) / reps
+
+    uneven = [entry(int(rng.integers(0, 4)), int(rng.integers(16, 145)), dev) for _ in range(32)]
+    v_uneven, ms_uneven = time_batch(uneven, 3)
+    eight = [entry(2, 64, dev) for _ in range(8)]
+    v_256, ms_256 = time_batch(eight, 3)
+    batched = {"uneven32_bf16": {"value": v_uneven, "unit": UNIT, "ms_per_batch": ms_uneven,
+                                 "frames": 32, "crops": "128^2..384^2", "hypotheses": "16..144"},
+               "crop256x8_bf16": {"value": v_256, "unit": UNIT, "ms_per_batch": ms_256, "frames": 8,
+                                  "hypotheses": 64}}
+
+    # served form: host (page-locked) BF16 frames staged by the server per request
+    host = []
+    for d in dev:
+        h = {}
+        for k, v in d.items():
+            if isinstance(v, list):
+                h[k] = [x.cpu().pin_memory() for x in v]
+            else:
+                h[k] = v.cpu().pin_memory()
+        host.append(h)
+    sweep = []
+    budget = 16 << 30
+    for streams in (2, 8, 64):
+        server = B.Server(B.Options(max_points=384 * 384, max_hyps=64 * 144), budget, max_slots=64)
+        duration = 3.0
+        arrivals = []
+        for s_ in range(streams):
+            t = rng.exponential(1 / 30.0)
+            while t < duration:
+                arrivals.append(t)
+                t += rng.exponential(1 / 30.0)
+        arrivals.sort()
+        reqs = [entry(int(rng.integers(0, 4)), int(rng.integers(16, 145)), host) for _ in arrivals]
+        tickets, rejected = [], 0
+        lat, units, done_t = [], 0, []
+        lock = threading.Lock()
+        stop = [False]
+
+        def poller():
+            while True:
+                with lock:
+                    pend = list(tickets)
+                    fin = stop[0]
+                if fin and not pend:
+                    return
+                for tk in pend:
+                    ok, r, l_ = server.poll(tk)
+                    if ok:
+                        with lock:
+                            tickets.remove(tk)
+                            lat.append(l_)
+                            done_t.append(time.perf_counter())
+                        nonlocal_units[0] += r.hyp_iters
+                time.sleep(0.0005)
+
+        nonlocal_units = [0]
+        th = threading.Thread(target=poller)
+        th.start()
+        t0 = time.perf_counter()
+        for a, fa in zip(arrivals, reqs):
+            dt = t0 + a - time.perf_counter()
+            if dt > 0:
+                time.sleep(dt)
+            try:
+                tk = server.submit(fa)
+                with lock:
+                    tickets.append(tk)
+            except B.PilotError as e:
+                if e.status != B.PILOT_EBUSY:
+                    raise
+                rejected += 1
+        with lock:
+            stop[0] = True
+        th.join()
+        span = (max(done_t) - t0) if done_t else 1.0
+        st = server.stats()
+        server.close()
+        sweep.append({"streams": streams, "offered_fps": len(arrivals) / duration,
+                      "completed_fps": len(lat) / span, "rejected_ebusy": rejected,
+                      "hyp_iter_per_s": nonlocal_units[0] / span,
+                      "p50_ms": float(np.percentile(lat, 50)) if lat else None,
+                      "p99_ms": float(np.percentile(lat, 99)) if lat else None,
+                      "peak_active": st["peak_active"], "rounds": st["rounds"]})
+    served = {"sweep": sweep, "hbm_budget_bytes": budget, "max_slots": 64, "storage": "bf16",
+              "arrivals": "30 Hz per stream, exponential inter-arrival (mean 33 ms), 3 s",
+              "frames": "host page-locked BF16 frames, crops 128^2..384^2, 16..144 hypotheses"}
+    return batched, served
 
 
 def run_oracle_sample(frame, n_hyps: int, threads: int):
@@ -301,6 +425,8 @@ def run_ours(args):
     gather_gbs = units_per_launch * gather_bytes_per_unit(C, elem) / (avg_launch_ms * 1e-3) / 1e9
     traffic = traffic_per_launch(units_per_launch)
 
+    batched, served = batched_and_served(args, B, S, torch, world, stream) if not args.no_forms else ({}, {})
+
     h2d = sum(a.nbytes for k, v in B.host_arrays(frame).items() for a in (v if isinstance(v, list) else [v]))
     d2h = frame.M * (12 * 8 + 8 + 4 + 4) + 16
 
@@ -333,6 +459,8 @@ def run_ours(args):
                              "gather_bytes_per_unit": gather_bytes_per_unit(C, elem), "gather_GBps": gather_gbs,
                              "build_share_of_step": build_ms / total_ms},
                 "precision_forms": precision,
+                "batched_form": batched,
+                "served_form": served,
                 "clocks": clk,
                 "cpu_baseline": cpu}
         print(json.dumps(line), flush=True)
