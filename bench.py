@@ -183,6 +183,7 @@ def batched_and_served(args, B, S, torch, world, stream):
 
     def time_batch(fas, reps):
         solver = B.Solver(B.Options(max_points=384 * 384, max_hyps=sum(fa.M for fa in fas), max_frames=len(fas)))
+        sched, _ = solver.autotune(fas, batched=True, reps=1, stream=stream)
         solver.solve_batch(fas, stream)
         ts, units = [], 0
         for _ in range(reps):
@@ -195,16 +196,17 @@ def batched_and_served(args, B, S, torch, world, stream):
             ts.append(e0.elapsed_time(e1))
             units += sum(r.hyp_iters for r in res)
         solver.close()
-        return world * units / (sum(ts) / 1e3), sum(ts) / reps
+        return world * units / (sum(ts) / 1e3), sum(ts) / reps, sched
 
     uneven = [entry(int(rng.integers(0, 4)), int(rng.integers(16, 145)), dev) for _ in range(32)]
-    v_uneven, ms_uneven = time_batch(uneven, 3)
+    v_uneven, ms_uneven, sc_uneven = time_batch(uneven, 3)
     eight = [entry(2, 64, dev) for _ in range(8)]
-    v_256, ms_256 = time_batch(eight, 3)
+    v_256, ms_256, sc_256 = time_batch(eight, 3)
     batched = {"uneven32_bf16": {"value": v_uneven, "unit": UNIT, "ms_per_batch": ms_uneven,
-                                 "frames": 32, "crops": "128^2..384^2", "hypotheses": "16..144"},
+                                 "frames": 32, "crops": "128^2..384^2", "hypotheses": "16..144",
+                                 "schedule": sc_uneven},
                "crop256x8_bf16": {"value": v_256, "unit": UNIT, "ms_per_batch": ms_256, "frames": 8,
-                                  "hypotheses": 64}}
+                                  "hypotheses": 64, "schedule": sc_256}}
 
     # served form: host (page-locked) BF16 frames staged by the server per request
     host = []
@@ -379,6 +381,7 @@ def run_ours(args):
             units += r.hyp_iters
         return times, build_ms, build_n, launches, units, r
 
+    plain_schedule, _ = solver.autotune([dev], batched=False, reps=3, stream=stream)
     for _ in range(args.warmup):
         solver.solve(dev, stream)
         solver.solve(host, stream)
@@ -446,6 +449,7 @@ def run_ours(args):
                 "config": {"workload": WORKLOAD, "points": frame.N, "hypotheses": frame.M, "channels": C,
                            "levels": [list(q.shape[:2]) for q in frame.qry_feat], "iters_per_level": [10, 10, 10],
                            "feature_dtype": "f32", "form": "plain single frame, one stream",
+                           "schedule": plain_schedule,
                            "l2": "flushed between steps (512 MiB write)", "replicas": world},
                 "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
                         "d2h_bytes_per_step": int(d2h), "ms_per_step": e2e_ms / args.steps},

@@ -154,6 +154,29 @@ pilot_status pilot_align_validate(const pilot_align_config* cfg, const pilot_fra
 pilot_status pilot_align_solve(pilot_align_handle* h, const pilot_frame* frame,
                                pilot_result* result, void* stream);
 
+/* Schedule of the build pass: chosen per frame shape by pilot_align_autotune, else the
+ * defaults (tile 1024, as many CTAs per SM as fit, longest frames first). */
+typedef struct {
+    int tile;         /* anchors per reduction tile: 512, 1024, 2048 or 4096 */
+    int ctas_per_sm;  /* batched form: persistent CTAs per SM; 0 = as many as fit */
+    int job_order;    /* batched form: 0 = frames with more anchors first, 1 = frames interleaved */
+} pilot_schedule;
+
+/* Autotuner: time the candidate schedules (4 tiles; for the batched form also 1 or 2 CTAs
+ * per SM and both job orders) on these frames, `reps` timed runs each after one warm-up, and
+ * keep the fastest for frames of this shape (storage type, C, and the powers of two of the
+ * mean anchor and hypothesis counts).  batched = 0 tunes pilot_align_solve on frames[0];
+ * batched = 1 tunes pilot_align_solve_batch on all frames.  *chosen and *best_ms (may be
+ * NULL) receive the winner and its mean time.  Results of later solves may differ from the
+ * default schedule's in the last bits (the reduction tile changes the summation order). */
+pilot_status pilot_align_autotune(pilot_align_handle* h, const pilot_frame* frames, int n_frames,
+                                  int batched, int reps, pilot_schedule* chosen, double* best_ms,
+                                  void* stream);
+
+/* The schedule the next solve of such frames would use (tuned or default). */
+pilot_status pilot_align_get_schedule(const pilot_align_handle* h, const pilot_frame* frames,
+                                      int n_frames, int batched, pilot_schedule* out);
+
 /* Batched form: solve n_frames independent frames (uneven N, M, map sizes, intrinsics,
  * priors) in one pass per pyramid level.  Each level is one persistent launch whose CTAs
  * pull (frame, hypothesis) jobs, longest first, and run a job's whole LM loop at that
@@ -162,8 +185,9 @@ pilot_status pilot_align_solve(pilot_align_handle* h, const pilot_frame* frame,
  * Requirements: every frame is a DEVICE frame; all frames share C, L, feat_dtype and the
  * presence of per-channel scales; n_frames <= max_frames; the hypotheses of all frames
  * together <= max_hyps, at most 8192 per frame.  results[i] receives frame i's outputs
- * exactly as pilot_align_solve would (the reduction order is the same, so each frame's
- * outputs are bitwise those of its own pilot_align_solve, whatever else is in the batch).
+ * exactly as pilot_align_solve would: with the same tile (both untuned, or tuned alike)
+ * the reduction order is the same, so each frame's outputs are bitwise those of its own
+ * pilot_align_solve, whatever else is in the batch.
  * Synchronous on `stream`. */
 pilot_status pilot_align_solve_batch(pilot_align_handle* h, const pilot_frame* frames, int n_frames,
                                      pilot_result* results, void* stream);

@@ -63,6 +63,8 @@ SIGNATURES = {
     "pilot_align_validate": (ct.c_int, [ct.POINTER(pilot_align_config), ct.POINTER(pilot_frame)]),
     "pilot_align_solve": (ct.c_int, [_vp, ct.POINTER(pilot_frame), ct.POINTER(pilot_result), _vp]),
     "pilot_align_solve_batch": (ct.c_int, [_vp, _vp, ct.c_int, _vp, _vp]),
+    "pilot_align_autotune": (ct.c_int, [_vp, _vp, ct.c_int, ct.c_int, ct.c_int, _vp, ct.POINTER(ct.c_double), _vp]),
+    "pilot_align_get_schedule": (ct.c_int, [_vp, _vp, ct.c_int, ct.c_int, _vp]),
     "pilot_align_debug_normal_eq": (ct.c_int, [_vp, ct.POINTER(pilot_frame), ct.c_int, _vp, _vp, _vp]),
     "pilot_align_profile": (ct.c_int, [_vp, ct.POINTER(ct.c_double), ct.POINTER(ct.c_int), ct.POINTER(ct.c_int)]),
     "pilot_align_normal_eq_noalloc": (ct.c_int, [ct.POINTER(pilot_align_config), ct.POINTER(pilot_frame), ct.c_int,
@@ -78,6 +80,10 @@ SIGNATURES = {
     "pilot_serve_get_stats": (ct.c_int, [_vp, _vp]),
     "pilot_serve_destroy": (None, [_vp]),
 }
+
+
+class pilot_schedule(ct.Structure):
+    _fields_ = [("tile", ct.c_int), ("ctas_per_sm", ct.c_int), ("job_order", ct.c_int)]
 
 
 class pilot_serve_stats(ct.Structure):
@@ -306,6 +312,29 @@ class Solver:
         check(load().pilot_align_solve_batch(self.h, ct.cast(frames, _vp), n, ct.cast(res, _vp),
                                              self._stream(stream)))
         return [Result(o["T"], o["cost"], o["nv"], o["st"], int(o["best"][0]), int(o["hi"][0])) for o in outs]
+
+    @staticmethod
+    def _frame_array(fas):
+        frames = (pilot_frame * len(fas))()
+        for i, fa in enumerate(fas):
+            frames[i] = fa.c
+        return frames
+
+    def autotune(self, fas: list, batched: bool, reps: int = 2, stream=None) -> tuple[dict, float]:
+        """pilot_align_autotune: returns the chosen schedule and its mean time (ms)."""
+        frames = self._frame_array(fas)
+        sc = pilot_schedule()
+        ms = ct.c_double()
+        check(load().pilot_align_autotune(self.h, ct.cast(frames, _vp), len(fas), int(batched), int(reps),
+                                          ct.cast(ct.byref(sc), _vp), ct.byref(ms), self._stream(stream)))
+        return {"tile": sc.tile, "ctas_per_sm": sc.ctas_per_sm, "job_order": sc.job_order}, ms.value
+
+    def schedule(self, fas: list, batched: bool) -> dict:
+        frames = self._frame_array(fas)
+        sc = pilot_schedule()
+        check(load().pilot_align_get_schedule(self.h, ct.cast(frames, _vp), len(fas), int(batched),
+                                              ct.cast(ct.byref(sc), _vp)))
+        return {"tile": sc.tile, "ctas_per_sm": sc.ctas_per_sm, "job_order": sc.job_order}
 
     def normal_eq(self, fa: FrameArgs, level: int, T_cw, stream=None) -> np.ndarray:
         T = np.ascontiguousarray(T_cw, np.float64).reshape(-1, 12)

@@ -17,6 +17,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <map>
 #include <string>
 #include <vector>
 
@@ -49,7 +50,8 @@ pilot_status cuda_fail(cudaError_t e, const char* what) {
         if (e_ != cudaSuccess) return cuda_fail(e_, what);  \
     } while (0)
 
-constexpr int kTile = 1024;          // anchors per build-pass tile
+constexpr int kTile = 1024;          // default anchors per build-pass tile
+constexpr int kMinTile = 512;        // smallest tile the autotuner tries (sizes the workspace)
 
 bool channels_supported(int C) { return C == 4 || C == 8 || C == 16 || C == 32 || C == 64; }
 
@@ -180,6 +182,10 @@ struct pilot_align_handle {
     cudaGraphExec_t gexec = nullptr;
     long long graph_key = -1;
     int level_grid = 0;
+    // autotuned schedules by frame-shape key; a forced schedule while tuning
+    std::map<long long, pilot_schedule> tuned;
+    bool forcing = false;
+    pilot_schedule forced{};
     int build_launches = 0;
     int total_launches = 0;
     double build_ms = 0.0;
@@ -262,7 +268,7 @@ pilot_status bind_frame(pilot_align_handle* h, const pilot_frame* f, cudaStream_
 }
 
 BuildParams build_params(pilot_align_handle* h, const pilot_frame* f, const DevFrame& d, int level,
-                         int n_active, const int* active) {
+                         int n_active, const int* active, int tile = kTile) {
     BuildParams b{};
     const size_t N = (size_t)f->N;
     b.px = d.points;
@@ -292,8 +298,8 @@ BuildParams build_params(pilot_align_handle* h, const pilot_frame* f, const DevF
     b.state = h->state;
     b.partial = h->partial;
     b.n_active = n_active;
-    b.tile = kTile;
-    b.n_tiles = f->N > 0 ? (f->N + kTile - 1) / kTile : 1;
+    b.tile = tile;
+    b.n_tiles = f->N > 0 ? (f->N + tile - 1) / tile : 1;
     return b;
 }
 
@@ -367,6 +373,30 @@ pilot_status run_build(pilot_align_handle* h, pilot_dtype dt, const BuildParams&
     ++h->build_launches;
     ++h->total_launches;
     return PILOT_OK;
+}
+
+long long schedule_key(int batched, pilot_dtype dt, int C, double mean_n, double mean_m) {
+    const int nb = (int)floor(log2(mean_n > 1.0 ? mean_n : 1.0));
+    const int mb = (int)floor(log2(mean_m > 1.0 ? mean_m : 1.0));
+    return ((long long)batched << 40) | ((long long)dt << 32) | ((long long)C << 16) | ((long long)nb << 8) |
+           (long long)mb;
+}
+
+long long frames_key(const pilot_frame* frames, int n, int batched) {
+    double sn = 0, sm = 0;
+    for (int i = 0; i < n; ++i) {
+        sn += frames[i].N;
+        sm += frames[i].M;
+    }
+    return schedule_key(batched, frames[0].feat_dtype, frames[0].C, sn / n, sm / n);
+}
+
+pilot_schedule default_schedule() { return pilot_schedule{kTile, 0, 0}; }
+
+pilot_schedule schedule_for(const pilot_align_handle* h, const pilot_frame* frames, int n, int batched) {
+    if (h->forcing) return h->forced;
+    auto it = h->tuned.find(frames_key(frames, n, batched));
+    return it != h->tuned.end() ? it->second : default_schedule();
 }
 
 struct DeviceGuard {
@@ -499,16 +529,24 @@ cudaError_t level_occupancy_query(pilot_dtype dt, int C, bool scaled, int* n) {
 
 namespace {
 
+long long graph_key(pilot_dtype dt, int C, bool scaled, int L, const pilot_schedule& sc) {
+    return ((long long)dt << 40) | ((long long)C << 32) | ((long long)scaled << 31) | ((long long)L << 28) |
+           ((long long)sc.tile << 8) | (long long)sc.ctas_per_sm;
+}
+
 // Records the whole batched solve on h->bstream: descriptor upload, per-frame set-up,
 // one persistent launch per level (+ per-frame top-K), selection, result download.
-pilot_status capture_batch_graph(pilot_align_handle* h, pilot_dtype dt, int C, bool scaled, int L) {
+pilot_status capture_batch_graph(pilot_align_handle* h, pilot_dtype dt, int C, bool scaled, int L,
+                                 const pilot_schedule& sc) {
     const pilot_align_config& c = h->cfg;
     const BatchLayout lay = BatchLayout::make(c.max_frames, c.max_hyps);
     int dev = 0, sms = 0, per_sm = 0;
     PILOT_CUDA(cudaGetDevice(&dev), "cudaGetDevice");
     PILOT_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev), "SM count");
     PILOT_CUDA(level_occupancy(dt, C, scaled, &per_sm), "occupancy query");
-    h->level_grid = sms * (per_sm > 0 ? per_sm : 1);
+    if (per_sm < 1) per_sm = 1;
+    if (sc.ctas_per_sm > 0 && sc.ctas_per_sm < per_sm) per_sm = sc.ctas_per_sm;
+    h->level_grid = sms * per_sm;
     if (h->gexec) cudaGraphExecDestroy(h->gexec);
     if (h->graph) cudaGraphDestroy(h->graph);
     h->gexec = nullptr;
@@ -538,7 +576,7 @@ pilot_status capture_batch_graph(pilot_align_handle* h, pilot_dtype dt, int C, b
         a.level = level;
         a.n_jobs_index = level;
         for (int l = 0; l < PILOT_MAX_LEVELS; ++l) a.iters[l] = c.iters_per_level[l];
-        a.tile = kTile;
+        a.tile = sc.tile;
         a.damping_mode = c.damping_mode;
         a.huber = (float)c.huber_photo;
         a.lambda0 = c.lambda0;
@@ -560,7 +598,7 @@ pilot_status capture_batch_graph(pilot_align_handle* h, pilot_dtype dt, int C, b
     if (e2 != cudaSuccess) return cuda_fail(e2, "graph capture end");
     h->graph = g;
     PILOT_CUDA(cudaGraphInstantiate(&h->gexec, g, 0), "graph instantiate");
-    h->graph_key = ((long long)dt << 32) | ((long long)C << 16) | ((long long)scaled << 8) | (long long)L;
+    h->graph_key = graph_key(dt, C, scaled, L, sc);
     return PILOT_OK;
 }
 
@@ -592,7 +630,7 @@ pilot_status pilot_align_create(const pilot_align_config* cfg_in, pilot_align_ha
         return cuda_fail(e, "cudaGetDevice");
     }
     const size_t M = (size_t)cfg.max_hyps;
-    h->max_tiles = cfg.max_points > 0 ? (cfg.max_points + kTile - 1) / kTile : 1;
+    h->max_tiles = cfg.max_points > 0 ? (cfg.max_points + kMinTile - 1) / kMinTile : 1;
     const ResultLayout lay = ResultLayout::make(cfg.max_hyps);
     std::vector<float> ones(cfg.max_channels, 1.0f);
 #define ALLOC(ptr, bytes)                                      \
@@ -660,9 +698,10 @@ pilot_status pilot_align_solve(pilot_align_handle* h, const pilot_frame* f, pilo
     int cur = 0, n_active = M;
     const PriorParams prior = prior_params(c, f, d);
 
+    const int tile = schedule_for(h, f, 1, 0).tile;
     for (int level = f->L - 1; level >= 0; --level) {
         const int iters = c.iters_per_level[level];
-        BuildParams b = build_params(h, f, d, level, n_active, h->active[cur]);
+        BuildParams b = build_params(h, f, d, level, n_active, h->active[cur], tile);
         EpilogueParams ep{};
         ep.state = h->state;
         ep.pose32 = h->pose32;
@@ -825,6 +864,7 @@ pilot_status pilot_align_solve_batch(pilot_align_handle* h, const pilot_frame* f
     }
     // hypotheses per frame and level (top-K is deterministic in count), and the job
     // tables: frames with more anchors first (longest job first), slots in order
+    const pilot_schedule sc = schedule_for(h, frames, n, 1);
     std::vector<int> order(n);
     for (int i = 0; i < n; ++i) order[i] = i;
     std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return frames[a].N > frames[b].N; });
@@ -834,12 +874,25 @@ pilot_status pilot_align_solve_batch(pilot_align_handle* h, const pilot_frame* f
     for (int level = L - 1; level >= 0; --level) {
         int nj = 0;
         for (int i = 0; i < n; ++i) nactive[(size_t)level * lay.max_frames + i] = cur[i];
-        for (int oi = 0; oi < n; ++oi) {
-            const int i = order[oi];
-            for (int k = 0; k < cur[i]; ++k) {
-                job_frame[(size_t)level * lay.max_jobs + nj] = i;
-                job_slot[(size_t)level * lay.max_jobs + nj] = k;
-                ++nj;
+        if (sc.job_order == 1) {
+            int most = 0;
+            for (int i = 0; i < n; ++i) most = std::max(most, cur[i]);
+            for (int k = 0; k < most; ++k)
+                for (int oi = 0; oi < n; ++oi) {
+                    const int i = order[oi];
+                    if (k >= cur[i]) continue;
+                    job_frame[(size_t)level * lay.max_jobs + nj] = i;
+                    job_slot[(size_t)level * lay.max_jobs + nj] = k;
+                    ++nj;
+                }
+        } else {
+            for (int oi = 0; oi < n; ++oi) {
+                const int i = order[oi];
+                for (int k = 0; k < cur[i]; ++k) {
+                    job_frame[(size_t)level * lay.max_jobs + nj] = i;
+                    job_slot[(size_t)level * lay.max_jobs + nj] = k;
+                    ++nj;
+                }
             }
         }
         hdr->n_jobs[level] = nj;
@@ -849,9 +902,9 @@ pilot_status pilot_align_solve_batch(pilot_align_handle* h, const pilot_frame* f
             if (level > 0 && K > 0 && K < cur[i]) cur[i] = K;
         }
     }
-    const long long key = ((long long)f0.feat_dtype << 32) | ((long long)f0.C << 16) | ((long long)scaled << 8) | (long long)L;
+    const long long key = graph_key(f0.feat_dtype, f0.C, scaled, L, sc);
     if (!h->gexec || h->graph_key != key)
-        if ((st = capture_batch_graph(h, f0.feat_dtype, f0.C, scaled, L)) != PILOT_OK) return st;
+        if ((st = capture_batch_graph(h, f0.feat_dtype, f0.C, scaled, L, sc)) != PILOT_OK) return st;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     PILOT_CUDA(cudaGraphLaunch(h->gexec, s), "batch graph launch");
     PILOT_CUDA(cudaStreamSynchronize(s), "batch solve");
@@ -869,6 +922,78 @@ pilot_status pilot_align_solve_batch(pilot_align_handle* h, const pilot_frame* f
         if (out.best) *out.best = best[i];
         if (out.hyp_iters) *out.hyp_iters = hyp_iters[i];
     }
+    return PILOT_OK;
+}
+
+pilot_status pilot_align_autotune(pilot_align_handle* h, const pilot_frame* frames, int n, int batched,
+                                  int reps, pilot_schedule* chosen, double* best_ms, void* stream) {
+    if (!h || !frames || n < 1) return fail(PILOT_EINVAL, "handle or frames missing");
+    if (batched && n > h->cfg.max_frames) return fail(PILOT_EINVAL, "more frames than max_frames");
+    if (reps < 1) reps = 1;
+    std::vector<pilot_schedule> cands;
+    for (int tile : {512, 1024, 2048, 4096}) {
+        if (!batched) {
+            cands.push_back(pilot_schedule{tile, 0, 0});
+            continue;
+        }
+        for (int per_sm : {1, 0})
+            for (int order : {0, 1}) cands.push_back(pilot_schedule{tile, per_sm, order});
+    }
+    // results are discarded: one scratch record per hypothesis
+    long long total = 0;
+    for (int i = 0; i < (batched ? n : 1); ++i) total += frames[i].M;
+    std::vector<double> T(12 * (size_t)total), cost(total);
+    std::vector<int> nv(total), hs(total), best(n);
+    std::vector<long long> hi(n);
+    std::vector<pilot_result> res(n);
+    size_t o = 0;
+    for (int i = 0; i < (batched ? n : 1); ++i) {
+        res[i] = pilot_result{T.data() + 12 * o, cost.data() + o, nv.data() + o, hs.data() + o, &best[i], &hi[i]};
+        o += frames[i].M;
+    }
+    DeviceGuard guard(h->device);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    cudaEvent_t e0, e1;
+    PILOT_CUDA(cudaEventCreate(&e0), "event create");
+    PILOT_CUDA(cudaEventCreate(&e1), "event create");
+    double best_t = 1e300;
+    pilot_schedule win = default_schedule();
+    pilot_status st = PILOT_OK;
+    h->forcing = true;
+    for (const pilot_schedule& sc : cands) {
+        h->forced = sc;
+        float total_ms = 0.f;
+        for (int r = 0; r <= reps && st == PILOT_OK; ++r) {
+            cudaEventRecord(e0, s);
+            st = batched ? pilot_align_solve_batch(h, frames, n, res.data(), stream)
+                         : pilot_align_solve(h, frames, res.data(), stream);
+            cudaEventRecord(e1, s);
+            cudaEventSynchronize(e1);
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            if (r > 0) total_ms += ms;          // the first run warms up (and captures the graph)
+        }
+        if (st != PILOT_OK) break;
+        const double mean = total_ms / reps;
+        if (mean < best_t) {
+            best_t = mean;
+            win = sc;
+        }
+    }
+    h->forcing = false;
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (st != PILOT_OK) return st;
+    h->tuned[frames_key(frames, batched ? n : 1, batched)] = win;
+    if (chosen) *chosen = win;
+    if (best_ms) *best_ms = best_t;
+    return PILOT_OK;
+}
+
+pilot_status pilot_align_get_schedule(const pilot_align_handle* h, const pilot_frame* frames, int n,
+                                      int batched, pilot_schedule* out) {
+    if (!h || !frames || n < 1 || !out) return fail(PILOT_EINVAL, "handle, frames or out missing");
+    *out = schedule_for(h, frames, batched ? n : 1, batched);
     return PILOT_OK;
 }
 

@@ -111,3 +111,28 @@ def test_batch_validation(torch):
     with pytest.raises(B.PilotError, match="max_frames"):
         B.Solver(B.Options(max_frames=1)).solve_batch([a, a])
     assert solver.solve_batch([]) == []
+
+
+def test_autotuner_picks_a_schedule_that_keeps_the_results(torch):
+    """pilot_align_autotune times the candidate schedules on the caller's frames and keeps
+    the fastest for that frame shape; solves with the tuned schedule select the same pose
+    (the reduction tile only changes the summation order)."""
+    frames = uneven_frames(sides=(64, 64, 64, 64), hyps=(6, 6, 6, 6), base=1600)
+    fas = args_for(frames)
+    solver = B.Solver(B.Options())
+    default = solver.schedule(fas, batched=True)
+    assert default == {"tile": 1024, "ctas_per_sm": 0, "job_order": 0}
+    before = solver.solve_batch(fas)
+    chosen, ms = solver.autotune(fas, batched=True, reps=1)
+    assert chosen["tile"] in (512, 1024, 2048, 4096) and chosen["ctas_per_sm"] in (0, 1) and ms > 0
+    assert solver.schedule(fas, batched=True) == chosen
+    after = solver.solve_batch(fas)
+    plain_chosen, _ = solver.autotune(fas[:1], batched=False, reps=1)
+    assert solver.schedule(fas[:1], batched=False) == plain_chosen
+    for i, f in enumerate(frames):
+        a, b = before[i], after[i]
+        assert (a.best >= 0) == (b.best >= 0)
+        if a.best >= 0:
+            assert S.rotation_error_deg(a.T_cw[a.best], b.T_cw[b.best]) < 1e-3
+            assert S.translation_error_m(a.T_cw[a.best], b.T_cw[b.best]) < 1e-3
+            assert a.cost[a.best] == pytest.approx(b.cost[b.best], rel=1e-5)
