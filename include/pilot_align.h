@@ -83,8 +83,8 @@ typedef struct {
     double huber_range;      /* delta of the range Huber, metres (Eq. 7); 0 -> 1.0 */
     int keep_top_k[PILOT_MAX_LEVELS]; /* after level l > 0 keep the K lowest objectives
                                          for the finer levels; 0 = keep all */
-    double min_valid_frac;   /* acceptance / status threshold, fraction of valid anchors;
-                                negative -> 0.05 */
+    double min_valid_frac;   /* acceptance / status threshold, fraction of valid anchors
+                                in [0, 1]; 0 = no threshold (0.05 is the usual value) */
     int max_points;          /* workspace sizing: largest N, M, C the handle accepts */
     int max_hyps;
     int max_channels;
