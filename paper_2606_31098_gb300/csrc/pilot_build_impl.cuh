@@ -123,6 +123,70 @@ __device__ __forceinline__ void channel(ChanSums& a, float t00, float t01, float
     a.b1 = fmaf(fv, r, a.b1);
 }
 
+// ---- two channels per instruction: packed FP32x2 arithmetic (each lane of the pair is
+// rounded exactly like the scalar operation) ----
+typedef unsigned long long f2;
+
+__device__ __forceinline__ f2 pk(float lo, float hi) {
+    f2 r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
+    return r;
+}
+__device__ __forceinline__ void upk(f2 v, float& lo, float& hi) {
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
+}
+__device__ __forceinline__ f2 sub2(f2 a, f2 b) {
+    f2 r;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+    return r;
+}
+__device__ __forceinline__ f2 mul2(f2 a, f2 b) {
+    f2 r;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+    return r;
+}
+__device__ __forceinline__ f2 fma2(f2 a, f2 b, f2 c) {
+    f2 r;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r) : "l"(a), "l"(b), "l"(c));
+    return r;
+}
+
+// Six sums over channel pairs: lane .lo of each accumulates even channels, .hi odd ones.
+struct ChanSums2 {
+    f2 s, m00, m01, m11, b0, b1;
+};
+
+// Two channels at once: the same operations as channel(), in packed form.
+template <bool SCALED>
+__device__ __forceinline__ void channel_pair(ChanSums2& a, f2 t00, f2 t01, f2 t10, f2 t11, f2 fr,
+                                             f2 ax, f2 ay, f2 sq, f2 sr) {
+    const f2 bq = sub2(t01, t00);
+    const f2 cq = sub2(t10, t00);
+    const f2 dq = sub2(sub2(t11, t10), bq);
+    f2 fu = fma2(dq, ay, bq);
+    f2 fv = fma2(dq, ax, cq);
+    f2 f = fma2(ax, fu, fma2(ay, cq, t00));
+    if constexpr (SCALED) {
+        f = mul2(f, sq);
+        fu = mul2(fu, sq);
+        fv = mul2(fv, sq);
+        fr = mul2(fr, sr);
+    }
+    const f2 r = sub2(f, fr);
+    a.s = fma2(r, r, a.s);
+    a.m00 = fma2(fu, fu, a.m00);
+    a.m01 = fma2(fu, fv, a.m01);
+    a.m11 = fma2(fv, fv, a.m11);
+    a.b0 = fma2(fu, r, a.b0);
+    a.b1 = fma2(fv, r, a.b1);
+}
+
+__device__ __forceinline__ float hsum(f2 v) {
+    float lo, hi;
+    upk(v, lo, hi);
+    return lo + hi;
+}
+
 // The level-specific inputs of the anchor loop.
 struct LevelView {
     const float* px;
@@ -238,7 +302,8 @@ __device__ __forceinline__ void accumulate_anchors(const LevelView& v, const flo
                 const Elem* t00 = qry + oi;
                 const Elem* t10 = t00 + WC;
                 const Elem* fr = ref + ri;
-                ChanSums cs{0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+                const f2 ax2 = pk(axi, axi), ay2 = pk(ayi, ayi), z2 = pk(0.f, 0.f);
+                ChanSums2 cs{z2, z2, z2, z2, z2, z2};
 #pragma unroll
                 for (int k = 0; k < NV; ++k) {
                     const int c = VW * (q + k * LP);
@@ -249,16 +314,19 @@ __device__ __forceinline__ void accumulate_anchors(const LevelView& v, const flo
                     load_vec<DT, VW>(t10 + c + C, a11);
                     load_vec<DT, VW>(fr + c, rr);
 #pragma unroll
-                    for (int e = 0; e < VW; ++e)
-                        channel<SCALED>(cs, a00[e], a01[e], a10[e], a11[e], rr[e], axi, ayi,
-                                        qs[k * VW + e], rs[k * VW + e]);
+                    for (int e = 0; e < VW; e += 2)
+                        channel_pair<SCALED>(cs, pk(a00[e], a00[e + 1]), pk(a01[e], a01[e + 1]),
+                                             pk(a10[e], a10[e + 1]), pk(a11[e], a11[e + 1]),
+                                             pk(rr[e], rr[e + 1]), ax2, ay2,
+                                             pk(qs[k * VW + e], qs[k * VW + e + 1]),
+                                             pk(rs[k * VW + e], rs[k * VW + e + 1]));
                 }
-                P2[u][0] = cs.s;
-                P2[u][1] = cs.m00;
-                P2[u][2] = cs.m01;
-                P2[u][3] = cs.m11;
-                P2[u][4] = cs.b0;
-                P2[u][5] = cs.b1;
+                P2[u][0] = hsum(cs.s);
+                P2[u][1] = hsum(cs.m00);
+                P2[u][2] = hsum(cs.m01);
+                P2[u][3] = hsum(cs.m11);
+                P2[u][4] = hsum(cs.b0);
+                P2[u][5] = hsum(cs.b1);
             }
             if constexpr (LP > 1) {
                 const bool upper = (q & HALF) != 0;
@@ -359,7 +427,7 @@ __device__ __forceinline__ float cta_reduce(float* acc, float (*red)[kAcc]) {
 }
 
 template <pilot_dtype DT, int C, bool SCALED>
-__global__ void __launch_bounds__(kBuildThreads)
+__global__ void __launch_bounds__(kBuildThreads, 2)
 build_kernel(const BuildParams p) {
     __shared__ float red[kBuildThreads / 32][kAcc];
     const int slot = blockIdx.y;
@@ -380,7 +448,7 @@ build_kernel(const BuildParams p) {
 // ticket of its hypothesis sums the tile records (FP64, 8 chains per value, fixed order)
 // and runs lm_step.  A hypothesis without a candidate runs its step in tile 0's CTA.
 template <pilot_dtype DT, int C, bool SCALED>
-__global__ void __launch_bounds__(kBuildThreads)
+__global__ void __launch_bounds__(kBuildThreads, 2)
 build_fused_kernel(const FusedBuildParams fp) {
     const BuildParams& p = fp.b;
     __shared__ float red[kBuildThreads / 32][kAcc];

@@ -66,11 +66,18 @@ class SceneConfig:
     pitch_deg: tuple = (30.0, 70.0)       # depression of the optical axis below horizon
     ref_noise: float = 0.01               # std of the noise added to reference descriptors
     n_hyps: int = 64
-    hyp_mode: str = "xy_yaw"              # "xy_yaw": U(+-dxy, +-dxy, +-dyaw); "rot_trans": exact angle/offset
+    hyp_mode: str = "xy_yaw"              # "xy_yaw": U(+-dxy, +-dxy, +-dyaw); "rot_trans": exact angle/offset;
+                                          # "grid": grid_xy^2 x grid_yaw_deg around a perturbed prior
     hyp_xy: float = 10.0                  # metres
     hyp_yaw_deg: float = 5.0              # degrees
     hyp_rot_deg: float = 3.0              # rot_trans mode: rotation angle about a random axis
     hyp_trans: float = 5.0                # rot_trans mode: translation length
+    # grid mode: the (x, y, yaw) grid of Supp. "Multi-Hypothesis Refinement" around a prior
+    grid_xy: tuple = tuple(float(v) for v in range(-10, 11, 2))      # metres, x and y
+    grid_yaw_deg: tuple = (-9.0, -7.0, -5.0, -3.0, -1.0, 1.0, 3.0, 5.0, 7.0, 9.0)
+    prior_xy: float = 4.0                 # prior = GT shifted by U(+-prior_xy) in x and y
+    prior_yaw_deg: float = 4.0            # ... and rotated by U(+-prior_yaw_deg) in yaw
+    n_anchors: int = 0                    # > 0: sample this many valid anchors of the crop
     use_gravity: bool = True
     gravity_noise_deg: float = 0.2
     w_grav: float = 1e2
@@ -94,13 +101,27 @@ def config_full_frame(n_hyps: int = 64) -> SceneConfig:
     return SceneConfig(n_hyps=n_hyps)
 
 
-def config_reduced_frame(crop_side: int = 70, n_hyps: int = 6, channels: int = 32,
+def config_paper_schedule(n_anchors: int = 500, crop_side: int = 256) -> SceneConfig:
+    """The paper's own refinement schedule (Sec. V-A "Implementation Details", Supp.
+    "Multi-Hypothesis Refinement"): 500 geo-anchors sampled from the crop, the 1210
+    hypotheses of the 11 x 11 (x, y) grid (+-10 m, 2 m steps) times 10 yaw offsets
+    (+-1, 3, 5, 7, 9 deg) around a prior pose, images resized to 512 px (levels 384x512 /
+    192x256 / 96x128, focal length scaled so the field of view stays that of the full
+    frame).  The solve keeps the best 128 after the coarse level and runs 2 / 3 / 4
+    iterations from coarse to fine."""
+    return SceneConfig(crop_side=crop_side, levels=((384, 512), (192, 256), (96, 128)),
+                       f0=600.0 * 512.0 / 640.0, hyp_mode="grid", n_anchors=n_anchors)
+
+
+def config_reduced_frame(crop_side: int = 90, n_hyps: int = 6, channels: int = 32,
                          levels=((240, 320), (120, 160), (60, 80)), f0: float = 600.0,
                          gsd: float = 1.0) -> SceneConfig:
     """The full-frame recipe shrunk so that the FP64 oracle finishes in seconds, while
-    still spanning several point tiles and a ragged tail (70^2 = 4900 anchors).  The
+    still spanning several point tiles and a ragged tail (90^2 = 8100 anchors).  The
     focal length stays that of the full frame (600 px at the finest level), so a pixel
-    subtends the same angle and the pose is as well conditioned per anchor."""
+    subtends the same angle and the pose is as well conditioned per anchor; with fewer
+    anchors the weakest direction of the FP32 objective flattens toward the 1 mm parity
+    tolerance, which 90^2 anchors keep well clear of."""
     return SceneConfig(crop_side=crop_side, gsd=gsd, channels=channels, levels=levels,
                        f0=f0, n_hyps=n_hyps)
 
@@ -347,12 +368,31 @@ def make_frame(cfg: SceneConfig, seed: int) -> Frame:
         refs.append(f.astype(np.float32))
     for f in refs:
         f[~valid] = 0.0
+    if cfg.n_anchors > 0:
+        # sample geo-anchors among the crop cells seen at every level (Sec. V-A: the
+        # refinement runs on a fixed number of valid anchors drawn from the crop)
+        cand = np.flatnonzero(valid)
+        if cand.size < cfg.n_anchors:
+            raise ValueError(f"only {cand.size} valid crop cells for {cfg.n_anchors} anchors")
+        keep = np.sort(np.random.default_rng(kids[6]).choice(cand, cfg.n_anchors, replace=False))
+        points = np.ascontiguousarray(points[:, keep])
+        valid = valid[keep]
+        refs = [np.ascontiguousarray(f[keep]) for f in refs]
 
     # hypotheses
     M = cfg.n_hyps
+    if cfg.hyp_mode == "grid":
+        r_prior = np.random.default_rng(kids[7])
+        pdx, pdy = r_prior.uniform(-cfg.prior_xy, cfg.prior_xy, 2)
+        prior = _perturb_xy_yaw(T_gt, pdx, pdy, np.deg2rad(r_prior.uniform(-cfg.prior_yaw_deg, cfg.prior_yaw_deg)))
+        grid = [(gx, gy, gp) for gx in cfg.grid_xy for gy in cfg.grid_xy for gp in cfg.grid_yaw_deg]
+        M = len(grid)
     hyps = np.empty((M, 12))
     for m in range(M):
-        if cfg.hyp_mode == "xy_yaw":
+        if cfg.hyp_mode == "grid":
+            gx, gy, gp = grid[m]
+            hyps[m] = _perturb_xy_yaw(prior, gx, gy, np.deg2rad(gp))
+        elif cfg.hyp_mode == "xy_yaw":
             dx, dy = r_hyp.uniform(-cfg.hyp_xy, cfg.hyp_xy, 2)
             dpsi = np.deg2rad(r_hyp.uniform(-cfg.hyp_yaw_deg, cfg.hyp_yaw_deg))
             hyps[m] = _perturb_xy_yaw(T_gt, dx, dy, dpsi)
@@ -381,7 +421,8 @@ def make_frame(cfg: SceneConfig, seed: int) -> Frame:
                  use_range=cfg.use_range, range_m=float(rng_meas), w_range=cfg.w_range,
                  dsm=dsm, dsm_x0=x0, dsm_y0=y0, dsm_gsd=gsd, seed=seed,
                  meta=dict(alt=alt, pitch_deg=float(np.rad2deg(pitch)), yaw_deg=float(np.rad2deg(yaw)),
-                           range_true=float(rng_true), crop_side=S))
+                           range_true=float(rng_true), crop_side=S,
+                           T_prior=prior if cfg.hyp_mode == "grid" else None))
 
 
 def frame_seed(workload: int, index: int) -> int:

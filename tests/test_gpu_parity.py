@@ -3,7 +3,7 @@
 Build pass: normal equations of the total objective (Eq. 7, Eq. 8) at identical inputs,
 every level, element by element under the scale-aware 1e-5 tolerance.  Whole solve
 (Eq. 8-9, Sec. IV-E): final poses within 1e-3 deg / 1 mm, statuses equal.  Sizes span
-several 1024-anchor tiles with a ragged tail (70^2 = 4900), odd hypothesis counts, and
+several 1024-anchor tiles with a ragged tail (90^2 = 8100), odd hypothesis counts, and
 the full 256^2-crop, C = 32, 3-level workload on sampled hypotheses.
 """
 import dataclasses
