@@ -309,6 +309,56 @@ def batched_and_served(args, B, S, torch, world, stream):
     return batched, served
 
 
+def paper_schedule_form(args, B, S, torch, world, stream):
+    """The paper's own refinement schedule (Sec. V-A, Supp. "Multi-Hypothesis Refinement"):
+    500 sampled anchors, 1210 grid hypotheses, best 128 kept after the coarse level, 2 / 3 / 4
+    iterations coarse to fine (3316 hyp*iter per frame), 384x512 / 192x256 / 96x128 levels,
+    C = 32.  Plain FP32 solves one frame at a time; the batched form solves 8 frames per
+    graph replay (the FP64 oracle's time for such a frame is in cpu_baseline)."""
+    frames = [S.make_frame(S.config_paper_schedule(), S.frame_seed(6, i)) for i in range(2)]
+    po = dict(iters=(4, 3, 2, 0), keep_top_k=(0, 0, 128, 0), max_points=500)
+    flush = torch.empty(512 * 1024 * 1024, dtype=torch.uint8, device="cuda")
+
+    def timed(fn, reps):
+        fn()
+        fn()
+        ts, units = [], 0
+        for _ in range(reps):
+            flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            u = fn()
+            e1.record(stream)
+            e1.synchronize()
+            ts.append(e0.elapsed_time(e1))
+            units += u
+        return ts, units
+
+    out = {}
+    solver = B.Solver(B.Options(max_hyps=1210, **po))
+    fas = [B.FrameArgs(f, B.device_arrays(f), is_device=True) for f in frames]
+    k = [0]
+
+    def plain():
+        k[0] ^= 1
+        return solver.solve(fas[k[0]], stream).hyp_iters
+    ts, units = timed(plain, 6)
+    out["plain_f32"] = {"ms_per_frame": sum(ts) / len(ts), "value": world * units / (sum(ts) / 1e3), "unit": UNIT}
+    solver.close()
+    for dt in (B.F32, B.BF16):
+        bs = B.Solver(B.Options(max_hyps=1210 * 8, max_frames=8, **po))
+        qa = [B.FrameArgs(f, B.quantized_device_arrays(f, dt), is_device=True, dtype=dt) for f in frames] * 4
+        ts, units = timed(lambda: sum(r.hyp_iters for r in bs.solve_batch(qa, stream)), 3)
+        out[f"batched8_{B.DTYPE_NAMES[dt]}"] = {"ms_per_frame": sum(ts) / len(ts) / 8,
+                                                "value": world * units / (sum(ts) / 1e3), "unit": UNIT}
+        bs.close()
+    out["hyp_iter_per_frame"] = 1210 * 2 + 128 * 3 + 128 * 4
+    out["workload"] = ("500 sampled anchors, 1210 grid hypotheses (11 x 11 x 10), top 128 after the coarse "
+                       "level, 2/3/4 LM iterations, levels 384x512/192x256/96x128, C=32, priors on")
+    out["paper_context"] = "optimiser 43.82 ms per frame on an RTX 5090 for this schedule (Supp. runtime table)"
+    return out
+
+
 def run_oracle_sample(frame, n_hyps: int, threads: int):
     """Solve `n_hyps` hypotheses of the frame with the FP64 oracle; returns
     (hyp_iters, seconds)."""
@@ -445,6 +495,7 @@ def run_ours(args):
     traffic = traffic_per_launch(units_per_launch)
 
     batched, served = batched_and_served(args, B, S, torch, world, stream) if not args.no_forms else ({}, {})
+    paper = paper_schedule_form(args, B, S, torch, world, stream) if not args.no_forms else {}
 
     h2d = sum(a.nbytes for k, v in B.host_arrays(frame).items() for a in (v if isinstance(v, list) else [v]))
     d2h = frame.M * (12 * 8 + 8 + 4 + 4) + 16
@@ -457,6 +508,12 @@ def run_ours(args):
         cpu = {"value": u / s, "unit": UNIT, "cores": threads, "kind": "oracle",
                "sample": f"{nh} of the 64 hypotheses of the same frame, all 3 levels x 10 iterations "
                          f"({u} hyp*iter in {s:.1f} s)"}
+        if paper:
+            from oracle import oracle as O
+            pf = S.make_frame(S.config_paper_schedule(), S.frame_seed(6, 0))
+            t0 = time.perf_counter()
+            O.solve(pf, O.SolverOptions(iters=(4, 3, 2, 0), keep_top_k=(0, 0, 128, 0)), n_threads=threads)
+            cpu["paper_schedule_ms_per_frame"] = 1e3 * (time.perf_counter() - t0)
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -480,7 +537,7 @@ def run_ours(args):
                              "build_share_of_step": build_ms / total_ms},
                 "precision_forms": precision,
                 "batched_form": batched,
-                "served_form": served,
+                "served_form": served, "paper_schedule_form": paper,
                 "clocks": clk,
                 "cpu_baseline": cpu}
         print(json.dumps(line), flush=True)

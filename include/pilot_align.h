@@ -154,8 +154,9 @@ pilot_status pilot_align_validate(const pilot_align_config* cfg, const pilot_fra
 pilot_status pilot_align_solve(pilot_align_handle* h, const pilot_frame* frame,
                                pilot_result* result, void* stream);
 
-/* Schedule of the build pass: chosen per frame shape by pilot_align_autotune, else the
- * defaults (tile 1024, as many CTAs per SM as fit, longest frames first). */
+/* Schedule of the build pass: chosen per frame shape by pilot_align_autotune (or set by
+ * pilot_align_set_schedule), else the defaults (tile 1024, as many CTAs per SM as fit,
+ * longest frames first). */
 typedef struct {
     int tile;         /* anchors per reduction tile: 512, 1024, 2048 or 4096 */
     int ctas_per_sm;  /* batched form: persistent CTAs per SM; 0 = as many as fit */
@@ -173,7 +174,13 @@ pilot_status pilot_align_autotune(pilot_align_handle* h, const pilot_frame* fram
                                   int batched, int reps, pilot_schedule* chosen, double* best_ms,
                                   void* stream);
 
-/* The schedule the next solve of such frames would use (tuned or default). */
+/* Use `schedule` for later solves of frames of this shape (the key pilot_align_autotune
+ * uses), replacing any tuned schedule: pins a schedule across runs, since the tile changes
+ * the summation order.  EINVAL if a field is outside the values listed above. */
+pilot_status pilot_align_set_schedule(pilot_align_handle* h, const pilot_frame* frames, int n_frames,
+                                      int batched, const pilot_schedule* schedule);
+
+/* The schedule the next solve of such frames would use (tuned, set or default). */
 pilot_status pilot_align_get_schedule(const pilot_align_handle* h, const pilot_frame* frames,
                                       int n_frames, int batched, pilot_schedule* out);
 

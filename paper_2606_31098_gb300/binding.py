@@ -65,6 +65,7 @@ SIGNATURES = {
     "pilot_align_solve_batch": (ct.c_int, [_vp, _vp, ct.c_int, _vp, _vp]),
     "pilot_align_autotune": (ct.c_int, [_vp, _vp, ct.c_int, ct.c_int, ct.c_int, _vp, ct.POINTER(ct.c_double), _vp]),
     "pilot_align_get_schedule": (ct.c_int, [_vp, _vp, ct.c_int, ct.c_int, _vp]),
+    "pilot_align_set_schedule": (ct.c_int, [_vp, _vp, ct.c_int, ct.c_int, _vp]),
     "pilot_align_debug_normal_eq": (ct.c_int, [_vp, ct.POINTER(pilot_frame), ct.c_int, _vp, _vp, _vp]),
     "pilot_align_profile": (ct.c_int, [_vp, ct.POINTER(ct.c_double), ct.POINTER(ct.c_int), ct.POINTER(ct.c_int)]),
     "pilot_align_normal_eq_noalloc": (ct.c_int, [ct.POINTER(pilot_align_config), ct.POINTER(pilot_frame), ct.c_int,
@@ -84,6 +85,10 @@ SIGNATURES = {
 
 class pilot_schedule(ct.Structure):
     _fields_ = [("tile", ct.c_int), ("ctas_per_sm", ct.c_int), ("job_order", ct.c_int)]
+
+
+def _schedule_dict(sc: pilot_schedule) -> dict:
+    return {"tile": sc.tile, "ctas_per_sm": sc.ctas_per_sm, "job_order": sc.job_order}
 
 
 class pilot_serve_stats(ct.Structure):
@@ -327,14 +332,22 @@ class Solver:
         ms = ct.c_double()
         check(load().pilot_align_autotune(self.h, ct.cast(frames, _vp), len(fas), int(batched), int(reps),
                                           ct.cast(ct.byref(sc), _vp), ct.byref(ms), self._stream(stream)))
-        return {"tile": sc.tile, "ctas_per_sm": sc.ctas_per_sm, "job_order": sc.job_order}, ms.value
+        return _schedule_dict(sc), ms.value
 
     def schedule(self, fas: list, batched: bool) -> dict:
         frames = self._frame_array(fas)
         sc = pilot_schedule()
         check(load().pilot_align_get_schedule(self.h, ct.cast(frames, _vp), len(fas), int(batched),
                                               ct.cast(ct.byref(sc), _vp)))
-        return {"tile": sc.tile, "ctas_per_sm": sc.ctas_per_sm, "job_order": sc.job_order}
+        return _schedule_dict(sc)
+
+    def set_schedule(self, fas: list, batched: bool, tile: int = 1024, ctas_per_sm: int = 0,
+                     job_order: int = 0) -> None:
+        """pilot_align_set_schedule: pin the schedule for frames of this shape."""
+        frames = self._frame_array(fas)
+        sc = pilot_schedule(tile, ctas_per_sm, job_order)
+        check(load().pilot_align_set_schedule(self.h, ct.cast(frames, _vp), len(fas), int(batched),
+                                              ct.cast(ct.byref(sc), _vp)))
 
     def normal_eq(self, fa: FrameArgs, level: int, T_cw, stream=None) -> np.ndarray:
         T = np.ascontiguousarray(T_cw, np.float64).reshape(-1, 12)

@@ -187,7 +187,11 @@ __device__ __forceinline__ void store_pose32(float* dst, const double* T) {
 // only on entry) gets the priors at the evaluated pose; then (init) it becomes the current
 // state, or (step) the candidate is accepted or rejected; then the next candidate is
 // solved for and, if cand32 is given, written there in FP32.  Single thread.
-__device__ inline void lm_update(HypState& st, int mode, int solve_next, int damping_mode,
+//
+// Not inlined: every kernel of a translation unit (plain fused, batched, served) then runs
+// the same compiled instructions, so the compiler cannot contract a * b + c into an FMA in
+// one caller and not in another, and the forms stay bitwise equal.
+static __device__ __noinline__ void lm_update(HypState& st, int mode, int solve_next, int damping_mode,
                                  const PriorParams& prior, double* E, double min_valid,
                                  float* cand32, double* eval_out) {
     const bool evaluated = (mode == kEpiStep) ? (st.has_cand != 0) : true;

@@ -698,7 +698,8 @@ pilot_status pilot_align_solve(pilot_align_handle* h, const pilot_frame* f, pilo
     int cur = 0, n_active = M;
     const PriorParams prior = prior_params(c, f, d);
 
-    const int tile = schedule_for(h, f, 1, 0).tile;
+    const pilot_schedule sched = schedule_for(h, f, 1, 0);
+    const int tile = sched.tile;
     for (int level = f->L - 1; level >= 0; --level) {
         const int iters = c.iters_per_level[level];
         BuildParams b = build_params(h, f, d, level, n_active, h->active[cur], tile);
@@ -987,6 +988,17 @@ pilot_status pilot_align_autotune(pilot_align_handle* h, const pilot_frame* fram
     h->tuned[frames_key(frames, batched ? n : 1, batched)] = win;
     if (chosen) *chosen = win;
     if (best_ms) *best_ms = best_t;
+    return PILOT_OK;
+}
+
+pilot_status pilot_align_set_schedule(pilot_align_handle* h, const pilot_frame* frames, int n, int batched,
+                                      const pilot_schedule* sc) {
+    if (!h || !frames || n < 1 || !sc) return fail(PILOT_EINVAL, "handle, frames or schedule missing");
+    if (sc->tile != 512 && sc->tile != 1024 && sc->tile != 2048 && sc->tile != 4096)
+        return fail(PILOT_EINVAL, "tile %d is not 512, 1024, 2048 or 4096", sc->tile);
+    if (sc->ctas_per_sm < 0 || sc->ctas_per_sm > 2) return fail(PILOT_EINVAL, "ctas_per_sm %d outside [0, 2]", sc->ctas_per_sm);
+    if (sc->job_order < 0 || sc->job_order > 1) return fail(PILOT_EINVAL, "job_order %d outside [0, 1]", sc->job_order);
+    h->tuned[frames_key(frames, batched ? n : 1, batched)] = *sc;
     return PILOT_OK;
 }
 

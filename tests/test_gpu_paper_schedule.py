@@ -1,0 +1,105 @@
+"""The paper's own refinement schedule (Sec. V-A "Implementation Details"; Supp.
+"Multi-Hypothesis Refinement"): 500 geo-anchors sampled from the crop, the 1210 hypotheses
+of the (x, y, yaw) grid around a prior pose, the best 128 kept after the coarse level, and
+2 / 3 / 4 LM iterations from coarse to fine.  The oracle solves such a frame whole in under
+a second, so every hypothesis is compared at full size.
+
+With 2-4 iterations per level no hypothesis has converged: an end point is the end of its
+LM path, and FP32 and FP64 follow the same path unless an accept/reject decision falls
+within FP32 resolution of a tie.  The checks are therefore: equal iteration and pruning
+counts; survivor sets after the coarse level equal up to near-ties at rank 128; every
+hypothesis kept by both within 1e-3 deg / 1 mm of the oracle's end point; at least 99 % of
+all hypotheses within it, the others (pruned hypotheses whose coarse path split at such a
+decision) reporting the FP64 objective of their own end pose; and the selected pose within
+1e-3 deg / 1 mm of the oracle's, objectives within 1e-5.
+"""
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_2606_31098_gb300 import binding as B
+from paper_2606_31098_gb300 import scenes as S
+
+from gpu_support import device_frame, pose_errors, require_cuda, to_oracle_opts
+from test_gpu_batch import args_for, assert_same
+
+pytestmark = pytest.mark.gpu
+
+ITERS = (4, 3, 2, 0)            # level 0 (finest) .. level 2 (coarsest)
+KEEP = (0, 0, 128, 0)           # after the coarse level keep the best 128
+HYP_ITERS = 1210 * 2 + 128 * 3 + 128 * 4
+
+
+def paper_opts(**kw):
+    return B.Options(iters=ITERS, keep_top_k=KEEP, max_hyps=1210, max_points=500, **kw)
+
+
+@pytest.fixture(scope="module")
+def torch():
+    return require_cuda()
+
+
+@pytest.fixture(scope="module")
+def frames():
+    return [S.make_frame(S.config_paper_schedule(), S.frame_seed(6, i)) for i in range(2)]
+
+
+@pytest.mark.parametrize("k", [0, 1])
+def test_paper_schedule_matches_the_oracle(torch, frames, k):
+    f = frames[k]
+    assert f.N == 500 and f.M == 1210
+    opts = paper_opts()
+    g = B.Solver(opts).solve(device_frame(f))
+    oo = to_oracle_opts(opts)
+    o = O.solve(f, oo)
+    assert g.hyp_iters == o.hyp_iters == HYP_ITERS
+    assert (g.status == B.HYP_PRUNED).sum() == (o.status == O.HYP_PRUNED).sum() == 1210 - 128
+    kept_g = set(np.flatnonzero(g.status != B.HYP_PRUNED))
+    kept_o = set(np.flatnonzero(o.status != O.HYP_PRUNED))
+    assert len(kept_g ^ kept_o) <= 4, f"survivor sets differ in {len(kept_g ^ kept_o)} hypotheses"
+    err = np.array([pose_errors(g.T_cw[m], o.T_cw[m]) for m in range(f.M)])
+    agree = (err[:, 0] < 1e-3) & (err[:, 1] < 1e-3)
+    both = sorted(kept_g & kept_o)
+    assert agree[both].all(), f"kept hypotheses off: {np.flatnonzero(~agree[both])[:5]}, {err[both].max(0)}"
+    assert agree.mean() >= 0.99, f"only {agree.mean():.4f} of the end points agree"
+    for m in np.flatnonzero(~agree):
+        assert g.status[m] == B.HYP_PRUNED
+        E = O.evaluate(f, oo, 2, g.T_cw[m])
+        assert g.cost[m] == pytest.approx(E[27], rel=1e-4), f"hyp {m}: reported objective"
+    assert g.best >= 0 and o.best >= 0
+    er, et = pose_errors(g.T_cw[g.best], o.T_cw[o.best])
+    assert er < 1e-3 and et < 1e-3, f"selected pose {er:.2e} deg {et:.2e} m"
+    assert g.cost[g.best] == pytest.approx(o.cost[o.best], rel=1e-5)
+
+
+def test_pinned_schedule_is_used(torch, frames):
+    """pilot_align_set_schedule pins the schedule for frames of this shape; with 500 anchors
+    every tile size covers the frame in one tile, so all give bitwise equal results."""
+    fa = device_frame(frames[0])
+    solver = B.Solver(paper_opts())
+    out = []
+    for tile in (512, 2048, 4096):
+        solver.set_schedule([fa], batched=False, tile=tile)
+        assert solver.schedule([fa], batched=False) == {"tile": tile, "ctas_per_sm": 0, "job_order": 0}
+        out.append(solver.solve(fa))
+    assert_same(out[0], out[1])
+    assert_same(out[0], out[2])
+
+
+def test_set_schedule_rejects_unknown_values(torch, frames):
+    solver = B.Solver(paper_opts())
+    fa = device_frame(frames[0])
+    for bad in (dict(tile=768), dict(job_order=2), dict(ctas_per_sm=-1), dict(ctas_per_sm=3)):
+        with pytest.raises(B.PilotError, match="outside|is not"):
+            solver.set_schedule([fa], batched=False, **bad)
+
+
+def test_paper_schedule_batched_equals_plain(torch, frames):
+    """The batched form on paper-schedule frames (1210 hypotheses each, top-128 inside the
+    captured graph) is bitwise the plain solve of each frame."""
+    fas = args_for(frames)
+    opts = B.Options(iters=ITERS, keep_top_k=KEEP, max_hyps=1210 * len(frames), max_points=500)
+    solver = B.Solver(opts)
+    batch = solver.solve_batch(fas)
+    for i, fa in enumerate(fas):
+        assert_same(batch[i], solver.solve(fa), what=f"frame {i}")
