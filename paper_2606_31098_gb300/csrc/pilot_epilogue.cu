@@ -83,43 +83,88 @@ __global__ void level_init_kernel(HypState* st, float* pose32, const int* active
     store_pose32(pose32 + 12 * m, st[m].T);
 }
 
-__device__ __forceinline__ bool ranks_before(const HypState& a, int ia, const HypState& b, int ib,
-                                             double min_valid) {
-    // ordering key (unusable, cost, index); unusable = non-finite or too few visible
-    const bool bad_a = !(isfinite(a.cost) && a.n_valid >= min_valid);
-    const bool bad_b = !(isfinite(b.cost) && b.n_valid >= min_valid);
+// Ranking key of a hypothesis: (unusable, cost, index), unusable = non-finite objective or
+// too few visible anchors; unusable ones compare by index only.
+__device__ __forceinline__ void rank_key(const HypState& h, double min_valid, int* bad, double* c) {
+    *bad = !(isfinite(h.cost) && h.n_valid >= min_valid);
+    *c = isfinite(h.cost) ? h.cost : 0.0;
+}
+
+__device__ __forceinline__ bool key_before(int bad_a, double ca, int ia, int bad_b, double cb, int ib) {
     if (bad_a != bad_b) return !bad_a;
-    const double ca = isfinite(a.cost) ? a.cost : 0.0;
-    const double cb = isfinite(b.cost) ? b.cost : 0.0;
     if (ca != cb) return ca < cb;
     return ia < ib;
 }
 
+// Top-K (Supp. "Multi-Hypothesis Refinement") over the n hypotheses listed in act[0, n) of
+// S: every hypothesis of rank >= K is marked pruned, and the survivors' indices are
+// written, in their order in act, to act_out[0, K) (act_out may be act).  One block
+// (blockDim.x a multiple of 32, at most 1024); the keys are streamed through shared memory
+// in blocks of blockDim.x, and the survivors are placed by a block-wide prefix count.
+__device__ void topk_select(HypState* S, const int* act, int* act_out, int n, int K, double min_valid) {
+    __shared__ double kc[1024];
+    __shared__ int kb[1024];
+    __shared__ int ki[1024];
+    __shared__ int wsum[32];
+    __shared__ int s_base;
+    const int bd = blockDim.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    for (int r0 = 0; r0 < n; r0 += bd) {
+        const int s = r0 + tid;
+        int m = -1, bad = 1, rank = 0;
+        double c = 0.0;
+        if (s < n) {
+            m = act[s];
+            rank_key(S[m], min_valid, &bad, &c);
+        }
+        for (int c0 = 0; c0 < n; c0 += bd) {
+            __syncthreads();
+            if (c0 + tid < n) {
+                const int m2 = act[c0 + tid];
+                rank_key(S[m2], min_valid, &kb[tid], &kc[tid]);
+                ki[tid] = m2;
+            }
+            __syncthreads();
+            if (s < n) {
+                const int lim = min(bd, n - c0);
+                for (int j = 0; j < lim; ++j) rank += key_before(kb[j], kc[j], ki[j], bad, c, m) ? 1 : 0;
+            }
+        }
+        if (s < n && rank >= K) {
+            S[m].active = 0;
+            S[m].status = PILOT_HYP_PRUNED;
+        }
+    }
+    if (tid == 0) s_base = 0;
+    __syncthreads();
+    for (int c0 = 0; c0 < n; c0 += bd) {
+        const int s = c0 + tid;
+        int m = -1;
+        bool keep = false;
+        if (s < n) {
+            m = act[s];
+            keep = S[m].active != 0;
+        }
+        const unsigned bal = __ballot_sync(0xffffffffu, keep);
+        if (lane == 0) wsum[warp] = __popc(bal);
+        __syncthreads();
+        int off = s_base;
+        for (int w = 0; w < warp; ++w) off += wsum[w];
+        if (keep) act_out[off + __popc(bal & ((1u << lane) - 1u))] = m;
+        __syncthreads();
+        if (tid == 0) {
+            int t = 0;
+            for (int w = 0; w < bd / 32; ++w) t += wsum[w];
+            s_base += t;
+        }
+        __syncthreads();
+    }
+}
+
 // One block.  Ranks the active hypotheses, marks all but the K first as pruned, and
-// writes the surviving indices, in increasing order, to active_out.
+// writes the surviving indices, in their order in active_in, to active_out.
 __global__ void prune_kernel(HypState* st, const int* active_in, int* active_out, int n, int K,
                              const double* min_valid_ptr) {
-    const double min_valid = *min_valid_ptr;
-    for (int s = threadIdx.x; s < n; s += blockDim.x) {
-        const int m = active_in[s];
-        int rank = 0;
-        for (int s2 = 0; s2 < n; ++s2) {
-            const int m2 = active_in[s2];
-            rank += ranks_before(st[m2], m2, st[m], m, min_valid) ? 1 : 0;
-        }
-        if (rank >= K) {
-            st[m].active = 0;
-            st[m].status = PILOT_HYP_PRUNED;
-        }
-    }
-    __syncthreads();
-    for (int s = threadIdx.x; s < n; s += blockDim.x) {
-        const int m = active_in[s];
-        if (!st[m].active) continue;
-        int pos = 0;
-        for (int s2 = 0; s2 < s; ++s2) pos += st[active_in[s2]].active;
-        active_out[pos] = m;
-    }
+    topk_select(st, active_in, active_out, n, K, *min_valid_ptr);
 }
 
 // One block of 1024 threads: number of valid anchors (4 flags per load when aligned).
@@ -236,41 +281,11 @@ __device__ void count_frame(const FrameDesc& f, double frac, double* min_valid) 
     __syncthreads();
 }
 
-// Top-K of one frame among its n active hypotheses (same ranking as prune_kernel).  The
-// frame's active list is compacted in place (read fully before any write; at most 8
-// survivors per thread, so blockDim.x x 8 >= n).
+// Top-K of one frame among its n active hypotheses (same ranking as prune_kernel); the
+// frame's active list is compacted in place.
 __device__ void prune_frame(const FrameDesc& f, HypState* st, int* active, int n, int K, double mv) {
     if (K <= 0 || K >= n) return;
-    int* act = active + f.hyp_offset;
-    HypState* S = st + f.hyp_offset;
-    for (int s = threadIdx.x; s < n; s += blockDim.x) {
-        const int m = act[s];
-        int rank = 0;
-        for (int s2 = 0; s2 < n; ++s2) {
-            const int m2 = act[s2];
-            rank += ranks_before(S[m2], m2, S[m], m, mv) ? 1 : 0;
-        }
-        if (rank >= K) {
-            S[m].active = 0;
-            S[m].status = PILOT_HYP_PRUNED;
-        }
-    }
-    __syncthreads();
-    int keep_pos[8];
-    int keep_val[8];
-    int nk = 0;
-    for (int s = threadIdx.x; s < n && nk < 8; s += blockDim.x) {
-        const int m = act[s];
-        if (!S[m].active) continue;
-        int pos = 0;
-        for (int s2 = 0; s2 < s; ++s2) pos += S[act[s2]].active;
-        keep_pos[nk] = pos;
-        keep_val[nk] = m;
-        ++nk;
-    }
-    __syncthreads();
-    for (int i = 0; i < nk; ++i) act[keep_pos[i]] = keep_val[i];
-    __syncthreads();
+    topk_select(st + f.hyp_offset, active + f.hyp_offset, active + f.hyp_offset, n, K, mv);
 }
 
 // Statuses, per-hypothesis outputs (at the global hypothesis index) and the argmin of
