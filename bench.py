@@ -484,14 +484,19 @@ def run_ours(args):
     value = replica_throughput(units, total_ms, world)
     e2e_value = replica_throughput(e2e_units, e2e_ms, world)
 
-    # roofline of the dominant kernel (the build pass)
+    # roofline of the dominant kernel (the build pass).  The hypotheses run in `parts`
+    # concurrent launches per LM iteration (one per stream), so launch durations overlap:
+    # achieved is the build pass' algorithmic work over the whole timed solves divided by
+    # their device time (which also holds the ~1 % of small kernels: a lower bound).
     C, elem = frame.C, 4
-    units_per_launch = frame.N * frame.M          # no pruning: every launch runs all hypotheses
+    parts = min(plain_schedule["streams"] or 2, frame.M)
+    units_per_launch = frame.N * (frame.M // parts)   # no pruning: equal parts every launch
+    build_units = units_per_launch * build_n           # over the timed device-frame solves
     avg_launch_ms = build_ms / max(build_n, 1)
-    achieved_tflops = units_per_launch * flops_per_unit(C) / (avg_launch_ms * 1e-3) / 1e12
+    achieved_tflops = build_units * flops_per_unit(C) / (total_ms * 1e-3) / 1e12
     sm_max = (clk or {}).get("sm_max_mhz") or (load_peaks() or {}).get("sm_max_mhz", 2070.0)
     peak_tflops = SM_COUNT * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
-    gather_gbs = units_per_launch * gather_bytes_per_unit(C, elem) / (avg_launch_ms * 1e-3) / 1e9
+    gather_gbs = build_units * gather_bytes_per_unit(C, elem) / (total_ms * 1e-3) / 1e9
     traffic = traffic_per_launch(units_per_launch)
 
     batched, served = batched_and_served(args, B, S, torch, world, stream) if not args.no_forms else ({}, {})
@@ -521,7 +526,8 @@ def run_ours(args):
                 "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic (seeded scene generator)",
                 "config": {"workload": WORKLOAD, "points": frame.N, "hypotheses": frame.M, "channels": C,
                            "levels": [list(q.shape[:2]) for q in frame.qry_feat], "iters_per_level": [10, 10, 10],
-                           "feature_dtype": "f32", "form": "plain single frame, one stream",
+                           "feature_dtype": "f32",
+                           "form": f"plain single frame, hypotheses in {parts} concurrent launches per iteration",
                            "schedule": plain_schedule,
                            "l2": "flushed between steps (512 MiB write)", "replicas": world},
                 "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
@@ -532,9 +538,9 @@ def run_ours(args):
                              "frac": achieved_tflops / peak_tflops, "traffic": traffic,
                              "peak_basis": f"FP32 FMA: {SM_COUNT} SMs x {FP32_LANES_PER_SM} lanes x 2 x {sm_max:.0f} MHz",
                              "flops_per_unit": flops_per_unit(C), "units_per_launch": units_per_launch,
-                             "avg_launch_ms": avg_launch_ms, "launches": build_n,
-                             "gather_bytes_per_unit": gather_bytes_per_unit(C, elem), "gather_GBps": gather_gbs,
-                             "build_share_of_step": build_ms / total_ms},
+                             "avg_launch_ms": avg_launch_ms, "launches": build_n, "concurrent_launches": parts,
+                             "achieved_basis": "build-pass units of the timed solves x flops per unit / their device time",
+                             "gather_bytes_per_unit": gather_bytes_per_unit(C, elem), "gather_GBps": gather_gbs},
                 "precision_forms": precision,
                 "batched_form": batched,
                 "served_form": served, "paper_schedule_form": paper,

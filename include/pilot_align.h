@@ -161,10 +161,14 @@ typedef struct {
     int tile;         /* anchors per reduction tile: 512, 1024, 2048 or 4096 */
     int ctas_per_sm;  /* batched form: persistent CTAs per SM; 0 = as many as fit */
     int job_order;    /* batched form: 0 = frames with more anchors first, 1 = frames interleaved */
+    int streams;      /* plain form: 1 = one launch per LM iteration over all hypotheses;
+                         2..4 = the hypotheses in that many parts, each launched on its own
+                         stream, so that the FP64 steps ending one part's launch overlap the
+                         other parts' gathers; 0 = 2.  Bitwise the same results. */
 } pilot_schedule;
 
-/* Autotuner: time the candidate schedules (4 tiles; for the batched form also 1 or 2 CTAs
- * per SM and both job orders) on these frames, `reps` timed runs each after one warm-up, and
+/* Autotuner: time the candidate schedules (4 tiles; for the plain form 1 or 2 streams, for
+ * the batched form 1 or 2 CTAs per SM and both job orders) on these frames, `reps` timed runs each after one warm-up, and
  * keep the fastest for frames of this shape (storage type, C, and the powers of two of the
  * mean anchor and hypothesis counts).  batched = 0 tunes pilot_align_solve on frames[0];
  * batched = 1 tunes pilot_align_solve_batch on all frames.  *chosen and *best_ms (may be

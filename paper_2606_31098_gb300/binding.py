@@ -84,11 +84,11 @@ SIGNATURES = {
 
 
 class pilot_schedule(ct.Structure):
-    _fields_ = [("tile", ct.c_int), ("ctas_per_sm", ct.c_int), ("job_order", ct.c_int)]
+    _fields_ = [("tile", ct.c_int), ("ctas_per_sm", ct.c_int), ("job_order", ct.c_int), ("streams", ct.c_int)]
 
 
 def _schedule_dict(sc: pilot_schedule) -> dict:
-    return {"tile": sc.tile, "ctas_per_sm": sc.ctas_per_sm, "job_order": sc.job_order}
+    return {"tile": sc.tile, "ctas_per_sm": sc.ctas_per_sm, "job_order": sc.job_order, "streams": sc.streams}
 
 
 class pilot_serve_stats(ct.Structure):
@@ -342,10 +342,10 @@ class Solver:
         return _schedule_dict(sc)
 
     def set_schedule(self, fas: list, batched: bool, tile: int = 1024, ctas_per_sm: int = 0,
-                     job_order: int = 0) -> None:
+                     job_order: int = 0, streams: int = 0) -> None:
         """pilot_align_set_schedule: pin the schedule for frames of this shape."""
         frames = self._frame_array(fas)
-        sc = pilot_schedule(tile, ctas_per_sm, job_order)
+        sc = pilot_schedule(tile, ctas_per_sm, job_order, streams)
         check(load().pilot_align_set_schedule(self.h, ct.cast(frames, _vp), len(fas), int(batched),
                                               ct.cast(ct.byref(sc), _vp)))
 

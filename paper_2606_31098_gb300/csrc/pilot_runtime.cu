@@ -51,6 +51,8 @@ pilot_status cuda_fail(cudaError_t e, const char* what) {
     } while (0)
 
 constexpr int kTile = 1024;          // default anchors per build-pass tile
+constexpr int kMaxStreams = 4;       // plain form: most concurrent hypothesis parts
+constexpr int kDefaultStreams = 2;   // plain form: parts when the schedule says 0
 constexpr int kMinTile = 512;        // smallest tile the autotuner tries (sizes the workspace)
 
 bool channels_supported(int C) { return C == 4 || C == 8 || C == 16 || C == 32 || C == 64; }
@@ -178,6 +180,10 @@ struct pilot_align_handle {
     double* bmin_valid = nullptr;
     int* bcounters = nullptr;
     cudaStream_t bstream = nullptr;
+    // plain form, multi-stream schedule: extra streams, a fork event and their join events
+    cudaStream_t pstream[kMaxStreams - 1] = {};
+    cudaEvent_t pfork = nullptr;
+    cudaEvent_t pjoin[kMaxStreams - 1] = {};
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t gexec = nullptr;
     long long graph_key = -1;
@@ -352,7 +358,7 @@ cudaError_t dispatch_build_fused(pilot_dtype dt, const FusedBuildParams& b, cuda
 
 // One build launch, plain (ep == nullptr) or with the FP64 step fused in.
 pilot_status run_build(pilot_align_handle* h, pilot_dtype dt, const BuildParams& b, cudaStream_t s,
-                       const EpilogueParams* ep = nullptr) {
+                       const EpilogueParams* ep = nullptr, int slot_offset = 0) {
     const bool prof = h->cfg.profile != 0;
     size_t k = 2 * (size_t)h->build_launches;
     if (prof) {
@@ -364,7 +370,7 @@ pilot_status run_build(pilot_align_handle* h, pilot_dtype dt, const BuildParams&
         PILOT_CUDA(cudaEventRecord(h->events[k], s), "event record");
     }
     if (ep) {
-        FusedBuildParams fb{b, *ep, h->tickets, h->min_valid};
+        FusedBuildParams fb{b, *ep, h->tickets + slot_offset, h->min_valid};
         PILOT_CUDA(dispatch_build_fused(dt, fb, s), "fused build-pass launch");
     } else {
         PILOT_CUDA(dispatch_build(dt, b, s), "build-pass launch");
@@ -391,7 +397,7 @@ long long frames_key(const pilot_frame* frames, int n, int batched) {
     return schedule_key(batched, frames[0].feat_dtype, frames[0].C, sn / n, sm / n);
 }
 
-pilot_schedule default_schedule() { return pilot_schedule{kTile, 0, 0}; }
+pilot_schedule default_schedule() { return pilot_schedule{kTile, 0, 0, 0}; }
 
 pilot_schedule schedule_for(const pilot_align_handle* h, const pilot_frame* frames, int n, int batched) {
     if (h->forcing) return h->forced;
@@ -437,6 +443,11 @@ void release(pilot_align_handle* h) {
     cudaFree(h->bmin_valid);
     cudaFree(h->bcounters);
     if (h->bstream) cudaStreamDestroy(h->bstream);
+    for (int i = 0; i < kMaxStreams - 1; ++i) {
+        if (h->pstream[i]) cudaStreamDestroy(h->pstream[i]);
+        if (h->pjoin[i]) cudaEventDestroy(h->pjoin[i]);
+    }
+    if (h->pfork) cudaEventDestroy(h->pfork);
     delete h;
 }
 
@@ -700,6 +711,14 @@ pilot_status pilot_align_solve(pilot_align_handle* h, const pilot_frame* f, pilo
 
     const pilot_schedule sched = schedule_for(h, f, 1, 0);
     const int tile = sched.tile;
+    const int n_streams = sched.streams > 0 ? sched.streams : kDefaultStreams;
+    if (n_streams > 1 && !h->pfork) {
+        PILOT_CUDA(cudaEventCreateWithFlags(&h->pfork, cudaEventDisableTiming), "fork event");
+        for (int i = 0; i < kMaxStreams - 1; ++i) {
+            PILOT_CUDA(cudaStreamCreateWithFlags(&h->pstream[i], cudaStreamNonBlocking), "extra stream");
+            PILOT_CUDA(cudaEventCreateWithFlags(&h->pjoin[i], cudaEventDisableTiming), "join event");
+        }
+    }
     for (int level = f->L - 1; level >= 0; --level) {
         const int iters = c.iters_per_level[level];
         BuildParams b = build_params(h, f, d, level, n_active, h->active[cur], tile);
@@ -715,10 +734,37 @@ pilot_status pilot_align_solve(pilot_align_handle* h, const pilot_frame* f, pilo
         ep.prior = prior;
         PILOT_CUDA(launch_level_init(h->state, h->pose32, h->active[cur], n_active, c.lambda0, s), "level_init launch");
         ++h->total_launches;
+        // parts of the active list, part p = slots [off[p], off[p + 1]) on stream p (s for
+        // p = 0), each with its own slice of the partial records and tickets
+        const int parts = n_streams < n_active ? n_streams : n_active;
+        int off[kMaxStreams + 1];
+        BuildParams bp[kMaxStreams];
+        EpilogueParams epp[kMaxStreams];
+        cudaStream_t sp[kMaxStreams];
+        for (int p = 0; p <= parts; ++p) off[p] = (int)(((long long)n_active * p) / parts);
+        for (int p = 0; p < parts; ++p) {
+            bp[p] = b;
+            epp[p] = ep;
+            bp[p].n_active = epp[p].n_active = off[p + 1] - off[p];
+            bp[p].active_idx = epp[p].active_idx = b.active_idx + off[p];
+            bp[p].partial = b.partial + (size_t)off[p] * b.n_tiles * kAcc;
+            epp[p].partial = bp[p].partial;
+            sp[p] = p ? h->pstream[p - 1] : s;
+        }
+        if (parts > 1) {
+            PILOT_CUDA(cudaEventRecord(h->pfork, s), "fork record");
+            for (int p = 1; p < parts; ++p) PILOT_CUDA(cudaStreamWaitEvent(sp[p], h->pfork, 0), "fork wait");
+        }
         for (int k = 0; k <= iters; ++k) {
-            ep.mode = (k == 0) ? kEpiInit : kEpiStep;
-            ep.solve_next = k < iters;
-            if ((st = run_build(h, f->feat_dtype, b, s, &ep)) != PILOT_OK) return st;
+            for (int p = 0; p < parts; ++p) {
+                epp[p].mode = (k == 0) ? kEpiInit : kEpiStep;
+                epp[p].solve_next = k < iters;
+                if ((st = run_build(h, f->feat_dtype, bp[p], sp[p], &epp[p], off[p])) != PILOT_OK) return st;
+            }
+        }
+        for (int p = 1; p < parts; ++p) {
+            PILOT_CUDA(cudaEventRecord(h->pjoin[p - 1], sp[p]), "join record");
+            PILOT_CUDA(cudaStreamWaitEvent(s, h->pjoin[p - 1], 0), "join wait");
         }
         hyp_iters += (long long)n_active * iters;
         const int K = c.keep_top_k[level];
@@ -934,11 +980,11 @@ pilot_status pilot_align_autotune(pilot_align_handle* h, const pilot_frame* fram
     std::vector<pilot_schedule> cands;
     for (int tile : {512, 1024, 2048, 4096}) {
         if (!batched) {
-            cands.push_back(pilot_schedule{tile, 0, 0});
+            for (int streams : {1, 2}) cands.push_back(pilot_schedule{tile, 0, 0, streams});
             continue;
         }
         for (int per_sm : {1, 0})
-            for (int order : {0, 1}) cands.push_back(pilot_schedule{tile, per_sm, order});
+            for (int order : {0, 1}) cands.push_back(pilot_schedule{tile, per_sm, order, 0});
     }
     // results are discarded: one scratch record per hypothesis
     long long total = 0;
@@ -998,6 +1044,8 @@ pilot_status pilot_align_set_schedule(pilot_align_handle* h, const pilot_frame* 
         return fail(PILOT_EINVAL, "tile %d is not 512, 1024, 2048 or 4096", sc->tile);
     if (sc->ctas_per_sm < 0 || sc->ctas_per_sm > 2) return fail(PILOT_EINVAL, "ctas_per_sm %d outside [0, 2]", sc->ctas_per_sm);
     if (sc->job_order < 0 || sc->job_order > 1) return fail(PILOT_EINVAL, "job_order %d outside [0, 1]", sc->job_order);
+    if (sc->streams < 0 || sc->streams > kMaxStreams)
+        return fail(PILOT_EINVAL, "streams %d outside [0, %d]", sc->streams, kMaxStreams);
     h->tuned[frames_key(frames, batched ? n : 1, batched)] = *sc;
     return PILOT_OK;
 }

@@ -121,7 +121,7 @@ def test_autotuner_picks_a_schedule_that_keeps_the_results(torch):
     fas = args_for(frames)
     solver = B.Solver(B.Options())
     default = solver.schedule(fas, batched=True)
-    assert default == {"tile": 1024, "ctas_per_sm": 0, "job_order": 0}
+    assert default == {"tile": 1024, "ctas_per_sm": 0, "job_order": 0, "streams": 0}
     before = solver.solve_batch(fas)
     chosen, ms = solver.autotune(fas, batched=True, reps=1)
     assert chosen["tile"] in (512, 1024, 2048, 4096) and chosen["ctas_per_sm"] in (0, 1) and ms > 0
@@ -136,3 +136,21 @@ def test_autotuner_picks_a_schedule_that_keeps_the_results(torch):
             assert S.rotation_error_deg(a.T_cw[a.best], b.T_cw[b.best]) < 1e-3
             assert S.translation_error_m(a.T_cw[a.best], b.T_cw[b.best]) < 1e-3
             assert a.cost[a.best] == pytest.approx(b.cost[b.best], rel=1e-5)
+
+
+def test_plain_form_concurrent_parts_give_equal_results(torch):
+    """The plain form's multi-stream schedule runs the hypotheses in 1-4 parts, one launch
+    per part per LM iteration on its own stream; each hypothesis' records, tickets and FP64
+    step are its own, so every split (uneven ones included, with top-K between levels)
+    gives bitwise the one-launch results."""
+    f = S.make_frame(S.config_reduced_frame(n_hyps=9), S.frame_seed(3, 1700))
+    fa = args_for([f])[0]
+    opts = B.Options(iters=(3, 3, 3, 0), keep_top_k=(0, 3, 7, 0))
+    out = {}
+    for streams in (1, 2, 3, 4):
+        solver = B.Solver(opts)
+        solver.set_schedule([fa], batched=False, tile=1024, streams=streams)
+        out[streams] = solver.solve(fa)
+        solver.close()
+    for streams in (2, 3, 4):
+        assert_same(out[1], out[streams], what=f"{streams} parts")

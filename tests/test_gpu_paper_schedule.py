@@ -80,7 +80,7 @@ def test_pinned_schedule_is_used(torch, frames):
     out = []
     for tile in (512, 2048, 4096):
         solver.set_schedule([fa], batched=False, tile=tile)
-        assert solver.schedule([fa], batched=False) == {"tile": tile, "ctas_per_sm": 0, "job_order": 0}
+        assert solver.schedule([fa], batched=False) == {"tile": tile, "ctas_per_sm": 0, "job_order": 0, "streams": 0}
         out.append(solver.solve(fa))
     assert_same(out[0], out[1])
     assert_same(out[0], out[2])
