@@ -156,11 +156,11 @@ pilot_status pilot_align_solve(pilot_align_handle* h, const pilot_frame* frame,
 
 /* Schedule of the build pass: chosen per frame shape by pilot_align_autotune (or set by
  * pilot_align_set_schedule), else the defaults (tile 1024, as many CTAs per SM as fit,
- * longest frames first). */
+ * larger frames first). */
 typedef struct {
     int tile;         /* anchors per reduction tile: 512, 1024, 2048 or 4096 */
     int ctas_per_sm;  /* batched form: persistent CTAs per SM; 0 = as many as fit */
-    int job_order;    /* batched form: 0 = frames with more anchors first, 1 = frames interleaved */
+    int job_order;    /* batched form: 0 = frames with more anchors first, 1 = frames in the caller's order */
     int streams;      /* plain form: 1 = one launch per LM iteration over all hypotheses;
                          2..4 = the hypotheses in that many parts, each launched on its own
                          stream, so that the FP64 steps ending one part's launch overlap the
@@ -189,13 +189,18 @@ pilot_status pilot_align_get_schedule(const pilot_align_handle* h, const pilot_f
                                       int n_frames, int batched, pilot_schedule* out);
 
 /* Batched form: solve n_frames independent frames (uneven N, M, map sizes, intrinsics,
- * priors) in one pass per pyramid level.  Each level is one persistent launch whose CTAs
- * pull (frame, hypothesis) jobs, longest first, and run a job's whole LM loop at that
- * level; the launches, the per-frame top-K and the selection are replayed from a CUDA
- * graph captured on the first call (and again when the storage type, C or L changes).
+ * priors) in one pass per pyramid level.  Each level is one persistent cooperative launch
+ * that runs the level's LM iterations in lockstep over all (frame, hypothesis) jobs: per
+ * iteration its CTAs claim work items (runs of anchor tiles of one job, frames with more
+ * anchors first unless the schedule says otherwise) from one counter, then, after a grid
+ * barrier, every job's FP64 step runs on one warp lane.  The launches, the per-frame top-K
+ * and the selection are replayed from a CUDA graph captured on the first call (and again
+ * when the storage type, C, L or schedule changes).
  * Requirements: every frame is a DEVICE frame; all frames share C, L, feat_dtype and the
  * presence of per-channel scales; n_frames <= max_frames; the hypotheses of all frames
- * together <= max_hyps, at most 8192 per frame.  results[i] receives frame i's outputs
+ * together <= max_hyps, at most 8192 per frame.  PILOT_ETIMEOUT if a grid barrier wait
+ * gave up (only when the device could not keep every CTA resident; results are then
+ * invalid).  results[i] receives frame i's outputs
  * exactly as pilot_align_solve would: with the same tile (both untuned, or tuned alike)
  * the reduction order is the same, so each frame's outputs are bitwise those of its own
  * pilot_align_solve, whatever else is in the batch.

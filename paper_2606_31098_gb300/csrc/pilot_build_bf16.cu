@@ -1,6 +1,7 @@
 // Build-pass instantiations for BF16 feature storage (one translation unit per
 // storage type so that they compile in parallel).
 #include "pilot_build_impl.cuh"
+#include "pilot_level_impl.cuh"
 
 namespace pilot {
 template cudaError_t launch_build_dtype<PILOT_BF16>(const BuildParams&, cudaStream_t);

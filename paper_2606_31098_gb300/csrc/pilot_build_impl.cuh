@@ -496,123 +496,6 @@ build_fused_kernel(const FusedBuildParams fp) {
     }
 }
 
-// Batched form: one persistent launch per level for a whole batch of frames.  CTAs pull
-// (frame, hypothesis) jobs from a counter and run the job's whole LM loop at this level:
-// for each iteration, every 1024-anchor tile of the frame is accumulated and reduced
-// exactly as in build_fused_kernel (same thread mapping, same FP32 tile sums, same
-// 8-chain FP64 order), then thread 0 runs the FP64 step.  A frame's result is therefore
-// bitwise the one its plain solve gives, whatever else is in the batch, and one CTA's
-// FP64 step overlaps with the gathers of the other CTAs.
-template <pilot_dtype DT, int C, bool SCALED>
-__global__ void __launch_bounds__(kBuildThreads, 2)
-level_persistent_kernel(const LevelArgs a) {
-    __shared__ float red[kBuildThreads / 32][kAcc];
-    __shared__ float tilebuf[kAcc];
-    __shared__ double part[8][kAcc];
-    __shared__ double E[kAcc];
-    __shared__ float pose[12];
-    __shared__ int s_job;
-    __shared__ int s_eval;
-    const int tid = threadIdx.x;
-    const int n_jobs = a.header->n_jobs[a.n_jobs_index];
-    for (;;) {
-        if (tid == 0) s_job = atomicAdd(a.counter, 1);
-        __syncthreads();
-        const int job = s_job;
-        if (job >= n_jobs) break;
-        const FrameDesc* fd = a.frames + a.job_frame[job];
-        const int level = a.level >= 0 ? a.level : fd->level;
-        const int iters = a.iters[level];
-        const int hyp = fd->hyp_offset + a.active[fd->hyp_offset + a.job_slot[job]];
-        HypState& st = a.state[hyp];
-        const LevelView v{fd->px, fd->py, fd->pz, fd->weight, fd->valid, fd->qry[level], fd->ref[level],
-                          fd->qscale[level], fd->rscale[level], fd->H[level], fd->W[level],
-                          fd->fx[level], fd->fy[level], fd->cx[level], fd->cy[level], a.huber};
-        const double min_valid = a.min_valid[a.job_frame[job]];
-        const int N = fd->N;
-        const int n_tiles = N > 0 ? (N + a.tile - 1) / a.tile : 1;
-        if (tid == 0) {
-            st.lambda = a.lambda0;
-            st.last_fail = 0;
-            st.has_cand = 1;
-            store_pose32(pose, st.T);
-        }
-        __syncthreads();
-        for (int k = 0; k <= iters; ++k) {
-            if (tid == 0) s_eval = (k == 0) || st.has_cand;
-            __syncthreads();
-            if (s_eval) {
-                double chain = 0.0;      // chain tid >> 5 of value tid & 31
-                for (int t = 0; t < n_tiles; ++t) {
-                    float acc[kNumSums];
-#pragma unroll
-                    for (int i = 0; i < kNumSums; ++i) acc[i] = 0.f;
-                    const int j0 = t * a.tile;
-                    accumulate_anchors<DT, C, SCALED, kBuildThreads>(v, pose, j0, min(j0 + a.tile, N), acc);
-                    const float val = cta_reduce<kBuildThreads>(acc, red);
-                    if (tid < kAcc) tilebuf[tid] = val;
-                    __syncthreads();
-                    if ((tid >> 5) == (t & 7)) chain += (double)tilebuf[tid & 31];
-                    __syncthreads();
-                }
-                part[tid >> 5][tid & 31] = chain;
-                __syncthreads();
-                if (tid < kAcc) {
-                    double sum = 0.0;
-#pragma unroll
-                    for (int c = 0; c < 8; ++c) sum += part[c][tid];
-                    E[tid] = sum;
-                }
-                __syncthreads();
-            }
-            if (tid == 0)
-                lm_update(st, k == 0 ? kEpiInit : kEpiStep, k < iters, a.damping_mode, fd->prior, E,
-                          min_valid, pose, nullptr);
-            __syncthreads();
-        }
-    }
-}
-
-template <pilot_dtype DT, int C>
-cudaError_t launch_level_persistent_typed(bool scaled, const LevelArgs& a, int grid, cudaStream_t s) {
-    if (scaled)
-        level_persistent_kernel<DT, C, true><<<grid, kBuildThreads, 0, s>>>(a);
-    else
-        level_persistent_kernel<DT, C, false><<<grid, kBuildThreads, 0, s>>>(a);
-    return cudaGetLastError();
-}
-
-template <pilot_dtype DT>
-cudaError_t launch_level_persistent_dtype(int C, bool scaled, const LevelArgs& a, int grid,
-                                          cudaStream_t s) {
-    switch (C) {
-        case 4: return launch_level_persistent_typed<DT, 4>(scaled, a, grid, s);
-        case 8: return launch_level_persistent_typed<DT, 8>(scaled, a, grid, s);
-        case 16: return launch_level_persistent_typed<DT, 16>(scaled, a, grid, s);
-        case 32: return launch_level_persistent_typed<DT, 32>(scaled, a, grid, s);
-        case 64: return launch_level_persistent_typed<DT, 64>(scaled, a, grid, s);
-        default: return cudaErrorInvalidValue;
-    }
-}
-
-template <pilot_dtype DT, int C, bool SCALED>
-cudaError_t occupancy_typed(int* n) {
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(n, level_persistent_kernel<DT, C, SCALED>,
-                                                         kBuildThreads, 0);
-}
-
-template <pilot_dtype DT>
-cudaError_t level_persistent_occupancy(int C, bool scaled, int* n) {
-    switch (C) {
-        case 4: return scaled ? occupancy_typed<DT, 4, true>(n) : occupancy_typed<DT, 4, false>(n);
-        case 8: return scaled ? occupancy_typed<DT, 8, true>(n) : occupancy_typed<DT, 8, false>(n);
-        case 16: return scaled ? occupancy_typed<DT, 16, true>(n) : occupancy_typed<DT, 16, false>(n);
-        case 32: return scaled ? occupancy_typed<DT, 32, true>(n) : occupancy_typed<DT, 32, false>(n);
-        case 64: return scaled ? occupancy_typed<DT, 64, true>(n) : occupancy_typed<DT, 64, false>(n);
-        default: return cudaErrorInvalidValue;
-    }
-}
-
 template <pilot_dtype DT, int C>
 cudaError_t launch_build_typed(const BuildParams& p, cudaStream_t s) {
     dim3 grid(p.n_tiles, p.n_active);

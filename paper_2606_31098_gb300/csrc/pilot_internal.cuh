@@ -18,6 +18,19 @@ namespace pilot {
 
 constexpr int kAcc = 32;           // padded width of one partial-sum record
 constexpr int kNumSums = 29;       // 21 H + 6 g + cost + n_valid
+constexpr unsigned kSpinLimit = 1u << 23;   // polls (>= 256 ns apart) before a barrier wait gives up
+constexpr int kSyncWords = 4;      // per persistent level launch: claims, arrivals, generations, pad
+constexpr int kItemAnchors = 4096; // persistent level kernel: anchors per work item (whole tiles)
+constexpr int kSmemFrames = 512;   // persistent level kernel: frame tables staged in shared memory up to this
+
+// Tiles per work item of the persistent level kernel for a reduction tile of `tile` anchors.
+__host__ __device__ inline int tiles_per_item(int tile) { return tile >= kItemAnchors ? 1 : kItemAnchors / tile; }
+
+// Work items per job of a frame of N anchors.
+__host__ __device__ inline int items_per_job(int N, int tile, int tpi) {
+    const int tiles = N > 0 ? (N + tile - 1) / tile : 1;
+    return (tiles + tpi - 1) / tpi;
+}
 constexpr int kBuildThreads = 256;
 constexpr float kZNear = 0.1f;
 
@@ -128,25 +141,35 @@ enum FrameFlags { kFlagInit = 1, kFlagPrune = 2, kFlagFinalize = 4 };
 // Batch header, rewritten before every batch (the captured graph reads it).
 struct BatchHeader {
     int n_frames;
-    int n_jobs[PILOT_MAX_LEVELS];
+    int n_listed[PILOT_MAX_LEVELS];   // frames listed for each level's persistent launch
     int total_hyps;
 };
 
-// Persistent level kernel arguments.  Job j of level l is (job_frame[j], job_slot[j]):
-// the job_slot-th entry of that frame's active list.
+// Persistent level kernel arguments.  A launch's jobs (one per active hypothesis of a listed
+// frame) and work items are numbered frame after frame in list order: listed frame i is
+// frames[fr_list[i]]; its jobs are fr_job[i] .. fr_job[i + 1] - 1 (its active slots in
+// order) and its items fr_item[i] .. fr_item[i + 1] - 1, items_per_job(N) consecutive items
+// per job, each covering tiles_per_item anchor tiles.  Tile t of the job whose first item is
+// q keeps its record at partial[q * tiles_per_item + t].
 struct LevelArgs {
     const BatchHeader* header;
     const FrameDesc* frames;
-    const int* job_frame;
-    const int* job_slot;
+    const int* fr_list;
+    const int* fr_item;
+    const int* fr_job;
     const int* active;         // per frame: active[hyp_offset + slot] = local hypothesis
     HypState* state;           // global hypothesis index
     const double* min_valid;   // per frame
-    int* counter;              // job counter of this level (zero before the launch)
+    float* pose32;             // [job][12] FP32 pose to evaluate next
+    unsigned* job_meta;        // [job] hypothesis index | 0x80000000 when it has a pose to evaluate
+    float* partial;            // tile records
+    unsigned long long* sync;  // [0] item claims, [1] barrier arrivals, [2] barrier generations; zero before the launch
+    unsigned* error;           // set to 1 when a barrier wait gives up
     int level;                 // >= 0: every frame runs this level; -1: each its own level
-    int n_jobs_index;          // which header->n_jobs entry counts this launch's jobs
+    int list_index;            // which header->n_listed entry counts this launch's frames
     int iters[PILOT_MAX_LEVELS];
-    int tile, damping_mode;
+    int k_max;                 // iterations of the longest job of the launch
+    int tile, tiles_per_item, damping_mode;
     float huber;
     double lambda0;
 };

@@ -1,0 +1,249 @@
+// Batched form's persistent level kernel (one cooperative launch per pyramid level for a
+// whole batch of frames, or for a serving round).  It reuses the build pass' anchor loop
+// (accumulate_anchors, cta_reduce) and the FP64 step (lm_update), in the plain form's
+// summation order, so a frame's results are bitwise those of its plain solve.
+#pragma once
+
+#include "pilot_build_impl.cuh"
+
+namespace pilot {
+
+// Grid-wide barrier of the persistent level kernel (cooperative launch: all CTAs resident).
+// sync[1] counts arrivals over all generations, sync[2] is the number of completed
+// generations.  The wait is bounded: past kSpinLimit polls, or when another CTA has failed,
+// the error word is set and false is returned, and the kernel returns; the host reports
+// the error.
+__device__ __forceinline__ bool grid_sync(unsigned long long* sync, unsigned* error, unsigned& gen) {
+    __shared__ int s_ok;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        int ok = 1;
+        const unsigned long long target = (unsigned long long)(gen + 1) * gridDim.x;
+        if (atomicAdd(sync + 1, 1ull) + 1ull == target) {
+            atomicExch(sync + 2, (unsigned long long)(gen + 1));
+        } else {
+            unsigned spins = 0;
+            while (__ldcg(sync + 2) < (unsigned long long)(gen + 1)) {
+                if (__ldcg(error) != 0u) {
+                    ok = 0;
+                    break;
+                }
+                if (++spins > kSpinLimit) {
+                    atomicExch(error, 1u);
+                    ok = 0;
+                    break;
+                }
+                __nanosleep(256);
+            }
+        }
+        __threadfence();
+        s_ok = ok;
+    }
+    __syncthreads();
+    ++gen;
+    return s_ok != 0;
+}
+
+// Batched form: one persistent (cooperative) launch per level for a whole batch of frames.
+// The level's LM iterations run in lockstep over all jobs (a job = one hypothesis of one
+// frame): in iteration k the CTAs claim the work items (runs of up to tiles_per_item
+// consecutive anchor tiles of one job) of every job that has a pose to evaluate, from one
+// counter, and write each tile's FP32 record exactly as build_fused_kernel does (same thread
+// mapping, same sums); after a grid barrier each job's
+// FP64 step runs on lane 0 of one warp, on the tile records summed in the plain form's
+// 8-chain FP64 order, and writes the job's next candidate; a second barrier ends the
+// iteration.  A frame's result is therefore bitwise the one its plain solve gives, whatever
+// else is in the batch; the items balance the gathers over all CTAs, and the FP64 steps of
+// all jobs run at once, one per warp.
+template <pilot_dtype DT, int C, bool SCALED>
+__global__ void __launch_bounds__(kBuildThreads, 2)
+level_persistent_kernel(const LevelArgs a) {
+    constexpr int kWarps = kBuildThreads / 32;
+    constexpr unsigned kEval = 0x80000000u;          // job_meta: "has a pose to evaluate" bit
+    __shared__ float red[kWarps][kAcc];
+    __shared__ double E[kWarps][kAcc];
+    __shared__ float pose[12];
+    __shared__ long long s_item;
+    __shared__ int s_frame, s_job, s_first, s_t0;
+    __shared__ unsigned s_meta;
+    // frame tables, staged when the launch lists few frames
+    __shared__ int s_fitem[kSmemFrames + 1], s_fjob[kSmemFrames + 1], s_flist[kSmemFrames], s_fipj[kSmemFrames];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int n_fr = a.header->n_listed[a.list_index];
+    const int tpi = a.tiles_per_item;
+    const bool staged = n_fr <= kSmemFrames;
+    if (staged)
+        for (int i = tid; i <= n_fr; i += kBuildThreads) {
+            s_fitem[i] = a.fr_item[i];
+            s_fjob[i] = a.fr_job[i];
+            if (i < n_fr) {
+                s_flist[i] = a.fr_list[i];
+                s_fipj[i] = items_per_job(a.frames[s_flist[i]].N, a.tile, tpi);
+            }
+        }
+    __syncthreads();
+    auto fitem = [&](int i) { return staged ? s_fitem[i] : a.fr_item[i]; };
+    auto fjob = [&](int i) { return staged ? s_fjob[i] : a.fr_job[i]; };
+    auto flist = [&](int i) { return staged ? s_flist[i] : a.fr_list[i]; };
+    auto fipj = [&](int i) { return staged ? s_fipj[i] : items_per_job(a.frames[a.fr_list[i]].N, a.tile, tpi); };
+    // listed frame holding x: last i < n_fr with table(i) <= x (empty frames are skipped)
+    auto find = [&](bool items, long long x) {
+        int lo = 0, hi = n_fr - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if ((items ? fitem(mid) : fjob(mid)) <= x) lo = mid;
+            else hi = mid - 1;
+        }
+        return lo;
+    };
+    const int n_items = fitem(n_fr), n_jobs = fjob(n_fr);
+    const int n_warps = gridDim.x * kWarps;
+    unsigned gen = 0;
+    // level start of every job: its hypothesis, LM state and FP32 start pose (pose32 and
+    // job_meta are indexed by job within this launch).  Job j's state is only ever read and
+    // written by lane 0 of global warp j (mod the warp count), here and in the steps below,
+    // so one SM's L1 sees all its accesses; other CTAs read pose32 and job_meta from L2.
+    for (int job = blockIdx.x * kWarps + warp; job < n_jobs; job += n_warps) {
+        if (lane != 0) continue;
+        const int i = find(false, job);
+        const FrameDesc* fd = a.frames + flist(i);
+        const int hyp = fd->hyp_offset + a.active[fd->hyp_offset + job - fjob(i)];
+        HypState& st = a.state[hyp];
+        st.lambda = a.lambda0;
+        st.last_fail = 0;
+        st.has_cand = 1;
+        store_pose32(a.pose32 + 12 * (size_t)job, st.T);
+        a.job_meta[job] = (unsigned)hyp | kEval;
+    }
+    if (!grid_sync(a.sync, a.error, gen)) return;
+    const unsigned long long round = (unsigned long long)n_items + gridDim.x;   // claims per iteration
+    for (int k = 0; k <= a.k_max; ++k) {
+        // gather: the work items of iteration k, claimed one at a time
+        for (;;) {
+            if (tid == 0) {
+                const long long item = (long long)(atomicAdd(a.sync, 1ull) - (unsigned long long)k * round);
+                s_item = item;
+                if (item < n_items) {
+                    const int i = find(true, item);
+                    const int ipj = fipj(i);
+                    const int local = (int)(item - fitem(i));
+                    const int slot = local / ipj;
+                    s_frame = flist(i);
+                    s_job = fjob(i) + slot;
+                    s_first = fitem(i) + slot * ipj;
+                    s_t0 = (local - slot * ipj) * tpi;
+                }
+            }
+            __syncthreads();
+            if (s_item >= n_items) break;
+            const int job = s_job;
+            if (tid < 12) pose[tid] = __ldcg(a.pose32 + 12 * (size_t)job + tid);
+            if (tid == 0) s_meta = __ldcg(a.job_meta + job);
+            __syncthreads();
+            const FrameDesc* fd = a.frames + s_frame;
+            const int level = a.level >= 0 ? a.level : fd->level;
+            if (k <= a.iters[level] && (s_meta & kEval)) {
+                const LevelView v{fd->px, fd->py, fd->pz, fd->weight, fd->valid, fd->qry[level], fd->ref[level],
+                                  fd->qscale[level], fd->rscale[level], fd->H[level], fd->W[level],
+                                  fd->fx[level], fd->fy[level], fd->cx[level], fd->cy[level], a.huber};
+                const int n_t = fd->N > 0 ? (fd->N + a.tile - 1) / a.tile : 1;
+                const int t1 = min(s_t0 + tpi, n_t);
+                for (int t = s_t0; t < t1; ++t) {
+                    float acc[kNumSums];
+#pragma unroll
+                    for (int i = 0; i < kNumSums; ++i) acc[i] = 0.f;
+                    const int j0 = t * a.tile;
+                    accumulate_anchors<DT, C, SCALED, kBuildThreads>(v, pose, j0, min(j0 + a.tile, fd->N), acc);
+                    const float val = cta_reduce<kBuildThreads>(acc, red);
+                    if (tid < kAcc) a.partial[((size_t)s_first * tpi + t) * kAcc + tid] = val;
+                }
+            }
+            __syncthreads();
+        }
+        if (!grid_sync(a.sync, a.error, gen)) return;
+        // FP64 steps: job j on lane 0 of global warp j (mod the warp count)
+        for (int job = blockIdx.x * kWarps + warp; job < n_jobs; job += n_warps) {
+            const int i = find(false, job);
+            const int f = flist(i);
+            const FrameDesc* fd = a.frames + f;
+            const int level = a.level >= 0 ? a.level : fd->level;
+            const int iters = a.iters[level];
+            if (k > iters) continue;
+            const unsigned meta = __ldcg(a.job_meta + job);
+            const int hyp = (int)(meta & ~kEval);
+            const bool evaluated = (meta & kEval) != 0;
+            if (evaluated && lane < kNumSums) {
+                const int n_t = fd->N > 0 ? (fd->N + a.tile - 1) / a.tile : 1;
+                const int first = fitem(i) + (job - fjob(i)) * fipj(i);
+                const float* src = a.partial + (size_t)first * tpi * kAcc + lane;
+                double sum = 0.0;
+                for (int c = 0; c < 8; ++c) {
+                    double part = 0.0;
+                    for (int t = c; t < n_t; t += 8) part += (double)__ldcg(src + (size_t)t * kAcc);
+                    sum += part;
+                }
+                E[warp][lane] = sum;
+            }
+            __syncwarp();
+            if (lane == 0) {
+                HypState& st = a.state[hyp];
+                lm_update(st, k == 0 ? kEpiInit : kEpiStep, k < iters, a.damping_mode, fd->prior, E[warp],
+                          a.min_valid[f], a.pose32 + 12 * (size_t)job, nullptr);
+                a.job_meta[job] = (unsigned)hyp | (st.has_cand ? kEval : 0u);
+            }
+            __syncwarp();
+        }
+        if (!grid_sync(a.sync, a.error, gen)) return;
+    }
+}
+
+template <pilot_dtype DT, int C>
+cudaError_t launch_level_persistent_typed(bool scaled, const LevelArgs& a, int grid, cudaStream_t s) {
+    // cooperative: the grid barrier needs every CTA resident at once
+    cudaLaunchConfig_t cfg{};
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(kBuildThreads);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = s;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    if (scaled) return cudaLaunchKernelEx(&cfg, level_persistent_kernel<DT, C, true>, a);
+    return cudaLaunchKernelEx(&cfg, level_persistent_kernel<DT, C, false>, a);
+}
+
+template <pilot_dtype DT>
+cudaError_t launch_level_persistent_dtype(int C, bool scaled, const LevelArgs& a, int grid,
+                                          cudaStream_t s) {
+    switch (C) {
+        case 4: return launch_level_persistent_typed<DT, 4>(scaled, a, grid, s);
+        case 8: return launch_level_persistent_typed<DT, 8>(scaled, a, grid, s);
+        case 16: return launch_level_persistent_typed<DT, 16>(scaled, a, grid, s);
+        case 32: return launch_level_persistent_typed<DT, 32>(scaled, a, grid, s);
+        case 64: return launch_level_persistent_typed<DT, 64>(scaled, a, grid, s);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+template <pilot_dtype DT, int C, bool SCALED>
+cudaError_t occupancy_typed(int* n) {
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(n, level_persistent_kernel<DT, C, SCALED>,
+                                                         kBuildThreads, 0);
+}
+
+template <pilot_dtype DT>
+cudaError_t level_persistent_occupancy(int C, bool scaled, int* n) {
+    switch (C) {
+        case 4: return scaled ? occupancy_typed<DT, 4, true>(n) : occupancy_typed<DT, 4, false>(n);
+        case 8: return scaled ? occupancy_typed<DT, 8, true>(n) : occupancy_typed<DT, 8, false>(n);
+        case 16: return scaled ? occupancy_typed<DT, 16, true>(n) : occupancy_typed<DT, 16, false>(n);
+        case 32: return scaled ? occupancy_typed<DT, 32, true>(n) : occupancy_typed<DT, 32, false>(n);
+        case 64: return scaled ? occupancy_typed<DT, 64, true>(n) : occupancy_typed<DT, 64, false>(n);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+}  // namespace pilot

@@ -178,7 +178,8 @@ struct pilot_align_handle {
     size_t bres_bytes = 0;
     int* bactive = nullptr;
     double* bmin_valid = nullptr;
-    int* bcounters = nullptr;
+    unsigned long long* bsync = nullptr;   // per level: item claims, barrier arrivals, generations
+    unsigned* bjob_meta = nullptr;         // per job of a level launch: hypothesis | evaluate bit
     cudaStream_t bstream = nullptr;
     // plain form, multi-stream schedule: extra streams, a fork event and their join events
     cudaStream_t pstream[kMaxStreams - 1] = {};
@@ -441,7 +442,8 @@ void release(pilot_align_handle* h) {
     if (h->bres_host) cudaFreeHost(h->bres_host);
     cudaFree(h->bactive);
     cudaFree(h->bmin_valid);
-    cudaFree(h->bcounters);
+    cudaFree(h->bsync);
+    cudaFree(h->bjob_meta);
     if (h->bstream) cudaStreamDestroy(h->bstream);
     for (int i = 0; i < kMaxStreams - 1; ++i) {
         if (h->pstream[i]) cudaStreamDestroy(h->pstream[i]);
@@ -473,7 +475,7 @@ namespace {
 
 // Layout of the batch descriptor block (device copy and pinned host staging).
 struct BatchLayout {
-    size_t off_hdr, off_frames, off_nactive, off_job_frame, off_job_slot, bytes;
+    size_t off_hdr, off_frames, off_nactive, off_fr_list, off_fr_item, off_fr_job, bytes;
     int max_frames, max_jobs;
     static BatchLayout make(int max_frames, int max_hyps) {
         auto a256 = [](size_t b) { return (b + 255) / 256 * 256; };
@@ -483,9 +485,10 @@ struct BatchLayout {
         l.off_hdr = 0;
         l.off_frames = a256(sizeof(BatchHeader));
         l.off_nactive = a256(l.off_frames + sizeof(FrameDesc) * (size_t)max_frames);
-        l.off_job_frame = a256(l.off_nactive + sizeof(int) * PILOT_MAX_LEVELS * (size_t)max_frames);
-        l.off_job_slot = a256(l.off_job_frame + sizeof(int) * PILOT_MAX_LEVELS * (size_t)max_hyps);
-        l.bytes = a256(l.off_job_slot + sizeof(int) * PILOT_MAX_LEVELS * (size_t)max_hyps);
+        l.off_fr_list = a256(l.off_nactive + sizeof(int) * PILOT_MAX_LEVELS * (size_t)max_frames);
+        l.off_fr_item = a256(l.off_fr_list + sizeof(int) * PILOT_MAX_LEVELS * (size_t)max_frames);
+        l.off_fr_job = a256(l.off_fr_item + sizeof(int) * PILOT_MAX_LEVELS * (size_t)(max_frames + 1));
+        l.bytes = a256(l.off_fr_job + sizeof(int) * PILOT_MAX_LEVELS * (size_t)(max_frames + 1));
         return l;
     }
 };
@@ -495,14 +498,17 @@ pilot_status batch_alloc(pilot_align_handle* h) {
     const pilot_align_config& c = h->cfg;
     const BatchLayout lay = BatchLayout::make(c.max_frames, c.max_hyps);
     h->bdesc_bytes = lay.bytes;
-    h->bres_bytes = ResultLayout::make(c.max_hyps).bytes + sizeof(int) * (size_t)c.max_frames;
+    // result block, then the best index per frame, then the barrier error word
+    h->bres_bytes = ResultLayout::make(c.max_hyps).bytes + sizeof(int) * ((size_t)c.max_frames + 1);
     PILOT_CUDA(cudaMalloc((void**)&h->bdesc_dev, h->bdesc_bytes), "batch descriptor allocation");
     PILOT_CUDA(cudaMallocHost((void**)&h->bdesc_host, h->bdesc_bytes), "batch descriptor staging");
     PILOT_CUDA(cudaMalloc((void**)&h->bres_dev, h->bres_bytes), "batch result allocation");
     PILOT_CUDA(cudaMallocHost((void**)&h->bres_host, h->bres_bytes), "batch result staging");
     PILOT_CUDA(cudaMalloc((void**)&h->bactive, sizeof(int) * (size_t)c.max_hyps), "batch active lists");
     PILOT_CUDA(cudaMalloc((void**)&h->bmin_valid, sizeof(double) * (size_t)c.max_frames), "batch thresholds");
-    PILOT_CUDA(cudaMalloc((void**)&h->bcounters, sizeof(int) * PILOT_MAX_LEVELS), "batch counters");
+    PILOT_CUDA(cudaMalloc((void**)&h->bsync, sizeof(unsigned long long) * kSyncWords * PILOT_MAX_LEVELS),
+               "batch level counters");
+    PILOT_CUDA(cudaMalloc((void**)&h->bjob_meta, sizeof(unsigned) * (size_t)c.max_hyps), "batch job table");
     PILOT_CUDA(cudaStreamCreateWithFlags(&h->bstream, cudaStreamNonBlocking), "batch stream");
     return PILOT_OK;
 }
@@ -566,11 +572,16 @@ pilot_status capture_batch_graph(pilot_align_handle* h, pilot_dtype dt, int C, b
     const BatchHeader* hdr = reinterpret_cast<const BatchHeader*>(h->bdesc_dev + lay.off_hdr);
     const FrameDesc* frames = reinterpret_cast<const FrameDesc*>(h->bdesc_dev + lay.off_frames);
     const int* nactive = reinterpret_cast<const int*>(h->bdesc_dev + lay.off_nactive);
-    const int* job_frame = reinterpret_cast<const int*>(h->bdesc_dev + lay.off_job_frame);
-    const int* job_slot = reinterpret_cast<const int*>(h->bdesc_dev + lay.off_job_slot);
+    const int* fr_list = reinterpret_cast<const int*>(h->bdesc_dev + lay.off_fr_list);
+    const int* fr_item = reinterpret_cast<const int*>(h->bdesc_dev + lay.off_fr_item);
+    const int* fr_job = reinterpret_cast<const int*>(h->bdesc_dev + lay.off_fr_job);
+    unsigned* error = reinterpret_cast<unsigned*>(h->bres_dev + ResultLayout::make(c.max_hyps).bytes +
+                                                  sizeof(int) * (size_t)c.max_frames);
     PILOT_CUDA(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal), "graph capture begin");
     cudaError_t e = cudaMemcpyAsync(h->bdesc_dev, h->bdesc_host, h->bdesc_bytes, cudaMemcpyHostToDevice, s);
-    if (e == cudaSuccess) e = cudaMemsetAsync(h->bcounters, 0, sizeof(int) * PILOT_MAX_LEVELS, s);
+    if (e == cudaSuccess)
+        e = cudaMemsetAsync(h->bsync, 0, sizeof(unsigned long long) * kSyncWords * PILOT_MAX_LEVELS, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(error, 0, sizeof(unsigned), s);
     if (e == cudaSuccess) e = launch_batch_init(hdr, frames, h->state, h->bactive, c.max_frames, s);
     if (e == cudaSuccess)
         e = launch_batch_count_valid(hdr, frames, c.min_valid_frac, h->bmin_valid, c.max_frames, s);
@@ -578,16 +589,23 @@ pilot_status capture_batch_graph(pilot_align_handle* h, pilot_dtype dt, int C, b
         LevelArgs a{};
         a.header = hdr;
         a.frames = frames;
-        a.job_frame = job_frame + (size_t)level * lay.max_jobs;
-        a.job_slot = job_slot + (size_t)level * lay.max_jobs;
+        a.fr_list = fr_list + (size_t)level * lay.max_frames;
+        a.fr_item = fr_item + (size_t)level * (lay.max_frames + 1);
+        a.fr_job = fr_job + (size_t)level * (lay.max_frames + 1);
         a.active = h->bactive;
         a.state = h->state;
         a.min_valid = h->bmin_valid;
-        a.counter = h->bcounters + level;
+        a.pose32 = h->pose32;
+        a.job_meta = h->bjob_meta;
+        a.partial = h->partial;
+        a.sync = h->bsync + (size_t)level * kSyncWords;
+        a.error = error;
         a.level = level;
-        a.n_jobs_index = level;
+        a.list_index = level;
         for (int l = 0; l < PILOT_MAX_LEVELS; ++l) a.iters[l] = c.iters_per_level[l];
+        a.k_max = c.iters_per_level[level];
         a.tile = sc.tile;
+        a.tiles_per_item = tiles_per_item(sc.tile);
         a.damping_mode = c.damping_mode;
         a.huber = (float)c.huber_photo;
         a.lambda0 = c.lambda0;
@@ -651,7 +669,9 @@ pilot_status pilot_align_create(const pilot_align_config* cfg_in, pilot_align_ha
     }
     ALLOC(h->state, sizeof(HypState) * M);
     ALLOC(h->pose32, sizeof(float) * 12 * M);
-    ALLOC(h->partial, sizeof(float) * kAcc * M * (size_t)h->max_tiles);
+    // tile records: plain form [slot][tile]; batched form [job_item * tiles_per_item + tile],
+    // which rounds each job's tiles up to whole work items
+    ALLOC(h->partial, sizeof(float) * kAcc * M * ((size_t)h->max_tiles + kItemAnchors / kMinTile));
     ALLOC(h->active[0], sizeof(int) * M);
     ALLOC(h->active[1], sizeof(int) * M);
     ALLOC(h->Tin, sizeof(double) * 12 * M);
@@ -870,8 +890,9 @@ pilot_status pilot_align_solve_batch(pilot_align_handle* h, const pilot_frame* f
     BatchHeader* hdr = reinterpret_cast<BatchHeader*>(hb + lay.off_hdr);
     FrameDesc* fds = reinterpret_cast<FrameDesc*>(hb + lay.off_frames);
     int* nactive = reinterpret_cast<int*>(hb + lay.off_nactive);
-    int* job_frame = reinterpret_cast<int*>(hb + lay.off_job_frame);
-    int* job_slot = reinterpret_cast<int*>(hb + lay.off_job_slot);
+    int* fr_list = reinterpret_cast<int*>(hb + lay.off_fr_list);
+    int* fr_item = reinterpret_cast<int*>(hb + lay.off_fr_item);
+    int* fr_job = reinterpret_cast<int*>(hb + lay.off_fr_job);
     memset(hdr, 0, sizeof(BatchHeader));
     hdr->n_frames = n;
     hdr->total_hyps = (int)total;
@@ -909,40 +930,31 @@ pilot_status pilot_align_solve_batch(pilot_align_handle* h, const pilot_frame* f
         d.prior = prior_params(c, f, dv);
         off += f->M;
     }
-    // hypotheses per frame and level (top-K is deterministic in count), and the job
-    // tables: frames with more anchors first (longest job first), slots in order
+    // hypotheses per frame and level (top-K is deterministic in count), and each level's
+    // frame list: frames with more anchors first (job_order 0) or in the caller's order (1);
+    // jobs and work items are numbered frame after frame in list order
     const pilot_schedule sc = schedule_for(h, frames, n, 1);
     std::vector<int> order(n);
     for (int i = 0; i < n; ++i) order[i] = i;
-    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return frames[a].N > frames[b].N; });
+    if (sc.job_order == 0)
+        std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return frames[a].N > frames[b].N; });
+    const int tpi = tiles_per_item(sc.tile);
     std::vector<long long> hyp_iters(n, 0);
     std::vector<int> cur(n);
     for (int i = 0; i < n; ++i) cur[i] = frames[i].M;
     for (int level = L - 1; level >= 0; --level) {
-        int nj = 0;
-        for (int i = 0; i < n; ++i) nactive[(size_t)level * lay.max_frames + i] = cur[i];
-        if (sc.job_order == 1) {
-            int most = 0;
-            for (int i = 0; i < n; ++i) most = std::max(most, cur[i]);
-            for (int k = 0; k < most; ++k)
-                for (int oi = 0; oi < n; ++oi) {
-                    const int i = order[oi];
-                    if (k >= cur[i]) continue;
-                    job_frame[(size_t)level * lay.max_jobs + nj] = i;
-                    job_slot[(size_t)level * lay.max_jobs + nj] = k;
-                    ++nj;
-                }
-        } else {
-            for (int oi = 0; oi < n; ++oi) {
-                const int i = order[oi];
-                for (int k = 0; k < cur[i]; ++k) {
-                    job_frame[(size_t)level * lay.max_jobs + nj] = i;
-                    job_slot[(size_t)level * lay.max_jobs + nj] = k;
-                    ++nj;
-                }
-            }
+        int* list = fr_list + (size_t)level * lay.max_frames;
+        int* items = fr_item + (size_t)level * (lay.max_frames + 1);
+        int* jobs = fr_job + (size_t)level * (lay.max_frames + 1);
+        items[0] = jobs[0] = 0;
+        for (int oi = 0; oi < n; ++oi) {
+            const int i = order[oi];
+            nactive[(size_t)level * lay.max_frames + i] = cur[i];
+            list[oi] = i;
+            jobs[oi + 1] = jobs[oi] + cur[i];
+            items[oi + 1] = items[oi] + cur[i] * items_per_job(frames[i].N, sc.tile, tpi);
         }
-        hdr->n_jobs[level] = nj;
+        hdr->n_listed[level] = n;
         for (int i = 0; i < n; ++i) {
             hyp_iters[i] += (long long)cur[i] * c.iters_per_level[level];
             const int K = c.keep_top_k[level];
@@ -959,6 +971,8 @@ pilot_status pilot_align_solve_batch(pilot_align_handle* h, const pilot_frame* f
     const ResultLayout rl = ResultLayout::make(c.max_hyps);
     const unsigned char* r = h->bres_host;
     const int* best = reinterpret_cast<const int*>(r + rl.bytes);
+    if (best[c.max_frames] != 0)
+        return fail(PILOT_ETIMEOUT, "batched solve: a level kernel's grid barrier timed out (results invalid)");
     for (int i = 0; i < n; ++i) {
         const int o = fds[i].hyp_offset, M = frames[i].M;
         pilot_result& out = results[i];

@@ -142,10 +142,13 @@ struct pilot_server {
     HypState* state = nullptr;
     int* active = nullptr;
     double* min_valid = nullptr;
-    int* counter = nullptr;
+    unsigned long long* sync = nullptr;   // level kernel: item claims, barrier arrivals, generations
+    float* pose32 = nullptr;              // [job][12] FP32 poses to evaluate
+    unsigned* job_meta = nullptr;         // [job] hypothesis | evaluate bit
+    float* partial = nullptr;             // [work item][kAcc] tile records
     unsigned char* desc_dev = nullptr;
     unsigned char* desc_host = nullptr;
-    size_t desc_bytes = 0, off_frames = 0, off_job_frame = 0, off_job_slot = 0;
+    size_t desc_bytes = 0, off_frames = 0, off_fr_list = 0, off_fr_item = 0, off_fr_job = 0;
     unsigned char* res_dev = nullptr;
     unsigned char* res_host = nullptr;
     size_t res_bytes = 0;
@@ -179,7 +182,10 @@ void release_buffers(pilot_server* s) {
     cudaFree(s->state);
     cudaFree(s->active);
     cudaFree(s->min_valid);
-    cudaFree(s->counter);
+    cudaFree(s->sync);
+    cudaFree(s->pose32);
+    cudaFree(s->job_meta);
+    cudaFree(s->partial);
     cudaFree(s->desc_dev);
     if (s->desc_host) cudaFreeHost(s->desc_host);
     cudaFree(s->res_dev);
@@ -244,7 +250,10 @@ cudaError_t capture_round(pilot_server* s) {
     const FrameDesc* frames = reinterpret_cast<const FrameDesc*>(s->desc_dev + s->off_frames);
     if ((e = cudaStreamBeginCapture(s->stream, cudaStreamCaptureModeThreadLocal)) != cudaSuccess) return e;
     e = cudaMemcpyAsync(s->desc_dev, s->desc_host, s->desc_bytes, cudaMemcpyHostToDevice, s->stream);
-    if (e == cudaSuccess) e = cudaMemsetAsync(s->counter, 0, sizeof(int), s->stream);
+    unsigned* error = reinterpret_cast<unsigned*>(s->res_dev + ResultLayout::make(s->cfg.max_hyps).bytes +
+                                                  sizeof(int) * (size_t)s->max_slots);
+    if (e == cudaSuccess) e = cudaMemsetAsync(s->sync, 0, sizeof(unsigned long long) * kSyncWords, s->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(error, 0, sizeof(unsigned), s->stream);
     if (e == cudaSuccess)
         e = launch_round_prepare(hdr, frames, s->state, s->active, s->cfg.min_valid_frac, s->min_valid,
                                  s->max_slots, s->stream);
@@ -252,16 +261,26 @@ cudaError_t capture_round(pilot_server* s) {
         LevelArgs a{};
         a.header = hdr;
         a.frames = frames;
-        a.job_frame = reinterpret_cast<const int*>(s->desc_dev + s->off_job_frame);
-        a.job_slot = reinterpret_cast<const int*>(s->desc_dev + s->off_job_slot);
+        a.fr_list = reinterpret_cast<const int*>(s->desc_dev + s->off_fr_list);
+        a.fr_item = reinterpret_cast<const int*>(s->desc_dev + s->off_fr_item);
+        a.fr_job = reinterpret_cast<const int*>(s->desc_dev + s->off_fr_job);
         a.active = s->active;
         a.state = s->state;
         a.min_valid = s->min_valid;
-        a.counter = s->counter;
+        a.pose32 = s->pose32;
+        a.job_meta = s->job_meta;
+        a.partial = s->partial;
+        a.sync = s->sync;
+        a.error = error;
         a.level = -1;
-        a.n_jobs_index = 0;
-        for (int l = 0; l < PILOT_MAX_LEVELS; ++l) a.iters[l] = s->cfg.iters_per_level[l];
+        a.list_index = 0;
+        a.k_max = 0;
+        for (int l = 0; l < PILOT_MAX_LEVELS; ++l) {
+            a.iters[l] = s->cfg.iters_per_level[l];
+            a.k_max = std::max(a.k_max, a.iters[l]);
+        }
         a.tile = kPlainTile;
+        a.tiles_per_item = tiles_per_item(kPlainTile);
         a.damping_mode = s->cfg.damping_mode;
         a.huber = (float)s->cfg.huber_photo;
         a.lambda0 = s->cfg.lambda0;
@@ -316,14 +335,16 @@ void write_round(pilot_server* s) {
     const pilot_align_config& c = s->cfg;
     BatchHeader* hdr = reinterpret_cast<BatchHeader*>(s->desc_host);
     FrameDesc* fds = reinterpret_cast<FrameDesc*>(s->desc_host + s->off_frames);
-    int* jf = reinterpret_cast<int*>(s->desc_host + s->off_job_frame);
-    int* js = reinterpret_cast<int*>(s->desc_host + s->off_job_slot);
+    int* list = reinterpret_cast<int*>(s->desc_host + s->off_fr_list);
+    int* items = reinterpret_cast<int*>(s->desc_host + s->off_fr_item);
+    int* jobs = reinterpret_cast<int*>(s->desc_host + s->off_fr_job);
     memset(hdr, 0, sizeof(BatchHeader));
     hdr->n_frames = s->max_slots;
     memset(fds, 0, sizeof(FrameDesc) * (size_t)s->max_slots);
     std::vector<Request*> order = s->running;
     std::stable_sort(order.begin(), order.end(), [](Request* a, Request* b) { return a->src.N > b->src.N; });
-    int nj = 0;
+    int nl = 0;
+    items[0] = jobs[0] = 0;
     for (Request* r : order) {
         const pilot_frame& f = r->dev;
         FrameDesc& d = fds[r->slot];
@@ -357,13 +378,12 @@ void write_round(pilot_server* s) {
         d.flags = (r->initialized ? 0 : kFlagInit) | ((r->level > 0 && K > 0 && K < r->n_active) ? kFlagPrune : 0) |
                   (r->level == 0 ? kFlagFinalize : 0);
         d.prior = frame_prior(c, &f, f.dsm);
-        for (int k = 0; k < r->n_active; ++k) {
-            jf[nj] = r->slot;
-            js[nj] = k;
-            ++nj;
-        }
+        list[nl] = r->slot;
+        jobs[nl + 1] = jobs[nl] + r->n_active;
+        items[nl + 1] = items[nl] + r->n_active * items_per_job(f.N, kPlainTile, tiles_per_item(kPlainTile));
+        ++nl;
     }
-    hdr->n_jobs[0] = nj;
+    hdr->n_listed[0] = nl;
 }
 
 // After a round: advance levels, collect finished frames.
@@ -436,8 +456,12 @@ void worker_main(pilot_server* s) {
         if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
         lock.lock();
         ++s->rounds;
+        const unsigned* barrier_error = reinterpret_cast<const unsigned*>(
+            s->res_host + ResultLayout::make(s->cfg.max_hyps).bytes + sizeof(int) * (size_t)s->max_slots);
         if (e != cudaSuccess) {
             fail_all(s, e, "serving round");
+        } else if (*barrier_error != 0) {
+            fail_all(s, cudaErrorTimeout, "serving round (level kernel grid barrier timed out)");
         } else {
             after_round(s);
         }
@@ -472,15 +496,24 @@ pilot_status pilot_serve_create(const pilot_align_config* cfg_in, size_t hbm_bud
     if (e != cudaSuccess) return bad("cudaGetDevice");
     const size_t H = (size_t)cfg.max_hyps;
     s->off_frames = a256(sizeof(BatchHeader));
-    s->off_job_frame = a256(s->off_frames + sizeof(FrameDesc) * (size_t)max_slots);
-    s->off_job_slot = a256(s->off_job_frame + sizeof(int) * H);
-    s->desc_bytes = a256(s->off_job_slot + sizeof(int) * H);
-    s->res_bytes = ResultLayout::make(cfg.max_hyps).bytes + sizeof(int) * (size_t)max_slots;
+    s->off_fr_list = a256(s->off_frames + sizeof(FrameDesc) * (size_t)max_slots);
+    s->off_fr_item = a256(s->off_fr_list + sizeof(int) * (size_t)max_slots);
+    s->off_fr_job = a256(s->off_fr_item + sizeof(int) * ((size_t)max_slots + 1));
+    s->desc_bytes = a256(s->off_fr_job + sizeof(int) * ((size_t)max_slots + 1));
+    // result block, the best index per slot, then the barrier error word
+    s->res_bytes = ResultLayout::make(cfg.max_hyps).bytes + sizeof(int) * ((size_t)max_slots + 1);
+    const size_t max_tiles = cfg.max_points > 0 ? ((size_t)cfg.max_points + kPlainTile - 1) / kPlainTile : 1;
     if ((e = cudaMalloc((void**)&s->arena, hbm_budget)) != cudaSuccess) return bad("arena allocation");
     if ((e = cudaMalloc((void**)&s->state, sizeof(HypState) * H)) != cudaSuccess) return bad("state allocation");
     if ((e = cudaMalloc((void**)&s->active, sizeof(int) * H)) != cudaSuccess) return bad("active lists");
     if ((e = cudaMalloc((void**)&s->min_valid, sizeof(double) * (size_t)max_slots)) != cudaSuccess) return bad("thresholds");
-    if ((e = cudaMalloc((void**)&s->counter, sizeof(int))) != cudaSuccess) return bad("counter");
+    if ((e = cudaMalloc((void**)&s->sync, sizeof(unsigned long long) * kSyncWords)) != cudaSuccess)
+        return bad("level counters");
+    if ((e = cudaMalloc((void**)&s->pose32, sizeof(float) * 12 * H)) != cudaSuccess) return bad("candidates");
+    if ((e = cudaMalloc((void**)&s->job_meta, sizeof(unsigned) * H)) != cudaSuccess) return bad("job table");
+    if ((e = cudaMalloc((void**)&s->partial,
+                        sizeof(float) * kAcc * H * (max_tiles + tiles_per_item(kPlainTile)))) != cudaSuccess)
+        return bad("tile records");
     if ((e = cudaMalloc((void**)&s->desc_dev, s->desc_bytes)) != cudaSuccess) return bad("descriptors");
     if ((e = cudaMallocHost((void**)&s->desc_host, s->desc_bytes)) != cudaSuccess) return bad("descriptor staging");
     if ((e = cudaMalloc((void**)&s->res_dev, s->res_bytes)) != cudaSuccess) return bad("results");
