@@ -66,6 +66,9 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--seed-index", type=int, default=0)
     ap.add_argument("--no-forms", action="store_true", help="skip the batched and served measurements")
+    ap.add_argument("--pin-schedule", default="", metavar="TILE:STREAMS",
+                    help="skip the autotuner: plain form with this tile and stream count, batched form with "
+                         "this tile (for profiling runs, whose timings would mislead the autotuner)")
     return ap.parse_args()
 
 
@@ -205,7 +208,11 @@ def batched_and_served(args, B, S, torch, world, stream):
 
     def time_batch(fas, reps):
         solver = B.Solver(B.Options(max_points=384 * 384, max_hyps=sum(fa.M for fa in fas), max_frames=len(fas)))
-        sched, _ = solver.autotune(fas, batched=True, reps=1, stream=stream)
+        if args.pin_schedule:
+            solver.set_schedule(fas, batched=True, tile=int(args.pin_schedule.split(":")[0]))
+            sched = solver.schedule(fas, batched=True)
+        else:
+            sched, _ = solver.autotune(fas, batched=True, reps=1, stream=stream)
         solver.solve_batch(fas, stream)
         ts, units = [], 0
         for _ in range(reps):
@@ -453,7 +460,12 @@ def run_ours(args):
             units += r.hyp_iters
         return times, build_ms, build_n, launches, units, r
 
-    plain_schedule, _ = solver.autotune([dev], batched=False, reps=3, stream=stream)
+    if args.pin_schedule:
+        tile, streams = (int(v) for v in args.pin_schedule.split(":"))
+        solver.set_schedule([dev], batched=False, tile=tile, streams=streams)
+        plain_schedule = solver.schedule([dev], batched=False)
+    else:
+        plain_schedule, _ = solver.autotune([dev], batched=False, reps=3, stream=stream)
     for _ in range(args.warmup):
         solver.solve(dev, stream)
         solver.solve(host, stream)
@@ -474,6 +486,7 @@ def run_ours(args):
     precision = {}
     for dt in (B.BF16, B.FP8E4M3):
         qa = B.FrameArgs(frame, B.quantized_device_arrays(frame, dt), is_device=True, dtype=dt)
+        solver.set_schedule([qa], batched=False, tile=plain_schedule["tile"], streams=plain_schedule["streams"])
         for _ in range(2):
             solver.solve(qa, stream)
         qt, qb, qn, _, qu, _ = timed(qa, max(3, args.steps // 3))
