@@ -511,6 +511,10 @@ def run_ours(args):
     peak_tflops = SM_COUNT * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
     gather_gbs = build_units * gather_bytes_per_unit(C, elem) / (total_ms * 1e-3) / 1e9
     traffic = traffic_per_launch(units_per_launch)
+    # measured ceilings on this GPU: FP32 FMA throughput, and the same 4-tap gathers from the
+    # finest map at random pixels (no reuse between samples)
+    probe_fma = B.probe_fma(stream)
+    probe_gather = B.probe_gather(dev.arrays["qry_feat"][0], B.F32, 1 << 24, stream)
 
     batched, served = batched_and_served(args, B, S, torch, world, stream) if not args.no_forms else ({}, {})
     paper = paper_schedule_form(args, B, S, torch, world, stream) if not args.no_forms else {}
@@ -553,7 +557,10 @@ def run_ours(args):
                              "flops_per_unit": flops_per_unit(C), "units_per_launch": units_per_launch,
                              "avg_launch_ms": avg_launch_ms, "launches": build_n, "concurrent_launches": parts,
                              "achieved_basis": "build-pass units of the timed solves x flops per unit / their device time",
-                             "gather_bytes_per_unit": gather_bytes_per_unit(C, elem), "gather_GBps": gather_gbs},
+                             "gather_bytes_per_unit": gather_bytes_per_unit(C, elem), "gather_GBps": gather_gbs,
+                             "probes": {"fma_TFLOPs": probe_fma, "frac_of_probe_fma": achieved_tflops / probe_fma,
+                                        "gather_random_pixels_GBps": probe_gather,
+                                        "gather_vs_probe": gather_gbs / probe_gather}},
                 "precision_forms": precision,
                 "batched_form": batched,
                 "served_form": served, "paper_schedule_form": paper,

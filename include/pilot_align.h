@@ -208,6 +208,29 @@ pilot_status pilot_align_get_schedule(const pilot_align_handle* h, const pilot_f
 pilot_status pilot_align_solve_batch(pilot_align_handle* h, const pilot_frame* frames, int n_frames,
                                      pilot_result* results, void* stream);
 
+/* Roofline probes (the paper has no counterpart): measured ceilings the build pass is
+ * compared against.  pilot_probe_fma: FP32 FMA throughput in TFLOP/s (packed FP32x2 FMAs on
+ * every SM).  pilot_probe_gather: GB/s of the build pass' access pattern without its
+ * arithmetic -- `samples` 4-tap bilinear footprints (taps (r, c), (r, c + 1), (r + 1, c),
+ * (r + 1, c + 1), C contiguous channels each) at uniformly random pixels of a device NHWC map
+ * of H x W x C elements of `dtype`, one 16-byte load per lane; bytes counted = samples x 4 x
+ * C x element size.  The map must be 16-byte aligned with C x element size in {16, 32, 64,
+ * 128} bytes.  Each times one launch after a warm-up one on `stream`; synchronous. */
+pilot_status pilot_probe_fma(double* tflops, void* stream);
+pilot_status pilot_probe_gather(const void* map, int H, int W, int C, pilot_dtype dtype, long long samples,
+                                double* gbps, void* stream);
+
+/* Failure-detection self-test of the batched form's grid barrier (the paper has no
+ * counterpart; the persistent level kernel's barrier waits are bounded in time so that a
+ * device that cannot keep every CTA resident yields PILOT_ETIMEOUT instead of a hang).
+ * Launches that kernel with no work and a barrier that waits for one CTA more than the
+ * launch has, so every CTA gives up after timeout_ms (1 .. 10000) and sets the error word.
+ * Returns PILOT_OK when the timeout was reported and the launch ended (*elapsed_ms, may be
+ * NULL, receives its device time); the handle stays usable.  Overwrites the handle's batch
+ * descriptors, which the next pilot_align_solve_batch uploads again.  Synchronous. */
+pilot_status pilot_align_selftest_barrier_timeout(pilot_align_handle* h, double timeout_ms, double* elapsed_ms,
+                                                  void* stream);
+
 /* Evaluate the normal equations of the total objective (Eq. 7, Eq. 8) at the given
  * poses on one level, without any LM step: out29 (HOST, M x 29 doubles) receives per
  * pose the 21 upper-triangle entries of J^T W J (row-major), the 6 entries of J^T W r,

@@ -66,6 +66,10 @@ SIGNATURES = {
     "pilot_align_autotune": (ct.c_int, [_vp, _vp, ct.c_int, ct.c_int, ct.c_int, _vp, ct.POINTER(ct.c_double), _vp]),
     "pilot_align_get_schedule": (ct.c_int, [_vp, _vp, ct.c_int, ct.c_int, _vp]),
     "pilot_align_set_schedule": (ct.c_int, [_vp, _vp, ct.c_int, ct.c_int, _vp]),
+    "pilot_align_selftest_barrier_timeout": (ct.c_int, [_vp, ct.c_double, ct.POINTER(ct.c_double), _vp]),
+    "pilot_probe_fma": (ct.c_int, [ct.POINTER(ct.c_double), _vp]),
+    "pilot_probe_gather": (ct.c_int, [_vp, ct.c_int, ct.c_int, ct.c_int, ct.c_int, ct.c_longlong,
+                                      ct.POINTER(ct.c_double), _vp]),
     "pilot_align_debug_normal_eq": (ct.c_int, [_vp, ct.POINTER(pilot_frame), ct.c_int, _vp, _vp, _vp]),
     "pilot_align_profile": (ct.c_int, [_vp, ct.POINTER(ct.c_double), ct.POINTER(ct.c_int), ct.POINTER(ct.c_int)]),
     "pilot_align_normal_eq_noalloc": (ct.c_int, [ct.POINTER(pilot_align_config), ct.POINTER(pilot_frame), ct.c_int,
@@ -341,6 +345,13 @@ class Solver:
                                               ct.cast(ct.byref(sc), _vp)))
         return _schedule_dict(sc)
 
+    def selftest_barrier_timeout(self, timeout_ms: float, stream=None) -> float:
+        """pilot_align_selftest_barrier_timeout: returns the launch's device time (ms)."""
+        ms = ct.c_double()
+        check(load().pilot_align_selftest_barrier_timeout(self.h, float(timeout_ms), ct.byref(ms),
+                                                          self._stream(stream)))
+        return ms.value
+
     def set_schedule(self, fas: list, batched: bool, tile: int = 1024, ctas_per_sm: int = 0,
                      job_order: int = 0, streams: int = 0) -> None:
         """pilot_align_set_schedule: pin the schedule for frames of this shape."""
@@ -373,6 +384,22 @@ def normal_eq_noalloc(opts: Options, fa: FrameArgs, level: int, T_cw_dev, out29_
                                                  _ptr(out29_dev), Solver._stream(stream))
 
 
+def probe_fma(stream=None) -> float:
+    """pilot_probe_fma: measured FP32 FMA throughput (TFLOP/s)."""
+    v = ct.c_double()
+    check(load().pilot_probe_fma(ct.byref(v), Solver._stream(stream)))
+    return v.value
+
+
+def probe_gather(map_dev, dtype: int, samples: int = 1 << 24, stream=None) -> float:
+    """pilot_probe_gather on a device H x W x C map: 4-tap gathers at random pixels (GB/s)."""
+    H, W, C = map_dev.shape
+    v = ct.c_double()
+    check(load().pilot_probe_gather(ct.c_void_p(map_dev.data_ptr()), int(H), int(W), int(C), int(dtype),
+                                    int(samples), ct.byref(v), Solver._stream(stream)))
+    return v.value
+
+
 def quantize_features(src, dtype: int, per_channel: bool = False, stream=None):
     """pilot_quantize_features on a contiguous FP32 CUDA tensor (..., C): returns the
     quantised tensor (torch bfloat16 / float16 / uint8 bytes for E4M3) and the C scales."""
@@ -390,7 +417,9 @@ def quantize_features(src, dtype: int, per_channel: bool = False, stream=None):
 
 def quantized_device_arrays(frame, dtype: int, per_channel: bool = False, T_hyps=None, device="cuda") -> dict:
     """Device arrays of a frame with the query maps and reference descriptors quantised on
-    the GPU (each map and each reference block with its own per-channel scales)."""
+    the GPU (each map and each reference block with its own per-channel scales).  BF16 and
+    FP16 without per-channel scaling store the values themselves (every scale is exactly 1),
+    so no scale arrays are passed and the solver takes its unscaled path (the same values)."""
     arrs = device_arrays(frame, T_hyps, device)
     if dtype == F32:
         return arrs
@@ -399,7 +428,9 @@ def quantized_device_arrays(frame, dtype: int, per_channel: bool = False, T_hyps
         a, sa = quantize_features(q, dtype, per_channel)
         b, sb = quantize_features(r, dtype, per_channel) if r.numel() else (r.to(a.dtype), sa.clone())
         qf.append(a); qs.append(sa); rf.append(b); rs.append(sb)
-    arrs.update(qry_feat=qf, qry_scale=qs, ref_feat=rf, ref_scale=rs)
+    arrs.update(qry_feat=qf, ref_feat=rf)
+    if dtype == FP8E4M3 or per_channel:
+        arrs.update(qry_scale=qs, ref_scale=rs)
     return arrs
 
 

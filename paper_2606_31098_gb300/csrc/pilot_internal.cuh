@@ -18,7 +18,7 @@ namespace pilot {
 
 constexpr int kAcc = 32;           // padded width of one partial-sum record
 constexpr int kNumSums = 29;       // 21 H + 6 g + cost + n_valid
-constexpr unsigned kSpinLimit = 1u << 23;   // polls (>= 256 ns apart) before a barrier wait gives up
+constexpr unsigned long long kBarrierTimeoutNs = 2000000000ull;   // level kernel: longest barrier wait
 constexpr int kSyncWords = 4;      // per persistent level launch: claims, arrivals, generations, pad
 constexpr int kItemAnchors = 4096; // persistent level kernel: anchors per work item (whole tiles)
 constexpr int kSmemFrames = 512;   // persistent level kernel: frame tables staged in shared memory up to this
@@ -165,6 +165,8 @@ struct LevelArgs {
     float* partial;            // tile records
     unsigned long long* sync;  // [0] item claims, [1] barrier arrivals, [2] barrier generations; zero before the launch
     unsigned* error;           // set to 1 when a barrier wait gives up
+    unsigned long long barrier_timeout_ns;   // longest barrier wait
+    int barrier_extra;         // 0; > 0 only in the failure self-test (a barrier that cannot complete)
     int level;                 // >= 0: every frame runs this level; -1: each its own level
     int list_index;            // which header->n_listed entry counts this launch's frames
     int iters[PILOT_MAX_LEVELS];

@@ -8,28 +8,36 @@
 
 namespace pilot {
 
+__device__ __forceinline__ unsigned long long global_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
 // Grid-wide barrier of the persistent level kernel (cooperative launch: all CTAs resident).
 // sync[1] counts arrivals over all generations, sync[2] is the number of completed
-// generations.  The wait is bounded: past kSpinLimit polls, or when another CTA has failed,
-// the error word is set and false is returned, and the kernel returns; the host reports
-// the error.
-__device__ __forceinline__ bool grid_sync(unsigned long long* sync, unsigned* error, unsigned& gen) {
+// generations; a generation completes when gridDim.x + extra CTAs have arrived (extra is 0
+// except in the failure self-test, where it makes the barrier impossible).  The wait is
+// bounded in time: past timeout_ns, or as soon as another CTA has given up, the error word
+// is set, false is returned and the kernel returns; the host reports the error.
+__device__ __forceinline__ bool grid_sync(unsigned long long* sync, unsigned* error, unsigned& gen,
+                                          unsigned long long timeout_ns, int extra) {
     __shared__ int s_ok;
     __syncthreads();
     if (threadIdx.x == 0) {
         __threadfence();
         int ok = 1;
-        const unsigned long long target = (unsigned long long)(gen + 1) * gridDim.x;
+        const unsigned long long target = (unsigned long long)(gen + 1) * (gridDim.x + (unsigned)extra);
         if (atomicAdd(sync + 1, 1ull) + 1ull == target) {
             atomicExch(sync + 2, (unsigned long long)(gen + 1));
         } else {
-            unsigned spins = 0;
+            const unsigned long long t0 = global_ns();
             while (__ldcg(sync + 2) < (unsigned long long)(gen + 1)) {
                 if (__ldcg(error) != 0u) {
                     ok = 0;
                     break;
                 }
-                if (++spins > kSpinLimit) {
+                if (global_ns() - t0 > timeout_ns) {
                     atomicExch(error, 1u);
                     ok = 0;
                     break;
@@ -116,7 +124,7 @@ level_persistent_kernel(const LevelArgs a) {
         store_pose32(a.pose32 + 12 * (size_t)job, st.T);
         a.job_meta[job] = (unsigned)hyp | kEval;
     }
-    if (!grid_sync(a.sync, a.error, gen)) return;
+    if (!grid_sync(a.sync, a.error, gen, a.barrier_timeout_ns, a.barrier_extra)) return;
     const unsigned long long round = (unsigned long long)n_items + gridDim.x;   // claims per iteration
     for (int k = 0; k <= a.k_max; ++k) {
         // gather: the work items of iteration k, claimed one at a time
@@ -161,7 +169,7 @@ level_persistent_kernel(const LevelArgs a) {
             }
             __syncthreads();
         }
-        if (!grid_sync(a.sync, a.error, gen)) return;
+        if (!grid_sync(a.sync, a.error, gen, a.barrier_timeout_ns, a.barrier_extra)) return;
         // FP64 steps: job j on lane 0 of global warp j (mod the warp count)
         for (int job = blockIdx.x * kWarps + warp; job < n_jobs; job += n_warps) {
             const int i = find(false, job);
@@ -194,7 +202,7 @@ level_persistent_kernel(const LevelArgs a) {
             }
             __syncwarp();
         }
-        if (!grid_sync(a.sync, a.error, gen)) return;
+        if (!grid_sync(a.sync, a.error, gen, a.barrier_timeout_ns, a.barrier_extra)) return;
     }
 }
 

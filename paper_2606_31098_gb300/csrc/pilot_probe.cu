@@ -1,0 +1,178 @@
+// Roofline probes: measured ceilings for the build pass on the device at hand.
+//
+//   pilot_probe_fma     FP32 FMA throughput: packed fma.rn.f32x2 on four independent
+//                       chains per thread, every SM busy.
+//   pilot_probe_gather  the build pass' access pattern without its arithmetic: 4-tap
+//                       bilinear footprints of C contiguous channels at uniformly random
+//                       pixels of an NHWC map, one 16-byte load per lane, lane groups
+//                       covering a whole tap (so each load instruction touches one line per
+//                       group).  Random pixels give no reuse between samples, so this is the
+//                       L2-to-SM gather rate of the map's layout.
+#include <cuda_runtime.h>
+
+#include "pilot_internal.cuh"
+
+namespace pilot {
+namespace {
+
+__device__ unsigned g_probe_sink;      // keeps the probes' results live
+
+__device__ __forceinline__ unsigned mix32(unsigned x) {
+    // a 32-bit integer hash (xorshift-multiply rounds) for uniform pixel choices
+    x ^= x >> 16;
+    x *= 0x7feb352du;
+    x ^= x >> 15;
+    x *= 0x846ca68bu;
+    x ^= x >> 16;
+    return x;
+}
+
+__global__ void fma_probe_kernel(int iters, float a, float b) {
+    unsigned long long x[4];
+    for (int i = 0; i < 4; ++i) {
+        const float lo = threadIdx.x * 1e-3f + 2 * i, hi = lo + 1.0f;
+        asm("mov.b64 %0, {%1, %2};" : "=l"(x[i]) : "f"(lo), "f"(hi));
+    }
+    unsigned long long A, Bv;
+    asm("mov.b64 %0, {%1, %1};" : "=l"(A) : "f"(a));
+    asm("mov.b64 %0, {%1, %1};" : "=l"(Bv) : "f"(b));
+    for (int it = 0; it < iters; ++it) {
+#pragma unroll
+        for (int i = 0; i < 4; ++i) asm volatile("fma.rn.f32x2 %0, %0, %1, %2;" : "+l"(x[i]) : "l"(A), "l"(Bv));
+    }
+    unsigned acc = 0;
+    for (int i = 0; i < 4; ++i) acc ^= (unsigned)x[i] ^ (unsigned)(x[i] >> 32);
+    if (acc == 0x9e3779b9u) atomicXor(&g_probe_sink, acc);
+}
+
+// LP lanes per sample, each reading 16 bytes of each of the 4 taps (a tap = 16 * LP bytes).
+template <int LP>
+__global__ void gather_probe_kernel(const uint4* map, int H, int W, long long samples, unsigned seed) {
+    const int q = threadIdx.x & (LP - 1);
+    const long long groups = (long long)gridDim.x * blockDim.x / LP;
+    const long long g0 = ((long long)blockIdx.x * blockDim.x + threadIdx.x) / LP;
+    const size_t row = (size_t)W * LP;          // uint4s per map row
+    unsigned acc = 0;
+    for (long long sidx = g0; sidx < samples; sidx += 2 * groups) {
+        // two samples per step for two footprints in flight
+        unsigned v[2][4][4];
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
+            const long long si = sidx + u * groups;
+            const unsigned h = mix32((unsigned)si ^ seed);
+            const int r = (int)((h >> 16) % (unsigned)(H - 1)), c = (int)((h & 0xffffu) % (unsigned)(W - 1));
+            const uint4* t00 = map + (size_t)r * row + (size_t)c * LP + q;
+            const bool live = si < samples;
+            const uint4 z = make_uint4(0, 0, 0, 0);
+            const uint4 a = live ? __ldg(t00) : z, b = live ? __ldg(t00 + LP) : z;
+            const uint4 cc = live ? __ldg(t00 + row) : z, d = live ? __ldg(t00 + row + LP) : z;
+            v[u][0][0] = a.x ^ a.y; v[u][0][1] = a.z ^ a.w;
+            v[u][1][0] = b.x ^ b.y; v[u][1][1] = b.z ^ b.w;
+            v[u][2][0] = cc.x ^ cc.y; v[u][2][1] = cc.z ^ cc.w;
+            v[u][3][0] = d.x ^ d.y; v[u][3][1] = d.z ^ d.w;
+        }
+#pragma unroll
+        for (int u = 0; u < 2; ++u)
+#pragma unroll
+            for (int k = 0; k < 4; ++k) acc ^= v[u][k][0] ^ v[u][k][1];
+    }
+    if (acc == 0x9e3779b9u) atomicXor(&g_probe_sink, acc);
+}
+
+template <int LP>
+cudaError_t launch_gather(const void* map, int H, int W, long long samples, unsigned seed, int grid,
+                          cudaStream_t s) {
+    gather_probe_kernel<LP><<<grid, 256, 0, s>>>(static_cast<const uint4*>(map), H, W, samples, seed);
+    return cudaGetLastError();
+}
+
+// Device time of one launch after a warm-up one.
+template <typename F>
+cudaError_t time_launch(F launch, cudaStream_t s, float* ms) {
+    cudaEvent_t e0, e1;
+    cudaError_t e = cudaEventCreate(&e0);
+    if (e != cudaSuccess) return e;
+    if ((e = cudaEventCreate(&e1)) != cudaSuccess) {
+        cudaEventDestroy(e0);
+        return e;
+    }
+    e = launch();
+    if (e == cudaSuccess) e = cudaEventRecord(e0, s);
+    if (e == cudaSuccess) e = launch();
+    if (e == cudaSuccess) e = cudaEventRecord(e1, s);
+    if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+    if (e == cudaSuccess) e = cudaEventElapsedTime(ms, e0, e1);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    return e;
+}
+
+pilot_status probe_fail(pilot_status st, const char* m) {
+    record_error(m);
+    return st;
+}
+
+int sm_count() {
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return 0;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
+    return sms;
+}
+
+}  // namespace
+}  // namespace pilot
+
+using namespace pilot;
+
+extern "C" {
+
+pilot_status pilot_probe_fma(double* tflops, void* stream) {
+    if (!tflops) return probe_fail(PILOT_EINVAL, "tflops is NULL");
+    const int sms = sm_count();
+    if (sms <= 0) return probe_fail(PILOT_ECUDA, "no CUDA device");
+    const int grid = sms * 8, threads = 256, iters = 1 << 14;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    float ms = 0.f;
+    const cudaError_t e = time_launch(
+        [&]() {
+            fma_probe_kernel<<<grid, threads, 0, s>>>(iters, 0.999f, 0.001f);
+            return cudaGetLastError();
+        },
+        s, &ms);
+    if (e != cudaSuccess) return probe_fail(PILOT_ECUDA, cudaGetErrorString(e));
+    // 4 packed FMAs = 8 FMAs = 16 flops per thread and iteration
+    *tflops = 16.0 * iters * (double)grid * threads / (ms * 1e-3) / 1e12;
+    return PILOT_OK;
+}
+
+pilot_status pilot_probe_gather(const void* map, int H, int W, int C, pilot_dtype dtype, long long samples,
+                                double* gbps, void* stream) {
+    if (!map || !gbps) return probe_fail(PILOT_EINVAL, "map or gbps is NULL");
+    if (H < 2 || W < 2 || H > 65535 || W > 65535) return probe_fail(PILOT_EINVAL, "map must be 2..65535 on each side");
+    if (samples < 1) return probe_fail(PILOT_EINVAL, "samples must be positive");
+    if (reinterpret_cast<uintptr_t>(map) % 16) return probe_fail(PILOT_EINVAL, "map must be 16-byte aligned");
+    const int elem = dtype == PILOT_F32 ? 4 : (dtype == PILOT_FP8E4M3 ? 1 : 2);
+    const int tap = C * elem;
+    if (tap % 16 || tap / 16 < 1 || tap / 16 > 8 || (tap / 16 & (tap / 16 - 1)))
+        return probe_fail(PILOT_EINVAL, "a tap (C x element size) must be 16, 32, 64 or 128 bytes");
+    const int sms = sm_count();
+    if (sms <= 0) return probe_fail(PILOT_ECUDA, "no CUDA device");
+    const int grid = sms * 8;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    float ms = 0.f;
+    cudaError_t e = cudaSuccess;
+    auto go = [&]() {
+        switch (tap / 16) {
+            case 1: return launch_gather<1>(map, H, W, samples, 0x1234567u, grid, s);
+            case 2: return launch_gather<2>(map, H, W, samples, 0x1234567u, grid, s);
+            case 4: return launch_gather<4>(map, H, W, samples, 0x1234567u, grid, s);
+            default: return launch_gather<8>(map, H, W, samples, 0x1234567u, grid, s);
+        }
+    };
+    e = time_launch(go, s, &ms);
+    if (e != cudaSuccess) return probe_fail(PILOT_ECUDA, cudaGetErrorString(e));
+    *gbps = (double)samples * 4.0 * tap / (ms * 1e-3) / 1e9;
+    return PILOT_OK;
+}
+
+}  // extern "C"

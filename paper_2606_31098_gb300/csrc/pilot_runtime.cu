@@ -600,6 +600,8 @@ pilot_status capture_batch_graph(pilot_align_handle* h, pilot_dtype dt, int C, b
         a.partial = h->partial;
         a.sync = h->bsync + (size_t)level * kSyncWords;
         a.error = error;
+        a.barrier_timeout_ns = kBarrierTimeoutNs;
+        a.barrier_extra = 0;
         a.level = level;
         a.list_index = level;
         for (int l = 0; l < PILOT_MAX_LEVELS; ++l) a.iters[l] = c.iters_per_level[l];
@@ -853,6 +855,67 @@ pilot_status pilot_align_debug_normal_eq(pilot_align_handle* h, const pilot_fram
     PILOT_CUDA(cudaMemcpyAsync(out29, h->eval_out, sizeof(double) * kNumSums * M, cudaMemcpyDeviceToHost, s),
                "normal-equation copy");
     PILOT_CUDA(cudaStreamSynchronize(s), "debug_normal_eq");
+    return PILOT_OK;
+}
+
+pilot_status pilot_align_selftest_barrier_timeout(pilot_align_handle* h, double timeout_ms, double* elapsed_ms,
+                                                  void* stream) {
+    if (!h) return fail(PILOT_EINVAL, "handle is NULL");
+    if (!(timeout_ms >= 1.0 && timeout_ms <= 10000.0)) return fail(PILOT_EINVAL, "timeout_ms must be in [1, 10000]");
+    DeviceGuard guard(h->device);
+    pilot_status st;
+    if ((st = batch_alloc(h)) != PILOT_OK) return st;
+    const pilot_align_config& c = h->cfg;
+    const BatchLayout lay = BatchLayout::make(c.max_frames, c.max_hyps);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    int dev = 0, sms = 0, per_sm = 0;
+    PILOT_CUDA(cudaGetDevice(&dev), "cudaGetDevice");
+    PILOT_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev), "SM count");
+    PILOT_CUDA(level_occupancy(PILOT_F32, 32, false, &per_sm), "occupancy query");
+    unsigned* error = reinterpret_cast<unsigned*>(h->bres_dev + ResultLayout::make(c.max_hyps).bytes +
+                                                  sizeof(int) * (size_t)c.max_frames);
+    // an empty frame list: the kernel's level-start pass has no jobs, and its first barrier
+    // waits for one CTA more than the grid holds
+    PILOT_CUDA(cudaMemsetAsync(h->bdesc_dev, 0, h->bdesc_bytes, s), "descriptor reset");
+    PILOT_CUDA(cudaMemsetAsync(h->bsync, 0, sizeof(unsigned long long) * kSyncWords, s), "counter reset");
+    PILOT_CUDA(cudaMemsetAsync(error, 0, sizeof(unsigned), s), "error reset");
+    LevelArgs a{};
+    a.header = reinterpret_cast<const BatchHeader*>(h->bdesc_dev + lay.off_hdr);
+    a.frames = reinterpret_cast<const FrameDesc*>(h->bdesc_dev + lay.off_frames);
+    a.fr_list = reinterpret_cast<const int*>(h->bdesc_dev + lay.off_fr_list);
+    a.fr_item = reinterpret_cast<const int*>(h->bdesc_dev + lay.off_fr_item);
+    a.fr_job = reinterpret_cast<const int*>(h->bdesc_dev + lay.off_fr_job);
+    a.active = h->bactive;
+    a.state = h->state;
+    a.min_valid = h->bmin_valid;
+    a.pose32 = h->pose32;
+    a.job_meta = h->bjob_meta;
+    a.partial = h->partial;
+    a.sync = h->bsync;
+    a.error = error;
+    a.barrier_timeout_ns = (unsigned long long)(timeout_ms * 1e6);
+    a.barrier_extra = 1;
+    a.level = 0;
+    a.list_index = 0;
+    a.k_max = 0;
+    a.tile = kTile;
+    a.tiles_per_item = tiles_per_item(kTile);
+    cudaEvent_t e0, e1;
+    PILOT_CUDA(cudaEventCreate(&e0), "event create");
+    PILOT_CUDA(cudaEventCreate(&e1), "event create");
+    cudaError_t e = cudaEventRecord(e0, s);
+    if (e == cudaSuccess) e = launch_level(PILOT_F32, 32, false, a, sms * (per_sm > 0 ? per_sm : 1), s);
+    if (e == cudaSuccess) e = cudaEventRecord(e1, s);
+    unsigned flag = 0;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&flag, error, sizeof flag, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    float ms = 0.f;
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (e != cudaSuccess) return cuda_fail(e, "barrier self-test");
+    if (elapsed_ms) *elapsed_ms = ms;
+    if (flag != 1u) return fail(PILOT_ECUDA, "barrier self-test: the impossible barrier did not report its timeout");
     return PILOT_OK;
 }
 

@@ -272,6 +272,8 @@ cudaError_t capture_round(pilot_server* s) {
         a.partial = s->partial;
         a.sync = s->sync;
         a.error = error;
+        a.barrier_timeout_ns = kBarrierTimeoutNs;
+        a.barrier_extra = 0;
         a.level = -1;
         a.list_index = 0;
         a.k_max = 0;

@@ -72,4 +72,6 @@ def dequantize(t, scale, dtype) -> np.ndarray:
         v = bits.view(np.float16).astype(np.float32)
     else:
         v = decode_e4m3(bits)
+    if scale is None:                 # stored without scales: the values are used as stored
+        return v.astype(np.float32)
     return (v * scale.cpu().numpy().astype(np.float32)).astype(np.float32)

@@ -113,6 +113,22 @@ def test_batch_validation(torch):
     assert solver.solve_batch([]) == []
 
 
+def test_barrier_timeout_is_reported_and_the_handle_stays_usable(torch):
+    """Failure detection without a fault: the level kernel's grid barrier waits are bounded
+    in time.  The self-test launches that kernel with a barrier that cannot complete; every
+    CTA must give up after the timeout, report it, and leave the context and the handle
+    usable (a batched solve afterwards still equals the plain solves)."""
+    solver = B.Solver(B.Options())
+    ms = solver.selftest_barrier_timeout(100.0)
+    assert 90.0 <= ms < 5000.0
+    fas = args_for(uneven_frames(sides=(30, 44), hyps=(3, 2), base=1650))
+    batch = solver.solve_batch(fas)
+    for i, fa in enumerate(fas):
+        assert_same(batch[i], solver.solve(fa), what=f"frame {i}")
+    with pytest.raises(B.PilotError, match="timeout_ms"):
+        solver.selftest_barrier_timeout(0.5)
+
+
 def test_autotuner_picks_a_schedule_that_keeps_the_results(torch):
     """pilot_align_autotune times the candidate schedules on the caller's frames and keeps
     the fastest for that frame shape; solves with the tuned schedule select the same pose

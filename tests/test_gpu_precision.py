@@ -59,10 +59,11 @@ def test_quantiser_matches_the_format_definitions(torch, dt, ref_dt, per_channel
 
 def quantised_frame(torch, frame, dt, T=None):
     arrs = B.quantized_device_arrays(frame, dt, T_hyps=T)
+    L = len(arrs["qry_feat"])
     deq = dict(qry_feat=[dequantize(q, s, {B.BF16: BF16, B.F16: F16, B.FP8E4M3: FP8}[dt]).reshape(q.shape)
-                         for q, s in zip(arrs["qry_feat"], arrs["qry_scale"])],
+                         for q, s in zip(arrs["qry_feat"], arrs.get("qry_scale") or [None] * L)],
                ref_feat=[dequantize(r, s, {B.BF16: BF16, B.F16: F16, B.FP8E4M3: FP8}[dt]).reshape(r.shape)
-                         for r, s in zip(arrs["ref_feat"], arrs["ref_scale"])])
+                         for r, s in zip(arrs["ref_feat"], arrs.get("ref_scale") or [None] * L)])
     return B.FrameArgs(frame, arrs, is_device=True, dtype=dt), frame.replace(**deq)
 
 
