@@ -484,7 +484,7 @@ def run_ours(args):
 
     # the same plain form on reduced-precision storage (GPU-quantised maps, FP32 math)
     precision = {}
-    for dt in (B.BF16, B.FP8E4M3):
+    for dt in (B.BF16, B.F16, B.FP8E4M3):
         qa = B.FrameArgs(frame, B.quantized_device_arrays(frame, dt), is_device=True, dtype=dt)
         solver.set_schedule([qa], batched=False, tile=plain_schedule["tile"], streams=plain_schedule["streams"])
         for _ in range(2):

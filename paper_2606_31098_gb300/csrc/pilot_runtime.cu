@@ -183,6 +183,9 @@ struct pilot_align_handle {
     cudaStream_t bstream = nullptr;
     // plain form, multi-stream schedule: extra streams, a fork event and their join events
     cudaStream_t pstream[kMaxStreams - 1] = {};
+    // host frames: stream for the finer levels' copies and one event per level
+    cudaStream_t cstream = nullptr;
+    cudaEvent_t level_ready[PILOT_MAX_LEVELS] = {};
     cudaEvent_t pfork = nullptr;
     cudaEvent_t pjoin[kMaxStreams - 1] = {};
     cudaGraph_t graph = nullptr;
@@ -232,8 +235,12 @@ pilot_status stage_copy(pilot_align_handle* h, int slot, const void* src, size_t
     return PILOT_OK;
 }
 
+// Device view of frame f.  A host frame is staged into the handle's buffers with
+// asynchronous copies on s; when `fine` is given, the maps and references of every level but
+// the coarsest go on that second stream instead, finest last, and level_ready[l] is recorded
+// there after level l, so that the coarse levels' solve overlaps the finer levels' copies.
 pilot_status bind_frame(pilot_align_handle* h, const pilot_frame* f, cudaStream_t s, DevFrame* d,
-                        bool copy_T) {
+                        bool copy_T, cudaStream_t fine = nullptr, cudaEvent_t* level_ready = nullptr) {
     const size_t es = dtype_size(f->feat_dtype);
     const size_t N = (size_t)f->N, C = (size_t)f->C;
     if (f->is_device) {
@@ -264,11 +271,18 @@ pilot_status bind_frame(pilot_align_handle* h, const pilot_frame* f, cudaStream_
     if (f->use_range) {
         STAGE(kStDsm, f->dsm, sizeof(float) * (size_t)f->dsm_H * f->dsm_W, d->dsm, const float*);
     }
-    for (int l = 0; l < f->L; ++l) {
-        STAGE(kStRef0 + l, f->ref_feat[l], es * N * C, d->ref[l], const void*);
-        STAGE(kStQry0 + l, f->qry_feat[l], es * (size_t)f->H[l] * f->W[l] * C, d->qry[l], const void*);
-        STAGE(kStRs0 + l, f->ref_scale[l], sizeof(float) * C, d->rs[l], const float*);
-        STAGE(kStQs0 + l, f->qry_scale[l], sizeof(float) * C, d->qs[l], const float*);
+    for (int l = f->L - 1; l >= 0; --l) {
+        const cudaStream_t sl = (fine && l < f->L - 1) ? fine : s;
+        if ((st = stage_copy(h, kStRef0 + l, f->ref_feat[l], es * N * C, sl, &p)) != PILOT_OK) return st;
+        d->ref[l] = p;
+        if ((st = stage_copy(h, kStQry0 + l, f->qry_feat[l], es * (size_t)f->H[l] * f->W[l] * C, sl, &p)) != PILOT_OK)
+            return st;
+        d->qry[l] = p;
+        if ((st = stage_copy(h, kStRs0 + l, f->ref_scale[l], sizeof(float) * C, sl, &p)) != PILOT_OK) return st;
+        d->rs[l] = static_cast<const float*>(p);
+        if ((st = stage_copy(h, kStQs0 + l, f->qry_scale[l], sizeof(float) * C, sl, &p)) != PILOT_OK) return st;
+        d->qs[l] = static_cast<const float*>(p);
+        if (sl == fine) PILOT_CUDA(cudaEventRecord(level_ready[l], fine), "level copy event");
     }
 #undef STAGE
     return PILOT_OK;
@@ -450,6 +464,9 @@ void release(pilot_align_handle* h) {
         if (h->pjoin[i]) cudaEventDestroy(h->pjoin[i]);
     }
     if (h->pfork) cudaEventDestroy(h->pfork);
+    if (h->cstream) cudaStreamDestroy(h->cstream);
+    for (int i = 0; i < PILOT_MAX_LEVELS; ++i)
+        if (h->level_ready[i]) cudaEventDestroy(h->level_ready[i]);
     delete h;
 }
 
@@ -721,7 +738,13 @@ pilot_status pilot_align_solve(pilot_align_handle* h, const pilot_frame* f, pilo
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     const pilot_align_config& c = h->cfg;
     DevFrame d;
-    if ((st = bind_frame(h, f, s, &d, true)) != PILOT_OK) return st;
+    const bool overlap = !f->is_device && f->L > 1;     // finer levels copied while coarse ones solve
+    if (overlap && !h->cstream) {
+        PILOT_CUDA(cudaStreamCreateWithFlags(&h->cstream, cudaStreamNonBlocking), "copy stream");
+        for (int i = 0; i < PILOT_MAX_LEVELS; ++i)
+            PILOT_CUDA(cudaEventCreateWithFlags(&h->level_ready[i], cudaEventDisableTiming), "level event");
+    }
+    if ((st = bind_frame(h, f, s, &d, true, overlap ? h->cstream : nullptr, h->level_ready)) != PILOT_OK) return st;
     const int M = f->M;
 
     PILOT_CUDA(cudaMemsetAsync(h->tickets, 0, sizeof(unsigned) * M, s), "ticket reset");
@@ -754,6 +777,7 @@ pilot_status pilot_align_solve(pilot_align_handle* h, const pilot_frame* f, pilo
         ep.lambda0 = c.lambda0;
         ep.damping_mode = c.damping_mode;
         ep.prior = prior;
+        if (overlap && level < f->L - 1) PILOT_CUDA(cudaStreamWaitEvent(s, h->level_ready[level], 0), "level copy wait");
         PILOT_CUDA(launch_level_init(h->state, h->pose32, h->active[cur], n_active, c.lambda0, s), "level_init launch");
         ++h->total_launches;
         // parts of the active list, part p = slots [off[p], off[p + 1]) on stream p (s for

@@ -170,3 +170,17 @@ def test_plain_form_concurrent_parts_give_equal_results(torch):
         solver.close()
     for streams in (2, 3, 4):
         assert_same(out[1], out[streams], what=f"{streams} parts")
+
+
+def test_roofline_probes(torch):
+    """The measured ceilings bench.py compares the build pass with: positive and within the
+    device's nominal rates (FP32 FMA below 2 x 128 lanes x SMs x 2.2 GHz; the gather below
+    40 TB/s), and malformed maps are rejected."""
+    fma = B.probe_fma()
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    assert 0 < fma < 2 * 128 * sms * 2.2e9 / 1e12
+    m = torch.zeros((64, 80, 32), dtype=torch.float32, device="cuda")
+    gb = B.probe_gather(m, B.F32, 1 << 16)
+    assert 0 < gb < 40000
+    with pytest.raises(B.PilotError, match="tap"):
+        B.probe_gather(torch.zeros((64, 80, 3), dtype=torch.float32, device="cuda"), B.F32, 1 << 10)
