@@ -84,13 +84,18 @@ __global__ void level_init_kernel(HypState* st, float* pose32, const int* active
 }
 
 // Ranking key of a hypothesis: (unusable, cost, index), unusable = non-finite objective or
-// too few visible anchors; unusable ones compare by index only.
-__device__ __forceinline__ void rank_key(const HypState& h, double min_valid, int* bad, double* c) {
+// too few visible anchors; unusable ones compare by index only.  The cost is compared as an
+// order-preserving 64-bit integer image of the double (both zeros map to one value), which
+// orders exactly as the doubles do but keeps the n^2 comparisons off the FP64 pipe.
+__device__ __forceinline__ void rank_key(const HypState& h, double min_valid, int* bad,
+                                         unsigned long long* c) {
     *bad = !(isfinite(h.cost) && h.n_valid >= min_valid);
-    *c = isfinite(h.cost) ? h.cost : 0.0;
+    const unsigned long long u = (unsigned long long)__double_as_longlong((isfinite(h.cost) ? h.cost : 0.0) + 0.0);
+    *c = (u >> 63) ? ~u : (u | 0x8000000000000000ull);
 }
 
-__device__ __forceinline__ bool key_before(int bad_a, double ca, int ia, int bad_b, double cb, int ib) {
+__device__ __forceinline__ bool key_before(int bad_a, unsigned long long ca, int ia, int bad_b,
+                                           unsigned long long cb, int ib) {
     if (bad_a != bad_b) return !bad_a;
     if (ca != cb) return ca < cb;
     return ia < ib;
@@ -102,19 +107,27 @@ __device__ __forceinline__ bool key_before(int bad_a, double ca, int ia, int bad
 // (blockDim.x a multiple of 32, at most 1024); the keys are streamed through shared memory
 // in blocks of blockDim.x, and the survivors are placed by a block-wide prefix count.
 __device__ void topk_select(HypState* S, const int* act, int* act_out, int n, int K, double min_valid) {
-    __shared__ double kc[1024];
+    __shared__ unsigned long long kc[1024];
     __shared__ int kb[1024];
     __shared__ int ki[1024];
     __shared__ int wsum[32];
     __shared__ int s_base;
     const int bd = blockDim.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    for (int r0 = 0; r0 < n; r0 += bd) {
-        const int s = r0 + tid;
-        int m = -1, bad = 1, rank = 0;
-        double c = 0.0;
-        if (s < n) {
-            m = act[s];
-            rank_key(S[m], min_valid, &bad, &c);
+    constexpr int R = 4;                       // hypotheses ranked per thread and pass
+    for (int r0 = 0; r0 < n; r0 += R * bd) {
+        int m[R], bad[R], rank[R];
+        unsigned long long c[R];
+#pragma unroll
+        for (int u = 0; u < R; ++u) {
+            const int s = r0 + u * bd + tid;
+            m[u] = -1;
+            bad[u] = 1;
+            c[u] = 0;
+            rank[u] = 0;
+            if (s < n) {
+                m[u] = act[s];
+                rank_key(S[m[u]], min_valid, &bad[u], &c[u]);
+            }
         }
         for (int c0 = 0; c0 < n; c0 += bd) {
             __syncthreads();
@@ -124,15 +137,20 @@ __device__ void topk_select(HypState* S, const int* act, int* act_out, int n, in
                 ki[tid] = m2;
             }
             __syncthreads();
-            if (s < n) {
-                const int lim = min(bd, n - c0);
-                for (int j = 0; j < lim; ++j) rank += key_before(kb[j], kc[j], ki[j], bad, c, m) ? 1 : 0;
+            const int lim = min(bd, n - c0);
+            for (int j = 0; j < lim; ++j) {
+                const int bj = kb[j], ij = ki[j];
+                const unsigned long long cj = kc[j];
+#pragma unroll
+                for (int u = 0; u < R; ++u) rank[u] += key_before(bj, cj, ij, bad[u], c[u], m[u]) ? 1 : 0;
             }
         }
-        if (s < n && rank >= K) {
-            S[m].active = 0;
-            S[m].status = PILOT_HYP_PRUNED;
-        }
+#pragma unroll
+        for (int u = 0; u < R; ++u)
+            if (m[u] >= 0 && rank[u] >= K) {
+                S[m[u]].active = 0;
+                S[m[u]].status = PILOT_HYP_PRUNED;
+            }
     }
     if (tid == 0) s_base = 0;
     __syncthreads();
@@ -193,7 +211,8 @@ __global__ void count_valid_kernel(const uint8_t* valid, int N, double frac, dou
     }
 }
 
-// One block of 256 threads: final statuses, result block, argmin (ties -> lowest index).
+// One block (blockDim.x a power of two, at most 1024): final statuses, result block, argmin
+// (ties -> lowest index).
 __global__ void finalize_kernel(HypState* st, int M, const double* min_valid_ptr,
                                 unsigned char* res, ResultLayout lay) {
     const double min_valid = *min_valid_ptr;
@@ -202,8 +221,8 @@ __global__ void finalize_kernel(HypState* st, int M, const double* min_valid_ptr
     int* nv = reinterpret_cast<int*>(res + lay.off_nvalid);
     int* status = reinterpret_cast<int*>(res + lay.off_status);
     int* best = reinterpret_cast<int*>(res + lay.off_best);
-    __shared__ double bc[256];
-    __shared__ int bi[256];
+    __shared__ double bc[1024];
+    __shared__ int bi[1024];
     double my_c = 0.0;
     int my_i = -1;
     for (int m = threadIdx.x; m < M; m += blockDim.x) {
@@ -472,7 +491,7 @@ cudaError_t launch_count_valid(const uint8_t* valid, int N, double frac, double*
 
 cudaError_t launch_finalize(HypState* st, int M, const double* min_valid, unsigned char* result,
                             ResultLayout lay, cudaStream_t s) {
-    finalize_kernel<<<1, 256, 0, s>>>(st, M, min_valid, result, lay);
+    finalize_kernel<<<1, 1024, 0, s>>>(st, M, min_valid, result, lay);
     return cudaGetLastError();
 }
 
