@@ -102,56 +102,50 @@ __device__ __forceinline__ bool key_before(int bad_a, unsigned long long ca, int
 }
 
 // Top-K (Supp. "Multi-Hypothesis Refinement") over the n hypotheses listed in act[0, n) of
-// S: every hypothesis of rank >= K is marked pruned, and the survivors' indices are
-// written, in their order in act, to act_out[0, K) (act_out may be act).  One block
-// (blockDim.x a multiple of 32, at most 1024); the keys are streamed through shared memory
-// in blocks of blockDim.x, and the survivors are placed by a block-wide prefix count.
-__device__ void topk_select(HypState* S, const int* act, int* act_out, int n, int K, double min_valid) {
-    __shared__ unsigned long long kc[1024];
-    __shared__ int kb[1024];
-    __shared__ int ki[1024];
+// S, in two passes.  rank_mark: each thread of a block takes one listed hypothesis from
+// [s_begin, s_begin + blockDim.x), counts the listed hypotheses that rank before it (keys
+// streamed through shared memory blockDim.x at a time) and marks it pruned if that count is
+// K or more; many blocks share the n^2 comparisons.  compact_active (one block, blockDim.x a
+// multiple of 32, at most 1024, after every rank_mark block has finished): writes the
+// survivors' indices, in their order in act, to act_out[0, K) (act_out may be act) by a
+// block-wide prefix count.
+constexpr int kRankThreads = 256;
+
+__device__ void rank_mark(HypState* S, const int* act, int n, int K, double min_valid, int s_begin) {
+    __shared__ unsigned long long kc[kRankThreads];
+    __shared__ int kb[kRankThreads];
+    __shared__ int ki[kRankThreads];
+    const int tid = threadIdx.x;
+    const int s = s_begin + tid;
+    int m = -1, bad = 1, rank = 0;
+    unsigned long long c = 0;
+    if (s < n) {
+        m = act[s];
+        rank_key(S[m], min_valid, &bad, &c);
+    }
+    for (int c0 = 0; c0 < n; c0 += kRankThreads) {
+        __syncthreads();
+        if (c0 + tid < n) {
+            const int m2 = act[c0 + tid];
+            rank_key(S[m2], min_valid, &kb[tid], &kc[tid]);
+            ki[tid] = m2;
+        }
+        __syncthreads();
+        if (s < n) {
+            const int lim = min(kRankThreads, n - c0);
+            for (int j = 0; j < lim; ++j) rank += key_before(kb[j], kc[j], ki[j], bad, c, m) ? 1 : 0;
+        }
+    }
+    if (s < n && rank >= K) {
+        S[m].active = 0;
+        S[m].status = PILOT_HYP_PRUNED;
+    }
+}
+
+__device__ void compact_active(const HypState* S, const int* act, int* act_out, int n) {
     __shared__ int wsum[32];
     __shared__ int s_base;
     const int bd = blockDim.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    constexpr int R = 4;                       // hypotheses ranked per thread and pass
-    for (int r0 = 0; r0 < n; r0 += R * bd) {
-        int m[R], bad[R], rank[R];
-        unsigned long long c[R];
-#pragma unroll
-        for (int u = 0; u < R; ++u) {
-            const int s = r0 + u * bd + tid;
-            m[u] = -1;
-            bad[u] = 1;
-            c[u] = 0;
-            rank[u] = 0;
-            if (s < n) {
-                m[u] = act[s];
-                rank_key(S[m[u]], min_valid, &bad[u], &c[u]);
-            }
-        }
-        for (int c0 = 0; c0 < n; c0 += bd) {
-            __syncthreads();
-            if (c0 + tid < n) {
-                const int m2 = act[c0 + tid];
-                rank_key(S[m2], min_valid, &kb[tid], &kc[tid]);
-                ki[tid] = m2;
-            }
-            __syncthreads();
-            const int lim = min(bd, n - c0);
-            for (int j = 0; j < lim; ++j) {
-                const int bj = kb[j], ij = ki[j];
-                const unsigned long long cj = kc[j];
-#pragma unroll
-                for (int u = 0; u < R; ++u) rank[u] += key_before(bj, cj, ij, bad[u], c[u], m[u]) ? 1 : 0;
-            }
-        }
-#pragma unroll
-        for (int u = 0; u < R; ++u)
-            if (m[u] >= 0 && rank[u] >= K) {
-                S[m[u]].active = 0;
-                S[m[u]].status = PILOT_HYP_PRUNED;
-            }
-    }
     if (tid == 0) s_base = 0;
     __syncthreads();
     for (int c0 = 0; c0 < n; c0 += bd) {
@@ -178,11 +172,14 @@ __device__ void topk_select(HypState* S, const int* act, int* act_out, int n, in
     }
 }
 
-// One block.  Ranks the active hypotheses, marks all but the K first as pruned, and
-// writes the surviving indices, in their order in active_in, to active_out.
-__global__ void prune_kernel(HypState* st, const int* active_in, int* active_out, int n, int K,
-                             const double* min_valid_ptr) {
-    topk_select(st, active_in, active_out, n, K, *min_valid_ptr);
+// Plain form: blockIdx.x ranks listed hypotheses [256 blockIdx.x, + 256).
+__global__ void prune_rank_kernel(HypState* st, const int* active_in, int n, int K, const double* min_valid_ptr) {
+    rank_mark(st, active_in, n, K, *min_valid_ptr, blockIdx.x * kRankThreads);
+}
+
+// Plain form: the survivors, in their order in active_in, to active_out.
+__global__ void prune_compact_kernel(const HypState* st, const int* active_in, int* active_out, int n) {
+    compact_active(st, active_in, active_out, n);
 }
 
 // One block of 1024 threads: number of valid anchors (4 flags per load when aligned).
@@ -300,13 +297,6 @@ __device__ void count_frame(const FrameDesc& f, double frac, double* min_valid) 
     __syncthreads();
 }
 
-// Top-K of one frame among its n active hypotheses (same ranking as prune_kernel); the
-// frame's active list is compacted in place.
-__device__ void prune_frame(const FrameDesc& f, HypState* st, int* active, int n, int K, double mv) {
-    if (K <= 0 || K >= n) return;
-    topk_select(st + f.hyp_offset, active + f.hyp_offset, active + f.hyp_offset, n, K, mv);
-}
-
 // Statuses, per-hypothesis outputs (at the global hypothesis index) and the argmin of
 // one frame.  blockDim.x <= 1024, a power of two.
 __device__ void finalize_frame(const FrameDesc& f, int fi, HypState* st, double mv,
@@ -374,11 +364,27 @@ __global__ void batch_count_valid_kernel(const BatchHeader* hdr, const FrameDesc
     count_frame(frames[blockIdx.x], frac, min_valid + blockIdx.x);
 }
 
-__global__ void batch_prune_kernel(const BatchHeader* hdr, const FrameDesc* frames, HypState* st,
-                                   int* active, const int* n_active, int K, const double* min_valid) {
+// Batched form, top-K after a level: blockIdx.x is the frame, blockIdx.y a block of 256 of
+// its listed hypotheses (frames whose count is at most K keep all of them).
+__global__ void batch_rank_kernel(const BatchHeader* hdr, const FrameDesc* frames, HypState* st,
+                                  const int* active, const int* n_active, int K, const double* min_valid) {
     const int fi = blockIdx.x;
     if (fi >= hdr->n_frames) return;
-    prune_frame(frames[fi], st, active, n_active[fi], K, min_valid[fi]);
+    const int n = n_active[fi];
+    if (K <= 0 || K >= n || (int)blockIdx.y * kRankThreads >= n) return;
+    const FrameDesc& f = frames[fi];
+    rank_mark(st + f.hyp_offset, active + f.hyp_offset, n, K, min_valid[fi], blockIdx.y * kRankThreads);
+}
+
+// Batched form: each pruned frame's active list compacted in place.
+__global__ void batch_compact_kernel(const BatchHeader* hdr, const FrameDesc* frames, const HypState* st,
+                                     int* active, const int* n_active, int K) {
+    const int fi = blockIdx.x;
+    if (fi >= hdr->n_frames) return;
+    const int n = n_active[fi];
+    if (K <= 0 || K >= n) return;
+    const FrameDesc& f = frames[fi];
+    compact_active(st + f.hyp_offset, active + f.hyp_offset, active + f.hyp_offset, n);
 }
 
 __global__ void batch_finalize_kernel(const BatchHeader* hdr, const FrameDesc* frames, HypState* st,
@@ -398,13 +404,24 @@ __global__ void round_prepare_kernel(const BatchHeader* hdr, const FrameDesc* fr
     count_frame(f, frac, min_valid + fi);
 }
 
+// Serving round, top-K of the frames that finished a pruning level (as batch_rank_kernel).
+__global__ void round_rank_kernel(const BatchHeader* hdr, const FrameDesc* frames, HypState* st,
+                                  const int* active, const double* min_valid) {
+    const int fi = blockIdx.x;
+    if (fi >= hdr->n_frames) return;
+    const FrameDesc& f = frames[fi];
+    if (!(f.flags & kFlagPrune) || (int)blockIdx.y * kRankThreads >= f.n_active) return;
+    rank_mark(st + f.hyp_offset, active + f.hyp_offset, f.n_active, f.keep, min_valid[fi], blockIdx.y * kRankThreads);
+}
+
 __global__ void round_finish_kernel(const BatchHeader* hdr, const FrameDesc* frames, HypState* st,
                                     int* active, const double* min_valid, unsigned char* res,
                                     int max_hyps) {
     const int fi = blockIdx.x;
     if (fi >= hdr->n_frames) return;
     const FrameDesc& f = frames[fi];
-    if (f.flags & kFlagPrune) prune_frame(f, st, active, f.n_active, f.keep, min_valid[fi]);
+    if (f.flags & kFlagPrune)
+        compact_active(st + f.hyp_offset, active + f.hyp_offset, active + f.hyp_offset, f.n_active);
     if (f.flags & kFlagFinalize) finalize_frame(f, fi, st, min_valid[fi], res, max_hyps);
 }
 
@@ -424,8 +441,12 @@ cudaError_t launch_batch_count_valid(const BatchHeader* hdr, const FrameDesc* fr
 
 cudaError_t launch_batch_prune(const BatchHeader* hdr, const FrameDesc* frames, HypState* st,
                                int* active, const int* n_active, int keep, const double* min_valid,
-                               int max_frames, cudaStream_t s) {
-    batch_prune_kernel<<<max_frames, 1024, 0, s>>>(hdr, frames, st, active, n_active, keep, min_valid);
+                               int max_frames, int max_frame_hyps, cudaStream_t s) {
+    const dim3 grid(max_frames, (max_frame_hyps + kRankThreads - 1) / kRankThreads);
+    batch_rank_kernel<<<grid, kRankThreads, 0, s>>>(hdr, frames, st, active, n_active, keep, min_valid);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    batch_compact_kernel<<<max_frames, 1024, 0, s>>>(hdr, frames, st, active, n_active, keep);
     return cudaGetLastError();
 }
 
@@ -445,7 +466,11 @@ cudaError_t launch_round_prepare(const BatchHeader* hdr, const FrameDesc* frames
 
 cudaError_t launch_round_finish(const BatchHeader* hdr, const FrameDesc* frames, HypState* st,
                                 int* active, const double* min_valid, unsigned char* result,
-                                int max_hyps, int max_frames, cudaStream_t s) {
+                                int max_hyps, int max_frames, int max_frame_hyps, cudaStream_t s) {
+    const dim3 grid(max_frames, (max_frame_hyps + kRankThreads - 1) / kRankThreads);
+    round_rank_kernel<<<grid, kRankThreads, 0, s>>>(hdr, frames, st, active, min_valid);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
     round_finish_kernel<<<max_frames, 1024, 0, s>>>(hdr, frames, st, active, min_valid, result, max_hyps);
     return cudaGetLastError();
 }
@@ -479,7 +504,12 @@ cudaError_t launch_level_init(HypState* st, float* pose32, const int* active_idx
 
 cudaError_t launch_prune(HypState* st, const int* active_in, int* active_out, int n_active,
                          int keep, const double* min_valid, cudaStream_t s) {
-    prune_kernel<<<1, 1024, 0, s>>>(st, active_in, active_out, n_active, keep, min_valid);
+    if (n_active <= 0) return cudaSuccess;
+    prune_rank_kernel<<<(n_active + kRankThreads - 1) / kRankThreads, kRankThreads, 0, s>>>(st, active_in, n_active,
+                                                                                            keep, min_valid);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    prune_compact_kernel<<<1, 1024, 0, s>>>(st, active_in, active_out, n_active);
     return cudaGetLastError();
 }
 

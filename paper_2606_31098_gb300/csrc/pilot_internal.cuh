@@ -21,6 +21,7 @@ constexpr int kNumSums = 29;       // 21 H + 6 g + cost + n_valid
 constexpr unsigned long long kBarrierTimeoutNs = 2000000000ull;   // level kernel: longest barrier wait
 constexpr int kSyncWords = 4;      // per persistent level launch: claims, arrivals, generations, pad
 constexpr int kItemAnchors = 4096; // persistent level kernel: anchors per work item (whole tiles)
+constexpr int kMaxFrameHyps = 8192; // batched and served forms: hypotheses of one frame at most
 constexpr int kSmemFrames = 512;   // persistent level kernel: frame tables staged in shared memory up to this
 
 // Tiles per work item of the persistent level kernel for a reduction tile of `tile` anchors.
@@ -224,7 +225,7 @@ cudaError_t launch_batch_count_valid(const BatchHeader* hdr, const FrameDesc* fr
                                      double* min_valid, int max_frames, cudaStream_t s);
 cudaError_t launch_batch_prune(const BatchHeader* hdr, const FrameDesc* frames, HypState* st,
                                int* active, const int* n_active, int keep, const double* min_valid,
-                               int max_frames, cudaStream_t s);
+                               int max_frames, int max_frame_hyps, cudaStream_t s);
 cudaError_t launch_batch_finalize(const BatchHeader* hdr, const FrameDesc* frames, HypState* st,
                                   const double* min_valid, unsigned char* result, int max_hyps,
                                   int max_frames, cudaStream_t s);
@@ -234,7 +235,7 @@ cudaError_t launch_round_prepare(const BatchHeader* hdr, const FrameDesc* frames
                                  cudaStream_t s);
 cudaError_t launch_round_finish(const BatchHeader* hdr, const FrameDesc* frames, HypState* st,
                                 int* active, const double* min_valid, unsigned char* result,
-                                int max_hyps, int max_frames, cudaStream_t s);
+                                int max_hyps, int max_frames, int max_frame_hyps, cudaStream_t s);
 
 // Sets the message pilot_align_last_error() returns on the calling thread.
 void record_error(const char* msg);

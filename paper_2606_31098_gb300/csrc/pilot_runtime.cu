@@ -632,7 +632,7 @@ pilot_status capture_batch_graph(pilot_align_handle* h, pilot_dtype dt, int C, b
         const int K = c.keep_top_k[level];
         if (e == cudaSuccess && level > 0 && K > 0)
             e = launch_batch_prune(hdr, frames, h->state, h->bactive, nactive + (size_t)level * lay.max_frames, K,
-                                   h->bmin_valid, c.max_frames, s);
+                                   h->bmin_valid, c.max_frames, std::min(c.max_hyps, kMaxFrameHyps), s);
     }
     if (e == cudaSuccess)
         e = launch_batch_finalize(hdr, frames, h->state, h->bmin_valid, h->bres_dev, c.max_hyps, c.max_frames, s);
@@ -959,7 +959,7 @@ pilot_status pilot_align_solve_batch(pilot_align_handle* h, const pilot_frame* f
         if (!f->is_device) return fail(PILOT_EINVAL, "frame %d: the batched form needs device frames", i);
         if (f->C != f0.C || f->L != f0.L || f->feat_dtype != f0.feat_dtype)
             return fail(PILOT_EINVAL, "frame %d: C, L and feat_dtype must match frame 0", i);
-        if (f->M > 8192) return fail(PILOT_EINVAL, "frame %d: M = %d above 8192", i, f->M);
+        if (f->M > kMaxFrameHyps) return fail(PILOT_EINVAL, "frame %d: M = %d above %d", i, f->M, kMaxFrameHyps);
         for (int l = 0; l < f->L; ++l) {
             const bool sl = f->qry_scale[l] || f->ref_scale[l];
             if (i == 0 && l == 0) scaled = sl;

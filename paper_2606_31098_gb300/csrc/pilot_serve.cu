@@ -290,7 +290,7 @@ cudaError_t capture_round(pilot_server* s) {
     }
     if (e == cudaSuccess)
         e = launch_round_finish(hdr, frames, s->state, s->active, s->min_valid, s->res_dev, s->cfg.max_hyps,
-                                s->max_slots, s->stream);
+                                s->max_slots, std::min(s->cfg.max_hyps, kMaxFrameHyps), s->stream);
     if (e == cudaSuccess) e = cudaMemcpyAsync(s->res_host, s->res_dev, s->res_bytes, cudaMemcpyDeviceToHost, s->stream);
     cudaGraph_t g = nullptr;
     const cudaError_t e2 = cudaStreamEndCapture(s->stream, &g);
@@ -535,7 +535,7 @@ pilot_status pilot_serve_submit(pilot_server* s, const pilot_frame* f, uint64_t*
     pilot_status st = check_frame(s->cfg, f);
     if (st != PILOT_OK) return st;
     if (f->M == 0) return sfail(PILOT_EINVAL, "a served frame needs at least one hypothesis");
-    if (f->M > 8192) return sfail(PILOT_EINVAL, "M above 8192");
+    if (f->M > kMaxFrameHyps) return sfail(PILOT_EINVAL, "M above 8192");
     bool scaled = false;
     for (int l = 0; l < f->L; ++l) {
         const bool sl = f->qry_scale[l] || f->ref_scale[l];
