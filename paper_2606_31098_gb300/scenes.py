@@ -425,6 +425,81 @@ def make_frame(cfg: SceneConfig, seed: int) -> Frame:
                            T_prior=prior if cfg.hyp_mode == "grid" else None))
 
 
+# ------------------------------------------------------------------ global TDOM/DSM map
+
+@dataclass
+class GlobalMap:
+    """A georeferenced TDOM/DSM pair: cell (r, c) is centred at (x0 + (c + 1/2) gsd,
+    y0 + (r + 1/2) gsd); the map's origin is its centre (x0 = y0 = -side gsd / 2)."""
+
+    dsm: np.ndarray               # (side, side) float32 heights, metres
+    tdom: np.ndarray              # (side, side, 3) uint8 RGB
+    x0: float
+    y0: float
+    gsd: float
+
+
+def make_global_map(side: int = 4096, gsd: float = 0.5, n_hills: int = 2048, n_boxes: int = 4096,
+                    seed: int = 0) -> GlobalMap:
+    """The crop-recipe terrain scaled to a whole map (Gaussian hills of sigma 10 m and
+    amplitude U(0, 15) m, box buildings of U(5, 40) m on U(6, 16) m footprints), each added on
+    its own window; the TDOM is a seeded colour texture (blurred noise at several scales,
+    shaded by height) so that every map layer varies pixel to pixel."""
+    rng = np.random.default_rng(seed)
+    dsm = np.zeros((side, side), np.float32)
+    half = side * gsd / 2.0
+    x0 = y0 = -half
+    sig = 10.0 / gsd                                   # hill sigma in cells
+    rad = int(np.ceil(4 * sig))
+    ax = np.arange(-rad, rad + 1, dtype=np.float32)
+    for _ in range(n_hills):
+        cr, cc = rng.uniform(0, side, 2)
+        amp = rng.uniform(0.0, 15.0)
+        r0, c0 = int(cr), int(cc)
+        rs, cs = slice(max(r0 - rad, 0), min(r0 + rad + 1, side)), slice(max(c0 - rad, 0), min(c0 + rad + 1, side))
+        gr = np.exp(-((np.arange(rs.start, rs.stop) + 0.5 - cr) ** 2) / (2 * sig * sig))
+        gc = np.exp(-((np.arange(cs.start, cs.stop) + 0.5 - cc) ** 2) / (2 * sig * sig))
+        dsm[rs, cs] += (amp * np.outer(gr, gc)).astype(np.float32)
+    del ax
+    for _ in range(n_boxes):
+        cr, cc = rng.uniform(0, side, 2)
+        sr, sc = rng.uniform(6.0, 16.0, 2) / gsd
+        h = np.float32(rng.uniform(5.0, 40.0))
+        rs = slice(max(int(cr - sr / 2), 0), min(int(cr + sr / 2) + 1, side))
+        cs = slice(max(int(cc - sc / 2), 0), min(int(cc + sc / 2) + 1, side))
+        np.maximum(dsm[rs, cs], h, out=dsm[rs, cs])
+    tex = np.zeros((side, side, 3), np.float32)
+    for k in range(3):
+        for scale, w in ((2.0, 0.5), (8.0, 1.0), (32.0, 1.0)):
+            small = max(side // int(scale), 8)
+            noise = ndimage.gaussian_filter(rng.standard_normal((small, small)), 1.0, mode="wrap")
+            tex[:, :, k] += w * ndimage.zoom(noise, side / small, order=1)[:side, :side]
+    tex = (tex - tex.mean()) / (tex.std() + 1e-6)
+    shade = (dsm - dsm.mean()) / (dsm.std() + 1e-6)
+    rgb = 128.0 + 40.0 * tex + 20.0 * shade[:, :, None]
+    return GlobalMap(dsm=dsm, tdom=np.clip(rgb, 0, 255).astype(np.uint8), x0=x0, y0=y0, gsd=gsd)
+
+
+def crop_prior(gmap: GlobalMap, seed: int, img_w: int = 640, img_h: int = 480, f: float = 600.0,
+               altitude=(120.0, 300.0), pitch_deg=(30.0, 70.0), margin: float = 400.0):
+    """A seeded pose prior over the map (altitude, pitch and yaw as the frame recipe, optical
+    axis through a surface point at least `margin` metres inside the map edge) and the
+    intrinsics of its image (principal point at the image centre)."""
+    rng = np.random.default_rng(seed)
+    half = gmap.dsm.shape[0] * gmap.gsd / 2.0
+    tx, ty = rng.uniform(-half + margin, half - margin, 2)
+    c = int(np.clip((tx - gmap.x0) / gmap.gsd, 0, gmap.dsm.shape[1] - 1))
+    r = int(np.clip((ty - gmap.y0) / gmap.gsd, 0, gmap.dsm.shape[0] - 1))
+    target = np.array([tx, ty, float(gmap.dsm[r, c])])
+    alt = rng.uniform(*altitude)
+    pitch = np.deg2rad(rng.uniform(*pitch_deg))
+    yaw = rng.uniform(0.0, 2.0 * np.pi)
+    d = np.cos(pitch) * np.array([np.cos(yaw), np.sin(yaw), 0.0]) + np.sin(pitch) * np.array([0, 0, -1.0])
+    C = target - (alt - target[2]) / np.sin(pitch) * d
+    return dict(T_cw=look_pose(C, yaw, pitch), fx=f, fy=f, cx=img_w / 2.0, cy=img_h / 2.0,
+                img_w=img_w, img_h=img_h, altitude=alt)
+
+
 def frame_seed(workload: int, index: int) -> int:
     """Seed of frame `index` of workload number `workload` (1_000_000 * workload + index)."""
     return 1_000_000 * workload + index
