@@ -366,6 +366,34 @@ def paper_schedule_form(args, B, S, torch, world, stream):
     return out
 
 
+def crop_form(B, S, torch, stream):
+    """The TDOM/DSM reference crop (Supp. "TDOM/DSM Reference Crop") on the serving workload's
+    map (4096 x 4096 cells at 0.5 m): device time per crop (corner-ray footprint with 8000
+    samples of 0.25 m per ray, homography, warp and geo-anchor lift) for 256^2 and 384^2 crops,
+    over 16 seeded pose priors."""
+    g = S.make_global_map(side=4096, seed=31)
+    dm = B.MapArgs(torch.as_tensor(g.dsm, device="cuda"), torch.as_tensor(g.tdom, device="cuda"), g.x0, g.y0, g.gsd)
+    priors = [S.crop_prior(g, k) for k in range(16)]
+    out = {"map": "4096 x 4096 cells at 0.5 m (TDOM RGB + DSM)", "ray_samples": 8000, "ray_step_m": 0.25,
+           "paper_context": "TDOM/DSM crop 13.17 ms per frame on the CPU (Supp. runtime table)"}
+    for S_ in (256, 384):
+        ps = [B.crop_params(pr["T_cw"], pr["fx"], pr["fy"], pr["cx"], pr["cy"], pr["img_w"], pr["img_h"],
+                            0.0, 0.25, 8000, S_) for pr in priors]
+        bufs = B.crop_reference(dm, ps[0], stream=stream)
+        for p in ps:
+            B.crop_reference(dm, p, out=bufs, stream=stream)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(4):
+            for p in ps:
+                B.crop_reference(dm, p, out=bufs, stream=stream)
+        e1.record(stream)
+        e1.synchronize()
+        out[f"ms_per_crop_{S_}"] = e0.elapsed_time(e1) / (4 * len(ps))
+    return out, g, priors
+
+
 def run_oracle_sample(frame, n_hyps: int, threads: int):
     """Solve `n_hyps` hypotheses of the frame with the FP64 oracle; returns
     (hyp_iters, seconds)."""
@@ -518,6 +546,7 @@ def run_ours(args):
 
     batched, served = batched_and_served(args, B, S, torch, world, stream) if not args.no_forms else ({}, {})
     paper = paper_schedule_form(args, B, S, torch, world, stream) if not args.no_forms else {}
+    crop, crop_map, crop_priors = crop_form(B, S, torch, stream) if not args.no_forms else ({}, None, None)
 
     h2d = sum(a.nbytes for k, v in B.host_arrays(frame).items() for a in (v if isinstance(v, list) else [v]))
     d2h = frame.M * (12 * 8 + 8 + 4 + 4) + 16
@@ -536,6 +565,15 @@ def run_ours(args):
             t0 = time.perf_counter()
             O.solve(pf, O.SolverOptions(iters=(4, 3, 2, 0), keep_top_k=(0, 0, 128, 0)), n_threads=threads)
             cpu["paper_schedule_ms_per_frame"] = 1e3 * (time.perf_counter() - t0)
+        if crop:
+            from oracle import crop as OC
+            om = OC.MapArgs(crop_map.dsm, crop_map.tdom, crop_map.x0, crop_map.y0, crop_map.gsd)
+            pr = crop_priors[0]
+            op = OC.params(pr["T_cw"], pr["fx"], pr["fy"], pr["cx"], pr["cy"], pr["img_w"], pr["img_h"],
+                           0.0, 0.25, 8000, 256)
+            t0 = time.perf_counter()
+            OC.crop(om, op)
+            cpu["crop_256_ms"] = 1e3 * (time.perf_counter() - t0)
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -563,7 +601,7 @@ def run_ours(args):
                                         "gather_vs_probe": gather_gbs / probe_gather}},
                 "precision_forms": precision,
                 "batched_form": batched,
-                "served_form": served, "paper_schedule_form": paper,
+                "served_form": served, "paper_schedule_form": paper, "crop_form": crop,
                 "clocks": clk,
                 "cpu_baseline": cpu}
         print(json.dumps(line), flush=True)

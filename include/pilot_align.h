@@ -208,6 +208,46 @@ pilot_status pilot_align_get_schedule(const pilot_align_handle* h, const pilot_f
 pilot_status pilot_align_solve_batch(pilot_align_handle* h, const pilot_frame* frames, int n_frames,
                                      pilot_result* results, void* stream);
 
+/* ---- TDOM/DSM reference crop (Supp. "TDOM/DSM Reference Crop"): the step before the
+ * solver that turns the global maps and a pose prior into a pixel-aligned 2.5D reference and
+ * its geo-anchors ---- */
+
+/* A georeferenced TDOM/DSM pair on the DEVICE: cell (r, c) is centred at
+ * (x0 + (c + 1/2) gsd, y0 + (r + 1/2) gsd); heights are read bilinearly between cell centres. */
+typedef struct {
+    const float* dsm;             /* H x W heights (metres), row-major; required */
+    const unsigned char* tdom;    /* H x W x 3 RGB, or NULL */
+    int H, W;                     /* >= 2 each */
+    double x0, y0, gsd;           /* gsd > 0 */
+} pilot_map;
+
+typedef struct {
+    double T_cw[12];              /* pose prior [R | t], world -> camera, row-major */
+    double fx, fy, cx, cy;        /* intrinsics of the query image, pixel-corner convention */
+    int img_w, img_h;             /* query image size: the corner rays pass through (0, 0), (W, 0), (W, H), (0, H) */
+    double s_min, s_step;         /* ray samples s_k = s_min + k s_step metres along each unit corner ray */
+    int n_samples;                /* 1 .. 4194304 */
+    int S;                        /* crop side in pixels, 1 .. 8192 */
+} pilot_crop_params;
+
+/* Reference crop, asynchronous on `stream`; allocates nothing.  Map footprint: for each image
+ * corner k the ray sample minimising |z_ray(s) - h_DSM(x_ray(s), y_ray(s))| (samples off the
+ * DSM skipped; ties to the nearer sample).  The homography maps the normalised crop square's
+ * corners (0, 0), (1, 0), (1, 1), (0, 1) to the footprint points of image corners 0..3 as
+ * offsets from the origin, the footprint centroid.  Warp and lift: crop pixel (u, v) (index
+ * v S + u) is read at its centre; its map coordinates come from the homography, and
+ *   points[v S + u], points[S^2 + v S + u], points[2 S^2 + v S + u] = x - ox, y - oy, DSM height
+ *   valid[v S + u] = 1 inside the DSM's cell-centre grid, else 0 (and zero outputs)
+ *   rgb[3 (v S + u) + k] = bilinear TDOM channel k as float (rgb may be NULL; zeros without a TDOM)
+ * geometry (28 doubles, device): H[9] (H[8] = 1), origin[2], footprint points[12] (x, y, z of
+ * image corners 0..3), sample index per corner (as double, -1 when a ray never crosses the DSM),
+ * and 1.0 when the crop is valid (all four rays found, homography non-singular), else 0.0 with
+ * every pixel invalid.  All outputs are device buffers owned by the caller (points 3 S^2 floats,
+ * valid S^2 bytes, rgb 3 S^2 floats, geometry 28 doubles, naturally aligned).  EINVAL on bad
+ * arguments (nothing launched); the crop's own failure is reported in geometry[27]. */
+pilot_status pilot_crop_reference(const pilot_map* map, const pilot_crop_params* params, float* points,
+                                  unsigned char* valid, float* rgb, double* geometry, void* stream);
+
 /* Roofline probes (the paper has no counterpart): measured ceilings the build pass is
  * compared against.  pilot_probe_fma: FP32 FMA throughput in TFLOP/s (packed FP32x2 FMAs on
  * every SM).  pilot_probe_gather: GB/s of the build pass' access pattern without its

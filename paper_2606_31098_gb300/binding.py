@@ -67,6 +67,7 @@ SIGNATURES = {
     "pilot_align_get_schedule": (ct.c_int, [_vp, _vp, ct.c_int, ct.c_int, _vp]),
     "pilot_align_set_schedule": (ct.c_int, [_vp, _vp, ct.c_int, ct.c_int, _vp]),
     "pilot_align_selftest_barrier_timeout": (ct.c_int, [_vp, ct.c_double, ct.POINTER(ct.c_double), _vp]),
+    "pilot_crop_reference": (ct.c_int, [_vp, _vp, _vp, _vp, _vp, _vp, _vp]),
     "pilot_probe_fma": (ct.c_int, [ct.POINTER(ct.c_double), _vp]),
     "pilot_probe_gather": (ct.c_int, [_vp, ct.c_int, ct.c_int, ct.c_int, ct.c_int, ct.c_longlong,
                                       ct.POINTER(ct.c_double), _vp]),
@@ -85,6 +86,17 @@ SIGNATURES = {
     "pilot_serve_get_stats": (ct.c_int, [_vp, _vp]),
     "pilot_serve_destroy": (None, [_vp]),
 }
+
+
+class pilot_map(ct.Structure):
+    _fields_ = [("dsm", _vp), ("tdom", _vp), ("H", ct.c_int), ("W", ct.c_int),
+                ("x0", ct.c_double), ("y0", ct.c_double), ("gsd", ct.c_double)]
+
+
+class pilot_crop_params(ct.Structure):
+    _fields_ = [("T_cw", ct.c_double * 12), ("fx", ct.c_double), ("fy", ct.c_double), ("cx", ct.c_double),
+                ("cy", ct.c_double), ("img_w", ct.c_int), ("img_h", ct.c_int), ("s_min", ct.c_double),
+                ("s_step", ct.c_double), ("n_samples", ct.c_int), ("S", ct.c_int)]
 
 
 class pilot_schedule(ct.Structure):
@@ -382,6 +394,42 @@ def normal_eq_noalloc(opts: Options, fa: FrameArgs, level: int, T_cw_dev, out29_
     cfg = opts.to_c()
     return load().pilot_align_normal_eq_noalloc(ct.byref(cfg), ct.byref(fa.c), int(level), _ptr(T_cw_dev),
                                                  _ptr(out29_dev), Solver._stream(stream))
+
+
+class MapArgs:
+    """A pilot_map over device tensors (dsm (H, W) float32, tdom (H, W, 3) uint8 or None)."""
+
+    def __init__(self, dsm, tdom, x0: float, y0: float, gsd: float):
+        self.dsm, self.tdom = dsm, tdom
+        self.c = pilot_map(_ptr(dsm), _ptr(tdom), int(dsm.shape[0]), int(dsm.shape[1]), float(x0), float(y0),
+                           float(gsd))
+
+
+def crop_params(T_cw, fx, fy, cx, cy, img_w, img_h, s_min, s_step, n_samples, S) -> pilot_crop_params:
+    p = pilot_crop_params()
+    p.T_cw[:] = [float(v) for v in np.asarray(T_cw, np.float64).ravel()]
+    p.fx, p.fy, p.cx, p.cy = float(fx), float(fy), float(cx), float(cy)
+    p.img_w, p.img_h = int(img_w), int(img_h)
+    p.s_min, p.s_step, p.n_samples, p.S = float(s_min), float(s_step), int(n_samples), int(S)
+    return p
+
+
+def crop_reference(m: MapArgs, p: pilot_crop_params, with_rgb: bool = True, out: dict | None = None,
+                   stream=None) -> dict:
+    """pilot_crop_reference into device tensors (allocated here unless `out` is given):
+    points (3, S*S) f32, valid (S*S,) u8, rgb (S*S, 3) f32 or None, geometry (28,) f64.
+    Asynchronous on `stream`."""
+    import torch
+    S = p.S
+    if out is None:
+        dev = m.dsm.device
+        out = dict(points=torch.empty((3, S * S), dtype=torch.float32, device=dev),
+                   valid=torch.empty(S * S, dtype=torch.uint8, device=dev),
+                   rgb=torch.empty((S * S, 3), dtype=torch.float32, device=dev) if with_rgb else None,
+                   geometry=torch.empty(28, dtype=torch.float64, device=dev))
+    check(load().pilot_crop_reference(ct.byref(m.c), ct.byref(p), _ptr(out["points"]), _ptr(out["valid"]),
+                                      _ptr(out["rgb"]), _ptr(out["geometry"]), Solver._stream(stream)))
+    return out
 
 
 def probe_fma(stream=None) -> float:
