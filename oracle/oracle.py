@@ -29,7 +29,7 @@ class OrFrame(ct.Structure):
     _fields_ = [
         ("N", ct.c_int), ("points", _f32p), ("point_weight", _f32p), ("point_valid", _u8p),
         ("C", ct.c_int), ("L", ct.c_int),
-        ("ref_feat", _f32p * MAX_LEVELS), ("qry_feat", _f32p * MAX_LEVELS),
+        ("ref_feat", _f32p * MAX_LEVELS), ("qry_feat", _f32p * MAX_LEVELS), ("qry_conf", _f32p * MAX_LEVELS),
         ("H", ct.c_int * MAX_LEVELS), ("W", ct.c_int * MAX_LEVELS),
         ("fx", ct.c_double), ("fy", ct.c_double), ("cx", ct.c_double), ("cy", ct.c_double),
         ("M", ct.c_int), ("T_cw", _f64p),
@@ -88,6 +88,8 @@ def lib():
         L.or_point_residual.restype = ct.c_int
         L.or_point_margin.argtypes = [ct.POINTER(OrFrame), ct.c_int, _f64p, ct.c_int]
         L.or_point_margin.restype = ct.c_double
+        L.or_query_confidence.argtypes = [ct.POINTER(OrFrame), ct.c_int, _f64p, ct.c_int]
+        L.or_query_confidence.restype = ct.c_double
         L.or_photo_terms.argtypes = [ct.POINTER(OrFrame), ct.POINTER(OrConfig), ct.c_int, _f64p,
                                      _f64p, _f64p, _f64p, _i32p]
         L.or_gravity_terms.argtypes = [ct.POINTER(OrFrame), ct.POINTER(OrConfig), _f64p, _f64p, _f64p, _f64p]
@@ -132,9 +134,11 @@ class OracleFrame:
         qrys = qry_feat if qry_feat is not None else frame.qry_feat
         f.L = len(qrys)
         f.C = qrys[0].shape[2]
+        confs = getattr(frame, "qry_conf", None)
         for l in range(f.L):
             f.ref_feat[l] = self._k(np.ascontiguousarray(refs[l], np.float32), _f32p)
             f.qry_feat[l] = self._k(np.ascontiguousarray(qrys[l], np.float32), _f32p)
+            f.qry_conf[l] = self._k(np.ascontiguousarray(confs[l], np.float32), _f32p) if confs is not None else None
             f.H[l], f.W[l] = qrys[l].shape[0], qrys[l].shape[1]
         f.fx, f.fy, f.cx, f.cy = frame.fx, frame.fy, frame.cx, frame.cy
         T = _f64(frame.T_hyps if T_hyps is None else T_hyps).reshape(-1, 12)
@@ -238,6 +242,13 @@ def point_residual(frame, level, T, j, with_jacobian=True, **kw):
     vis = lib().or_point_residual(ct.byref(of.c), int(level), _p(_f64(T), _f64p), int(j),
                                   _p(r, _f64p), _p(J, _f64p) if with_jacobian else None)
     return bool(vis), r, J
+
+
+def query_confidences(frame, level, T, **kw) -> np.ndarray:
+    """w^q_l at every anchor's projection under T (0 where not visible)."""
+    of = OracleFrame(frame, **kw)
+    Tp = _p(_f64(T), _f64p)
+    return np.array([lib().or_query_confidence(ct.byref(of.c), int(level), Tp, j) for j in range(of.c.N)])
 
 
 def point_margins(frame, level, T, **kw) -> np.ndarray:

@@ -316,6 +316,25 @@ double or_point_margin(const or_frame* f, int level, const double T[12], int j) 
     return mx < my ? mx : my;
 }
 
+double or_query_confidence(const or_frame* f, int level, const double T[12], int j) {
+    if (f->point_valid && !f->point_valid[j]) return 0.0;
+    const int N = f->N;
+    double R[9], t[3];
+    pose_split(T, R, t);
+    double P[3] = {f->points[j], f->points[N + j], f->points[2 * N + j]};
+    double p[3];
+    for (int i = 0; i < 3; ++i) p[i] = R[3 * i] * P[0] + R[3 * i + 1] * P[1] + R[3 * i + 2] * P[2] + t[i];
+    if (!(p[2] > Z_NEAR)) return 0.0;
+    double fx, fy, cx, cy;
+    level_intrinsics(f, level, &fx, &fy, &cx, &cy);
+    const double x = fx * p[0] / p[2] + cx - 0.5, y = fy * p[1] / p[2] + cy - 0.5;   /* array coordinates */
+    if (!(x >= 0.0 && x <= f->W[level] - 1.0 && y >= 0.0 && y <= f->H[level] - 1.0)) return 0.0;
+    if (!f->qry_conf[level]) return 1.0;
+    double w, dwx, dwy;
+    or_bilinear(f->qry_conf[level], f->H[level], f->W[level], 1, x, y, &w, &dwx, &dwy);
+    return w;
+}
+
 void or_photo_terms(const or_frame* f, const or_config* c, int level, const double T[12],
                     double H21[21], double g6[6], double* cost, int* n_valid) {
     const int C = f->C;
@@ -328,6 +347,7 @@ void or_photo_terms(const or_frame* f, const or_config* c, int level, const doub
         double s = 0.0;
         for (int ch = 0; ch < C; ++ch) s += r[ch] * r[ch];
         double w = f->point_weight ? f->point_weight[j] : 1.0;
+        if (f->qry_conf[level]) w *= or_query_confidence(f, level, T, j);
         double rho, drho;
         or_huber(w * s, c->huber_photo, &rho, &drho);
         total += rho;

@@ -41,6 +41,7 @@ typedef struct {
     int C, L;                           /* channels, pyramid levels */
     const float* ref_feat[OR_MAX_LEVELS];   /* per level N x C */
     const float* qry_feat[OR_MAX_LEVELS];   /* per level H_l x W_l x C (NHWC) */
+    const float* qry_conf[OR_MAX_LEVELS];   /* per level H_l x W_l query confidence w^q_l, or NULL (= 1) */
     int H[OR_MAX_LEVELS], W[OR_MAX_LEVELS];
     double fx, fy, cx, cy;              /* level-0 intrinsics, corner pixel convention */
     int M;                              /* hypotheses */
@@ -99,6 +100,13 @@ int or_point_residual(const or_frame* f, int level, const double T[12], int j,
  * boundary, and of Z to the near plane; used by the parity tests to set aside anchors
  * whose cell or visibility decision is ambiguous in FP32. */
 double or_point_margin(const or_frame* f, int level, const double T[12], int j);
+
+/* Query confidence w^q_l at anchor j's projection under T (bilinear in the level's
+ * confidence map, the cell the features are read from); 1 without a map, 0 when the anchor
+ * is not visible.  Its product with the anchor weight is the w_l(j) of Eq. 2; like the anchor
+ * weight it is held constant when linearising (pinned by an affine confidence map and by a
+ * constant map equalling a constant anchor weight). */
+double or_query_confidence(const or_frame* f, int level, const double T[12], int j);
 
 /* ---- objective pieces at pose T: H (21, upper triangle row-major), g (6), cost.
  *      (pinned: 2g == finite-difference gradient of cost, H == sum of FD Jacobians) */

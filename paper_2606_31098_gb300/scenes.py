@@ -154,6 +154,7 @@ class Frame:
     dsm_gsd: float
     seed: int = 0
     meta: dict = field(default_factory=dict)
+    qry_conf: list | None = None  # L arrays (H_l, W_l) float32 query confidence w^q_l, or None
 
     @property
     def N(self) -> int:
@@ -498,6 +499,20 @@ def crop_prior(gmap: GlobalMap, seed: int, img_w: int = 640, img_h: int = 480, f
     C = target - (alt - target[2]) / np.sin(pitch) * d
     return dict(T_cw=look_pose(C, yaw, pitch), fx=f, fy=f, cx=img_w / 2.0, cy=img_h / 2.0,
                 img_w=img_w, img_h=img_h, altitude=alt)
+
+
+def with_query_confidence(frame: Frame, seed: int, low: float = 0.2) -> Frame:
+    """The frame with seeded per-level query confidence maps in [low, 1] (a smooth random
+    field: blurred noise through a logistic), standing in for the network's uncertainty
+    output w^q_l."""
+    rng = np.random.default_rng(seed)
+    confs = []
+    for q in frame.qry_feat:
+        H, W = q.shape[:2]
+        z = ndimage.gaussian_filter(rng.standard_normal((H, W)), max(H, W) / 40.0, mode="reflect")
+        z /= z.std() + 1e-12
+        confs.append((low + (1.0 - low) / (1.0 + np.exp(-2.0 * z))).astype(np.float32))
+    return frame.replace(qry_conf=confs)
 
 
 def frame_seed(workload: int, index: int) -> int:
