@@ -521,6 +521,19 @@ def run_ours(args):
         precision[B.DTYPE_NAMES[dt]] = {"value": world * qu / (sum(qt) / 1e3), "unit": UNIT,
                                         "ms_per_step": sum(qt) / len(qt), "build_avg_launch_ms": qb / max(qn, 1)}
 
+    # the same plain form with a query confidence map per level weighting the photo term
+    confidence = {}
+    cframe = S.with_query_confidence(frame, rank_seed_index(args.seed_index, rank) + 17)
+    for dt in (B.F32, B.BF16):
+        ca = B.FrameArgs(cframe, B.quantized_device_arrays(cframe, dt), is_device=True, dtype=dt)
+        solver.set_schedule([ca], batched=False, tile=plain_schedule["tile"], streams=plain_schedule["streams"])
+        for _ in range(2):
+            solver.solve(ca, stream)
+        ct, _, _, _, cu, _ = timed(ca, max(3, args.steps // 3))
+        confidence[B.DTYPE_NAMES[dt]] = {"value": world * cu / (sum(ct) / 1e3), "unit": UNIT,
+                                         "ms_per_step": sum(ct) / len(ct)}
+    solver.set_schedule([dev], batched=False, tile=plain_schedule["tile"], streams=plain_schedule["streams"])
+
     total_ms, e2e_ms = max_over_ranks([sum(times), sum(e2e_times)], world, "cuda")
     value = replica_throughput(units, total_ms, world)
     e2e_value = replica_throughput(e2e_units, e2e_ms, world)
@@ -599,7 +612,7 @@ def run_ours(args):
                              "probes": {"fma_TFLOPs": probe_fma, "frac_of_probe_fma": achieved_tflops / probe_fma,
                                         "gather_random_pixels_GBps": probe_gather,
                                         "gather_vs_probe": gather_gbs / probe_gather}},
-                "precision_forms": precision,
+                "precision_forms": precision, "confidence_form": confidence,
                 "batched_form": batched,
                 "served_form": served, "paper_schedule_form": paper, "crop_form": crop,
                 "clocks": clk,

@@ -110,6 +110,11 @@ typedef struct {
     const float* ref_scale[PILOT_MAX_LEVELS]; /* C per level or NULL (= 1) */
     const void* qry_feat[PILOT_MAX_LEVELS];   /* f_l^q: H_l x W_l x C (NHWC) per level */
     const float* qry_scale[PILOT_MAX_LEVELS]; /* C per level or NULL (= 1) */
+    const float* qry_conf[PILOT_MAX_LEVELS];  /* per level H_l x W_l query confidence w^q_l (FP32, 4-byte
+                                                 aligned), or NULL (= 1): an anchor's weight in Eq. 2 is
+                                                 point_weight x w^q_l read bilinearly at its projection
+                                                 (the cell of the feature taps), held constant when
+                                                 linearising (the uncertainty map of Sec. IV-C) */
     int H[PILOT_MAX_LEVELS], W[PILOT_MAX_LEVELS]; /* each >= 2 */
     double fx, fy, cx, cy;          /* level-0 pinhole intrinsics in pixels */
     int M;                          /* hypotheses */
@@ -196,8 +201,9 @@ pilot_status pilot_align_get_schedule(const pilot_align_handle* h, const pilot_f
  * barrier, every job's FP64 step runs on one warp lane.  The launches, the per-frame top-K
  * and the selection are replayed from a CUDA graph captured on the first call (and again
  * when the storage type, C, L or schedule changes).
- * Requirements: every frame is a DEVICE frame; all frames share C, L, feat_dtype and the
- * presence of per-channel scales; n_frames <= max_frames; the hypotheses of all frames
+ * Requirements: every frame is a DEVICE frame; all frames share C, L, feat_dtype, the
+ * presence of per-channel scales and of query confidence maps (each given on every level
+ * or on none); n_frames <= max_frames; the hypotheses of all frames
  * together <= max_hyps, at most 8192 per frame.  PILOT_ETIMEOUT if a grid barrier wait
  * gave up (only when the device could not keep every CTA resident; results are then
  * invalid).  results[i] receives frame i's outputs
@@ -335,7 +341,8 @@ void pilot_align_destroy(pilot_align_handle* h);
  * one persistent launch (replayed from a CUDA graph) whatever level each is at; frames that
  * arrive meanwhile join at the next round.  A frame's outputs are exactly those
  * pilot_align_solve gives for it, however many other frames are being served.  All served
- * frames must share C, L, feat_dtype and the presence of scales (fixed by the first frame). */
+ * frames must share C, L, feat_dtype and the presence of scales and of query confidence
+ * maps, each given on every level or on none (fixed by the first frame). */
 typedef struct pilot_server pilot_server;
 
 typedef struct {

@@ -138,7 +138,8 @@ class OracleFrame:
         for l in range(f.L):
             f.ref_feat[l] = self._k(np.ascontiguousarray(refs[l], np.float32), _f32p)
             f.qry_feat[l] = self._k(np.ascontiguousarray(qrys[l], np.float32), _f32p)
-            f.qry_conf[l] = self._k(np.ascontiguousarray(confs[l], np.float32), _f32p) if confs is not None else None
+            c = None if confs is None else confs[l]
+            f.qry_conf[l] = None if c is None else self._k(np.ascontiguousarray(c, np.float32), _f32p)
             f.H[l], f.W[l] = qrys[l].shape[0], qrys[l].shape[1]
         f.fx, f.fy, f.cx, f.cy = frame.fx, frame.fy, frame.cx, frame.cy
         T = _f64(frame.T_hyps if T_hyps is None else T_hyps).reshape(-1, 12)

@@ -39,7 +39,7 @@ class pilot_frame(ct.Structure):
         ("is_device", ct.c_int), ("N", ct.c_int), ("points", _vp), ("point_weight", _vp),
         ("point_valid", _vp), ("C", ct.c_int), ("L", ct.c_int), ("feat_dtype", ct.c_int),
         ("ref_feat", _vp * MAX_LEVELS), ("ref_scale", _vp * MAX_LEVELS),
-        ("qry_feat", _vp * MAX_LEVELS), ("qry_scale", _vp * MAX_LEVELS),
+        ("qry_feat", _vp * MAX_LEVELS), ("qry_scale", _vp * MAX_LEVELS), ("qry_conf", _vp * MAX_LEVELS),
         ("H", ct.c_int * MAX_LEVELS), ("W", ct.c_int * MAX_LEVELS),
         ("fx", ct.c_double), ("fy", ct.c_double), ("cx", ct.c_double), ("cy", ct.c_double),
         ("M", ct.c_int), ("T_cw", _vp),
@@ -187,7 +187,7 @@ class FrameArgs:
 
     `arrays` maps field names to numpy arrays (host frame, is_device = 0) or torch CUDA
     tensors (device frame, is_device = 1): points (3, N) f32, point_weight (N,) f32,
-    point_valid (N,) u8, ref_feat / qry_feat lists, optional ref_scale / qry_scale lists,
+    point_valid (N,) u8, ref_feat / qry_feat lists, optional ref_scale / qry_scale / qry_conf lists,
     T_cw (M, 12) f64, dsm (H_D, W_D) f32.  Scalars come from `frame` (a scenes.Frame).
     """
 
@@ -207,11 +207,13 @@ class FrameArgs:
         f.feat_dtype = dtype
         qs = arrays.get("qry_scale") or [None] * f.L
         rs = arrays.get("ref_scale") or [None] * f.L
+        qc = arrays.get("qry_conf") or [None] * f.L
         for l in range(f.L):
             f.qry_feat[l] = _ptr(qry[l])
             f.ref_feat[l] = _ptr(ref[l])
             f.qry_scale[l] = _ptr(qs[l])
             f.ref_scale[l] = _ptr(rs[l])
+            f.qry_conf[l] = _ptr(qc[l])
             f.H[l], f.W[l] = int(qry[l].shape[0]), int(qry[l].shape[1])
         f.fx, f.fy, f.cx, f.cy = frame.fx, frame.fy, frame.cx, frame.cy
         T = arrays["T_cw"]
@@ -244,9 +246,11 @@ def host_arrays(frame, T_hyps=None, pinned: bool = False) -> dict:
                 ref_feat=[np.ascontiguousarray(r, np.float32) for r in frame.ref_feat],
                 qry_feat=[np.ascontiguousarray(q, np.float32) for q in frame.qry_feat],
                 T_cw=T, dsm=np.ascontiguousarray(frame.dsm, np.float32))
+    if getattr(frame, "qry_conf", None) is not None:
+        arrs["qry_conf"] = [None if c is None else np.ascontiguousarray(c, np.float32) for c in frame.qry_conf]
     if pinned:
         import torch
-        pin = lambda a: torch.from_numpy(a).pin_memory()
+        pin = lambda a: None if a is None else torch.from_numpy(a).pin_memory()
         arrs = {k: ([pin(x) for x in v] if isinstance(v, list) else pin(v)) for k, v in arrs.items()}
     return arrs
 
@@ -255,7 +259,7 @@ def device_arrays(frame, T_hyps=None, device="cuda") -> dict:
     """Device (torch CUDA) copies of an FP32 frame's arrays."""
     import torch
     h = host_arrays(frame, T_hyps)
-    to = lambda a: torch.from_numpy(a).to(device)
+    to = lambda a: None if a is None else torch.from_numpy(a).to(device)
     return {k: ([to(x) for x in v] if isinstance(v, list) else to(v)) for k, v in h.items()}
 
 

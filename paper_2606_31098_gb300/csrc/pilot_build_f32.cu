@@ -6,6 +6,6 @@
 namespace pilot {
 template cudaError_t launch_build_dtype<PILOT_F32>(const BuildParams&, cudaStream_t);
 template cudaError_t launch_build_fused_dtype<PILOT_F32>(const FusedBuildParams&, cudaStream_t);
-template cudaError_t launch_level_persistent_dtype<PILOT_F32>(int, bool, const LevelArgs&, int, cudaStream_t);
-template cudaError_t level_persistent_occupancy<PILOT_F32>(int, bool, int*);
+template cudaError_t launch_level_persistent_dtype<PILOT_F32>(int, int, const LevelArgs&, int, cudaStream_t);
+template cudaError_t level_persistent_occupancy<PILOT_F32>(int, int, int*);
 }  // namespace pilot

@@ -198,19 +198,20 @@ struct LevelView {
     const void* ref;
     const float* qscale;
     const float* rscale;
+    const float* conf;
     int H, W;
     float fx, fy, cx, cy, huber;
 };
 
 __device__ __forceinline__ LevelView level_view(const BuildParams& p) {
-    return LevelView{p.px, p.py, p.pz, p.weight, p.valid, p.qry, p.ref, p.qscale, p.rscale,
+    return LevelView{p.px, p.py, p.pz, p.weight, p.valid, p.qry, p.ref, p.qscale, p.rscale, p.conf,
                      p.H, p.W, p.fx, p.fy, p.cx, p.cy, p.huber};
 }
 
 // Accumulate anchors [j_begin, j_end) at pose P (12 FP32 values) into this lane's 29
 // sums.  Every thread of the CTA calls it with the same range; threads are grouped as
 // described at the top of the file.
-template <pilot_dtype DT, int C, bool SCALED, int NTHREADS>
+template <pilot_dtype DT, int C, bool SCALED, bool CONF, int NTHREADS>
 __device__ __forceinline__ void accumulate_anchors(const LevelView& v, const float* P, int j_begin,
                                                    int j_end, float* acc) {
     using Elem = typename Storage<DT>::T;
@@ -256,7 +257,7 @@ __device__ __forceinline__ void accumulate_anchors(const LevelView& v, const flo
         const int jo = jb + q;
         bool vis = false;
         int off = 0;
-        float ax = 0.f, ay = 0.f, x = 0.f, y = 0.f, z = 1.f, iz = 1.f;
+        float ax = 0.f, ay = 0.f, x = 0.f, y = 0.f, z = 1.f, iz = 1.f, wq = 1.f;
         if (jo < j_end && (!v.valid || v.valid[jo])) {
             const float X = __ldg(v.px + jo), Y = __ldg(v.py + jo), Z = __ldg(v.pz + jo);
             // p = R P + t  (world -> camera)
@@ -275,6 +276,13 @@ __device__ __forceinline__ void accumulate_anchors(const LevelView& v, const flo
                     ay = ys - (float)r0;
                     off = (r0 * v.W + c0) * C;
                     vis = true;
+                    if constexpr (CONF) {  // query confidence, bilinear in the same cell
+                        const float* cp = v.conf + r0 * v.W + c0;
+                        const float c00 = __ldg(cp), c01 = __ldg(cp + 1);
+                        const float c10 = __ldg(cp + v.W), c11 = __ldg(cp + v.W + 1);
+                        const float bq = c01 - c00, cq = c10 - c00, dq = (c11 - c10) - bq;
+                        wq = fmaf(ax, fmaf(dq, ay, bq), fmaf(ay, cq, c00));
+                    }
                 }
             }
         }
@@ -362,7 +370,7 @@ __device__ __forceinline__ void accumulate_anchors(const LevelView& v, const flo
         if (vis) {
             const float s = S[0][0], m00 = S[0][1], m01 = S[0][2], m11 = S[0][3];
             const float b0 = S[0][4], b1 = S[0][5];
-            const float w = v.weight ? __ldg(v.weight + jo) : 1.0f;
+            const float w = (v.weight ? __ldg(v.weight + jo) : 1.0f) * wq;
             const float sw = w * s;
             float rho, drho;
             if (sw <= d2) {
@@ -426,7 +434,7 @@ __device__ __forceinline__ float cta_reduce(float* acc, float (*red)[kAcc]) {
     return v;
 }
 
-template <pilot_dtype DT, int C, bool SCALED>
+template <pilot_dtype DT, int C, bool SCALED, bool CONF>
 __global__ void __launch_bounds__(kBuildThreads, 2)
 build_kernel(const BuildParams p) {
     __shared__ float red[kBuildThreads / 32][kAcc];
@@ -438,7 +446,7 @@ build_kernel(const BuildParams p) {
 #pragma unroll
     for (int i = 0; i < kNumSums; ++i) acc[i] = 0.f;
     const int j0 = blockIdx.x * p.tile;
-    accumulate_anchors<DT, C, SCALED, kBuildThreads>(level_view(p), p.pose32 + 12 * hyp, j0,
+    accumulate_anchors<DT, C, SCALED, CONF, kBuildThreads>(level_view(p), p.pose32 + 12 * hyp, j0,
                                                      min(j0 + p.tile, p.N), acc);
     const float v = cta_reduce<kBuildThreads>(acc, red);
     if (threadIdx.x < kAcc) out[threadIdx.x] = v;
@@ -447,7 +455,7 @@ build_kernel(const BuildParams p) {
 // The same pass with the per-hypothesis FP64 step fused in: the CTA that takes the last
 // ticket of its hypothesis sums the tile records (FP64, 8 chains per value, fixed order)
 // and runs lm_step.  A hypothesis without a candidate runs its step in tile 0's CTA.
-template <pilot_dtype DT, int C, bool SCALED>
+template <pilot_dtype DT, int C, bool SCALED, bool CONF>
 __global__ void __launch_bounds__(kBuildThreads, 2)
 build_fused_kernel(const FusedBuildParams fp) {
     const BuildParams& p = fp.b;
@@ -466,7 +474,7 @@ build_fused_kernel(const FusedBuildParams fp) {
 #pragma unroll
     for (int i = 0; i < kNumSums; ++i) acc[i] = 0.f;
     const int j0 = blockIdx.x * p.tile;
-    accumulate_anchors<DT, C, SCALED, kBuildThreads>(level_view(p), p.pose32 + 12 * hyp, j0,
+    accumulate_anchors<DT, C, SCALED, CONF, kBuildThreads>(level_view(p), p.pose32 + 12 * hyp, j0,
                                                      min(j0 + p.tile, p.N), acc);
     const float v = cta_reduce<kBuildThreads>(acc, red);
     float* out = p.partial + ((size_t)slot * p.n_tiles + blockIdx.x) * kAcc;
@@ -499,20 +507,28 @@ build_fused_kernel(const FusedBuildParams fp) {
 template <pilot_dtype DT, int C>
 cudaError_t launch_build_typed(const BuildParams& p, cudaStream_t s) {
     dim3 grid(p.n_tiles, p.n_active);
-    if (p.qscale)
-        build_kernel<DT, C, true><<<grid, kBuildThreads, 0, s>>>(p);
+    if (p.qscale && p.conf)
+        build_kernel<DT, C, true, true><<<grid, kBuildThreads, 0, s>>>(p);
+    else if (p.qscale)
+        build_kernel<DT, C, true, false><<<grid, kBuildThreads, 0, s>>>(p);
+    else if (p.conf)
+        build_kernel<DT, C, false, true><<<grid, kBuildThreads, 0, s>>>(p);
     else
-        build_kernel<DT, C, false><<<grid, kBuildThreads, 0, s>>>(p);
+        build_kernel<DT, C, false, false><<<grid, kBuildThreads, 0, s>>>(p);
     return cudaGetLastError();
 }
 
 template <pilot_dtype DT, int C>
 cudaError_t launch_build_fused_typed(const FusedBuildParams& p, cudaStream_t s) {
     dim3 grid(p.b.n_tiles, p.b.n_active);
-    if (p.b.qscale)
-        build_fused_kernel<DT, C, true><<<grid, kBuildThreads, 0, s>>>(p);
+    if (p.b.qscale && p.b.conf)
+        build_fused_kernel<DT, C, true, true><<<grid, kBuildThreads, 0, s>>>(p);
+    else if (p.b.qscale)
+        build_fused_kernel<DT, C, true, false><<<grid, kBuildThreads, 0, s>>>(p);
+    else if (p.b.conf)
+        build_fused_kernel<DT, C, false, true><<<grid, kBuildThreads, 0, s>>>(p);
     else
-        build_fused_kernel<DT, C, false><<<grid, kBuildThreads, 0, s>>>(p);
+        build_fused_kernel<DT, C, false, false><<<grid, kBuildThreads, 0, s>>>(p);
     return cudaGetLastError();
 }
 

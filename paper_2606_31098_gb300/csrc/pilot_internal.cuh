@@ -18,6 +18,8 @@ namespace pilot {
 
 constexpr int kAcc = 32;           // padded width of one partial-sum record
 constexpr int kNumSums = 29;       // 21 H + 6 g + cost + n_valid
+constexpr int kVariantScaled = 1;   // per-channel dequantisation scales given
+constexpr int kVariantConf = 2;     // query confidence maps given
 constexpr unsigned long long kBarrierTimeoutNs = 2000000000ull;   // level kernel: longest barrier wait
 constexpr int kSyncWords = 4;      // per persistent level launch: claims, arrivals, generations, pad
 constexpr int kItemAnchors = 4096; // persistent level kernel: anchors per work item (whole tiles)
@@ -62,6 +64,7 @@ struct BuildParams {
     const void* ref;           // N x C
     const float* qscale;       // C or nullptr
     const float* rscale;       // C or nullptr
+    const float* conf;         // H x W query confidence or nullptr
     int N, C, H, W;
     float fx, fy, cx, cy;      // level intrinsics
     float huber;               // photo Huber delta
@@ -124,6 +127,7 @@ struct FrameDesc {
     const void* qry[PILOT_MAX_LEVELS];
     const float* rscale[PILOT_MAX_LEVELS];
     const float* qscale[PILOT_MAX_LEVELS];
+    const float* conf[PILOT_MAX_LEVELS];
     int N, M;
     int H[PILOT_MAX_LEVELS], W[PILOT_MAX_LEVELS];
     float fx[PILOT_MAX_LEVELS], fy[PILOT_MAX_LEVELS], cx[PILOT_MAX_LEVELS], cy[PILOT_MAX_LEVELS];
@@ -213,10 +217,10 @@ template <pilot_dtype DT>
 cudaError_t launch_build_fused_dtype(const FusedBuildParams& p, cudaStream_t s);
 
 template <pilot_dtype DT>
-cudaError_t launch_level_persistent_dtype(int C, bool scaled, const LevelArgs& a, int grid,
+cudaError_t launch_level_persistent_dtype(int C, int variant, const LevelArgs& a, int grid,
                                           cudaStream_t s);
 template <pilot_dtype DT>
-cudaError_t level_persistent_occupancy(int C, bool scaled, int* ctas_per_sm);
+cudaError_t level_persistent_occupancy(int C, int variant, int* ctas_per_sm);
 
 // batch bookkeeping (one block per frame; frames beyond header->n_frames return)
 cudaError_t launch_batch_init(const BatchHeader* hdr, const FrameDesc* frames, HypState* st,
@@ -247,8 +251,13 @@ pilot_status check_config(const pilot_align_config& c);
 pilot_status check_frame(const pilot_align_config& c, const pilot_frame* f);
 size_t dtype_bytes(pilot_dtype dt);
 PriorParams frame_prior(const pilot_align_config& c, const pilot_frame* f, const float* dsm_dev);
-cudaError_t level_launch(pilot_dtype dt, int C, bool scaled, const LevelArgs& a, int grid, cudaStream_t s);
-cudaError_t level_occupancy_query(pilot_dtype dt, int C, bool scaled, int* n);
+cudaError_t level_launch(pilot_dtype dt, int C, int variant, const LevelArgs& a, int grid, cudaStream_t s);
+cudaError_t level_occupancy_query(pilot_dtype dt, int C, int variant, int* n);
+// Kernel variant of a frame for the batched and served forms (every frame of one launch
+// shares it): kVariantScaled when both scale arrays are given on every level,
+// kVariantConf when a query confidence map is given on every level.  Returns -1 when
+// the scales are given on some levels only (or one of a pair), -2 for the confidences.
+int frame_variant(const pilot_frame* f);
 constexpr int kPlainTile = 1024;
 
 }  // namespace pilot

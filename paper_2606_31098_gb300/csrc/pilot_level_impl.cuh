@@ -64,7 +64,7 @@ __device__ __forceinline__ bool grid_sync(unsigned long long* sync, unsigned* er
 // iteration.  A frame's result is therefore bitwise the one its plain solve gives, whatever
 // else is in the batch; the items balance the gathers over all CTAs, and the FP64 steps of
 // all jobs run at once, one per warp.
-template <pilot_dtype DT, int C, bool SCALED>
+template <pilot_dtype DT, int C, bool SCALED, bool CONF>
 __global__ void __launch_bounds__(kBuildThreads, 2)
 level_persistent_kernel(const LevelArgs a) {
     constexpr int kWarps = kBuildThreads / 32;
@@ -153,7 +153,7 @@ level_persistent_kernel(const LevelArgs a) {
             const int level = a.level >= 0 ? a.level : fd->level;
             if (k <= a.iters[level] && (s_meta & kEval)) {
                 const LevelView v{fd->px, fd->py, fd->pz, fd->weight, fd->valid, fd->qry[level], fd->ref[level],
-                                  fd->qscale[level], fd->rscale[level], fd->H[level], fd->W[level],
+                                  fd->qscale[level], fd->rscale[level], fd->conf[level], fd->H[level], fd->W[level],
                                   fd->fx[level], fd->fy[level], fd->cx[level], fd->cy[level], a.huber};
                 const int n_t = fd->N > 0 ? (fd->N + a.tile - 1) / a.tile : 1;
                 const int t1 = min(s_t0 + tpi, n_t);
@@ -162,7 +162,7 @@ level_persistent_kernel(const LevelArgs a) {
 #pragma unroll
                     for (int i = 0; i < kNumSums; ++i) acc[i] = 0.f;
                     const int j0 = t * a.tile;
-                    accumulate_anchors<DT, C, SCALED, kBuildThreads>(v, pose, j0, min(j0 + a.tile, fd->N), acc);
+                    accumulate_anchors<DT, C, SCALED, CONF, kBuildThreads>(v, pose, j0, min(j0 + a.tile, fd->N), acc);
                     const float val = cta_reduce<kBuildThreads>(acc, red);
                     if (tid < kAcc) a.partial[((size_t)s_first * tpi + t) * kAcc + tid] = val;
                 }
@@ -207,7 +207,7 @@ level_persistent_kernel(const LevelArgs a) {
 }
 
 template <pilot_dtype DT, int C>
-cudaError_t launch_level_persistent_typed(bool scaled, const LevelArgs& a, int grid, cudaStream_t s) {
+cudaError_t launch_level_persistent_typed(int variant, const LevelArgs& a, int grid, cudaStream_t s) {
     // cooperative: the grid barrier needs every CTA resident at once
     cudaLaunchConfig_t cfg{};
     cudaLaunchAttribute attr[1];
@@ -219,37 +219,55 @@ cudaError_t launch_level_persistent_typed(bool scaled, const LevelArgs& a, int g
     cfg.stream = s;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    if (scaled) return cudaLaunchKernelEx(&cfg, level_persistent_kernel<DT, C, true>, a);
-    return cudaLaunchKernelEx(&cfg, level_persistent_kernel<DT, C, false>, a);
-}
-
-template <pilot_dtype DT>
-cudaError_t launch_level_persistent_dtype(int C, bool scaled, const LevelArgs& a, int grid,
-                                          cudaStream_t s) {
-    switch (C) {
-        case 4: return launch_level_persistent_typed<DT, 4>(scaled, a, grid, s);
-        case 8: return launch_level_persistent_typed<DT, 8>(scaled, a, grid, s);
-        case 16: return launch_level_persistent_typed<DT, 16>(scaled, a, grid, s);
-        case 32: return launch_level_persistent_typed<DT, 32>(scaled, a, grid, s);
-        case 64: return launch_level_persistent_typed<DT, 64>(scaled, a, grid, s);
+    switch (variant) {
+        case 0: return cudaLaunchKernelEx(&cfg, level_persistent_kernel<DT, C, false, false>, a);
+        case kVariantScaled: return cudaLaunchKernelEx(&cfg, level_persistent_kernel<DT, C, true, false>, a);
+        case kVariantConf: return cudaLaunchKernelEx(&cfg, level_persistent_kernel<DT, C, false, true>, a);
+        case kVariantScaled | kVariantConf:
+            return cudaLaunchKernelEx(&cfg, level_persistent_kernel<DT, C, true, true>, a);
         default: return cudaErrorInvalidValue;
     }
 }
 
-template <pilot_dtype DT, int C, bool SCALED>
-cudaError_t occupancy_typed(int* n) {
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(n, level_persistent_kernel<DT, C, SCALED>,
-                                                         kBuildThreads, 0);
+template <pilot_dtype DT>
+cudaError_t launch_level_persistent_dtype(int C, int variant, const LevelArgs& a, int grid,
+                                          cudaStream_t s) {
+    switch (C) {
+        case 4: return launch_level_persistent_typed<DT, 4>(variant, a, grid, s);
+        case 8: return launch_level_persistent_typed<DT, 8>(variant, a, grid, s);
+        case 16: return launch_level_persistent_typed<DT, 16>(variant, a, grid, s);
+        case 32: return launch_level_persistent_typed<DT, 32>(variant, a, grid, s);
+        case 64: return launch_level_persistent_typed<DT, 64>(variant, a, grid, s);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+template <pilot_dtype DT, int C>
+cudaError_t occupancy_typed(int variant, int* n) {
+    switch (variant) {
+        case 0: return cudaOccupancyMaxActiveBlocksPerMultiprocessor(n, level_persistent_kernel<DT, C, false, false>,
+                                                                     kBuildThreads, 0);
+        case kVariantScaled:
+            return cudaOccupancyMaxActiveBlocksPerMultiprocessor(n, level_persistent_kernel<DT, C, true, false>,
+                                                                 kBuildThreads, 0);
+        case kVariantConf:
+            return cudaOccupancyMaxActiveBlocksPerMultiprocessor(n, level_persistent_kernel<DT, C, false, true>,
+                                                                 kBuildThreads, 0);
+        case kVariantScaled | kVariantConf:
+            return cudaOccupancyMaxActiveBlocksPerMultiprocessor(n, level_persistent_kernel<DT, C, true, true>,
+                                                                 kBuildThreads, 0);
+        default: return cudaErrorInvalidValue;
+    }
 }
 
 template <pilot_dtype DT>
-cudaError_t level_persistent_occupancy(int C, bool scaled, int* n) {
+cudaError_t level_persistent_occupancy(int C, int variant, int* n) {
     switch (C) {
-        case 4: return scaled ? occupancy_typed<DT, 4, true>(n) : occupancy_typed<DT, 4, false>(n);
-        case 8: return scaled ? occupancy_typed<DT, 8, true>(n) : occupancy_typed<DT, 8, false>(n);
-        case 16: return scaled ? occupancy_typed<DT, 16, true>(n) : occupancy_typed<DT, 16, false>(n);
-        case 32: return scaled ? occupancy_typed<DT, 32, true>(n) : occupancy_typed<DT, 32, false>(n);
-        case 64: return scaled ? occupancy_typed<DT, 64, true>(n) : occupancy_typed<DT, 64, false>(n);
+        case 4: return occupancy_typed<DT, 4>(variant, n);
+        case 8: return occupancy_typed<DT, 8>(variant, n);
+        case 16: return occupancy_typed<DT, 16>(variant, n);
+        case 32: return occupancy_typed<DT, 32>(variant, n);
+        case 64: return occupancy_typed<DT, 64>(variant, n);
         default: return cudaErrorInvalidValue;
     }
 }

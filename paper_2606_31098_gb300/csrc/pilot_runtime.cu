@@ -125,6 +125,8 @@ pilot_status validate_frame(const pilot_align_config& c, const pilot_frame* f) {
             return fail(PILOT_EINVAL, "level %d feature pointers must be 16-byte aligned", l);
         if ((f->qry_scale[l] && !aligned(f->qry_scale[l], 16)) || (f->ref_scale[l] && !aligned(f->ref_scale[l], 16)))
             return fail(PILOT_EINVAL, "level %d scale pointers must be 16-byte aligned", l);
+        if (f->qry_conf[l] && !aligned(f->qry_conf[l], 4))
+            return fail(PILOT_EINVAL, "level %d confidence map must be 4-byte aligned", l);
     }
     if (f->use_gravity) {
         for (int i = 0; i < 3; ++i)
@@ -148,7 +150,7 @@ struct DevBuf {
 
 enum StageSlot { kStPoints, kStWeight, kStValid, kStT, kStDsm, kStRef0, kStQry0 = kStRef0 + PILOT_MAX_LEVELS,
                  kStRs0 = kStQry0 + PILOT_MAX_LEVELS, kStQs0 = kStRs0 + PILOT_MAX_LEVELS,
-                 kStCount = kStQs0 + PILOT_MAX_LEVELS };
+                 kStConf0 = kStQs0 + PILOT_MAX_LEVELS, kStCount = kStConf0 + PILOT_MAX_LEVELS };
 
 }  // namespace
 
@@ -214,6 +216,7 @@ struct DevFrame {
     const void* qry[PILOT_MAX_LEVELS] = {};
     const float* rs[PILOT_MAX_LEVELS] = {};
     const float* qs[PILOT_MAX_LEVELS] = {};
+    const float* conf[PILOT_MAX_LEVELS] = {};
 };
 
 pilot_status stage_copy(pilot_align_handle* h, int slot, const void* src, size_t bytes,
@@ -254,6 +257,7 @@ pilot_status bind_frame(pilot_align_handle* h, const pilot_frame* f, cudaStream_
             d->qry[l] = f->qry_feat[l];
             d->rs[l] = f->ref_scale[l];
             d->qs[l] = f->qry_scale[l];
+            d->conf[l] = f->qry_conf[l];
         }
         return PILOT_OK;
     }
@@ -282,6 +286,10 @@ pilot_status bind_frame(pilot_align_handle* h, const pilot_frame* f, cudaStream_
         d->rs[l] = static_cast<const float*>(p);
         if ((st = stage_copy(h, kStQs0 + l, f->qry_scale[l], sizeof(float) * C, sl, &p)) != PILOT_OK) return st;
         d->qs[l] = static_cast<const float*>(p);
+        if ((st = stage_copy(h, kStConf0 + l, f->qry_conf[l], sizeof(float) * (size_t)f->H[l] * f->W[l], sl, &p)) !=
+            PILOT_OK)
+            return st;
+        d->conf[l] = static_cast<const float*>(p);
         if (sl == fine) PILOT_CUDA(cudaEventRecord(level_ready[l], fine), "level copy event");
     }
 #undef STAGE
@@ -304,6 +312,7 @@ BuildParams build_params(pilot_align_handle* h, const pilot_frame* f, const DevF
         b.qscale = d.qs[level] ? d.qs[level] : h->ones;
         b.rscale = d.rs[level] ? d.rs[level] : h->ones;
     }
+    b.conf = d.conf[level];
     b.N = f->N;
     b.C = f->C;
     b.H = f->H[level];
@@ -479,13 +488,23 @@ pilot_align_config config_with_defaults(const pilot_align_config& c) { return wi
 pilot_status check_config(const pilot_align_config& c) { return validate_config(c); }
 pilot_status check_frame(const pilot_align_config& c, const pilot_frame* f) { return validate_frame(c, f); }
 size_t dtype_bytes(pilot_dtype dt) { return dtype_size(dt); }
+int frame_variant(const pilot_frame* f) {
+    int v = 0;
+    for (int l = 0; l < f->L; ++l) {
+        const bool sl = f->qry_scale[l] || f->ref_scale[l];
+        const int vl = (sl ? kVariantScaled : 0) | (f->qry_conf[l] ? kVariantConf : 0);
+        if (sl && (!f->qry_scale[l] || !f->ref_scale[l])) return -1;
+        if (l == 0) v = vl;
+        if ((vl ^ v) & kVariantScaled) return -1;
+        if ((vl ^ v) & kVariantConf) return -2;
+    }
+    return v;
+}
 PriorParams frame_prior(const pilot_align_config& c, const pilot_frame* f, const float* dsm_dev) {
     DevFrame d;
     d.dsm = f->use_range ? dsm_dev : nullptr;
     return prior_params(c, f, d);
 }
-cudaError_t level_launch(pilot_dtype dt, int C, bool scaled, const LevelArgs& a, int grid, cudaStream_t s);
-cudaError_t level_occupancy_query(pilot_dtype dt, int C, bool scaled, int* n);
 }  // namespace pilot
 
 namespace {
@@ -530,22 +549,22 @@ pilot_status batch_alloc(pilot_align_handle* h) {
     return PILOT_OK;
 }
 
-cudaError_t launch_level(pilot_dtype dt, int C, bool scaled, const LevelArgs& a, int grid, cudaStream_t s) {
+cudaError_t launch_level(pilot_dtype dt, int C, int variant, const LevelArgs& a, int grid, cudaStream_t s) {
     switch (dt) {
-        case PILOT_F32: return launch_level_persistent_dtype<PILOT_F32>(C, scaled, a, grid, s);
-        case PILOT_BF16: return launch_level_persistent_dtype<PILOT_BF16>(C, scaled, a, grid, s);
-        case PILOT_F16: return launch_level_persistent_dtype<PILOT_F16>(C, scaled, a, grid, s);
-        case PILOT_FP8E4M3: return launch_level_persistent_dtype<PILOT_FP8E4M3>(C, scaled, a, grid, s);
+        case PILOT_F32: return launch_level_persistent_dtype<PILOT_F32>(C, variant, a, grid, s);
+        case PILOT_BF16: return launch_level_persistent_dtype<PILOT_BF16>(C, variant, a, grid, s);
+        case PILOT_F16: return launch_level_persistent_dtype<PILOT_F16>(C, variant, a, grid, s);
+        case PILOT_FP8E4M3: return launch_level_persistent_dtype<PILOT_FP8E4M3>(C, variant, a, grid, s);
     }
     return cudaErrorInvalidValue;
 }
 
-cudaError_t level_occupancy(pilot_dtype dt, int C, bool scaled, int* n) {
+cudaError_t level_occupancy(pilot_dtype dt, int C, int variant, int* n) {
     switch (dt) {
-        case PILOT_F32: return level_persistent_occupancy<PILOT_F32>(C, scaled, n);
-        case PILOT_BF16: return level_persistent_occupancy<PILOT_BF16>(C, scaled, n);
-        case PILOT_F16: return level_persistent_occupancy<PILOT_F16>(C, scaled, n);
-        case PILOT_FP8E4M3: return level_persistent_occupancy<PILOT_FP8E4M3>(C, scaled, n);
+        case PILOT_F32: return level_persistent_occupancy<PILOT_F32>(C, variant, n);
+        case PILOT_BF16: return level_persistent_occupancy<PILOT_BF16>(C, variant, n);
+        case PILOT_F16: return level_persistent_occupancy<PILOT_F16>(C, variant, n);
+        case PILOT_FP8E4M3: return level_persistent_occupancy<PILOT_FP8E4M3>(C, variant, n);
     }
     return cudaErrorInvalidValue;
 }
@@ -553,31 +572,31 @@ cudaError_t level_occupancy(pilot_dtype dt, int C, bool scaled, int* n) {
 }  // namespace
 
 namespace pilot {
-cudaError_t level_launch(pilot_dtype dt, int C, bool scaled, const LevelArgs& a, int grid, cudaStream_t s) {
-    return launch_level(dt, C, scaled, a, grid, s);
+cudaError_t level_launch(pilot_dtype dt, int C, int variant, const LevelArgs& a, int grid, cudaStream_t s) {
+    return launch_level(dt, C, variant, a, grid, s);
 }
-cudaError_t level_occupancy_query(pilot_dtype dt, int C, bool scaled, int* n) {
-    return level_occupancy(dt, C, scaled, n);
+cudaError_t level_occupancy_query(pilot_dtype dt, int C, int variant, int* n) {
+    return level_occupancy(dt, C, variant, n);
 }
 }  // namespace pilot
 
 namespace {
 
-long long graph_key(pilot_dtype dt, int C, bool scaled, int L, const pilot_schedule& sc) {
-    return ((long long)dt << 40) | ((long long)C << 32) | ((long long)scaled << 31) | ((long long)L << 28) |
+long long graph_key(pilot_dtype dt, int C, int variant, int L, const pilot_schedule& sc) {
+    return ((long long)dt << 44) | ((long long)C << 36) | ((long long)variant << 32) | ((long long)L << 28) |
            ((long long)sc.tile << 8) | (long long)sc.ctas_per_sm;
 }
 
 // Records the whole batched solve on h->bstream: descriptor upload, per-frame set-up,
 // one persistent launch per level (+ per-frame top-K), selection, result download.
-pilot_status capture_batch_graph(pilot_align_handle* h, pilot_dtype dt, int C, bool scaled, int L,
+pilot_status capture_batch_graph(pilot_align_handle* h, pilot_dtype dt, int C, int variant, int L,
                                  const pilot_schedule& sc) {
     const pilot_align_config& c = h->cfg;
     const BatchLayout lay = BatchLayout::make(c.max_frames, c.max_hyps);
     int dev = 0, sms = 0, per_sm = 0;
     PILOT_CUDA(cudaGetDevice(&dev), "cudaGetDevice");
     PILOT_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev), "SM count");
-    PILOT_CUDA(level_occupancy(dt, C, scaled, &per_sm), "occupancy query");
+    PILOT_CUDA(level_occupancy(dt, C, variant, &per_sm), "occupancy query");
     if (per_sm < 1) per_sm = 1;
     if (sc.ctas_per_sm > 0 && sc.ctas_per_sm < per_sm) per_sm = sc.ctas_per_sm;
     h->level_grid = sms * per_sm;
@@ -628,7 +647,7 @@ pilot_status capture_batch_graph(pilot_align_handle* h, pilot_dtype dt, int C, b
         a.damping_mode = c.damping_mode;
         a.huber = (float)c.huber_photo;
         a.lambda0 = c.lambda0;
-        e = launch_level(dt, C, scaled, a, h->level_grid, s);
+        e = launch_level(dt, C, variant, a, h->level_grid, s);
         const int K = c.keep_top_k[level];
         if (e == cudaSuccess && level > 0 && K > 0)
             e = launch_batch_prune(hdr, frames, h->state, h->bactive, nactive + (size_t)level * lay.max_frames, K,
@@ -646,7 +665,7 @@ pilot_status capture_batch_graph(pilot_align_handle* h, pilot_dtype dt, int C, b
     if (e2 != cudaSuccess) return cuda_fail(e2, "graph capture end");
     h->graph = g;
     PILOT_CUDA(cudaGraphInstantiate(&h->gexec, g, 0), "graph instantiate");
-    h->graph_key = graph_key(dt, C, scaled, L, sc);
+    h->graph_key = graph_key(dt, C, variant, L, sc);
     return PILOT_OK;
 }
 
@@ -952,7 +971,7 @@ pilot_status pilot_align_solve_batch(pilot_align_handle* h, const pilot_frame* f
     pilot_status st;
     long long total = 0;
     const pilot_frame& f0 = frames[0];
-    bool scaled = false;
+    int variant = 0;
     for (int i = 0; i < n; ++i) {
         const pilot_frame* f = frames + i;
         if ((st = validate_frame(c, f)) != PILOT_OK) return fail(st, "frame %d: %s", i, g_last_error.c_str());
@@ -960,13 +979,12 @@ pilot_status pilot_align_solve_batch(pilot_align_handle* h, const pilot_frame* f
         if (f->C != f0.C || f->L != f0.L || f->feat_dtype != f0.feat_dtype)
             return fail(PILOT_EINVAL, "frame %d: C, L and feat_dtype must match frame 0", i);
         if (f->M > kMaxFrameHyps) return fail(PILOT_EINVAL, "frame %d: M = %d above %d", i, f->M, kMaxFrameHyps);
-        for (int l = 0; l < f->L; ++l) {
-            const bool sl = f->qry_scale[l] || f->ref_scale[l];
-            if (i == 0 && l == 0) scaled = sl;
-            if (sl != scaled || (sl && (!f->qry_scale[l] || !f->ref_scale[l])))
-                return fail(PILOT_EINVAL, "frame %d level %d: give both scale arrays on every level of every "
-                                          "frame, or none", i, l);
-        }
+        const int vf = frame_variant(f);
+        if (vf == -1) return fail(PILOT_EINVAL, "frame %d: give both scale arrays on every level, or none", i);
+        if (vf == -2) return fail(PILOT_EINVAL, "frame %d: give a confidence map on every level, or none", i);
+        if (i == 0) variant = vf;
+        if (vf != variant)
+            return fail(PILOT_EINVAL, "frame %d: scale and confidence presence must match frame 0", i);
         total += f->M;
     }
     if (total > c.max_hyps) return fail(PILOT_EINVAL, "batch has %lld hypotheses, above max_hyps = %d", total, c.max_hyps);
@@ -1002,6 +1020,7 @@ pilot_status pilot_align_solve_batch(pilot_align_handle* h, const pilot_frame* f
             d.qry[l] = f->qry_feat[l];
             d.rscale[l] = f->ref_scale[l];
             d.qscale[l] = f->qry_scale[l];
+            d.conf[l] = f->qry_conf[l];
             d.H[l] = f->H[l];
             d.W[l] = f->W[l];
             const double sc = ldexp(1.0, -l);
@@ -1048,9 +1067,9 @@ pilot_status pilot_align_solve_batch(pilot_align_handle* h, const pilot_frame* f
             if (level > 0 && K > 0 && K < cur[i]) cur[i] = K;
         }
     }
-    const long long key = graph_key(f0.feat_dtype, f0.C, scaled, L, sc);
+    const long long key = graph_key(f0.feat_dtype, f0.C, variant, L, sc);
     if (!h->gexec || h->graph_key != key)
-        if ((st = capture_batch_graph(h, f0.feat_dtype, f0.C, scaled, L, sc)) != PILOT_OK) return st;
+        if ((st = capture_batch_graph(h, f0.feat_dtype, f0.C, variant, L, sc)) != PILOT_OK) return st;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     PILOT_CUDA(cudaGraphLaunch(h->gexec, s), "batch graph launch");
     PILOT_CUDA(cudaStreamSynchronize(s), "batch solve");

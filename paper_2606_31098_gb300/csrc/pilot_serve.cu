@@ -106,6 +106,7 @@ size_t frame_bytes(const pilot_frame& f) {
         b += a256(es * N * C) + a256(es * (size_t)f.H[l] * f.W[l] * C);
         if (f.ref_scale[l]) b += a256(sizeof(float) * C);
         if (f.qry_scale[l]) b += a256(sizeof(float) * C);
+        if (f.qry_conf[l]) b += a256(sizeof(float) * (size_t)f.H[l] * f.W[l]);
     }
     b += a256(sizeof(double) * 12 * (size_t)f.M);
     if (f.use_range) b += a256(sizeof(float) * (size_t)f.dsm_H * f.dsm_W);
@@ -159,7 +160,7 @@ struct pilot_server {
     bool key_set = false;
     pilot_dtype dt = PILOT_F32;
     int C = 0, L = 0;
-    bool scaled = false;
+    int variant = 0;           // kVariantScaled | kVariantConf, shared by every served frame
     std::thread worker;
     std::mutex mu;
     std::condition_variable cv_work, cv_done;
@@ -229,6 +230,8 @@ cudaError_t stage_frame(pilot_server* s, Request& r) {
         d.qry_feat[l] = p;
         if (e == cudaSuccess) e = place(s, r, &cur, f.ref_scale[l], sizeof(float) * C, &d.ref_scale[l]);
         if (e == cudaSuccess) e = place(s, r, &cur, f.qry_scale[l], sizeof(float) * C, &d.qry_scale[l]);
+        if (e == cudaSuccess)
+            e = place(s, r, &cur, f.qry_conf[l], sizeof(float) * (size_t)f.H[l] * f.W[l], &d.qry_conf[l]);
     }
     if (e == cudaSuccess) e = place(s, r, &cur, f.T_cw, sizeof(double) * 12 * (size_t)f.M, &d.T_cw);
     if (e == cudaSuccess && f.use_range)
@@ -243,7 +246,7 @@ cudaError_t capture_round(pilot_server* s) {
     s->graph = nullptr;
     int sms = 0, per_sm = 0;
     cudaError_t e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, s->device);
-    if (e == cudaSuccess) e = level_occupancy_query(s->dt, s->C, s->scaled, &per_sm);
+    if (e == cudaSuccess) e = level_occupancy_query(s->dt, s->C, s->variant, &per_sm);
     if (e != cudaSuccess) return e;
     s->grid = sms * (per_sm > 0 ? per_sm : 1);
     const BatchHeader* hdr = reinterpret_cast<const BatchHeader*>(s->desc_dev);
@@ -286,7 +289,7 @@ cudaError_t capture_round(pilot_server* s) {
         a.damping_mode = s->cfg.damping_mode;
         a.huber = (float)s->cfg.huber_photo;
         a.lambda0 = s->cfg.lambda0;
-        e = level_launch(s->dt, s->C, s->scaled, a, s->grid, s->stream);
+        e = level_launch(s->dt, s->C, s->variant, a, s->grid, s->stream);
     }
     if (e == cudaSuccess)
         e = launch_round_finish(hdr, frames, s->state, s->active, s->min_valid, s->res_dev, s->cfg.max_hyps,
@@ -363,6 +366,7 @@ void write_round(pilot_server* s) {
             d.qry[l] = f.qry_feat[l];
             d.rscale[l] = f.ref_scale[l];
             d.qscale[l] = f.qry_scale[l];
+            d.conf[l] = f.qry_conf[l];
             d.H[l] = f.H[l];
             d.W[l] = f.W[l];
             const double sc = ldexp(1.0, -l);
@@ -536,13 +540,9 @@ pilot_status pilot_serve_submit(pilot_server* s, const pilot_frame* f, uint64_t*
     if (st != PILOT_OK) return st;
     if (f->M == 0) return sfail(PILOT_EINVAL, "a served frame needs at least one hypothesis");
     if (f->M > kMaxFrameHyps) return sfail(PILOT_EINVAL, "M above 8192");
-    bool scaled = false;
-    for (int l = 0; l < f->L; ++l) {
-        const bool sl = f->qry_scale[l] || f->ref_scale[l];
-        if (l == 0) scaled = sl;
-        if (sl != scaled || (sl && (!f->qry_scale[l] || !f->ref_scale[l])))
-            return sfail(PILOT_EINVAL, "give both scale arrays on every level, or none");
-    }
+    const int variant = frame_variant(f);
+    if (variant == -1) return sfail(PILOT_EINVAL, "give both scale arrays on every level, or none");
+    if (variant == -2) return sfail(PILOT_EINVAL, "give a confidence map on every level, or none");
     const size_t bytes = frame_bytes(*f);
     if (bytes > s->budget) return sfail(PILOT_EINVAL, "the frame needs more device memory than the whole budget");
     std::unique_lock<std::mutex> lock(s->mu);
@@ -554,13 +554,13 @@ pilot_status pilot_serve_submit(pilot_server* s, const pilot_frame* f, uint64_t*
         s->dt = f->feat_dtype;
         s->C = f->C;
         s->L = f->L;
-        s->scaled = scaled;
+        s->variant = variant;
         const cudaError_t e = capture_round(s);
         if (prev >= 0 && prev != s->device) cudaSetDevice(prev);
         if (e != cudaSuccess) return sfail(PILOT_ECUDA, std::string("round graph: ") + cudaGetErrorString(e));
         s->key_set = true;
-    } else if (f->feat_dtype != s->dt || f->C != s->C || f->L != s->L || scaled != s->scaled) {
-        return sfail(PILOT_EINVAL, "every served frame must share C, L, feat_dtype and scale presence");
+    } else if (f->feat_dtype != s->dt || f->C != s->C || f->L != s->L || variant != s->variant) {
+        return sfail(PILOT_EINVAL, "every served frame must share C, L, feat_dtype, scale and confidence presence");
     }
     if ((int)s->pending.size() >= s->max_pending) return sfail(PILOT_EBUSY, "pending queue full");
     std::unique_ptr<Request> r(new Request());

@@ -134,6 +134,7 @@ extern "C" pilot_status pilot_align_normal_eq_noalloc(const pilot_align_config* 
     } else if (f->qry_scale[level] || f->ref_scale[level]) {
         return fail_msg(PILOT_EINVAL, "pilot_align_normal_eq_noalloc needs both or neither scale array");
     }
+    b.conf = f->qry_conf[level];
     b.N = f->N;
     b.C = f->C;
     b.H = f->H[level];
