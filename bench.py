@@ -366,6 +366,43 @@ def paper_schedule_form(args, B, S, torch, world, stream):
     return out
 
 
+def seeding_form(B, S, n_frames: int = 24):
+    """Synthetic analogue of the seeding ablation (Supp. "Effect of Multi-hypothesis
+    Sampling"): the paper's schedule on frames whose prior is 5-15 m / 5-15 deg off in
+    (x, y, yaw), solved from four hypothesis sets around the prior (none: the prior alone;
+    yaw: 10 yaw offsets; xy: the 11 x 11 grid; joint: all 1210).  Pose errors of the
+    selected hypothesis against the ground truth: medians and Recall@1/3/5/10 (m and deg).
+    An accuracy experiment on the CUDA path (batched FP32 solves), not a timed form."""
+    import concurrent.futures as cf
+    cfg = S.config_seeding_ablation()
+    with cf.ThreadPoolExecutor(max_workers=min(16, os.cpu_count() or 4)) as ex:
+        frames = list(ex.map(lambda i: S.make_frame(cfg, S.frame_seed(7, i)), range(n_frames)))
+    po = dict(iters=(4, 3, 2, 0), keep_top_k=(0, 0, 128, 0), max_points=500)
+    solver = B.Solver(B.Options(max_hyps=1210 * 8, max_frames=8, **po))
+    out = {}
+    for st in S.SEEDING_STRATEGIES:
+        errs = []
+        for b0 in range(0, n_frames, 8):
+            group = frames[b0:b0 + 8]
+            fas = []
+            for f in group:
+                hyps = S.seeding_hypotheses(f.meta["T_prior"], st, cfg)
+                fas.append(B.FrameArgs(f, B.device_arrays(f, T_hyps=hyps), is_device=True))
+            for f, r in zip(group, solver.solve_batch(fas)):
+                T = r.T_cw[r.best]
+                errs.append((S.translation_error_m(T, f.T_gt), S.rotation_error_deg(T, f.T_gt)))
+        e = np.array(errs)
+        out[st] = {"hypotheses": int(len(S.seeding_hypotheses(frames[0].meta["T_prior"], st, cfg))),
+                   "median_t_m": float(np.median(e[:, 0])), "median_R_deg": float(np.median(e[:, 1])),
+                   "recall_1_3_5_10": [float(100.0 * np.mean((e[:, 0] < th) & (e[:, 1] < th)))
+                                       for th in (1.0, 3.0, 5.0, 10.0)]}
+    solver.close()
+    out["frames"] = n_frames
+    out["workload"] = ("paper schedule (500 anchors, top 128 after coarse, 2/3/4 iterations), prior offset "
+                       "5-15 m horizontal and 5-15 deg yaw, seeded frames 7000000..")
+    return out
+
+
 def crop_form(B, S, torch, stream):
     """The TDOM/DSM reference crop (Supp. "TDOM/DSM Reference Crop") on the serving workload's
     map (4096 x 4096 cells at 0.5 m): device time per crop (corner-ray footprint with 8000
@@ -560,6 +597,7 @@ def run_ours(args):
     batched, served = batched_and_served(args, B, S, torch, world, stream) if not args.no_forms else ({}, {})
     paper = paper_schedule_form(args, B, S, torch, world, stream) if not args.no_forms else {}
     crop, crop_map, crop_priors = crop_form(B, S, torch, stream) if not args.no_forms else ({}, None, None)
+    seeding = seeding_form(B, S) if not args.no_forms else {}
 
     h2d = sum(a.nbytes for k, v in B.host_arrays(frame).items() for a in (v if isinstance(v, list) else [v]))
     d2h = frame.M * (12 * 8 + 8 + 4 + 4) + 16
@@ -615,6 +653,7 @@ def run_ours(args):
                 "precision_forms": precision, "confidence_form": confidence,
                 "batched_form": batched,
                 "served_form": served, "paper_schedule_form": paper, "crop_form": crop,
+                "seeding_ablation": seeding,
                 "clocks": clk,
                 "cpu_baseline": cpu}
         print(json.dumps(line), flush=True)

@@ -77,6 +77,8 @@ class SceneConfig:
     grid_yaw_deg: tuple = (-9.0, -7.0, -5.0, -3.0, -1.0, 1.0, 3.0, 5.0, 7.0, 9.0)
     prior_xy: float = 4.0                 # prior = GT shifted by U(+-prior_xy) in x and y
     prior_yaw_deg: float = 4.0            # ... and rotated by U(+-prior_yaw_deg) in yaw
+    prior_ring: tuple | None = None       # (lo, hi): instead, |dxy| ~ U(lo, hi) m in a uniform
+                                          # direction and |dyaw| ~ U(lo, hi) deg with a random sign
     n_anchors: int = 0                    # > 0: sample this many valid anchors of the crop
     use_gravity: bool = True
     gravity_noise_deg: float = 0.2
@@ -111,6 +113,16 @@ def config_paper_schedule(n_anchors: int = 500, crop_side: int = 256) -> SceneCo
     iterations from coarse to fine."""
     return SceneConfig(crop_side=crop_side, levels=((384, 512), (192, 256), (96, 128)),
                        f0=600.0 * 512.0 / 640.0, hyp_mode="grid", n_anchors=n_anchors)
+
+
+def config_seeding_ablation() -> SceneConfig:
+    """The paper's schedule with the prior drawn at 5-15 m horizontal offset and 5-15 deg
+    yaw offset (the pose-prior uncertainty of Sec. V-A's data: 5-15 m, 5-15 deg), for the
+    synthetic analogue of the seeding ablation (Supp. "Effect of Multi-hypothesis
+    Sampling"; hypotheses from seeding_hypotheses)."""
+    cfg = config_paper_schedule()
+    cfg.prior_ring = (5.0, 15.0)
+    return cfg
 
 
 def config_reduced_frame(crop_side: int = 90, n_hyps: int = 6, channels: int = 32,
@@ -384,8 +396,15 @@ def make_frame(cfg: SceneConfig, seed: int) -> Frame:
     M = cfg.n_hyps
     if cfg.hyp_mode == "grid":
         r_prior = np.random.default_rng(kids[7])
-        pdx, pdy = r_prior.uniform(-cfg.prior_xy, cfg.prior_xy, 2)
-        prior = _perturb_xy_yaw(T_gt, pdx, pdy, np.deg2rad(r_prior.uniform(-cfg.prior_yaw_deg, cfg.prior_yaw_deg)))
+        if cfg.prior_ring is None:
+            pdx, pdy = r_prior.uniform(-cfg.prior_xy, cfg.prior_xy, 2)
+            pyaw = r_prior.uniform(-cfg.prior_yaw_deg, cfg.prior_yaw_deg)
+        else:
+            lo, hi = cfg.prior_ring
+            rad, ang = r_prior.uniform(lo, hi), r_prior.uniform(0.0, 2.0 * np.pi)
+            pdx, pdy = rad * np.cos(ang), rad * np.sin(ang)
+            pyaw = r_prior.choice([-1.0, 1.0]) * r_prior.uniform(lo, hi)
+        prior = _perturb_xy_yaw(T_gt, pdx, pdy, np.deg2rad(pyaw))
         grid = [(gx, gy, gp) for gx in cfg.grid_xy for gy in cfg.grid_xy for gp in cfg.grid_yaw_deg]
         M = len(grid)
     hyps = np.empty((M, 12))
@@ -424,6 +443,25 @@ def make_frame(cfg: SceneConfig, seed: int) -> Frame:
                  meta=dict(alt=alt, pitch_deg=float(np.rad2deg(pitch)), yaw_deg=float(np.rad2deg(yaw)),
                            range_true=float(rng_true), crop_side=S,
                            T_prior=prior if cfg.hyp_mode == "grid" else None))
+
+
+SEEDING_STRATEGIES = ("none", "yaw", "xy", "joint")
+
+
+def seeding_hypotheses(T_prior: np.ndarray, strategy: str, cfg: SceneConfig | None = None) -> np.ndarray:
+    """Initial hypotheses around a prior pose for the four seeding strategies of the
+    multi-hypothesis ablation (Supp. "Effect of Multi-hypothesis Sampling"): "none" is the
+    prior alone, "yaw" the yaw offsets of the grid at the prior's position, "xy" the (x, y)
+    grid at the prior's yaw, "joint" the full (x, y, psi) grid (cfg's grid_xy x grid_xy x
+    grid_yaw_deg; the paper's 11 x 11 x 10 by default).  Returns (M, 12) world->camera poses,
+    x outermost and psi innermost as in the grid mode of make_frame."""
+    cfg = cfg or SceneConfig()
+    xy = cfg.grid_xy if strategy in ("xy", "joint") else (0.0,)
+    yaw = cfg.grid_yaw_deg if strategy in ("yaw", "joint") else (0.0,)
+    if strategy not in SEEDING_STRATEGIES:
+        raise ValueError(strategy)
+    return np.stack([_perturb_xy_yaw(T_prior, gx, gy, np.deg2rad(gp)).ravel()
+                     for gx in xy for gy in xy for gp in yaw])
 
 
 # ------------------------------------------------------------------ global TDOM/DSM map
