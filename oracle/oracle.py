@@ -46,6 +46,7 @@ class OrConfig(ct.Structure):
         ("iters", ct.c_int * MAX_LEVELS), ("lambda0", ct.c_double), ("damping_mode", ct.c_int),
         ("huber_photo", ct.c_double), ("huber_grav", ct.c_double), ("huber_range", ct.c_double),
         ("keep_top_k", ct.c_int * MAX_LEVELS), ("min_valid_frac", ct.c_double),
+        ("gate_grav", ct.c_double), ("gate_range", ct.c_double),
     ]
 
 
@@ -66,6 +67,8 @@ class SolverOptions:
     huber_range: float = 1.0
     keep_top_k: tuple = (0, 0, 0, 0)
     min_valid_frac: float = 0.05
+    gate_grav: float = 0.0            # prior residual gates; 0 = off
+    gate_range: float = 0.0
 
 
 _lib = None
@@ -171,6 +174,7 @@ def make_config(opts: SolverOptions) -> OrConfig:
     c.huber_photo, c.huber_grav, c.huber_range = opts.huber_photo, opts.huber_grav, opts.huber_range
     c.keep_top_k[:] = list(opts.keep_top_k) + [0] * (MAX_LEVELS - len(opts.keep_top_k))
     c.min_valid_frac = opts.min_valid_frac
+    c.gate_grav, c.gate_range = opts.gate_grav, opts.gate_range
     return c
 
 
@@ -256,6 +260,16 @@ def point_margins(frame, level, T, **kw) -> np.ndarray:
     of = OracleFrame(frame, T_hyps=np.asarray(T).reshape(1, 12), **kw)
     Tp = _p(_f64(T), _f64p)
     return np.array([lib().or_point_margin(ct.byref(of.c), int(level), Tp, j) for j in range(of.c.N)])
+
+
+def prior_terms(frame, opts: SolverOptions, which: str, T):
+    """H (21), g (6) and cost of one sensor prior ("gravity" or "range") at pose T."""
+    of = OracleFrame(frame, T_hyps=np.asarray(T).reshape(1, 12))
+    c = make_config(opts)
+    H, g, cost = np.zeros(21), np.zeros(6), np.zeros(1)
+    fn = lib().or_gravity_terms if which == "gravity" else lib().or_range_terms
+    fn(ct.byref(of.c), ct.byref(c), _p(_f64(T), _f64p), _p(H, _f64p), _p(g, _f64p), _p(cost, _f64p))
+    return H, g, float(cost[0])
 
 
 def gravity_residual(frame, T):

@@ -391,6 +391,14 @@ int or_gravity_terms(const or_frame* f, const or_config* c, const double T[12],
     or_gravity_residual(f, T, r, J);
     double s = r[0] * r[0] + r[1] * r[1] + r[2] * r[2];
     double rho, drho;
+    if (c->gate_grav > 0.0 && s > c->gate_grav * c->gate_grav) {
+        /* gated: constant cost at the gate, no pull on the pose */
+        or_huber(c->gate_grav * c->gate_grav, c->huber_grav, &rho, &drho);
+        for (int i = 0; i < 21; ++i) H21[i] = 0.0;
+        for (int i = 0; i < 6; ++i) g6[i] = 0.0;
+        *cost = f->w_grav * rho;
+        return 1;
+    }
     or_huber(s, c->huber_grav, &rho, &drho);
     add_JtJ(H, g, J, r, 3, f->w_grav * drho);
     for (int a = 0; a < 6; ++a)
@@ -446,6 +454,12 @@ int or_range_terms(const or_frame* f, const or_config* c, const double T[12],
     *cost = 0.0;
     if (!or_range_residual(f, T, &r, J)) return 0;   /* off the DSM: term dropped */
     double rho, drho;
+    if (c->gate_range > 0.0 && fabs(r) > c->gate_range) {
+        /* gated: constant cost at the gate, no pull on the pose */
+        or_huber(c->gate_range * c->gate_range, c->huber_range, &rho, &drho);
+        *cost = f->w_range * rho;
+        return 1;
+    }
     or_huber(r * r, c->huber_range, &rho, &drho);
     add_JtJ(H, g, J, &r, 1, f->w_range * drho);
     for (int a = 0; a < 6; ++a)

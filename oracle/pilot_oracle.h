@@ -65,6 +65,11 @@ typedef struct {
     double huber_photo, huber_grav, huber_range;
     int keep_top_k[OR_MAX_LEVELS];      /* applied after level l finishes; 0 = keep all */
     double min_valid_frac;
+    /* residual gates of the sensor priors (Supp. "Sensor-Prior Fusion in LM": a prior whose
+     * residual becomes excessively large is down-weighted): a residual norm above the gate
+     * contributes the constant cost w rho(gate^2) and nothing to H and g (a truncated
+     * Huber, continuous at the gate); 0 = no gate */
+    double gate_grav, gate_range;
 } or_config;
 
 typedef struct {
