@@ -431,6 +431,51 @@ def crop_form(B, S, torch, stream):
     return out, g, priors
 
 
+def tracking_form(B, S, gmap, n_frames: int = 60):
+    """Sequential localisation (Supp. "Runtime Analysis"; Sec. V-A's Failure Recovery
+    Count) of a seeded 60-frame flight over the 4096^2 map: constant-velocity priors, a
+    256^2 reference crop per frame, the paper's 1210-seed grid and schedule, prior gates
+    (gravity 0.1, range 3 m); 5 % of frames visually failed (random reference
+    descriptors).  Serial and with the map preparation one frame ahead.  Accuracy and
+    recoveries use the paper's 20 m / 20 deg rule; times are per frame: device time of the
+    crop (map-preparation stream) and of seeding + solve (localisation stream), and the
+    host wall time of a frame with the synthetic network (the feature extractor's stand-in,
+    on the host) included."""
+    from paper_2606_31098_gb300 import tracking as TK
+    tc = S.TrackConfig(n_frames=n_frames)
+    gt = S.make_trajectory(gmap, tc, seed=51)
+    bank = S.query_bank(tc, seed=52)
+    H0, W0 = tc.levels[0]
+    cam = TK.Camera(tc.f0, tc.f0, W0 / 2.0, H0 / 2.0, W0, H0)
+    grid_xy = tuple(float(v) for v in range(-10, 11, 2))
+    grid_yaw = (-9.0, -7.0, -5.0, -3.0, -1.0, 1.0, 3.0, 5.0, 7.0, 9.0)
+    opts = B.Options(iters=(4, 3, 2, 0), keep_top_k=(0, 0, 128, 0), max_hyps=1210, max_points=500,
+                     gate_grav=0.1, gate_range=3.0)
+    out = {"frames": n_frames, "rate_hz": tc.rate_hz,
+           "workload": "60-frame synthetic flight, 256^2 crops on a 4096^2 map, 1210 seeds, 500 anchors, "
+                       "2/3/4 iterations, 5 % visually failed frames"}
+    for mode in ("serial", "lookahead"):
+        tr = TK.SequentialTracker(gmap.dsm, None, gmap.x0, gmap.y0, gmap.gsd, cam,
+                                  TK.CropSettings(tc.crop_side, 0.0, tc.ray_step, tc.ray_samples), opts,
+                                  grid_xy, grid_yaw, mode=mode)
+        net = S.SyntheticNetwork(gmap, tc, bank, gt, 53)
+        res = TK.run_sequence(tr, gt, net)
+        tr.close()
+        e = res["err"]
+        ok = ~res["failed"]
+        tm = res["timings"][1:]                       # frame 0 includes first-use set-up
+        out[mode] = {"frc": res["frc"], "median_t_m": float(np.median(e[:, 0])),
+                     "median_R_deg": float(np.median(e[:, 1])),
+                     "recall_1_3_5_10": [float(100.0 * np.mean((e[:, 0] < th) & (e[:, 1] < th)))
+                                         for th in (1.0, 3.0, 5.0, 10.0)],
+                     "median_t_m_tracked": float(np.median(e[ok, 0])) if ok.any() else None,
+                     "crop_ms": float(np.mean([x.crop_ms for x in tm])),
+                     "seed_solve_ms": float(np.mean([x.solve_ms for x in tm])),
+                     "wall_ms": float(np.mean([x.wall_ms for x in tm])),
+                     "crops_prepared_ahead": int(sum(x.prepared_ahead for x in tm))}
+    return out
+
+
 def run_oracle_sample(frame, n_hyps: int, threads: int):
     """Solve `n_hyps` hypotheses of the frame with the FP64 oracle; returns
     (hyp_iters, seconds)."""
@@ -598,6 +643,7 @@ def run_ours(args):
     paper = paper_schedule_form(args, B, S, torch, world, stream) if not args.no_forms else {}
     crop, crop_map, crop_priors = crop_form(B, S, torch, stream) if not args.no_forms else ({}, None, None)
     seeding = seeding_form(B, S) if not args.no_forms else {}
+    tracking = tracking_form(B, S, crop_map) if not args.no_forms else {}
 
     h2d = sum(a.nbytes for k, v in B.host_arrays(frame).items() for a in (v if isinstance(v, list) else [v]))
     d2h = frame.M * (12 * 8 + 8 + 4 + 4) + 16
@@ -653,7 +699,7 @@ def run_ours(args):
                 "precision_forms": precision, "confidence_form": confidence,
                 "batched_form": batched,
                 "served_form": served, "paper_schedule_form": paper, "crop_form": crop,
-                "seeding_ablation": seeding,
+                "seeding_ablation": seeding, "tracking_form": tracking,
                 "clocks": clk,
                 "cpu_baseline": cpu}
         print(json.dumps(line), flush=True)

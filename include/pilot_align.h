@@ -91,6 +91,11 @@ typedef struct {
     int profile;             /* 1: time every build-pass launch with CUDA events */
     int max_frames;          /* batched form: largest number of frames per call; 0 -> 64
                                 (max_hyps then bounds the hypotheses of the whole batch) */
+    double gate_grav;        /* residual gates of the sensor priors (Supp. "Sensor-Prior
+                                Fusion in LM": an excessively large prior residual is
+                                down-weighted): a gravity residual norm above gate_grav, or a */
+    double gate_range;       /* range residual above gate_range metres, adds the constant
+                                cost w rho(gate^2) and nothing to H and g; 0 = no gate */
 } pilot_align_config;
 
 /* One query frame.  All pointers are owned by the caller and are either all device
@@ -253,6 +258,43 @@ typedef struct {
  * arguments (nothing launched); the crop's own failure is reported in geometry[27]. */
 pilot_status pilot_crop_reference(const pilot_map* map, const pilot_crop_params* params, float* points,
                                   unsigned char* valid, float* rgb, double* geometry, void* stream);
+
+/* ---------------------------------------------------------------- sequential tracking
+ * Pieces of the online loop (Supp. "Runtime Analysis": map preparation and localisation run
+ * as two asynchronous stages; Sec. V-A: failure recovery).  Poses are [R | t] world ->
+ * camera, 12 doubles row-major. */
+
+/* Constant-velocity prior `steps` frames after T_prev: with T_prev2 (the estimate one frame
+ * earlier) T_out = (T_prev T_prev2^-1)^steps T_prev, i.e. the last inter-frame motion in the
+ * body frame repeated; with T_prev2 = NULL, T_out = T_prev.  Host function, FP64; T_out may
+ * alias an input.  EINVAL on NULL, steps < 0 or non-finite input. */
+pilot_status pilot_pose_predict(const double* T_prev, const double* T_prev2, int steps, double* T_out);
+
+/* The pose re-expressed for points given relative to (dx, dy, 0): t_out = t + R (dx, dy, 0).
+ * A reference crop's anchors are offsets from its origin (ox, oy): pilot_pose_reorigin(T_world,
+ * ox, oy) gives the crop-local pose, pilot_pose_reorigin(T_local, -ox, -oy) the world pose.
+ * Host function; T_out may alias T. */
+pilot_status pilot_pose_reorigin(const double* T, double dx, double dy, double* T_out);
+
+#define PILOT_MAX_SEED_XY 32
+#define PILOT_MAX_SEED_YAW 64
+
+typedef struct {
+    double T_prior[12];                       /* prior pose, world -> camera */
+    double origin_x, origin_y;                /* crop origin: the seeds are written crop-local */
+    int n_xy, n_yaw;                          /* 1..32, 1..64 */
+    double grid_xy[PILOT_MAX_SEED_XY];        /* metres, applied to x and to y */
+    double grid_yaw_deg[PILOT_MAX_SEED_YAW];  /* degrees */
+} pilot_seed_params;
+
+/* Multi-hypothesis seeds around a prior (Sec. IV-E; Supp. "Multi-Hypothesis Refinement"):
+ * hypothesis m = (i_x n_xy + i_y) n_yaw + i_psi has its camera centre at C + (grid_xy[i_x],
+ * grid_xy[i_y], 0) and is turned about the world +z axis through its centre by
+ * grid_yaw_deg[i_psi] (R_wc' = Rz(psi) R_wc, roll and pitch kept), then re-origined to the
+ * crop.  Writes n_xy^2 n_yaw x 12 doubles to the DEVICE buffer T_out (8-byte aligned, owned by
+ * the caller) on `stream`, ready as a device frame's T_cw; asynchronous, allocates nothing.
+ * EINVAL on bad arguments (nothing launched). */
+pilot_status pilot_seed_hypotheses(const pilot_seed_params* params, double* T_out, void* stream);
 
 /* Roofline probes (the paper has no counterpart): measured ceilings the build pass is
  * compared against.  pilot_probe_fma: FP32 FMA throughput in TFLOP/s (packed FP32x2 FMAs on

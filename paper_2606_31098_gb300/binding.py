@@ -31,6 +31,7 @@ class pilot_align_config(ct.Structure):
         ("huber_range", ct.c_double), ("keep_top_k", ct.c_int * MAX_LEVELS),
         ("min_valid_frac", ct.c_double), ("max_points", ct.c_int), ("max_hyps", ct.c_int),
         ("max_channels", ct.c_int), ("profile", ct.c_int), ("max_frames", ct.c_int),
+        ("gate_grav", ct.c_double), ("gate_range", ct.c_double),
     ]
 
 
@@ -68,6 +69,9 @@ SIGNATURES = {
     "pilot_align_set_schedule": (ct.c_int, [_vp, _vp, ct.c_int, ct.c_int, _vp]),
     "pilot_align_selftest_barrier_timeout": (ct.c_int, [_vp, ct.c_double, ct.POINTER(ct.c_double), _vp]),
     "pilot_crop_reference": (ct.c_int, [_vp, _vp, _vp, _vp, _vp, _vp, _vp]),
+    "pilot_pose_predict": (ct.c_int, [_vp, _vp, ct.c_int, _vp]),
+    "pilot_pose_reorigin": (ct.c_int, [_vp, ct.c_double, ct.c_double, _vp]),
+    "pilot_seed_hypotheses": (ct.c_int, [_vp, _vp, _vp]),
     "pilot_probe_fma": (ct.c_int, [ct.POINTER(ct.c_double), _vp]),
     "pilot_probe_gather": (ct.c_int, [_vp, ct.c_int, ct.c_int, ct.c_int, ct.c_int, ct.c_longlong,
                                       ct.POINTER(ct.c_double), _vp]),
@@ -158,6 +162,8 @@ class Options:
     max_channels: int = 32
     profile: int = 0
     max_frames: int = 64
+    gate_grav: float = 0.0         # sensor-prior residual gates; 0 = off
+    gate_range: float = 0.0
 
     def to_c(self) -> pilot_align_config:
         c = pilot_align_config()
@@ -170,6 +176,7 @@ class Options:
         c.max_points, c.max_hyps, c.max_channels = self.max_points, self.max_hyps, self.max_channels
         c.profile = self.profile
         c.max_frames = self.max_frames
+        c.gate_grav, c.gate_range = self.gate_grav, self.gate_range
         return c
 
 
@@ -433,6 +440,62 @@ def crop_reference(m: MapArgs, p: pilot_crop_params, with_rgb: bool = True, out:
                    geometry=torch.empty(28, dtype=torch.float64, device=dev))
     check(load().pilot_crop_reference(ct.byref(m.c), ct.byref(p), _ptr(out["points"]), _ptr(out["valid"]),
                                       _ptr(out["rgb"]), _ptr(out["geometry"]), Solver._stream(stream)))
+    return out
+
+
+MAX_SEED_XY, MAX_SEED_YAW = 32, 64
+
+
+class pilot_seed_params(ct.Structure):
+    _fields_ = [("T_prior", ct.c_double * 12), ("origin_x", ct.c_double), ("origin_y", ct.c_double),
+                ("n_xy", ct.c_int), ("n_yaw", ct.c_int), ("grid_xy", ct.c_double * MAX_SEED_XY),
+                ("grid_yaw_deg", ct.c_double * MAX_SEED_YAW)]
+
+
+def _pose12(T) -> np.ndarray:
+    a = np.ascontiguousarray(T, np.float64).ravel()
+    if a.size != 12:
+        raise ValueError("a pose is 12 values [R | t]")
+    return a
+
+
+def pose_predict(T_prev, T_prev2=None, steps: int = 1) -> np.ndarray:
+    """pilot_pose_predict: constant-velocity prior `steps` frames after T_prev."""
+    a = _pose12(T_prev)
+    b = None if T_prev2 is None else _pose12(T_prev2)
+    out = np.empty(12)
+    check(load().pilot_pose_predict(a.ctypes.data, None if b is None else b.ctypes.data, int(steps),
+                                    out.ctypes.data))
+    return out
+
+
+def pose_reorigin(T, dx: float, dy: float) -> np.ndarray:
+    """pilot_pose_reorigin: the pose for points given relative to (dx, dy, 0)."""
+    a = _pose12(T)
+    out = np.empty(12)
+    check(load().pilot_pose_reorigin(a.ctypes.data, float(dx), float(dy), out.ctypes.data))
+    return out
+
+
+def seed_params(T_prior, grid_xy, grid_yaw_deg, origin=(0.0, 0.0)) -> pilot_seed_params:
+    p = pilot_seed_params()
+    p.T_prior[:] = [float(v) for v in _pose12(T_prior)]
+    p.origin_x, p.origin_y = float(origin[0]), float(origin[1])
+    p.n_xy, p.n_yaw = len(grid_xy), len(grid_yaw_deg)
+    if not (1 <= p.n_xy <= MAX_SEED_XY and 1 <= p.n_yaw <= MAX_SEED_YAW):
+        raise ValueError("grid sizes outside [1, 32] x [1, 64]")
+    p.grid_xy[:p.n_xy] = [float(v) for v in grid_xy]
+    p.grid_yaw_deg[:p.n_yaw] = [float(v) for v in grid_yaw_deg]
+    return p
+
+
+def seed_hypotheses(p: pilot_seed_params, out=None, stream=None):
+    """pilot_seed_hypotheses into a device tensor (M, 12) f64 (allocated here unless given)."""
+    import torch
+    M = p.n_xy * p.n_xy * p.n_yaw
+    if out is None:
+        out = torch.empty((M, 12), dtype=torch.float64, device="cuda")
+    check(load().pilot_seed_hypotheses(ct.byref(p), _ptr(out), Solver._stream(stream)))
     return out
 
 

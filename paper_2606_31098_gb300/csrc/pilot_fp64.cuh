@@ -42,7 +42,13 @@ __device__ inline void add_gravity(const PriorParams& pp, const double* T, doubl
         a[i] = T[4 * i] * pp.g_world[0] + T[4 * i + 1] * pp.g_world[1] + T[4 * i + 2] * pp.g_world[2];
     const double r[3] = {a[0] - pp.g_cam[0], a[1] - pp.g_cam[1], a[2] - pp.g_cam[2]};
     double rho, drho;
-    huber64(r[0] * r[0] + r[1] * r[1] + r[2] * r[2], pp.huber_grav, &rho, &drho);
+    const double s = r[0] * r[0] + r[1] * r[1] + r[2] * r[2];
+    if (pp.gate_grav > 0.0 && s > pp.gate_grav * pp.gate_grav) {   // gated: constant, no pull
+        huber64(pp.gate_grav * pp.gate_grav, pp.huber_grav, &rho, &drho);
+        E[27] += pp.w_grav * rho;
+        return;
+    }
+    huber64(s, pp.huber_grav, &rho, &drho);
     const double w = pp.w_grav * drho;
     // rotation block: w [a]x^T [a]x = w (|a|^2 I - a a^T); gradient: w [a]x r = w (a x r)
     const double aa = a[0] * a[0] + a[1] * a[1] + a[2] * a[2];
@@ -81,6 +87,11 @@ __device__ inline void add_range(const PriorParams& pp, const double* T, double*
                          n[2] * pp.q[0] - n[0] * pp.q[2],
                          n[0] * pp.q[1] - n[1] * pp.q[0]};
     double rho, drho;
+    if (pp.gate_range > 0.0 && fabs(r) > pp.gate_range) {          // gated: constant, no pull
+        huber64(pp.gate_range * pp.gate_range, pp.huber_range, &rho, &drho);
+        E[27] += pp.w_range * rho;
+        return;
+    }
     huber64(r * r, pp.huber_range, &rho, &drho);
     const double w = pp.w_range * drho;
     int k = 0;

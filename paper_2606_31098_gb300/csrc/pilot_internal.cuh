@@ -84,6 +84,7 @@ struct PriorParams {
     int use_range;
     double q[3];               // d^range * v (Eq. 4 ray scaled by the range), camera frame
     double w_range, huber_range;
+    double gate_grav, gate_range;   // residual gates (0 = none)
     const float* dsm;
     int dsm_H, dsm_W;
     double dsm_x0, dsm_y0, dsm_gsd;

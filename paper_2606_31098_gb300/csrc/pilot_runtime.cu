@@ -92,6 +92,8 @@ pilot_status validate_config(const pilot_align_config& c) {
         return fail(PILOT_EINVAL, "Huber thresholds must be > 0");
     if (!(c.min_valid_frac >= 0.0 && c.min_valid_frac <= 1.0))
         return fail(PILOT_EINVAL, "min_valid_frac must be in [0, 1]");
+    if (!(c.gate_grav >= 0.0 && isfinite(c.gate_grav)) || !(c.gate_range >= 0.0 && isfinite(c.gate_range)))
+        return fail(PILOT_EINVAL, "prior gates must be finite and >= 0");
     if (c.max_points < 0 || c.max_hyps < 1) return fail(PILOT_EINVAL, "max_points >= 0 and max_hyps >= 1 required");
     if (!channels_supported(c.max_channels))
         return fail(PILOT_EINVAL, "max_channels must be one of 4, 8, 16, 32, 64");
@@ -351,6 +353,8 @@ PriorParams prior_params(const pilot_align_config& c, const pilot_frame* f, cons
     }
     pp.w_range = f->w_range;
     pp.huber_range = c.huber_range;
+    pp.gate_grav = c.gate_grav;
+    pp.gate_range = c.gate_range;
     pp.dsm = d.dsm;
     pp.dsm_H = f->dsm_H;
     pp.dsm_W = f->dsm_W;

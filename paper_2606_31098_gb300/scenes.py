@@ -313,11 +313,26 @@ def read_map(fmap: np.ndarray, u: np.ndarray, v: np.ndarray) -> np.ndarray:
     return out
 
 
-def _ray_to_dsm(C, d, dsm, x0, y0, gsd, step=0.05, s_max=5000.0):
+def _point_height(dsm: np.ndarray, x0: float, y0: float, gsd: float, x: float, y: float) -> float:
+    """Bilinear DSM height at one world point (cell centres at x0 + (c+1/2) gsd), clamped to
+    the raster like dsm_height; reads only the four cells it needs."""
+    H, W = dsm.shape
+    c = min(max((x - x0) / gsd - 0.5, 0.0), W - 1.0)
+    r = min(max((y - y0) / gsd - 0.5, 0.0), H - 1.0)
+    c0, r0 = min(int(c), W - 2), min(int(r), H - 2)
+    ax, ay = c - c0, r - r0
+    t = dsm[r0:r0 + 2, c0:c0 + 2].astype(np.float64)
+    return float((1 - ay) * ((1 - ax) * t[0, 0] + ax * t[0, 1]) + ay * ((1 - ax) * t[1, 0] + ax * t[1, 1]))
+
+
+def _ray_to_dsm(C, d, dsm, x0, y0, gsd, step=0.05, s_max=5000.0, pointwise=False):
     """Distance along the ray C + s d to its first crossing of the bilinear DSM surface
-    (march, then bisection to 1e-9 m)."""
+    (march, then bisection to 1e-9 m).  pointwise=True reads four cells per sample (for
+    large maps) instead of scipy's interpolation of the whole raster."""
     def above(s):
         p = C + s * d
+        if pointwise:
+            return p[2] - _point_height(dsm, x0, y0, gsd, p[0], p[1])
         return p[2] - dsm_height(dsm, x0, y0, gsd, p[0], p[1])[0]
 
     s_lo, s = 0.0, step
@@ -571,3 +586,155 @@ def rotation_error_deg(Ta, Tb) -> float:
 def translation_error_m(Ta, Tb) -> float:
     """Distance between camera centres in metres."""
     return float(np.linalg.norm(camera_centre(Ta) - camera_centre(Tb)))
+
+
+# ------------------------------------------------------------------ sequential tracking
+
+@dataclass
+class TrackConfig:
+    """Recipe of a synthetic UAV sequence over a global TDOM/DSM map: a smooth flight
+    (speed and heading rate varying as sums of sinusoids), the paper's 512-px pyramid and
+    refinement schedule, and a reference crop per frame."""
+
+    n_frames: int = 60
+    rate_hz: float = 5.0
+    speed: tuple = (10.0, 18.0)                      # m/s
+    turn_rate_deg_s: float = 8.0                     # amplitude of the heading rate
+    altitude: tuple = (110.0, 140.0)                 # camera height above the datum, m
+    pitch_deg: tuple = (45.0, 60.0)                  # optical axis below the horizon
+    levels: tuple = ((384, 512), (192, 256), (96, 128))
+    f0: float = 480.0                                # level-0 focal length (600 px at 640 wide)
+    channels: int = 32
+    crop_side: int = 256
+    ray_step: float = 0.25                           # footprint ray samples, metres
+    ray_samples: int = 8000
+    n_anchors: int = 500
+    query_bank: int = 4                              # distinct query pyramids, used in turn
+    ref_noise: float = 0.01
+    degrade_prob: float = 0.05                       # frames whose reference descriptors are noise
+    degraded_frames: tuple = ()                      # ... and frames that always are
+    gravity_noise_deg: float = 0.2
+    range_noise: float = 0.1
+    w_grav: float = 1e2
+    w_range: float = 1e1
+
+
+def make_trajectory(gmap: GlobalMap, tc: TrackConfig, seed: int) -> np.ndarray:
+    """(n_frames, 12) ground-truth world->camera poses of a seeded smooth flight that starts
+    near the map centre; the camera looks forward along the heading."""
+    rng = np.random.default_rng(seed)
+    dt = 1.0 / tc.rate_hz
+    n = tc.n_frames
+    tt = np.arange(n) * dt
+    ph = rng.uniform(0, 2 * np.pi, 6)
+    w = rng.uniform(0.05, 0.2, 3)
+    v = 0.5 * (tc.speed[0] + tc.speed[1]) + 0.5 * (tc.speed[1] - tc.speed[0]) * np.sin(w[0] * tt + ph[0])
+    rate = np.deg2rad(tc.turn_rate_deg_s) * (0.6 * np.sin(w[1] * tt + ph[1]) + 0.4 * np.sin(3.1 * w[1] * tt + ph[2]))
+    yaw = rng.uniform(0, 2 * np.pi) + np.concatenate([[0.0], np.cumsum(rate[:-1] * dt)])
+    xy = np.zeros((n, 2))
+    xy[0] = rng.uniform(-100.0, 100.0, 2)
+    for k in range(1, n):
+        xy[k] = xy[k - 1] + v[k - 1] * dt * np.array([np.cos(yaw[k - 1]), np.sin(yaw[k - 1])])
+    alt = 0.5 * (tc.altitude[0] + tc.altitude[1]) + 0.5 * (tc.altitude[1] - tc.altitude[0]) * np.sin(w[2] * tt + ph[3])
+    pitch = np.deg2rad(0.5 * (tc.pitch_deg[0] + tc.pitch_deg[1])
+                       + 0.5 * (tc.pitch_deg[1] - tc.pitch_deg[0]) * np.sin(0.7 * w[2] * tt + ph[4]))
+    return np.array([look_pose(np.array([xy[k, 0], xy[k, 1], alt[k]]), yaw[k], pitch[k]) for k in range(n)])
+
+
+def query_bank(tc: TrackConfig, seed: int) -> list:
+    """tc.query_bank query pyramids (lists of (H_l, W_l, C) maps), the stand-in for the
+    feature network's query output; frame t uses pyramid t mod the bank size."""
+    cfg = SceneConfig(levels=tc.levels, channels=tc.channels)
+    ss = np.random.SeedSequence(seed).spawn(tc.query_bank * len(tc.levels))
+    out = []
+    for b in range(tc.query_bank):
+        out.append([_make_feature_map(H, W, tc.channels, cfg, np.random.default_rng(ss[b * len(tc.levels) + l]))
+                    for l, (H, W) in enumerate(tc.levels)])
+    return out
+
+
+def track_inputs(gmap: GlobalMap, tc: TrackConfig, bank: list, t: int, T_gt_world: np.ndarray,
+                 crop_points: np.ndarray, crop_valid: np.ndarray, origin, seed: int) -> Frame:
+    """Frame t of a sequence from its reference crop (the stand-in for the feature network:
+    reference descriptors are the query features at the anchors' ground-truth projections).
+
+    crop_points (3, S^2) are the crop's anchors as offsets from `origin` (ox, oy); anchors
+    seen with a 1-pixel margin at every level under the ground truth are eligible, and the
+    tc.n_anchors of them with the smallest seeded per-pixel keys are kept (so an anchor's
+    selection does not depend on the others).  With probability tc.degrade_prob the frame's
+    reference descriptors are replaced by random unit vectors (a visual failure).  Poses
+    and the DSM are crop-local; T_hyps is a placeholder the tracker replaces by its seeds."""
+    ss = np.random.SeedSequence([seed, t]).spawn(4)
+    r_key, r_ref, r_sens, r_deg = (np.random.default_rng(k) for k in ss)
+    ox, oy = float(origin[0]), float(origin[1])
+    R, tw = pose_parts(T_gt_world)
+    T_loc = np.hstack([R, (tw + R @ np.array([ox, oy, 0.0]))[:, None]]).ravel()
+    qry = bank[t % len(bank)]
+    pts = np.asarray(crop_points, np.float32)
+    ok = np.asarray(crop_valid).astype(bool).copy()
+    H0, W0 = tc.levels[0]
+    cx0, cy0 = W0 / 2.0, H0 / 2.0
+    uv = []
+    for lvl, (H, W) in enumerate(tc.levels):
+        s = 2.0 ** -lvl
+        u, v, z = project_gt(pts, T_loc, tc.f0 * s, cx0 * s, cy0 * s)
+        ok &= (z > 0.1) & (u - 0.5 >= 1.0) & (u - 0.5 <= W - 2.0) & (v - 0.5 >= 1.0) & (v - 0.5 <= H - 2.0)
+        uv.append((u, v))
+    keys = r_key.random(pts.shape[1])
+    cand = np.flatnonzero(ok)
+    keep = np.sort(cand[np.argsort(keys[cand], kind="stable")[:tc.n_anchors]])
+    if keep.size == 0:
+        raise ValueError(f"frame {t}: no crop anchor is seen at the ground truth")
+    refs = []
+    degraded = bool(r_deg.random() < tc.degrade_prob) or t in tc.degraded_frames
+    for lvl in range(len(tc.levels)):
+        u, v = uv[lvl]
+        f = read_map(qry[lvl], u[keep], v[keep]) + tc.ref_noise * r_ref.standard_normal((keep.size, tc.channels))
+        if degraded:
+            f = r_ref.standard_normal(f.shape)
+            f /= np.linalg.norm(f, axis=1, keepdims=True)
+        refs.append(f.astype(np.float32))
+    g_cam = R @ GRAVITY_WORLD
+    a = np.cross(g_cam, _unit(r_sens))
+    a /= np.linalg.norm(a)
+    g_meas = Rotation.from_rotvec(a * np.deg2rad(tc.gravity_noise_deg)).as_matrix() @ g_cam
+    C_loc = -R.T @ T_loc.reshape(3, 4)[:, 3]
+    d = R[2]                                         # optical axis in the world
+    rng_true = _ray_to_dsm(C_loc, d, gmap.dsm, gmap.x0 - ox, gmap.y0 - oy, gmap.gsd, step=tc.ray_step, pointwise=True)
+    rng_meas = rng_true + tc.range_noise * r_sens.standard_normal()
+    sub = np.ascontiguousarray(pts[:, keep])
+    return Frame(points=sub, point_valid=np.ones(keep.size, np.uint8),
+                 point_weight=np.ones(keep.size, np.float32), ref_feat=refs, qry_feat=qry,
+                 fx=tc.f0, fy=tc.f0, cx=cx0, cy=cy0, T_hyps=T_loc.reshape(1, 12).copy(), T_gt=T_loc,
+                 use_gravity=True, gravity_cam=g_meas, gravity_world=GRAVITY_WORLD.copy(), w_grav=tc.w_grav,
+                 use_range=True, range_m=float(rng_meas), w_range=tc.w_range,
+                 dsm=gmap.dsm, dsm_x0=gmap.x0 - ox, dsm_y0=gmap.y0 - oy, dsm_gsd=gmap.gsd,
+                 seed=seed, meta=dict(t=t, degraded=degraded, origin=(ox, oy), n_eligible=int(cand.size)))
+
+
+class SyntheticNetwork:
+    """The feature extractor's place in a tracked sequence: frame t's crop -> (Frame, device
+    arrays without T_cw).  Query pyramids of the bank are uploaded once and shared; the
+    per-frame anchors and reference descriptors come from track_inputs."""
+
+    def __init__(self, gmap: GlobalMap, tc: TrackConfig, bank: list, gt_poses: np.ndarray, seed: int,
+                 device: str = "cuda"):
+        self.gmap, self.tc, self.bank, self.gt, self.seed, self.device = gmap, tc, bank, gt_poses, seed, device
+        self._qdev = {}
+        self.frames = {}
+
+    def frame(self, t: int, crop: dict) -> Frame:
+        return track_inputs(self.gmap, self.tc, self.bank, t, self.gt[t], crop["points"], crop["valid"],
+                            crop["origin"], self.seed)
+
+    def __call__(self, t: int, crop: dict):
+        import torch
+        f = self.frame(t, crop)
+        self.frames[t] = f
+        b = t % len(self.bank)
+        if b not in self._qdev:
+            self._qdev[b] = [torch.from_numpy(np.ascontiguousarray(q)).to(self.device) for q in self.bank[b]]
+        to = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(self.device)
+        arrays = dict(points=to(f.points), point_weight=to(f.point_weight), point_valid=to(f.point_valid),
+                      ref_feat=[to(r) for r in f.ref_feat], qry_feat=self._qdev[b])
+        return f, arrays

@@ -44,7 +44,8 @@ def to_oracle_opts(opts: B.Options) -> O.SolverOptions:
     return O.SolverOptions(iters=tuple(opts.iters), lambda0=opts.lambda0, damping_mode=opts.damping_mode,
                            huber_photo=opts.huber_photo, huber_grav=opts.huber_grav,
                            huber_range=opts.huber_range, keep_top_k=tuple(opts.keep_top_k),
-                           min_valid_frac=opts.min_valid_frac)
+                           min_valid_frac=opts.min_valid_frac, gate_grav=opts.gate_grav,
+                           gate_range=opts.gate_range)
 
 
 def boundary_mask(frame, levels, poses) -> np.ndarray:
