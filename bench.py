@@ -352,6 +352,16 @@ def paper_schedule_form(args, B, S, torch, world, stream):
     ts, units = timed(plain, 6)
     out["plain_f32"] = {"ms_per_frame": sum(ts) / len(ts), "value": world * units / (sum(ts) / 1e3), "unit": UNIT}
     solver.close()
+    # one frame through the batched form (one persistent launch per level: all 1210 FP64
+    # steps of an iteration run at once, one per warp)
+    bs = B.Solver(B.Options(max_hyps=1210, max_frames=1, **po))
+
+    def batched1():
+        k[0] ^= 1
+        return bs.solve_batch([fas[k[0]]], stream)[0].hyp_iters
+    ts, units = timed(batched1, 6)
+    out["batched1_f32"] = {"ms_per_frame": sum(ts) / len(ts), "value": world * units / (sum(ts) / 1e3), "unit": UNIT}
+    bs.close()
     for dt in (B.F32, B.BF16):
         bs = B.Solver(B.Options(max_hyps=1210 * 8, max_frames=8, **po))
         qa = [B.FrameArgs(f, B.quantized_device_arrays(f, dt), is_device=True, dtype=dt) for f in frames] * 4

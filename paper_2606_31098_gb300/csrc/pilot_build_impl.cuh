@@ -467,7 +467,7 @@ build_fused_kernel(const FusedBuildParams fp) {
     const int hyp = p.active_idx[slot];
     const int tid = threadIdx.x;
     if (!p.state[hyp].has_cand) {                  // uniform over the CTA
-        if (blockIdx.x == 0 && tid == 0) lm_step(fp.ep, slot, E, *fp.min_valid);
+        if (blockIdx.x == 0 && tid < 32) lm_step(fp.ep, slot, E, &part[0][0], *fp.min_valid, tid);
         return;
     }
     float acc[kNumSums];
@@ -498,9 +498,9 @@ build_fused_kernel(const FusedBuildParams fp) {
         E[tid] = sum;
     }
     __syncthreads();
-    if (tid == 0) {
-        lm_step(fp.ep, slot, E, *fp.min_valid);
-        fp.tickets[slot] = 0u;
+    if (tid < 32) {                                // the warp-cooperative FP64 step
+        lm_step(fp.ep, slot, E, &part[0][0], *fp.min_valid, tid);
+        if (tid == 0) fp.tickets[slot] = 0u;
     }
 }
 

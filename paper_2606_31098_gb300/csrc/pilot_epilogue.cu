@@ -19,7 +19,7 @@ namespace pilot {
 namespace {
 
 // One block of 256 threads per hypothesis slot: FP64 sum of the tile records (8 partial
-// chains per value, combined in a fixed order), then the single-thread FP64 LM step.
+// chains per value, combined in a fixed order), then the FP64 LM step on warp 0.
 __global__ void epilogue_kernel(const EpilogueParams p, const double* min_valid_ptr) {
     const int slot = blockIdx.x;
     __shared__ double part[8][kAcc];
@@ -40,9 +40,9 @@ __global__ void epilogue_kernel(const EpilogueParams p, const double* min_valid_
         }
     }
     __syncthreads();
-    if (threadIdx.x != 0) return;
+    if (threadIdx.x >= 32) return;                 // warp 0 runs the FP64 step
     const double min_valid = (p.mode == kEpiEval) ? 0.0 : *min_valid_ptr;
-    lm_step(p, slot, E, min_valid);
+    lm_step(p, slot, E, &part[0][0], min_valid, threadIdx.x);
 }
 
 __global__ void hyp_init_kernel(HypState* st, const double* T_cw, int* active_idx, int M) {

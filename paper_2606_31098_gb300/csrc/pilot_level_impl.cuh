@@ -59,7 +59,7 @@ __device__ __forceinline__ bool grid_sync(unsigned long long* sync, unsigned* er
 // consecutive anchor tiles of one job) of every job that has a pose to evaluate, from one
 // counter, and write each tile's FP32 record exactly as build_fused_kernel does (same thread
 // mapping, same sums); after a grid barrier each job's
-// FP64 step runs on lane 0 of one warp, on the tile records summed in the plain form's
+// FP64 step runs on one warp (all lanes), on the tile records summed in the plain form's
 // 8-chain FP64 order, and writes the job's next candidate; a second barrier ends the
 // iteration.  A frame's result is therefore bitwise the one its plain solve gives, whatever
 // else is in the batch; the items balance the gathers over all CTAs, and the FP64 steps of
@@ -71,6 +71,7 @@ level_persistent_kernel(const LevelArgs a) {
     constexpr unsigned kEval = 0x80000000u;          // job_meta: "has a pose to evaluate" bit
     __shared__ float red[kWarps][kAcc];
     __shared__ double E[kWarps][kAcc];
+    __shared__ double Wsh[kWarps][128];         // FP64 step scratch, one block per warp
     __shared__ float pose[12];
     __shared__ long long s_item;
     __shared__ int s_frame, s_job, s_first, s_t0;
@@ -110,7 +111,7 @@ level_persistent_kernel(const LevelArgs a) {
     unsigned gen = 0;
     // level start of every job: its hypothesis, LM state and FP32 start pose (pose32 and
     // job_meta are indexed by job within this launch).  Job j's state is only ever read and
-    // written by lane 0 of global warp j (mod the warp count), here and in the steps below,
+    // written by global warp j (mod the warp count; lane 0 here, all lanes in the steps below),
     // so one SM's L1 sees all its accesses; other CTAs read pose32 and job_meta from L2.
     for (int job = blockIdx.x * kWarps + warp; job < n_jobs; job += n_warps) {
         if (lane != 0) continue;
@@ -170,7 +171,7 @@ level_persistent_kernel(const LevelArgs a) {
             __syncthreads();
         }
         if (!grid_sync(a.sync, a.error, gen, a.barrier_timeout_ns, a.barrier_extra)) return;
-        // FP64 steps: job j on lane 0 of global warp j (mod the warp count)
+        // FP64 steps: job j on global warp j (mod the warp count), all 32 lanes
         for (int job = blockIdx.x * kWarps + warp; job < n_jobs; job += n_warps) {
             const int i = find(false, job);
             const int f = flist(i);
@@ -194,12 +195,10 @@ level_persistent_kernel(const LevelArgs a) {
                 E[warp][lane] = sum;
             }
             __syncwarp();
-            if (lane == 0) {
-                HypState& st = a.state[hyp];
-                lm_update(st, k == 0 ? kEpiInit : kEpiStep, k < iters, a.damping_mode, fd->prior, E[warp],
-                          a.min_valid[f], a.pose32 + 12 * (size_t)job, nullptr);
-                a.job_meta[job] = (unsigned)hyp | (st.has_cand ? kEval : 0u);
-            }
+            HypState& st = a.state[hyp];
+            lm_update(st, k == 0 ? kEpiInit : kEpiStep, k < iters, a.damping_mode, fd->prior, E[warp], Wsh[warp],
+                      a.min_valid[f], a.pose32 + 12 * (size_t)job, nullptr, lane);
+            if (lane == 0) a.job_meta[job] = (unsigned)hyp | (st.has_cand ? kEval : 0u);
             __syncwarp();
         }
         if (!grid_sync(a.sync, a.error, gen, a.barrier_timeout_ns, a.barrier_extra)) return;
