@@ -477,6 +477,14 @@ build_fused_kernel(const FusedBuildParams fp) {
     accumulate_anchors<DT, C, SCALED, CONF, kBuildThreads>(level_view(p), p.pose32 + 12 * hyp, j0,
                                                      min(j0 + p.tile, p.N), acc);
     const float v = cta_reduce<kBuildThreads>(acc, red);
+    if (p.n_tiles == 1) {
+        // the only tile: its record is the sum (0 + x is what the 8-chain sum gives), no
+        // round trip through the partial buffer and the ticket
+        if (tid < kAcc) E[tid] = 0.0 + (double)v;
+        __syncthreads();
+        if (tid < 32) lm_step(fp.ep, slot, E, &part[0][0], *fp.min_valid, tid);
+        return;
+    }
     float* out = p.partial + ((size_t)slot * p.n_tiles + blockIdx.x) * kAcc;
     if (tid < kAcc) out[tid] = v;
     __threadfence();

@@ -100,7 +100,7 @@ __device__ inline void add_range(const PriorParams& pp, const double* T, double*
     double P[3];
 #pragma unroll
     for (int i = 0; i < 3; ++i) P[i] = T[i] * d[0] + T[4 + i] * d[1] + T[8 + i] * d[2];  // R^T d
-    const double inv_gsd = 1.0 / pp.dsm_gsd;
+    const double inv_gsd = pp.dsm_inv_gsd;
     const double gx = (P[0] - pp.dsm_x0) * inv_gsd - 0.5;
     const double gy = (P[1] - pp.dsm_y0) * inv_gsd - 0.5;
     if (!(gx >= 0.0 && gx <= pp.dsm_W - 1.0 && gy >= 0.0 && gy <= pp.dsm_H - 1.0)) return;
@@ -270,11 +270,18 @@ __device__ __forceinline__ void store_pose32(float* dst, const double* T) {
 static __device__ __noinline__ void lm_update(HypState& st, int mode, int solve_next, int damping_mode,
                                               const PriorParams& prior, double* E, double* W,
                                               double min_valid, float* cand32, double* eval_out, int lane) {
+    // every read of the state is issued here, before any write, as one round trip
     const int has_cand = st.has_cand;
     const double cost0 = st.cost;
     const double lambda0 = st.lambda;
+    const double* Tsrc = (mode == kEpiStep) ? st.Tc : st.T;
+    double Tev[12];
+#pragma unroll
+    for (int i = 0; i < 12; ++i) Tev[i] = Tsrc[i];
+    const double Hg_own = lane < 21 ? st.H[lane] : (lane < 27 ? st.g[lane - 21] : 0.0);
+    const double T_own = lane < 12 ? st.T[lane] : 0.0;
+    const double Tc_own = lane < 12 ? st.Tc[lane] : 0.0;
     const bool evaluated = (mode == kEpiStep) ? (has_cand != 0) : true;
-    const double* Tev = (mode == kEpiStep) ? st.Tc : st.T;
     if (evaluated) {
         if (prior.use_gravity) add_gravity(prior, Tev, E, lane);
         __syncwarp();
@@ -295,8 +302,8 @@ static __device__ __noinline__ void lm_update(HypState& st, int mode, int solve_
         take = E[27] < cost0 && E[28] >= min_valid;
         lambda = take ? fmax(lambda0 / 10.0, kLambdaMin) : fmin(lambda0 * 10.0, kLambdaMax);
     }
-    if (lane < 27) W[lane] = take ? E[lane] : (lane < 21 ? st.H[lane] : st.g[lane - 21]);
-    if (lane < 12) W[32 + lane] = (take && mode == kEpiStep) ? st.Tc[lane] : st.T[lane];
+    if (lane < 27) W[lane] = take ? E[lane] : Hg_own;
+    if (lane < 12) W[32 + lane] = (take && mode == kEpiStep) ? Tc_own : T_own;
     __syncwarp();
     if (take) {
         if (lane < 21) st.H[lane] = E[lane];

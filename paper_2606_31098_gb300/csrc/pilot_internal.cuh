@@ -87,7 +87,7 @@ struct PriorParams {
     double gate_grav, gate_range;   // residual gates (0 = none)
     const float* dsm;
     int dsm_H, dsm_W;
-    double dsm_x0, dsm_y0, dsm_gsd;
+    double dsm_x0, dsm_y0, dsm_gsd, dsm_inv_gsd;   // inv = 1 / gsd
 };
 
 enum EpilogueMode { kEpiInit = 0, kEpiStep = 1, kEpiEval = 2 };

@@ -361,6 +361,7 @@ PriorParams prior_params(const pilot_align_config& c, const pilot_frame* f, cons
     pp.dsm_x0 = f->dsm_x0;
     pp.dsm_y0 = f->dsm_y0;
     pp.dsm_gsd = f->dsm_gsd;
+    pp.dsm_inv_gsd = 1.0 / f->dsm_gsd;
     return pp;
 }
 

@@ -186,6 +186,9 @@ extern "C" pilot_status pilot_align_normal_eq_noalloc(const pilot_align_config* 
     pp.dsm_x0 = f->dsm_x0;
     pp.dsm_y0 = f->dsm_y0;
     pp.dsm_gsd = f->dsm_gsd;
+    pp.dsm_inv_gsd = 1.0 / f->dsm_gsd;
+    pp.gate_grav = cfg->gate_grav;
+    pp.gate_range = cfg->gate_range;
     e = launch_epilogue(ep, min_valid, s);
     if (e != cudaSuccess) return fail_msg(PILOT_ECUDA, std::string("epilogue launch: ") + cudaGetErrorString(e));
     return PILOT_OK;
