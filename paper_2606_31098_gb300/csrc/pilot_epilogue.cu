@@ -94,11 +94,11 @@ __device__ __forceinline__ void rank_key(const HypState& h, double min_valid, in
     *c = (u >> 63) ? ~u : (u | 0x8000000000000000ull);
 }
 
-__device__ __forceinline__ bool key_before(int bad_a, unsigned long long ca, int ia, int bad_b,
-                                           unsigned long long cb, int ib) {
-    if (bad_a != bad_b) return !bad_a;
-    if (ca != cb) return ca < cb;
-    return ia < ib;
+// The (unusable, cost image, index) order as one lexicographic comparison of two 64-bit
+// words: hi = unusable bit | cost image >> 1, lo = lowest cost-image bit | index.
+__device__ __forceinline__ ulonglong2 order_key(int bad, unsigned long long c, int idx) {
+    return make_ulonglong2(((unsigned long long)(bad != 0) << 63) | (c >> 1),
+                           ((c & 1ull) << 63) | (unsigned long long)(unsigned)idx);
 }
 
 // Top-K (Supp. "Multi-Hypothesis Refinement") over the n hypotheses listed in act[0, n) of
@@ -112,28 +112,35 @@ __device__ __forceinline__ bool key_before(int bad_a, unsigned long long ca, int
 constexpr int kRankThreads = 256;
 
 __device__ void rank_mark(HypState* S, const int* act, int n, int K, double min_valid, int s_begin) {
-    __shared__ unsigned long long kc[kRankThreads];
-    __shared__ int kb[kRankThreads];
-    __shared__ int ki[kRankThreads];
+    __shared__ ulonglong2 kk[kRankThreads];      // order keys of the current chunk
     const int tid = threadIdx.x;
     const int s = s_begin + tid;
-    int m = -1, bad = 1, rank = 0;
-    unsigned long long c = 0;
+    int m = -1, rank = 0;
+    ulonglong2 key = make_ulonglong2(~0ull, ~0ull);
     if (s < n) {
+        int bad;
+        unsigned long long c;
         m = act[s];
         rank_key(S[m], min_valid, &bad, &c);
+        key = order_key(bad, c, m);
     }
     for (int c0 = 0; c0 < n; c0 += kRankThreads) {
         __syncthreads();
         if (c0 + tid < n) {
+            int bad;
+            unsigned long long c;
             const int m2 = act[c0 + tid];
-            rank_key(S[m2], min_valid, &kb[tid], &kc[tid]);
-            ki[tid] = m2;
+            rank_key(S[m2], min_valid, &bad, &c);
+            kk[tid] = order_key(bad, c, m2);
         }
         __syncthreads();
         if (s < n) {
             const int lim = min(kRankThreads, n - c0);
-            for (int j = 0; j < lim; ++j) rank += key_before(kb[j], kc[j], ki[j], bad, c, m) ? 1 : 0;
+#pragma unroll 4
+            for (int j = 0; j < lim; ++j) {
+                const ulonglong2 o = kk[j];
+                rank += (o.x < key.x) | ((o.x == key.x) & (o.y < key.y));
+            }
         }
     }
     if (s < n && rank >= K) {
