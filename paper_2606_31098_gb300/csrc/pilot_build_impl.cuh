@@ -387,25 +387,41 @@ __device__ __forceinline__ void accumulate_anchors(const LevelView& v, const flo
             const float dv_dy = v.fy * iz, dv_dz = -v.fy * y * iz * iz;
             const float A0[6] = {du_dx, 0.f, du_dz, y * du_dz, z * du_dx - x * du_dz, -y * du_dx};
             const float A1[6] = {0.f, dv_dy, dv_dz, y * dv_dz - z * dv_dy, -x * dv_dz, x * dv_dy};
+            // A0[1] = A1[0] = 0: the terms they multiply are left out (adding a zero product
+            // leaves an FP32 sum unchanged, so the sums are the same as with them)
             float B0[6], B1[6], W0[6], W1[6];
 #pragma unroll
             for (int k = 0; k < 6; ++k) {
-                B0[k] = fmaf(m00, A0[k], m01 * A1[k]);
-                B1[k] = fmaf(m01, A0[k], m11 * A1[k]);
-                W0[k] = om * A0[k];
-                W1[k] = om * A1[k];
+                if (k == 0) {
+                    B0[k] = m00 * A0[k];
+                    B1[k] = m01 * A0[k];
+                } else if (k == 1) {
+                    B0[k] = m01 * A1[k];
+                    B1[k] = m11 * A1[k];
+                } else {
+                    B0[k] = fmaf(m00, A0[k], m01 * A1[k]);
+                    B1[k] = fmaf(m01, A0[k], m11 * A1[k]);
+                }
+                W0[k] = (k == 1) ? 0.f : om * A0[k];
+                W1[k] = (k == 0) ? 0.f : om * A1[k];
             }
             int e = 0;
 #pragma unroll
             for (int a = 0; a < 6; ++a) {
 #pragma unroll
                 for (int b = a; b < 6; ++b) {
-                    acc[e] = fmaf(W0[a], B0[b], fmaf(W1[a], B1[b], acc[e]));
+                    if (a == 0) acc[e] = fmaf(W0[a], B0[b], acc[e]);
+                    else if (a == 1) acc[e] = fmaf(W1[a], B1[b], acc[e]);
+                    else acc[e] = fmaf(W0[a], B0[b], fmaf(W1[a], B1[b], acc[e]));
                     ++e;
                 }
             }
 #pragma unroll
-            for (int a = 0; a < 6; ++a) acc[21 + a] = fmaf(W0[a], b0, fmaf(W1[a], b1, acc[21 + a]));
+            for (int a = 0; a < 6; ++a) {
+                if (a == 0) acc[21 + a] = fmaf(W0[a], b0, acc[21 + a]);
+                else if (a == 1) acc[21 + a] = fmaf(W1[a], b1, acc[21 + a]);
+                else acc[21 + a] = fmaf(W0[a], b0, fmaf(W1[a], b1, acc[21 + a]));
+            }
             acc[27] += rho;
             acc[28] += 1.0f;
         }
