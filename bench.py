@@ -69,7 +69,31 @@ def parse():
     ap.add_argument("--pin-schedule", default="", metavar="TILE:STREAMS",
                     help="skip the autotuner: plain form with this tile and stream count, batched form with "
                          "this tile (for profiling runs, whose timings would mislead the autotuner)")
+    ap.add_argument("--paper-schedule-only", action="store_true",
+                    help="profiling entry point: only the plain paper-schedule solve (3 warm-up + 20 timed "
+                         "solves of one frame), printed as one JSON line")
     return ap.parse_args()
+
+
+def paper_schedule_only(B, S, torch):
+    """The plain paper-schedule solve alone (see paper_schedule_form), for ncu captures."""
+    f = S.make_frame(S.config_paper_schedule(), S.frame_seed(6, 0))
+    solver = B.Solver(B.Options(iters=(4, 3, 2, 0), keep_top_k=(0, 0, 128, 0), max_points=500, max_hyps=1210))
+    fa = B.FrameArgs(f, B.device_arrays(f), is_device=True)
+    st = torch.cuda.current_stream()
+    for _ in range(3):
+        solver.solve(fa, st)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(st)
+    for _ in range(20):
+        r = solver.solve(fa, st)
+    e1.record(st)
+    e1.synchronize()
+    print(json.dumps({"form": "paper_schedule_plain_f32", "ms_per_frame": e0.elapsed_time(e1) / 20,
+                      "hyp_iters": r.hyp_iters, "schedule": solver.schedule([fa], batched=False)}), flush=True)
+    solver.close()
+    return 0
 
 
 def max_over_ranks(values, world: int, device: str):
@@ -549,6 +573,8 @@ def run_ours(args):
 
     build_ext.build()
     B.load()
+    if args.paper_schedule_only:
+        return paper_schedule_only(B, S, torch)
     frame = S.make_frame(S.config_full_frame(), S.frame_seed(2, rank_seed_index(args.seed_index, rank)))
     opts = B.Options(iters=(10, 10, 10, 0), max_points=frame.N, max_hyps=frame.M, max_channels=32, profile=1)
     solver = B.Solver(opts)
