@@ -52,3 +52,21 @@ def test_gates_change_the_objective(torch):
 def test_negative_gate_is_rejected(torch):
     with pytest.raises(B.PilotError, match="gates"):
         B.Solver(B.Options(gate_range=-1.0))
+
+
+def test_gated_forms_agree_bitwise(torch):
+    """The gates sit in the FP64 step every form shares: plain, batched and served solves of
+    frames with bad readings give bitwise the same outputs."""
+    from test_gpu_batch import args_for, assert_same
+    frames = [bad_sensor_frame(960 + i) for i in range(2)]
+    opts = B.Options(iters=(3, 3, 3, 0), gate_grav=0.05, gate_range=2.0)
+    solver = B.Solver(opts)
+    fas = args_for(frames)
+    plain = [solver.solve(fa) for fa in fas]
+    batch = solver.solve_batch(fas)
+    for i in range(2):
+        assert_same(batch[i], plain[i], what=f"batched frame {i}")
+    server = B.Server(opts, 1 << 30, max_slots=4)
+    res, _ = server.wait(server.submit(fas[0]))
+    assert_same(res, plain[0], what="served frame")
+    server.close()
