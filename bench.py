@@ -692,6 +692,23 @@ def run_ours(args):
         cpu = {"value": u / s, "unit": UNIT, "cores": threads, "kind": "oracle",
                "sample": f"{nh} of the 64 hypotheses of the same frame, all 3 levels x 10 iterations "
                          f"({u} hyp*iter in {s:.1f} s)"}
+        # the same on one core (one hypothesis), per anchor as well, and the small plain
+        # single-frame workload (4096 anchors, 1 hypothesis, one 120x160 level, 20 iterations)
+        u1, s1 = run_oracle_sample(frame, 1, 1)
+        cpu["value_1core"] = u1 / s1
+        cpu["point_hyp_iter_per_s"] = frame.N * u / s
+        cpu["point_hyp_iter_per_s_1core"] = frame.N * u1 / s1
+        from oracle import oracle as O
+        sf = S.make_frame(S.config_small_plain(), S.frame_seed(1, 0))
+        t0 = time.perf_counter()
+        rs = O.solve(sf, O.SolverOptions(iters=(20, 0, 0, 0)), n_threads=1)
+        el = time.perf_counter() - t0
+        cpu["small_plain_1core"] = {"hyp_iter_per_s": rs.hyp_iters / el, "point_hyp_iter_per_s": sf.N * rs.hyp_iters / el}
+        try:
+            cpu["cpu_model"] = next(l.split(":", 1)[1].strip() for l in open("/proc/cpuinfo")
+                                    if l.lower().startswith(("model name", "cpu part")))
+        except (OSError, StopIteration):
+            cpu["cpu_model"] = None
         if paper:
             from oracle import oracle as O
             pf = S.make_frame(S.config_paper_schedule(), S.frame_seed(6, 0))
