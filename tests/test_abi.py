@@ -78,7 +78,8 @@ def test_validate_rejects_malformed_frames(lib, mutation, needle):
 
 
 @pytest.mark.parametrize("field,value", [("lambda0", -1.0), ("damping_mode", 3), ("huber_photo", -0.1),
-                                         ("min_valid_frac", 1.5), ("max_channels", 12)])
+                                         ("min_valid_frac", 1.5), ("max_channels", 12), ("gate_range", -1.0),
+                                         ("gate_grav", float("nan"))])
 def test_validate_rejects_bad_options(lib, field, value):
     f, arrs = small_host_frame()
     opts = B.Options()
@@ -99,3 +100,28 @@ def test_null_arguments_are_errors_not_crashes(lib):
     assert lib.pilot_align_solve(None, None, None, None) == B.PILOT_EINVAL
     lib.pilot_align_destroy(None)
     assert isinstance(B.pilot_align_last_error(), str)
+
+
+def test_confidence_map_alignment_is_checked(lib):
+    f, arrs = small_host_frame()
+    buf = np.zeros(f.qry_feat[0].shape[0] * f.qry_feat[0].shape[1] + 1, np.float32)
+    fa = B.FrameArgs(f, arrs, is_device=False)
+    fa.c.qry_conf[0] = buf.ctypes.data + 2            # not 4-byte aligned
+    st, msg = B.validate(B.Options(), fa)
+    assert st == B.PILOT_EINVAL and "confidence" in msg
+
+
+def test_tracking_entry_points_reject_bad_arguments_before_any_launch(lib):
+    """pilot_seed_hypotheses and pilot_crop_reference validate on the host: these calls fail
+    without touching a device."""
+    T = np.eye(3, 4).ravel()
+    p = B.seed_params(T, [0.0], [0.0])
+    p.n_xy = 0
+    assert lib.pilot_seed_hypotheses(ct.byref(p), None, None) == B.PILOT_EINVAL
+    p.n_xy = 1
+    assert lib.pilot_seed_hypotheses(ct.byref(p), 3, None) == B.PILOT_EINVAL       # misaligned output
+    p.T_prior[0] = float("inf")
+    assert lib.pilot_seed_hypotheses(ct.byref(p), 8, None) == B.PILOT_EINVAL
+    assert lib.pilot_pose_predict(None, None, 1, None) == B.PILOT_EINVAL
+    assert lib.pilot_pose_reorigin(None, 0.0, 0.0, None) == B.PILOT_EINVAL
+    assert lib.pilot_crop_reference(None, None, None, None, None, None, None) == B.PILOT_EINVAL
