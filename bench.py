@@ -69,6 +69,10 @@ def parse():
     ap.add_argument("--pin-schedule", default="", metavar="TILE:STREAMS",
                     help="skip the autotuner: plain form with this tile and stream count, batched form with "
                          "this tile (for profiling runs, whose timings would mislead the autotuner)")
+    ap.add_argument("--crop-only", action="store_true",
+                    help="profiling entry point: only the reference-crop timing, printed as one JSON line")
+    ap.add_argument("--batched-only", action="store_true",
+                    help="profiling entry point: only the batched-form timings, printed as one JSON line")
     ap.add_argument("--paper-schedule-only", action="store_true",
                     help="profiling entry point: only the plain paper-schedule solve (3 warm-up + 20 timed "
                          "solves of one frame), printed as one JSON line")
@@ -211,7 +215,7 @@ def cpu_cores() -> int:
         return os.cpu_count() or 1
 
 
-def batched_and_served(args, B, S, torch, world, stream):
+def batched_and_served(args, B, S, torch, world, stream, served_too: bool = True):
     """The batched form (uneven frames, one persistent launch per level under a graph) and
     the served form (streams at 30 Hz with exponential inter-arrival times), both on BF16
     storage.  Four distinct frames (crops 128^2, 192^2, 256^2, 384^2, 144 hypotheses each)
@@ -261,6 +265,8 @@ def batched_and_served(args, B, S, torch, world, stream):
                "crop256x8_bf16": {"value": v_256, "unit": UNIT, "ms_per_batch": ms_256, "frames": 8,
                                   "hypotheses": 64, "schedule": sc_256}}
 
+    if not served_too:
+        return batched, {}
     # served form: host (page-locked) BF16 frames staged by the server per request
     host = []
     for d in dev:
@@ -578,6 +584,14 @@ def run_ours(args):
     B.load()
     if args.paper_schedule_only:
         return paper_schedule_only(B, S, torch)
+    if args.crop_only:
+        out, _, _ = crop_form(B, S, torch, torch.cuda.current_stream())
+        print(json.dumps({"form": "crop", **out}), flush=True)
+        return 0
+    if args.batched_only:
+        out, _ = batched_and_served(args, B, S, torch, world, torch.cuda.current_stream(), served_too=False)
+        print(json.dumps({"form": "batched", **out}), flush=True)
+        return 0
     frame = S.make_frame(S.config_full_frame(), S.frame_seed(2, rank_seed_index(args.seed_index, rank)))
     opts = B.Options(iters=(10, 10, 10, 0), max_points=frame.N, max_hyps=frame.M, max_channels=32, profile=1)
     solver = B.Solver(opts)
