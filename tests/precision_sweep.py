@@ -9,7 +9,7 @@ hypotheses per seed in FP64 would take minutes per seed; hypotheses are independ
 subset gives the same end points.)  Also reported: the error of the oracle's end point
 against the synthetic ground truth.
 
-    python tests/precision_sweep.py --seeds 64 --out gpurun_out/precision_sweep.json
+    python tests/precision_sweep.py --seeds 64 --out precision_sweep.json
 
 Test infrastructure (it runs the oracle); not collected by pytest.
 """
