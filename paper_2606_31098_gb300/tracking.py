@@ -26,6 +26,10 @@ import numpy as np
 from . import binding as B
 
 
+class CropFailure(RuntimeError):
+    """The reference crop around a prior failed (a corner ray never met the DSM)."""
+
+
 @dataclass
 class Camera:
     fx: float
@@ -131,7 +135,7 @@ class SequentialTracker:
         e1.synchronize()
         g = h["geometry"].numpy()
         if g[27] != 1.0:
-            raise RuntimeError("the reference crop failed (a corner ray never met the DSM)")
+            raise CropFailure("the reference crop failed (a corner ray never met the DSM)")
         return dict(points=h["points"].numpy(), valid=h["valid"].numpy(), origin=(float(g[9]), float(g[10])),
                     geometry=g.copy(), crop_ms=e0.elapsed_time(e1), slot=slot)
 
@@ -174,19 +178,31 @@ class SequentialTracker:
     def localise(self, t: int, network):
         """Localise frame t (frames are given in order).  `network(t, crop)` returns
         (frame, device_arrays): a scenes.Frame in the crop's local frame and its device
-        arrays (no T_cw).  Returns (world estimate, Result)."""
+        arrays (no T_cw).  Returns (world estimate, Result); when the crop around the prior
+        fails, the prior is the estimate and the Result is None."""
         torch = self.torch
         if t != len(self.state.history):
             raise ValueError(f"frame {t} out of order (expected {len(self.state.history)})")
         w0 = time.perf_counter()
         prior = self._prior(t)
-        prepared = self._take_prepared(t) if self.mode == "lookahead" else None
-        if prepared is not None:
-            crop_pose, crop = prepared
-            self._slot = crop["slot"]
-        else:
-            crop_pose = prior.copy()
-            crop = self._crop(crop_pose, self._slot)
+        prepared = None
+        try:
+            prepared = self._take_prepared(t) if self.mode == "lookahead" else None
+            if prepared is not None:
+                crop_pose, crop = prepared
+                self._slot = crop["slot"]
+            else:
+                crop_pose = prior.copy()
+                crop = self._crop(crop_pose, self._slot)
+        except CropFailure:
+            # no reference for this frame: the prior stands as its estimate
+            self._next_given = None
+            st = self.state
+            st.history.append(prior.copy())
+            st.priors.append(prior)
+            st.crop_poses.append(prior.copy())
+            st.timings.append(FrameTiming(0.0, 0.0, 1e3 * (time.perf_counter() - w0), False))
+            return prior.copy(), None
         self._next_given = None
         if self.mode == "lookahead":
             self._start_prepare(t + 1)     # map preparation of frame t+1 runs meanwhile
