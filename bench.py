@@ -280,9 +280,13 @@ def batched_and_served(args, B, S, torch, world, stream, served_too: bool = True
     sweep, sweep_paper = [], []
     budget = 16 << 30
     # 10 iterations per level, then the paper's 2 / 3 / 4 (coarse to fine)
-    for iters, streams, out in [((10, 10, 10, 0), 2, sweep), ((10, 10, 10, 0), 8, sweep), ((10, 10, 10, 0), 64, sweep),
-                                ((4, 3, 2, 0), 8, sweep_paper), ((4, 3, 2, 0), 64, sweep_paper)]:
+    sweep_levels = []
+    for iters, streams, out, lpr in [((10, 10, 10, 0), 2, sweep, 1), ((10, 10, 10, 0), 8, sweep, 1),
+                                     ((10, 10, 10, 0), 64, sweep, 1), ((4, 3, 2, 0), 8, sweep_paper, 1),
+                                     ((4, 3, 2, 0), 64, sweep_paper, 1), ((10, 10, 10, 0), 2, sweep_levels, 3),
+                                     ((4, 3, 2, 0), 8, sweep_levels, 3)]:
         server = B.Server(B.Options(iters=iters, max_points=384 * 384, max_hyps=64 * 144), budget, max_slots=64)
+        server.set_levels_per_round(lpr)
         duration = 3.0
         arrivals = []
         for s_ in range(streams):
@@ -336,13 +340,15 @@ def batched_and_served(args, B, S, torch, world, stream, served_too: bool = True
         span = (max(done_t) - t0) if done_t else 1.0
         st = server.stats()
         server.close()
-        out.append({"streams": streams, "offered_fps": len(arrivals) / duration,
+        out.append({"streams": streams, "iters": list(iters[:3]), "levels_per_round": lpr,
+                    "offered_fps": len(arrivals) / duration,
                       "completed_fps": len(lat) / span, "rejected_ebusy": rejected,
                       "hyp_iter_per_s": nonlocal_units[0] / span,
                       "p50_ms": float(np.percentile(lat, 50)) if lat else None,
                       "p99_ms": float(np.percentile(lat, 99)) if lat else None,
                       "peak_active": st["peak_active"], "rounds": st["rounds"]})
-    served = {"sweep": sweep, "sweep_paper_iterations": sweep_paper, "hbm_budget_bytes": budget,
+    served = {"sweep": sweep, "sweep_paper_iterations": sweep_paper, "sweep_three_levels_per_round": sweep_levels,
+              "hbm_budget_bytes": budget,
               "max_slots": 64, "storage": "bf16",
               "arrivals": "30 Hz per stream, exponential inter-arrival (mean 33 ms), 3 s",
               "frames": "host page-locked BF16 frames, crops 128^2..384^2, 16..144 hypotheses"}

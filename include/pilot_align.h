@@ -412,6 +412,15 @@ pilot_status pilot_serve_poll(pilot_server* s, uint64_t ticket, pilot_result* re
 pilot_status pilot_serve_wait(pilot_server* s, uint64_t ticket, pilot_result* result,
                               double* latency_ms, int timeout_ms);
 
+/* Pyramid levels every admitted frame advances per round (1 by default: one level per round,
+ * so frames that arrive meanwhile join after at most one level's work).  With n > 1 each round
+ * runs n levels back to back (one persistent launch each; between them the device applies
+ * the top-K and moves every listed frame to its next level), so a frame needs fewer rounds:
+ * lower latency when the load is light, longer rounds for frames that arrive meanwhile.
+ * Outputs are the same bitwise.  Only before the first pilot_serve_submit; EINVAL otherwise
+ * or for n outside [1, 4]. */
+pilot_status pilot_serve_set_levels_per_round(pilot_server* s, int levels);
+
 pilot_status pilot_serve_get_stats(pilot_server* s, pilot_serve_stats* out);
 
 /* Stops the worker after its current round and releases everything; tickets not yet

@@ -87,6 +87,7 @@ SIGNATURES = {
     "pilot_serve_poll": (ct.c_int, [_vp, ct.c_uint64, ct.POINTER(pilot_result), ct.POINTER(ct.c_int),
                                     ct.POINTER(ct.c_double)]),
     "pilot_serve_wait": (ct.c_int, [_vp, ct.c_uint64, ct.POINTER(pilot_result), ct.POINTER(ct.c_double), ct.c_int]),
+    "pilot_serve_set_levels_per_round": (ct.c_int, [_vp, ct.c_int]),
     "pilot_serve_get_stats": (ct.c_int, [_vp, _vp]),
     "pilot_serve_destroy": (None, [_vp]),
 }
@@ -565,6 +566,10 @@ class Server:
         check(lib.pilot_serve_create(ct.byref(self._cfg), int(hbm_budget), int(max_slots), ct.byref(h)))
         self.h = h
         self._frames = {}
+
+    def set_levels_per_round(self, levels: int):
+        """pilot_serve_set_levels_per_round (before the first submit)."""
+        check(load().pilot_serve_set_levels_per_round(self.h, int(levels)))
 
     def submit(self, fa: FrameArgs) -> int:
         """Queue a frame; returns its ticket (raises PilotError, status PILOT_EBUSY, when the

@@ -432,7 +432,45 @@ __global__ void round_finish_kernel(const BatchHeader* hdr, const FrameDesc* fra
     if (f.flags & kFlagFinalize) finalize_frame(f, fi, st, min_valid[fi], res, max_hyps);
 }
 
+// Serving round with several levels: after a level's finish, every listed frame moves on to
+// its next level on the device (what the host does between one-level rounds): a frame that
+// finished level 0 (finalised) drops out with no jobs; the others take their top-K, step to
+// the next finer level and get that level's flags; the job and item tables are rebuilt in
+// list order.  One thread: at most max_slots frames.
+__global__ void round_advance_kernel(const BatchHeader* hdr, FrameDesc* frames, const int* fr_list, int* fr_item,
+                                     int* fr_job, LevelKeep keep, int tile, int tpi) {
+    if (blockIdx.x != 0 || threadIdx.x != 0) return;
+    const int nl = hdr->n_listed[0];
+    fr_item[0] = 0;
+    fr_job[0] = 0;
+    for (int i = 0; i < nl; ++i) {
+        FrameDesc& f = frames[fr_list[i]];
+        if (f.n_active > 0) {
+            if (f.level == 0) {
+                f.n_active = 0;
+                f.flags = 0;
+            } else {
+                if (f.flags & kFlagPrune) f.n_active = f.keep;
+                f.level -= 1;
+                const int K = keep.k[f.level];
+                f.keep = K;
+                f.flags = ((f.level > 0 && K > 0 && K < f.n_active) ? kFlagPrune : 0) | (f.level == 0 ? kFlagFinalize : 0);
+            }
+        } else {
+            f.flags = 0;
+        }
+        fr_job[i + 1] = fr_job[i] + f.n_active;
+        fr_item[i + 1] = fr_item[i] + f.n_active * items_per_job(f.N, tile, tpi);
+    }
+}
+
 }  // namespace
+
+cudaError_t launch_round_advance(const BatchHeader* hdr, FrameDesc* frames, const int* fr_list, int* fr_item,
+                                 int* fr_job, const LevelKeep& keep, int tile, int tpi, cudaStream_t s) {
+    round_advance_kernel<<<1, 32, 0, s>>>(hdr, frames, fr_list, fr_item, fr_job, keep, tile, tpi);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_batch_init(const BatchHeader* hdr, const FrameDesc* frames, HypState* st,
                               int* active, int max_frames, cudaStream_t s) {

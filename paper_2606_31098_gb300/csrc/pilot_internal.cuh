@@ -235,6 +235,11 @@ cudaError_t launch_batch_finalize(const BatchHeader* hdr, const FrameDesc* frame
                                   const double* min_valid, unsigned char* result, int max_hyps,
                                   int max_frames, cudaStream_t s);
 // serving rounds: the same steps, each frame doing only what its flags ask for
+struct LevelKeep {
+    int k[PILOT_MAX_LEVELS];   // keep_top_k per level
+};
+cudaError_t launch_round_advance(const BatchHeader* hdr, FrameDesc* frames, const int* fr_list, int* fr_item,
+                                 int* fr_job, const LevelKeep& keep, int tile, int tpi, cudaStream_t s);
 cudaError_t launch_round_prepare(const BatchHeader* hdr, const FrameDesc* frames, HypState* st,
                                  int* active, double frac, double* min_valid, int max_frames,
                                  cudaStream_t s);

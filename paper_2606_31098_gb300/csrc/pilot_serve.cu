@@ -161,6 +161,7 @@ struct pilot_server {
     pilot_dtype dt = PILOT_F32;
     int C = 0, L = 0;
     int variant = 0;           // kVariantScaled | kVariantConf, shared by every served frame
+    int levels_per_round = 1;  // pyramid levels each admitted frame advances per round
     std::thread worker;
     std::mutex mu;
     std::condition_variable cv_work, cv_done;
@@ -255,45 +256,52 @@ cudaError_t capture_round(pilot_server* s) {
     e = cudaMemcpyAsync(s->desc_dev, s->desc_host, s->desc_bytes, cudaMemcpyHostToDevice, s->stream);
     unsigned* error = reinterpret_cast<unsigned*>(s->res_dev + ResultLayout::make(s->cfg.max_hyps).bytes +
                                                   sizeof(int) * (size_t)s->max_slots);
-    if (e == cudaSuccess) e = cudaMemsetAsync(s->sync, 0, sizeof(unsigned long long) * kSyncWords, s->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(error, 0, sizeof(unsigned), s->stream);
     if (e == cudaSuccess)
         e = launch_round_prepare(hdr, frames, s->state, s->active, s->cfg.min_valid_frac, s->min_valid,
                                  s->max_slots, s->stream);
-    if (e == cudaSuccess) {
-        LevelArgs a{};
-        a.header = hdr;
-        a.frames = frames;
-        a.fr_list = reinterpret_cast<const int*>(s->desc_dev + s->off_fr_list);
-        a.fr_item = reinterpret_cast<const int*>(s->desc_dev + s->off_fr_item);
-        a.fr_job = reinterpret_cast<const int*>(s->desc_dev + s->off_fr_job);
-        a.active = s->active;
-        a.state = s->state;
-        a.min_valid = s->min_valid;
-        a.pose32 = s->pose32;
-        a.job_meta = s->job_meta;
-        a.partial = s->partial;
-        a.sync = s->sync;
-        a.error = error;
-        a.barrier_timeout_ns = kBarrierTimeoutNs;
-        a.barrier_extra = 0;
-        a.level = -1;
-        a.list_index = 0;
-        a.k_max = 0;
-        for (int l = 0; l < PILOT_MAX_LEVELS; ++l) {
-            a.iters[l] = s->cfg.iters_per_level[l];
-            a.k_max = std::max(a.k_max, a.iters[l]);
-        }
-        a.tile = kPlainTile;
-        a.tiles_per_item = tiles_per_item(kPlainTile);
-        a.damping_mode = s->cfg.damping_mode;
-        a.huber = (float)s->cfg.huber_photo;
-        a.lambda0 = s->cfg.lambda0;
-        e = level_launch(s->dt, s->C, s->variant, a, s->grid, s->stream);
+    LevelArgs a{};
+    a.header = hdr;
+    a.frames = frames;
+    a.fr_list = reinterpret_cast<const int*>(s->desc_dev + s->off_fr_list);
+    a.fr_item = reinterpret_cast<const int*>(s->desc_dev + s->off_fr_item);
+    a.fr_job = reinterpret_cast<const int*>(s->desc_dev + s->off_fr_job);
+    a.active = s->active;
+    a.state = s->state;
+    a.min_valid = s->min_valid;
+    a.pose32 = s->pose32;
+    a.job_meta = s->job_meta;
+    a.partial = s->partial;
+    a.sync = s->sync;
+    a.error = error;
+    a.barrier_timeout_ns = kBarrierTimeoutNs;
+    a.barrier_extra = 0;
+    a.level = -1;
+    a.list_index = 0;
+    a.k_max = 0;
+    LevelKeep keep{};
+    for (int l = 0; l < PILOT_MAX_LEVELS; ++l) {
+        a.iters[l] = s->cfg.iters_per_level[l];
+        a.k_max = std::max(a.k_max, a.iters[l]);
+        keep.k[l] = s->cfg.keep_top_k[l];
     }
-    if (e == cudaSuccess)
-        e = launch_round_finish(hdr, frames, s->state, s->active, s->min_valid, s->res_dev, s->cfg.max_hyps,
-                                s->max_slots, std::min(s->cfg.max_hyps, kMaxFrameHyps), s->stream);
+    a.tile = kPlainTile;
+    a.tiles_per_item = tiles_per_item(kPlainTile);
+    a.damping_mode = s->cfg.damping_mode;
+    a.huber = (float)s->cfg.huber_photo;
+    a.lambda0 = s->cfg.lambda0;
+    // levels_per_round sub-rounds: each advances every listed frame by one level (a frame that
+    // finishes level 0 is finalised and has no jobs in the later sub-rounds)
+    for (int sub = 0; sub < s->levels_per_round && e == cudaSuccess; ++sub) {
+        if (sub > 0)
+            e = launch_round_advance(hdr, const_cast<FrameDesc*>(frames), a.fr_list, const_cast<int*>(a.fr_item),
+                                     const_cast<int*>(a.fr_job), keep, a.tile, a.tiles_per_item, s->stream);
+        if (e == cudaSuccess) e = cudaMemsetAsync(s->sync, 0, sizeof(unsigned long long) * kSyncWords, s->stream);
+        if (e == cudaSuccess) e = level_launch(s->dt, s->C, s->variant, a, s->grid, s->stream);
+        if (e == cudaSuccess)
+            e = launch_round_finish(hdr, frames, s->state, s->active, s->min_valid, s->res_dev, s->cfg.max_hyps,
+                                    s->max_slots, std::min(s->cfg.max_hyps, kMaxFrameHyps), s->stream);
+    }
     if (e == cudaSuccess) e = cudaMemcpyAsync(s->res_host, s->res_dev, s->res_bytes, cudaMemcpyDeviceToHost, s->stream);
     cudaGraph_t g = nullptr;
     const cudaError_t e2 = cudaStreamEndCapture(s->stream, &g);
@@ -401,12 +409,20 @@ void after_round(pilot_server* s) {
     std::vector<Request*> still;
     const double t = now_ms();
     for (Request* r : s->running) {
+        // the round advanced every listed frame by up to levels_per_round levels
         r->initialized = true;
-        r->hyp_iters += (long long)r->n_active * c.iters_per_level[r->level];
-        const int K = c.keep_top_k[r->level];
-        if (r->level > 0 && K > 0 && K < r->n_active) r->n_active = K;
-        if (r->level > 0) {
+        bool finished = false;
+        for (int sub = 0; sub < s->levels_per_round; ++sub) {
+            r->hyp_iters += (long long)r->n_active * c.iters_per_level[r->level];
+            const int K = c.keep_top_k[r->level];
+            if (r->level > 0 && K > 0 && K < r->n_active) r->n_active = K;
+            if (r->level == 0) {
+                finished = true;
+                break;
+            }
             --r->level;
+        }
+        if (!finished) {
             still.push_back(r);
             continue;
         }
@@ -615,6 +631,15 @@ pilot_status pilot_serve_wait(pilot_server* s, uint64_t ticket, pilot_result* re
         if (now_ms() >= deadline) return sfail(PILOT_ETIMEOUT, "wait timed out");
         s->cv_done.wait_for(lock, std::chrono::milliseconds(1));
     }
+}
+
+pilot_status pilot_serve_set_levels_per_round(pilot_server* s, int levels) {
+    if (!s) return sfail(PILOT_EINVAL, "server is NULL");
+    if (levels < 1 || levels > PILOT_MAX_LEVELS) return sfail(PILOT_EINVAL, "levels_per_round must be in [1, 4]");
+    std::unique_lock<std::mutex> lock(s->mu);
+    if (s->key_set) return sfail(PILOT_EINVAL, "set levels_per_round before the first frame is submitted");
+    s->levels_per_round = levels;
+    return PILOT_OK;
 }
 
 pilot_status pilot_serve_get_stats(pilot_server* s, pilot_serve_stats* out) {

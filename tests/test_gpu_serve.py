@@ -41,6 +41,32 @@ def test_served_mix_equals_plain_solves(torch):
     server.close()
 
 
+@pytest.mark.parametrize("levels", [2, 3])
+def test_several_levels_per_round_equal_plain_solves(torch, levels):
+    """With several levels per round the device advances each frame between launches (top-K,
+    next level, job tables); frames arriving mid-way join the next round. Outputs stay
+    bitwise those of the plain solves, with pruning on."""
+    frames = uneven_frames(sides=(40, 55, 70, 30, 62), hyps=(9, 7, 12, 5, 8), base=1150)
+    fas = args_for(frames)
+    opts = B.Options(iters=(3, 4, 2, 0), keep_top_k=(0, 3, 4, 0))
+    plain = [B.Solver(opts).solve(fa) for fa in fas]
+    server = B.Server(opts, BUDGET, max_slots=8)
+    server.set_levels_per_round(levels)
+    tickets = []
+    for i, fa in enumerate(fas):
+        tickets.append(server.submit(fa))
+        if i == 2:
+            time.sleep(0.003)
+    for i, t in enumerate(tickets):
+        res, _ = server.wait(t)
+        assert_same(res, plain[i], what=f"frame {i}, {levels} levels per round")
+    st = server.stats()
+    assert st["completed"] == len(fas) and st["active"] == 0
+    with pytest.raises(B.PilotError, match="before the first frame"):
+        server.set_levels_per_round(1)
+    server.close()
+
+
 def test_result_alone_equals_result_in_the_mix(torch):
     frames = uneven_frames(sides=(48, 66, 35), hyps=(5, 3, 6), base=1200)
     fas = args_for(frames, B.BF16)
