@@ -284,7 +284,8 @@ def batched_and_served(args, B, S, torch, world, stream, served_too: bool = True
     for iters, streams, out, lpr in [((10, 10, 10, 0), 2, sweep, 1), ((10, 10, 10, 0), 8, sweep, 1),
                                      ((10, 10, 10, 0), 64, sweep, 1), ((4, 3, 2, 0), 8, sweep_paper, 1),
                                      ((4, 3, 2, 0), 64, sweep_paper, 1), ((10, 10, 10, 0), 2, sweep_levels, 3),
-                                     ((4, 3, 2, 0), 8, sweep_levels, 3)]:
+                                     ((4, 3, 2, 0), 8, sweep_levels, 3), ((10, 10, 10, 0), 2, sweep_levels, 0),
+                                     ((4, 3, 2, 0), 8, sweep_levels, 0)]:
         server = B.Server(B.Options(iters=iters, max_points=384 * 384, max_hyps=64 * 144), budget, max_slots=64)
         server.set_levels_per_round(lpr)
         duration = 3.0
@@ -347,7 +348,7 @@ def batched_and_served(args, B, S, torch, world, stream, served_too: bool = True
                       "p50_ms": float(np.percentile(lat, 50)) if lat else None,
                       "p99_ms": float(np.percentile(lat, 99)) if lat else None,
                       "peak_active": st["peak_active"], "rounds": st["rounds"]})
-    served = {"sweep": sweep, "sweep_paper_iterations": sweep_paper, "sweep_three_levels_per_round": sweep_levels,
+    served = {"sweep": sweep, "sweep_paper_iterations": sweep_paper, "sweep_levels_per_round": sweep_levels,
               "hbm_budget_bytes": budget,
               "max_slots": 64, "storage": "bf16",
               "arrivals": "30 Hz per stream, exponential inter-arrival (mean 33 ms), 3 s",

@@ -417,8 +417,10 @@ pilot_status pilot_serve_wait(pilot_server* s, uint64_t ticket, pilot_result* re
  * runs n levels back to back (one persistent launch each; between them the device applies
  * the top-K and moves every listed frame to its next level), so a frame needs fewer rounds:
  * lower latency when the load is light, longer rounds for frames that arrive meanwhile.
+ * With n = 0 the count is chosen per frame and round: a frame whose level work (anchors x
+ * active hypotheses) is at most 2^21 runs all its remaining levels, a larger one one level.
  * Outputs are the same bitwise.  Only before the first pilot_serve_submit; EINVAL otherwise
- * or for n outside [1, 4]. */
+ * or for n outside [0, 4]. */
 pilot_status pilot_serve_set_levels_per_round(pilot_server* s, int levels);
 
 pilot_status pilot_serve_get_stats(pilot_server* s, pilot_serve_stats* out);

@@ -568,7 +568,7 @@ class Server:
         self._frames = {}
 
     def set_levels_per_round(self, levels: int):
-        """pilot_serve_set_levels_per_round (before the first submit)."""
+        """pilot_serve_set_levels_per_round (before the first submit; 0 = chosen per frame by size)."""
         check(load().pilot_serve_set_levels_per_round(self.h, int(levels)))
 
     def submit(self, fa: FrameArgs) -> int:

@@ -434,9 +434,10 @@ __global__ void round_finish_kernel(const BatchHeader* hdr, const FrameDesc* fra
 
 // Serving round with several levels: after a level's finish, every listed frame moves on to
 // its next level on the device (what the host does between one-level rounds): a frame that
-// finished level 0 (finalised) drops out with no jobs; the others take their top-K, step to
-// the next finer level and get that level's flags; the job and item tables are rebuilt in
-// list order.  One thread: at most max_slots frames.
+// finished level 0 (finalised), or that has used its quota of levels for the round, drops out
+// with no jobs; the others take their top-K, step to the next finer level and get that
+// level's flags; the job and item tables are rebuilt in list order.  One thread: at most
+// max_slots frames.
 __global__ void round_advance_kernel(const BatchHeader* hdr, FrameDesc* frames, const int* fr_list, int* fr_item,
                                      int* fr_job, LevelKeep keep, int tile, int tpi) {
     if (blockIdx.x != 0 || threadIdx.x != 0) return;
@@ -445,7 +446,13 @@ __global__ void round_advance_kernel(const BatchHeader* hdr, FrameDesc* frames, 
     fr_job[0] = 0;
     for (int i = 0; i < nl; ++i) {
         FrameDesc& f = frames[fr_list[i]];
-        if (f.n_active > 0) {
+        f.quota -= 1;
+        if (f.n_active > 0 && f.quota <= 0) {
+            // this frame's levels for the round are done: it idles until the next round (the
+            // host carries its level and active count over)
+            f.n_active = 0;
+            f.flags = 0;
+        } else if (f.n_active > 0) {
             if (f.level == 0) {
                 f.n_active = 0;
                 f.flags = 0;

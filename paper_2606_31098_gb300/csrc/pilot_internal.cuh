@@ -138,7 +138,7 @@ struct FrameDesc {
     int n_active;              // serving: hypotheses still active at that level
     int flags;                 // serving: kFlagInit | kFlagPrune | kFlagFinalize
     int keep;                  // serving: top-K after this level (kFlagPrune)
-    int pad;
+    int quota;                 // serving: levels this frame may still run in the current round
     PriorParams prior;
 };
 

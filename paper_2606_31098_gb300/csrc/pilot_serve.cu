@@ -115,13 +115,17 @@ size_t frame_bytes(const pilot_frame& f) {
 
 enum ReqState { kPending = 0, kActive = 1, kDone = 2, kFailed = 3 };
 
+// levels_per_round = 0: a frame whose level work (anchors x active hypotheses) is at most this
+// runs all its remaining levels in one round
+constexpr long long kSmallLevelWork = 1ll << 21;
+
 struct Request {
     uint64_t ticket = 0;
     pilot_frame src{};           // the caller's frame (pointers valid until done)
     pilot_frame dev{};           // the arena copy
     double t_submit = 0, t_admit = 0, t_done = 0;
     size_t arena_off = 0, arena_bytes = 0, hyp_off = 0;
-    int slot = -1, level = 0, n_active = 0;
+    int slot = -1, level = 0, n_active = 0, quota = 1;
     bool initialized = false;
     long long hyp_iters = 0;
     int state = kPending;
@@ -161,7 +165,7 @@ struct pilot_server {
     pilot_dtype dt = PILOT_F32;
     int C = 0, L = 0;
     int variant = 0;           // kVariantScaled | kVariantConf, shared by every served frame
-    int levels_per_round = 1;  // pyramid levels each admitted frame advances per round
+    int levels_per_round = 1;  // pyramid levels each admitted frame advances per round; 0: by size
     std::thread worker;
     std::mutex mu;
     std::condition_variable cv_work, cv_done;
@@ -292,7 +296,8 @@ cudaError_t capture_round(pilot_server* s) {
     a.lambda0 = s->cfg.lambda0;
     // levels_per_round sub-rounds: each advances every listed frame by one level (a frame that
     // finishes level 0 is finalised and has no jobs in the later sub-rounds)
-    for (int sub = 0; sub < s->levels_per_round && e == cudaSuccess; ++sub) {
+    const int subs = s->levels_per_round > 0 ? s->levels_per_round : s->L;
+    for (int sub = 0; sub < subs && e == cudaSuccess; ++sub) {
         if (sub > 0)
             e = launch_round_advance(hdr, const_cast<FrameDesc*>(frames), a.fr_list, const_cast<int*>(a.fr_item),
                                      const_cast<int*>(a.fr_job), keep, a.tile, a.tiles_per_item, s->stream);
@@ -392,6 +397,12 @@ void write_round(pilot_server* s) {
         d.flags = (r->initialized ? 0 : kFlagInit) | ((r->level > 0 && K > 0 && K < r->n_active) ? kFlagPrune : 0) |
                   (r->level == 0 ? kFlagFinalize : 0);
         d.prior = frame_prior(c, &f, f.dsm);
+        // levels this round: fixed, or (0) all remaining ones for a frame whose level work
+        // (anchors x active hypotheses) is small and one level otherwise
+        r->quota = s->levels_per_round > 0
+                       ? s->levels_per_round
+                       : ((long long)f.N * r->n_active <= kSmallLevelWork ? r->level + 1 : 1);
+        d.quota = r->quota;
         list[nl] = r->slot;
         jobs[nl + 1] = jobs[nl] + r->n_active;
         items[nl + 1] = items[nl] + r->n_active * items_per_job(f.N, kPlainTile, tiles_per_item(kPlainTile));
@@ -412,7 +423,7 @@ void after_round(pilot_server* s) {
         // the round advanced every listed frame by up to levels_per_round levels
         r->initialized = true;
         bool finished = false;
-        for (int sub = 0; sub < s->levels_per_round; ++sub) {
+        for (int sub = 0; sub < r->quota; ++sub) {
             r->hyp_iters += (long long)r->n_active * c.iters_per_level[r->level];
             const int K = c.keep_top_k[r->level];
             if (r->level > 0 && K > 0 && K < r->n_active) r->n_active = K;
@@ -635,7 +646,7 @@ pilot_status pilot_serve_wait(pilot_server* s, uint64_t ticket, pilot_result* re
 
 pilot_status pilot_serve_set_levels_per_round(pilot_server* s, int levels) {
     if (!s) return sfail(PILOT_EINVAL, "server is NULL");
-    if (levels < 1 || levels > PILOT_MAX_LEVELS) return sfail(PILOT_EINVAL, "levels_per_round must be in [1, 4]");
+    if (levels < 0 || levels > PILOT_MAX_LEVELS) return sfail(PILOT_EINVAL, "levels_per_round must be in [0, 4]");
     std::unique_lock<std::mutex> lock(s->mu);
     if (s->key_set) return sfail(PILOT_EINVAL, "set levels_per_round before the first frame is submitted");
     s->levels_per_round = levels;

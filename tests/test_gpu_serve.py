@@ -41,12 +41,14 @@ def test_served_mix_equals_plain_solves(torch):
     server.close()
 
 
-@pytest.mark.parametrize("levels", [2, 3])
+@pytest.mark.parametrize("levels", [2, 3, 0])
 def test_several_levels_per_round_equal_plain_solves(torch, levels):
     """With several levels per round the device advances each frame between launches (top-K,
     next level, job tables); frames arriving mid-way join the next round. Outputs stay
-    bitwise those of the plain solves, with pruning on."""
-    frames = uneven_frames(sides=(40, 55, 70, 30, 62), hyps=(9, 7, 12, 5, 8), base=1150)
+    bitwise those of the plain solves, with pruning on.  With 0 the count is per frame: the
+    256^2-anchor frame with 40 hypotheses (above 2^21 anchor x hypotheses) runs one level per
+    round while the small ones run all of theirs."""
+    frames = uneven_frames(sides=(40, 55, 256, 30, 62), hyps=(9, 7, 40, 5, 8), base=1150)
     fas = args_for(frames)
     opts = B.Options(iters=(3, 4, 2, 0), keep_top_k=(0, 3, 4, 0))
     plain = [B.Solver(opts).solve(fa) for fa in fas]
