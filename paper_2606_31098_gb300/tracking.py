@@ -26,6 +26,23 @@ import numpy as np
 from . import binding as B
 
 
+def frame_prior(t: int, history: list, given=None) -> np.ndarray:
+    """Frame t's prior: `given` (the initial pose, or the pose a recovery restarts from) when
+    set, else the prediction one frame on from the estimates of frames t-1 and t-2 (the last
+    one held when it is the only one)."""
+    if given is not None:
+        return np.asarray(given, np.float64).ravel().copy()
+    return B.pose_predict(history[t - 1], history[t - 2] if t >= 2 else None, 1)
+
+
+def lookahead_crop_pose(t: int, history: list, initial) -> np.ndarray:
+    """Crop pose of frame t made while frame t-1 is localised: predicted two frames on from
+    the estimates of frames t-2 and t-3 (frames 0 and 1: the initial pose)."""
+    if t <= 1:
+        return np.asarray(initial, np.float64).ravel().copy()
+    return B.pose_predict(history[t - 2], history[t - 3] if t >= 3 else None, 2)
+
+
 class CropFailure(RuntimeError):
     """The reference crop around a prior failed (a corner ray never met the DSM)."""
 
@@ -103,18 +120,10 @@ class SequentialTracker:
 
     # ------------------------------------------------------------------ poses
     def _prior(self, t: int) -> np.ndarray:
-        if self._next_given is not None:
-            return self._next_given.copy()
-        h = self.state.history
-        return B.pose_predict(h[t - 1], h[t - 2] if t >= 2 else None, 1)
+        return frame_prior(t, self.state.history, self._next_given)
 
     def _lookahead_pose(self, t: int) -> np.ndarray:
-        """Crop pose of frame t made while frame t-1 is localised: predicted two frames on
-        from the estimates of frames t-2 and t-3 (frames 0 and 1: the initial pose)."""
-        h = self.state.history
-        if t <= 1:
-            return self._initial.copy()
-        return B.pose_predict(h[t - 2], h[t - 3] if t >= 3 else None, 2)
+        return lookahead_crop_pose(t, self.state.history, self._initial)
 
     # ------------------------------------------------------------------ crops
     def _crop(self, T, slot: int) -> dict:

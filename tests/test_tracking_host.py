@@ -5,6 +5,7 @@ import pytest
 
 from oracle import tracking as TR
 from paper_2606_31098_gb300 import binding as B
+from paper_2606_31098_gb300 import tracking as TK
 
 from test_oracle_tracking import screw_sequence
 
@@ -44,3 +45,16 @@ def test_bad_arguments_are_rejected(lib):
         B.seed_params(T, [], [0.0])
     with pytest.raises(ValueError):
         B.seed_params(T, [0.0] * 33, [0.0])
+
+
+def test_tracker_pose_rules_match_the_oracle(lib):
+    """The tracker's prior and look-ahead crop pose (host code over pilot_pose_predict) follow
+    the oracle loop's rules for every frame of a history."""
+    hist = list(screw_sequence(9, seed=40) + 1e-4 * np.random.default_rng(1).standard_normal((9, 12)))
+    T0 = hist[0]
+    for t in range(1, 9):
+        np.testing.assert_allclose(TK.frame_prior(t, hist), TR.predict(hist[t - 1], hist[t - 2] if t >= 2 else None, 1),
+                                   rtol=1e-13, atol=1e-10)
+        np.testing.assert_allclose(TK.lookahead_crop_pose(t, hist, T0), TR.crop_prior_lookahead(t, hist, T0),
+                                   rtol=1e-13, atol=1e-10)
+    np.testing.assert_array_equal(TK.frame_prior(5, hist, given=T0), T0)
