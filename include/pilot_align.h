@@ -341,17 +341,25 @@ pilot_status pilot_align_profile(const pilot_align_handle* h, double* build_ms,
  * latency-bound loop that cannot risk an allocation's implicit device synchronisation.
  * This call allocates nothing and needs no handle; its scratch is a fixed array of about
  * 2.3 MB that every GPU loading this library holds until the process exits.
- *   cfg:    options (only the Huber thresholds are used; 0 means the default)
- *   frame:  a DEVICE frame (is_device = 1, else PILOT_EINVAL), N <= 65536 anchors
+ *   cfg:    options.  Read: huber_photo, huber_grav, huber_range (0 means the default),
+ *           gate_grav, gate_range, and the fields pilot_align_validate checks.  Not read:
+ *           max_points, max_hyps and max_channels -- the frame is checked against this
+ *           call's own limits below instead of a handle's workspace sizes.
+ *   frame:  a DEVICE frame (is_device = 1, else PILOT_EINVAL), N <= 65536 anchors, C <= 64.
+ *           Scales: as in the handle-based calls, a frame giving only one of qry_scale /
+ *           ref_scale on a level reads the missing one as ones.
  *   level:  pyramid level to evaluate
  *   T_cw:   DEVICE pointer, frame->M x 12 poses (frame->T_cw is ignored), M <= 256
  *   out29:  DEVICE pointer, frame->M x 29 doubles, written like debug_normal_eq's out29
+ *           (the same kernels and tile: bitwise the same values)
  *   stream: cudaStream_t as void*; the call only enqueues work: out29 is ready when the
  *           stream reaches that point.
  * Sizes beyond the limits return PILOT_EINVAL with the limit in pilot_align_last_error().
- * The first call on a device looks up the scratch address for that device (make that first
- * call before any stream capture).  All calls share the one scratch array: calls whose work
- * overlaps on the GPU race on it, so the caller must serialise them. */
+ * The first call in a CUDA context (per device) looks up the scratch address for it (make
+ * that first call before any stream capture); a context created anew, e.g. after
+ * cudaDeviceReset, gets a new lookup on its first call.  All calls share the one scratch
+ * array, which keeps the last call's contents: calls whose work overlaps on the GPU race on
+ * it, so the caller must serialise them. */
 pilot_status pilot_align_normal_eq_noalloc(const pilot_align_config* cfg, const pilot_frame* frame,
                                            int level, const double* T_cw, double* out29,
                                            void* stream);

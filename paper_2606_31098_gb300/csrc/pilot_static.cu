@@ -11,10 +11,13 @@
 // for the output.
 //
 // Host code cannot use the array's name as a device address (it names a host-side stand-in),
-// so the first call on each device, with that device current, looks the address up with
-// cudaGetSymbolAddress and caches it.  That first call should come before any stream
-// capture.  All calls share the one array: calls whose work overlaps on the GPU (two
-// streams, or two threads) race on it and must be serialised by the caller.
+// so the first call in each CUDA context (per device, with that device current) looks the
+// address up with cudaGetSymbolAddress and caches it under the context's unique id; a
+// context created anew (after cudaDeviceReset, say) gets a fresh lookup.  That first call
+// should come before any stream capture.  All calls share the one array: calls whose work
+// overlaps on the GPU (two streams, or two threads) race on it and must be serialised by
+// the caller.
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include <mutex>
@@ -44,30 +47,79 @@ constexpr size_t kScratchBytes =
 // build pass), so nothing needs clearing between calls.
 __device__ __align__(256) unsigned char g_noalloc_scratch[kScratchBytes];
 
+// Unit scales, read in place of a missing scale array when the frame gives only one of the
+// pair (the handle-based entry points read a missing one as ones too).
+__device__ __align__(16) float g_noalloc_ones[64] = {
+    1.f, 1.f, 1.f, 1.f, 1.f, 1.f, 1.f, 1.f, 1.f, 1.f, 1.f, 1.f, 1.f, 1.f, 1.f, 1.f,
+    1.f, 1.f, 1.f, 1.f, 1.f, 1.f, 1.f, 1.f, 1.f, 1.f, 1.f, 1.f, 1.f, 1.f, 1.f, 1.f,
+    1.f, 1.f, 1.f, 1.f, 1.f, 1.f, 1.f, 1.f, 1.f, 1.f, 1.f, 1.f, 1.f, 1.f, 1.f, 1.f,
+    1.f, 1.f, 1.f, 1.f, 1.f, 1.f, 1.f, 1.f, 1.f, 1.f, 1.f, 1.f, 1.f, 1.f, 1.f, 1.f};
+
 constexpr int kMaxDevices = 64;
 std::mutex g_mu;
-unsigned char* g_scratch_addr[kMaxDevices] = {};
+struct ScratchCache {
+    unsigned long long ctx_id;     // 0: nothing cached
+    unsigned char* scratch;
+    float* ones;
+};
+ScratchCache g_cache[kMaxDevices] = {};
+
+// Unique id of the calling thread's current CUDA context (0 when it cannot be read; the
+// caller then looks the addresses up on every call).  Read through the runtime's driver
+// entry-point query, so the library does not link the driver library itself.
+unsigned long long current_context_id() {
+    typedef CUresult (*GetCurrent)(CUcontext*);
+    typedef CUresult (*GetId)(CUcontext, unsigned long long*);
+    static GetCurrent get_current = nullptr;
+    static GetId get_id = nullptr;
+    static bool looked_up = false;
+    if (!looked_up) {
+        cudaDriverEntryPointQueryResult q1, q2;
+        void* f1 = nullptr;
+        void* f2 = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f1, 12000, cudaEnableDefault, &q1) == cudaSuccess &&
+            cudaGetDriverEntryPointByVersion("cuCtxGetId", &f2, 12000, cudaEnableDefault, &q2) == cudaSuccess &&
+            q1 == cudaDriverEntryPointSuccess && q2 == cudaDriverEntryPointSuccess) {
+            get_current = reinterpret_cast<GetCurrent>(f1);
+            get_id = reinterpret_cast<GetId>(f2);
+        }
+        looked_up = true;
+    }
+    if (!get_current || !get_id) return 0;
+    CUcontext ctx = nullptr;
+    unsigned long long id = 0;
+    if (get_current(&ctx) != CUDA_SUCCESS || !ctx || get_id(ctx, &id) != CUDA_SUCCESS) return 0;
+    return id;
+}
 
 pilot_status fail_msg(pilot_status st, const std::string& msg) {
     record_error(msg.c_str());
     return st;
 }
 
-// Device address of the scratch on the current device (looked up once per device).
-pilot_status scratch_address(unsigned char** out) {
+// Device addresses of the scratch and of the unit scales in the current context (looked
+// up once per device and context).
+pilot_status scratch_address(unsigned char** scratch, float** ones) {
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return fail_msg(PILOT_ECUDA, std::string("cudaGetDevice: ") + cudaGetErrorString(e));
     if (dev < 0 || dev >= kMaxDevices) return fail_msg(PILOT_EINVAL, "device ordinal beyond 64");
     std::lock_guard<std::mutex> lock(g_mu);
-    if (!g_scratch_addr[dev]) {
+    ScratchCache& c = g_cache[dev];
+    const unsigned long long ctx = current_context_id();   // 0 before the thread's first runtime call
+    if (ctx == 0 || c.ctx_id != ctx) {
         void* p = nullptr;
-        e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-        if (e != cudaSuccess || !p)
+        void* q = nullptr;
+        e = cudaGetSymbolAddress(&p, g_noalloc_scratch);     // makes the device's context current
+        if (e == cudaSuccess) e = cudaGetSymbolAddress(&q, g_noalloc_ones);
+        if (e != cudaSuccess || !p || !q)
             return fail_msg(PILOT_ECUDA, std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e));
-        g_scratch_addr[dev] = static_cast<unsigned char*>(p);
+        c.scratch = static_cast<unsigned char*>(p);
+        c.ones = static_cast<float*>(q);
+        c.ctx_id = current_context_id();
     }
-    *out = g_scratch_addr[dev];
+    *scratch = c.scratch;
+    *ones = c.ones;
     return PILOT_OK;
 }
 
@@ -91,20 +143,27 @@ extern "C" pilot_status pilot_align_normal_eq_noalloc(const pilot_align_config* 
                                                       const double* T_cw, double* out29,
                                                       void* stream) {
     if (!cfg || !f || !T_cw || !out29) return fail_msg(PILOT_EINVAL, "config, frame, T_cw or out29 is NULL");
-    pilot_status st = pilot_align_validate(cfg, f);
-    if (st != PILOT_OK) return st;
-    if (!f->is_device)
-        return fail_msg(PILOT_EINVAL, "pilot_align_normal_eq_noalloc needs a device frame (is_device = 1)");
     if (f->N > kStaticMaxPoints)
         return fail_msg(PILOT_EINVAL, "N = " + std::to_string(f->N) + " exceeds the fixed scratch limit of " +
                                           std::to_string(kStaticMaxPoints) + " anchors");
     if (f->M > kStaticMaxHyps)
         return fail_msg(PILOT_EINVAL, "M = " + std::to_string(f->M) + " exceeds the fixed scratch limit of " +
                                           std::to_string(kStaticMaxHyps) + " poses");
+    // the frame is checked against this call's own fixed limits, not the caller's workspace
+    // sizes (max_points, max_hyps, max_channels are not read)
+    pilot_align_config lim = *cfg;
+    lim.max_points = kStaticMaxPoints;
+    lim.max_hyps = kStaticMaxHyps;
+    lim.max_channels = 64;
+    pilot_status st = pilot_align_validate(&lim, f);
+    if (st != PILOT_OK) return st;
+    if (!f->is_device)
+        return fail_msg(PILOT_EINVAL, "pilot_align_normal_eq_noalloc needs a device frame (is_device = 1)");
     if (level < 0 || level >= f->L) return fail_msg(PILOT_EINVAL, "level outside [0, L)");
     if (f->M == 0) return PILOT_OK;
     unsigned char* base = nullptr;
-    if ((st = scratch_address(&base)) != PILOT_OK) return st;
+    float* ones = nullptr;
+    if ((st = scratch_address(&base, &ones)) != PILOT_OK) return st;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     HypState* state = reinterpret_cast<HypState*>(base + kOffState);
     float* pose32 = reinterpret_cast<float*>(base + kOffPose);
@@ -128,11 +187,10 @@ extern "C" pilot_status pilot_align_normal_eq_noalloc(const pilot_align_config* 
     b.valid = f->point_valid;
     b.qry = f->qry_feat[level];
     b.ref = f->ref_feat[level];
-    if (f->qry_scale[level] && f->ref_scale[level]) {
-        b.qscale = f->qry_scale[level];
-        b.rscale = f->ref_scale[level];
-    } else if (f->qry_scale[level] || f->ref_scale[level]) {
-        return fail_msg(PILOT_EINVAL, "pilot_align_normal_eq_noalloc needs both or neither scale array");
+    // scales: a missing one of the pair reads as ones, as in the handle-based entry points
+    if (f->qry_scale[level] || f->ref_scale[level]) {
+        b.qscale = f->qry_scale[level] ? f->qry_scale[level] : ones;
+        b.rscale = f->ref_scale[level] ? f->ref_scale[level] : ones;
     }
     b.conf = f->qry_conf[level];
     b.N = f->N;

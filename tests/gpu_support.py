@@ -62,20 +62,37 @@ def fp32_pose(T):
     return np.asarray(T, np.float64).astype(np.float32).astype(np.float64)
 
 
-def assert_normal_eq_close(gpu29, ora29, tol=NE_TOL, what="", F=None):
+# worst errors seen in this process, under the bounds asserted and under the residual-based
+# scales sqrt(H_aa cost) and cost (reported by test_normal_equation_error_scales)
+WORST = {"H": 0.0, "g": 0.0, "cost": 0.0, "g_residual_scale": 0.0, "cost_residual_scale": 0.0}
+
+
+def normal_eq_errors(gpu29, ora29, F=None):
+    """Errors of a GPU normal-equation record against the oracle's, relative to the
+    asserted scales (H: sqrt(H_aa H_bb); g: sqrt(H_aa F); cost: max(cost, 1e-3 F)) and to the
+    residual-based scales (g: sqrt(H_aa cost); cost: cost)."""
     gpu29 = np.asarray(gpu29)
     ora29 = np.asarray(ora29)
     Hg, Ho = O.unpack_H(gpu29[:21]), O.unpack_H(ora29[:21])
     F = max(float(ora29[28]) if F is None else F, 1.0)
     d = np.sqrt(np.maximum(np.diag(Ho), 0.0))
     scale = np.outer(d, d) + 1e-300
-    errH = np.abs(Hg - Ho) / scale
-    errg = np.abs(gpu29[21:27] - ora29[21:27]) / (d * np.sqrt(F) + 1e-300)
-    errc = abs(gpu29[27] - ora29[27]) / max(ora29[27], 1e-3 * F)
-    msg = f"{what} H {errH.max():.2e} g {errg.max():.2e} cost {errc:.2e} n {gpu29[28]} vs {ora29[28]}"
+    dg = np.abs(gpu29[21:27] - ora29[21:27])
+    dc = abs(gpu29[27] - ora29[27])
+    cost = max(float(ora29[27]), 1e-300)
+    return {"H": float((np.abs(Hg - Ho) / scale).max()), "g": float((dg / (d * np.sqrt(F) + 1e-300)).max()),
+            "cost": dc / max(cost, 1e-3 * F), "g_residual_scale": float((dg / (d * np.sqrt(cost) + 1e-300)).max()),
+            "cost_residual_scale": dc / cost}
+
+
+def assert_normal_eq_close(gpu29, ora29, tol=NE_TOL, what="", F=None):
+    e = normal_eq_errors(gpu29, ora29, F)
+    for k, v in e.items():
+        WORST[k] = max(WORST[k], v)
+    msg = f"{what} H {e['H']:.2e} g {e['g']:.2e} cost {e['cost']:.2e} n {gpu29[28]} vs {ora29[28]}"
     assert gpu29[28] == ora29[28], msg
-    assert errH.max() <= tol and errg.max() <= tol and errc <= tol, msg
-    return errH.max(), errg.max(), errc
+    assert e["H"] <= tol and e["g"] <= tol and e["cost"] <= tol, msg
+    return e["H"], e["g"], e["cost"]
 
 
 def pose_errors(Ta, Tb):

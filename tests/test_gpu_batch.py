@@ -98,6 +98,34 @@ def test_full_size_uneven_batch(torch):
         assert er < 0.2 and et < 1.0, (i, er, et)
 
 
+def test_batched_crop_sizes_bf16_against_the_oracle(torch):
+    """One BF16 frame of each crop size of the batched workload (128^2, 192^2, 256^2,
+    384^2 anchors, C = 32, 3 levels, priors on), solved together in one batch and checked
+    against the FP64 oracle fed the dequantised maps (the values the solver uses): statuses
+    equal, converged hypotheses and the selected pose within 1e-3 deg / 1 mm.  16
+    hypotheses per frame keep the oracle's run to seconds."""
+    from oracle import oracle as O
+    from gpu_support import assert_selection_agrees, assert_solutions_agree, to_oracle_opts
+    from precision_support import BF16, dequantize
+    frames = [S.make_frame(S.SceneConfig(crop_side=s_, n_hyps=16), S.frame_seed(3, 1100 + i))
+              for i, s_ in enumerate((128, 192, 256, 384))]
+    opts = B.Options(max_points=384 * 384, max_hyps=64)
+    solver = B.Solver(opts)
+    fas, deq = [], []
+    for f in frames:
+        arrs = B.quantized_device_arrays(f, B.BF16)
+        fas.append(B.FrameArgs(f, arrs, is_device=True, dtype=B.BF16))
+        deq.append(f.replace(qry_feat=[dequantize(q, None, BF16).reshape(q.shape) for q in arrs["qry_feat"]],
+                             ref_feat=[dequantize(r, None, BF16).reshape(r.shape) for r in arrs["ref_feat"]]))
+    batch = solver.solve_batch(fas)
+    solver.close()
+    for i, (fd, g) in enumerate(zip(deq, batch)):
+        o = O.solve(fd, to_oracle_opts(opts), n_threads=0)
+        n = assert_solutions_agree(fd, opts, g, o, min_converged=4)
+        assert_selection_agrees(fd, opts, g, o)
+        print(f"crop {fd.N} anchors: {n} of 16 converged, all within tolerance")
+
+
 def test_batch_validation(torch):
     frames = uneven_frames(sides=(20, 20), hyps=(2, 2), base=990)
     solver = B.Solver(B.Options())

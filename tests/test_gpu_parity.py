@@ -145,9 +145,10 @@ def test_solve_reduced_frame_all_hypotheses(torch, seed):
     assert_selection_agrees(f, opts, g, o)
 
 
-def test_solve_full_size_sampled_hypotheses(torch):
-    """The full 256^2 x C=32 x 3-level frame with 64 hypotheses on the GPU; the oracle
-    re-solves a sample of them (hypotheses are independent without pruning)."""
+def test_solve_full_size_all_hypotheses(torch):
+    """The full 256^2 x C=32 x 3-level frame with 64 hypotheses on the GPU against the
+    oracle's solve of all 64 (on every host core).  Statuses equal; every hypothesis whose
+    FP64 end point is converged, and the selected pose, within 1e-3 deg / 1 mm."""
     f = S.make_frame(S.config_full_frame(), S.frame_seed(2, 0))
     opts = B.Options()
     fa = device_frame(f)
@@ -156,16 +157,33 @@ def test_solve_full_size_sampled_hypotheses(torch):
     solver.close()
     assert g.hyp_iters == 64 * 30
     assert g.best >= 0 and g.status[g.best] == B.HYP_OK
-    sample = sorted({0, g.best, 17, 42})
-    o = O.solve(f, to_oracle_opts(opts), T_hyps=f.T_hyps[sample])
-    sub = B.Result(g.T_cw, g.cost, g.n_valid, g.status, g.best, g.hyp_iters)
-    assert_solutions_agree(f, opts, sub, o, idx=sample, min_converged=1)
-    k = sample.index(g.best)
-    assert converged(f, to_oracle_opts(opts), o.T_cw[k])
-    assert_pose_close(g.T_cw[g.best], o.T_cw[k], what="selected pose")
+    o = O.solve(f, to_oracle_opts(opts), n_threads=0)
+    assert o.hyp_iters == g.hyp_iters
+    n_conv = assert_solutions_agree(f, opts, g, o, min_converged=16)
+    print(f"full frame: {n_conv} of 64 hypotheses converged in FP64, all within tolerance")
+    assert_selection_agrees(f, opts, g, o)
     # the selected pose is close to the ground truth of the synthetic scene
     er, et = pose_errors(g.T_cw[g.best], f.T_gt)
     assert er < 0.1 and et < 0.5
+
+
+def test_normal_equation_error_scales(torch):
+    """The normal-equation bound asserted everywhere scales g by sqrt(H_aa F) and the cost
+    by max(cost, 1e-3 F), F the visible-anchor count: FP32 forms r = f - f_ref from values
+    of size |f|, so its rounding error scales with |f|, not with the residual, which is only
+    descriptor noise near the optimum.  This test records the worst error of the full frame
+    (every level, at the ground truth, near-converged poses and hypotheses) under both the
+    asserted scales and the residual-based ones (sqrt(H_aa cost), cost), and bounds the
+    latter too: the residual-based error stays within the factor sqrt(F / cost) of the
+    asserted one (about 20 at the optimum, where the cost per anchor is the noise,
+    C x 1e-4)."""
+    f = S.make_frame(S.config_full_frame(), S.frame_seed(2, 3))
+    poses = [f.T_gt, *random_poses(f.T_gt, 3, 5, trans=0.01, rot_deg=0.005), f.T_hyps[0], f.T_hyps[40]]
+    check_normal_eq(f, B.Options(), [0, 1, 2], poses)
+    from gpu_support import WORST
+    print("normal-equation worst errors:", {k: f"{v:.2e}" for k, v in WORST.items()})
+    assert WORST["g"] <= 1e-5 and WORST["cost"] <= 1e-5 and WORST["H"] <= 1e-5
+    assert WORST["g_residual_scale"] <= 2e-4 and WORST["cost_residual_scale"] <= 1e-5
 
 
 def test_pruning_keeps_a_valid_top_k(torch):
