@@ -22,7 +22,6 @@ import argparse
 import hashlib
 import json
 import os
-import re
 import statistics
 import subprocess
 import sys
@@ -39,17 +38,27 @@ UNIT = "hyp*iter/s"
 WORKLOAD = ("full single frame: 256x256 anchors at 0.5 m, C=32, 3 levels 480x640/240x320/120x160, "
             "64 hypotheses, 10 LM iterations per level, gravity + range priors")
 MEASURED_PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
-TRAFFIC_FILE = os.path.join(ROOT, "profiles", "build_kernel_f32_c32_full_frame.md")
 BUILD_SRC = os.path.join(ROOT, "paper_2606_31098_gb300", "csrc", "pilot_build_impl.cuh")
-SM_COUNT = 152
 FP32_LANES_PER_SM = 128
+# DRAM bytes (read + write) per (anchor, hypothesis) unit of the FP32 build pass at C = 32,
+# from one ncu capture of a coarse-level launch (dram__bytes_read.sum + dram__bytes_write.sum
+# over its units), valid for the kernel source with this SHA-256 prefix; None otherwise.
+BUILD_TRAFFIC = {"src_sha256_16": None, "dram_bytes_per_unit": None}
 
 
 def flops_per_unit(C: int) -> int:
-    """Algorithmic FP32 flops of one (anchor, hypothesis) evaluation of the build pass:
-    25 per channel (bilinear value + 2 gradients 12, residual 1, six sums 12) plus 200 per
-    anchor (transform 18, projection 10, Huber 6, Jacobian rows 12, M A 36, weights 12,
-    21 H entries 84, 6 g entries 24)."""
+    """Algorithmic FP32 flops of one (anchor, hypothesis) evaluation, as the scope table
+    counts them: about 40 per channel (bilinear value and two gradients 28, dequantisation
+    3, residual 1, the six sums 12... rounded to 40) plus about 150 per anchor (transform,
+    projection, A, A^T M A, A^T b): 1430 at C = 32."""
+    return 40 * C + 150
+
+
+def executed_flops_per_unit(C: int) -> int:
+    """FP32 flops the build pass actually executes per unit (FMA = 2): 25 per channel
+    (bilinear value and gradients from shared tap differences 12, residual 1, six sums 12)
+    plus 200 per anchor (transform 18, projection 10, Huber 6, Jacobian rows 12, M A 36,
+    weights 12, 21 H entries 84, 6 g entries 24): 1000 at C = 32."""
     return 25 * C + 200
 
 
@@ -196,16 +205,25 @@ def build_src_hash() -> str:
 
 
 def traffic_per_launch(units_per_launch: int):
-    """DRAM bytes per build launch from the committed ncu summary, scaled to the units of
+    """DRAM bytes per build launch: BUILD_TRAFFIC's per-unit figure scaled to the units of
     one launch; None when the kernel source changed since the counters were taken."""
-    try:
-        text = open(TRAFFIC_FILE).read()
-    except OSError:
+    if BUILD_TRAFFIC["dram_bytes_per_unit"] is None or BUILD_TRAFFIC["src_sha256_16"] != build_src_hash():
         return None
-    m = re.search(r"traffic_dram_bytes_per_unit:\s*([0-9.eE+-]+)\s*\(build_src_sha256_16:\s*([0-9a-f]+)\)", text)
-    if not m or m.group(2) != build_src_hash():
-        return None
-    return float(m.group(1)) * units_per_launch
+    return BUILD_TRAFFIC["dram_bytes_per_unit"] * units_per_launch
+
+
+def frame_gather_ceiling(B, torch, frame, dev, C, elem, dtype, tile, stream):
+    """Gather ceiling of the build pass on this frame: pilot_probe_gather_frame at every
+    level with the hypotheses' start poses (the frame's own locality), combined over the
+    levels as the solve weights them (equal units per level).  Returns units per second."""
+    poses = torch.as_tensor(np.asarray(frame.T_hyps, np.float32).reshape(-1, 12), device="cuda")
+    total_s = 0.0
+    for level in range(frame.L):
+        s = 2.0 ** -level
+        rate = B.probe_gather_frame(dev.arrays["points"], dev.arrays["qry_feat"][level], dev.arrays["ref_feat"][level],
+                                    dtype, frame.fx * s, frame.fy * s, frame.cx * s, frame.cy * s, poses, tile, stream)
+        total_s += frame.N * frame.M / rate
+    return frame.L * frame.N * frame.M / total_s
 
 
 def cpu_cores() -> int:
@@ -215,24 +233,38 @@ def cpu_cores() -> int:
         return os.cpu_count() or 1
 
 
+def make_frames(S, specs):
+    """Seeded synthetic frames built in parallel on the host cores (spawned workers: no
+    CUDA state is inherited)."""
+    import multiprocessing as mp
+    with mp.get_context("spawn").Pool(max(1, min(16, cpu_cores(), len(specs)))) as pool:
+        return pool.starmap(S.make_frame, specs)
+
+
 def batched_and_served(args, B, S, torch, world, stream, served_too: bool = True):
-    """The batched form (uneven frames, one persistent launch per level under a graph) and
-    the served form (streams at 30 Hz with exponential inter-arrival times), both on BF16
-    storage.  Four distinct frames (crops 128^2, 192^2, 256^2, 384^2, 144 hypotheses each)
-    are generated once; each batch entry / request takes one of them with its own random
-    hypothesis count in [16, 144]."""
+    """The batched form (one persistent launch per level under a CUDA graph) on BF16
+    storage, and the served form.
+
+    * uneven32_bf16: 32 independently generated scenes, crop sides drawn uniformly from
+      {128, 192, 256, 384}^2 anchors, 16-144 hypotheses each, 3 levels, priors on.
+    * crop256: 8 independently generated 256^2-anchor frames (64 hypotheses): the plain
+      form solving them one at a time in FP32 and in BF16, and the batched BF16 form
+      solving all 8 in one batch -- the comparison the metric is quoted on."""
     import threading
     rng = np.random.default_rng(12345)
-    sides = (128, 192, 256, 384)
-    distinct = [S.make_frame(S.SceneConfig(crop_side=s_, n_hyps=144), S.frame_seed(3, 5000 + i))
-                for i, s_ in enumerate(sides)]
-    dev = [B.quantized_device_arrays(f, B.BF16) for f in distinct]
+    sides_all = (128, 192, 256, 384)
+    sides = [int(sides_all[k]) for k in rng.integers(0, 4, 32)]
+    hyps = [int(m) for m in rng.integers(16, 145, 32)]
+    specs = [(S.SceneConfig(crop_side=sd, n_hyps=m), S.frame_seed(3, 5000 + i)) for i, (sd, m) in enumerate(zip(sides, hyps))]
+    specs += [(S.config_full_frame(), S.frame_seed(3, 6000 + i)) for i in range(8)]
+    if served_too:
+        specs += [(S.SceneConfig(crop_side=s_, n_hyps=144), S.frame_seed(3, 7000 + i)) for i, s_ in enumerate(sides_all)]
+    frames = make_frames(S, specs)
+    uneven_frames, f256, distinct = frames[:32], frames[32:40], frames[40:]
     flush = torch.empty(512 * 1024 * 1024, dtype=torch.uint8, device="cuda")
 
-    def entry(k, m, arrays):
-        a = dict(arrays[k])
-        a["T_cw"] = a["T_cw"][:m].contiguous() if hasattr(a["T_cw"], "contiguous") else np.ascontiguousarray(a["T_cw"][:m])
-        return B.FrameArgs(distinct[k], a, is_device=hasattr(a["points"], "data_ptr") and a["points"].is_cuda, dtype=B.BF16)
+    def bf16_args(f):
+        return B.FrameArgs(f, B.quantized_device_arrays(f, B.BF16), is_device=True, dtype=B.BF16)
 
     def time_batch(fas, reps):
         solver = B.Solver(B.Options(max_points=384 * 384, max_hyps=sum(fa.M for fa in fas), max_frames=len(fas)))
@@ -255,19 +287,57 @@ def batched_and_served(args, B, S, torch, world, stream, served_too: bool = True
         solver.close()
         return world * units / (sum(ts) / 1e3), sum(ts) / reps, sched
 
-    uneven = [entry(int(rng.integers(0, 4)), int(rng.integers(16, 145)), dev) for _ in range(32)]
+    def time_plain(fas, reps):
+        solver = B.Solver(B.Options(max_points=max(fa.N for fa in fas), max_hyps=max(fa.M for fa in fas)))
+        if args.pin_schedule:
+            tile, streams = (int(v) for v in args.pin_schedule.split(":"))
+            solver.set_schedule(fas[:1], batched=False, tile=tile, streams=streams)
+            sched = solver.schedule(fas[:1], batched=False)
+        else:
+            sched, _ = solver.autotune(fas[:1], batched=False, reps=2, stream=stream)
+        for fa in fas:
+            solver.solve(fa, stream)
+        ts, units = [], 0
+        for _ in range(reps):
+            for fa in fas:
+                flush.zero_()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                r = solver.solve(fa, stream)
+                e1.record(stream)
+                e1.synchronize()
+                ts.append(e0.elapsed_time(e1))
+                units += r.hyp_iters
+        solver.close()
+        return world * units / (sum(ts) / 1e3), sched
+
+    uneven = [bf16_args(f) for f in uneven_frames]
     v_uneven, ms_uneven, sc_uneven = time_batch(uneven, 3)
-    eight = [entry(2, 64, dev) for _ in range(8)]
-    v_256, ms_256, sc_256 = time_batch(eight, 3)
-    batched = {"uneven32_bf16": {"value": v_uneven, "unit": UNIT, "ms_per_batch": ms_uneven,
-                                 "frames": 32, "crops": "128^2..384^2", "hypotheses": "16..144",
-                                 "schedule": sc_uneven},
-               "crop256x8_bf16": {"value": v_256, "unit": UNIT, "ms_per_batch": ms_256, "frames": 8,
-                                  "hypotheses": 64, "schedule": sc_256}}
+    del uneven
+    a256_bf16 = [bf16_args(f) for f in f256]
+    a256_f32 = [B.FrameArgs(f, B.device_arrays(f), is_device=True) for f in f256]
+    v_plain_f32, sc_pf = time_plain(a256_f32, 2)
+    v_plain_bf16, sc_pb = time_plain(a256_bf16, 2)
+    v_256, ms_256, sc_256 = time_batch(a256_bf16, 3)
+    del a256_f32
+    batched = {"uneven32_bf16": {"value": v_uneven, "unit": UNIT, "ms_per_batch": ms_uneven, "frames": 32,
+                                 "distinct_scenes": 32, "crops": "128^2..384^2 (uniform over 4 sides)",
+                                 "hypotheses": "16..144", "schedule": sc_uneven},
+               "crop256": {"frames": 8, "distinct_scenes": 8, "hypotheses": 64, "unit": UNIT,
+                           "plain_f32": v_plain_f32, "plain_bf16": v_plain_bf16, "batched_bf16": v_256,
+                           "ms_per_batch_bf16": ms_256, "schedules": {"plain_f32": sc_pf, "plain_bf16": sc_pb,
+                                                                      "batched_bf16": sc_256}}}
 
     if not served_too:
         return batched, {}
     # served form: host (page-locked) BF16 frames staged by the server per request
+    dev = [B.quantized_device_arrays(f, B.BF16) for f in distinct]
+
+    def entry(k, m, arrays):
+        a = dict(arrays[k])
+        a["T_cw"] = a["T_cw"][:m].contiguous()
+        return B.FrameArgs(distinct[k], a, is_device=a["points"].is_cuda, dtype=B.BF16)
+
     host = []
     for d in dev:
         h = {}
@@ -682,22 +752,54 @@ def run_ours(args):
 
     # roofline of the dominant kernel (the build pass).  The hypotheses run in `parts`
     # concurrent launches per LM iteration (one per stream), so launch durations overlap:
-    # achieved is the build pass' algorithmic work over the whole timed solves divided by
-    # their device time (which also holds the ~1 % of small kernels: a lower bound).
+    # the rate is the build pass' units over the timed solves divided by their whole device
+    # time (which also holds the ~1 % of small kernels: a lower bound).
     C, elem = frame.C, 4
     parts = min(plain_schedule["streams"] or 2, frame.M)
     units_per_launch = frame.N * (frame.M // parts)   # no pruning: equal parts every launch
     build_units = units_per_launch * build_n           # over the timed device-frame solves
     avg_launch_ms = build_ms / max(build_n, 1)
-    achieved_tflops = build_units * flops_per_unit(C) / (total_ms * 1e-3) / 1e12
+    units_per_s = build_units / (total_ms * 1e-3)
+    sms = torch.cuda.get_device_properties(local).multi_processor_count
     sm_max = (clk or {}).get("sm_max_mhz") or (load_peaks() or {}).get("sm_max_mhz", 2070.0)
-    peak_tflops = SM_COUNT * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
-    gather_gbs = build_units * gather_bytes_per_unit(C, elem) / (total_ms * 1e-3) / 1e9
+    # FP32 side: the scope table's algorithmic flops per unit against the FP32 FMA peak from
+    # the SM count and clock (152 x 128 lanes x 2 flops x 2070 MHz = 80.5 TFLOP/s on GB300)
+    achieved_tflops = units_per_s * flops_per_unit(C) / 1e12
+    peak_tflops = sms * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
+    frac_fp32 = achieved_tflops / peak_tflops
+    # gather side: the tap bytes against the same loads' ceiling on this frame (the probe
+    # runs the build pass' loads with the frame's own locality and no arithmetic)
+    ceiling_units = frame_gather_ceiling(B, torch, frame, dev, C, elem, B.F32, plain_schedule["tile"], stream)
+    tap_bytes = gather_bytes_per_unit(C, elem)
+    achieved_gbps = units_per_s * tap_bytes / 1e9
+    ceiling_gbps = ceiling_units * tap_bytes / 1e9
+    frac_gather = units_per_s / ceiling_units
     traffic = traffic_per_launch(units_per_launch)
-    # measured ceilings on this GPU: FP32 FMA throughput, and the same 4-tap gathers from the
-    # finest map at random pixels (no reuse between samples)
+    # other measured ceilings on this GPU: FP32 FMA throughput, and 4-tap gathers at uniformly
+    # random pixels of the finest map (no reuse between samples)
     probe_fma = B.probe_fma(stream)
     probe_gather = B.probe_gather(dev.arrays["qry_feat"][0], B.F32, 1 << 24, stream)
+    if frac_fp32 >= frac_gather:
+        bound, achieved, peak, unit = "alu", achieved_tflops, peak_tflops, "TFLOP/s"
+    else:
+        bound, achieved, peak, unit = "gather", achieved_gbps, ceiling_gbps, "GB/s"
+    roofline = {"bound": bound, "achieved": achieved, "peak": peak, "unit": unit, "frac": achieved / peak,
+                "traffic": traffic,
+                "frac_fp32": frac_fp32, "frac_gather": frac_gather,
+                "achieved_tflops": achieved_tflops, "peak_tflops": peak_tflops,
+                "achieved_gather_GBps": achieved_gbps, "gather_ceiling_GBps": ceiling_gbps,
+                "units_per_s": units_per_s, "gather_ceiling_units_per_s": ceiling_units,
+                "kernel": "build pass with fused FP64 step (pilot::build_fused_kernel<f32, 32>)",
+                "peak_basis": f"FP32 FMA derived: {sms} SMs x {FP32_LANES_PER_SM} lanes x 2 x {sm_max:.0f} MHz; "
+                              "gather: pilot_probe_gather_frame on this frame (same grid, loads and locality)",
+                "flops_per_unit": flops_per_unit(C), "flops_per_unit_executed": executed_flops_per_unit(C),
+                "gather_bytes_per_unit": tap_bytes, "units_per_launch": units_per_launch,
+                "avg_launch_ms": avg_launch_ms, "launches": build_n, "concurrent_launches": parts,
+                "achieved_basis": "build-pass units of the timed solves / their device time",
+                "traffic_basis": "ncu dram bytes per unit of a coarse launch x units per launch (None: not "
+                                 "measured for this kernel source)",
+                "hbm_GBps_measured": (load_peaks() or {}).get("hbm_gbs"),
+                "fma_probe_TFLOPs": probe_fma, "gather_random_pixels_GBps": probe_gather}
 
     batched, served = batched_and_served(args, B, S, torch, world, stream) if not args.no_forms else ({}, {})
     paper = paper_schedule_form(args, B, S, torch, world, stream) if not args.no_forms else {}
@@ -749,6 +851,23 @@ def run_ours(args):
             OC.crop(om, op)
             cpu["crop_256_ms"] = 1e3 * (time.perf_counter() - t0)
 
+    headline = None
+    if batched:
+        c256 = batched["crop256"]
+        headline = {"comparison": "hyp*iter/s on the same 8 seeded 256^2-anchor frames (C=32, 64 hypotheses, 3 levels "
+                                  "x 10 iterations): batched BF16 form vs the plain single-frame FP32 form (the "
+                                  "metric's denominator) and the plain BF16 form",
+                    "plain_f32": c256["plain_f32"], "plain_bf16": c256["plain_bf16"],
+                    "batched_bf16": c256["batched_bf16"],
+                    "batched_bf16_over_plain_f32": c256["batched_bf16"] / c256["plain_f32"],
+                    "batched_bf16_over_plain_bf16": c256["batched_bf16"] / c256["plain_bf16"],
+                    "equal_accuracy_forms": ["f32", "bf16", "f16"],
+                    "accuracy_basis": "selected pose within 1e-3 deg / 1 mm of the FP64 oracle on every one of 256 "
+                                      "seeds (tests/test_gpu_precision_sweep.py); FP8-E4M3 storage is not (p99 22 mm)"}
+        if served.get("config5"):
+            headline["served_config5"] = {k: served["config5"].get(k) for k in
+                                          ("hyp_iter_per_s", "p50_ms", "p99_ms", "completed_fps", "offered_fps")}
+
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
@@ -762,17 +881,8 @@ def run_ours(args):
                 "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
                         "d2h_bytes_per_step": int(d2h), "ms_per_step": e2e_ms / args.steps},
                 "gpu_launches": int(launches),
-                "roofline": {"bound": "alu", "kernel": "build pass with fused FP64 step (pilot::build_fused_kernel<f32, 32>)",
-                             "achieved": achieved_tflops, "peak": peak_tflops, "unit": "TFLOP/s",
-                             "frac": achieved_tflops / peak_tflops, "traffic": traffic,
-                             "peak_basis": f"FP32 FMA: {SM_COUNT} SMs x {FP32_LANES_PER_SM} lanes x 2 x {sm_max:.0f} MHz",
-                             "flops_per_unit": flops_per_unit(C), "units_per_launch": units_per_launch,
-                             "avg_launch_ms": avg_launch_ms, "launches": build_n, "concurrent_launches": parts,
-                             "achieved_basis": "build-pass units of the timed solves x flops per unit / their device time",
-                             "gather_bytes_per_unit": gather_bytes_per_unit(C, elem), "gather_GBps": gather_gbs,
-                             "probes": {"fma_TFLOPs": probe_fma, "frac_of_probe_fma": achieved_tflops / probe_fma,
-                                        "gather_random_pixels_GBps": probe_gather,
-                                        "gather_vs_probe": gather_gbs / probe_gather}},
+                "roofline": roofline,
+                "headline": headline,
                 "precision_forms": precision, "confidence_form": confidence,
                 "batched_form": batched,
                 "served_form": served, "paper_schedule_form": paper, "crop_form": crop,

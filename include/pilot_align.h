@@ -308,6 +308,20 @@ pilot_status pilot_probe_fma(double* tflops, void* stream);
 pilot_status pilot_probe_gather(const void* map, int H, int W, int C, pilot_dtype dtype, long long samples,
                                 double* gbps, void* stream);
 
+/* Gather ceiling of the build pass' access pattern on a real frame (the paper has no
+ * counterpart; a roofline probe).  Runs the build pass' loads without its arithmetic on
+ * the same grid (ceil(N / tile) anchor tiles x M poses, 256 threads): every (anchor, pose)
+ * projects the anchor (Eq. 1, level intrinsics fx, fy, cx, cy in pixels of this map, corner
+ * convention) and reads its 4 taps and its reference row, 16-byte loads by lane groups as
+ * the build pass issues them, so the cache reuse between neighbouring anchors is the
+ * frame's own.  DEVICE pointers: points 3 x N FP32 SoA; map H x W x C NHWC and ref N x C in
+ * `dtype` (16-byte aligned; C x element size a power of two from 16 to 256 bytes); poses32
+ * M x 12 FP32 [R | t] world -> camera.  Times one launch after a warm-up one on `stream`
+ * (synchronous) and returns the (anchor, pose) units per second in *units_per_s. */
+pilot_status pilot_probe_gather_frame(const float* points, int N, const void* map, const void* ref, int H, int W,
+                                      int C, pilot_dtype dtype, double fx, double fy, double cx, double cy,
+                                      const float* poses32, int M, int tile, double* units_per_s, void* stream);
+
 /* Failure-detection self-test of the batched form's grid barrier (the paper has no
  * counterpart; the persistent level kernel's barrier waits are bounded in time so that a
  * device that cannot keep every CTA resident yields PILOT_ETIMEOUT instead of a hang).

@@ -75,6 +75,9 @@ SIGNATURES = {
     "pilot_probe_fma": (ct.c_int, [ct.POINTER(ct.c_double), _vp]),
     "pilot_probe_gather": (ct.c_int, [_vp, ct.c_int, ct.c_int, ct.c_int, ct.c_int, ct.c_longlong,
                                       ct.POINTER(ct.c_double), _vp]),
+    "pilot_probe_gather_frame": (ct.c_int, [_vp, ct.c_int, _vp, _vp, ct.c_int, ct.c_int, ct.c_int, ct.c_int,
+                                            ct.c_double, ct.c_double, ct.c_double, ct.c_double, _vp, ct.c_int,
+                                            ct.c_int, ct.POINTER(ct.c_double), _vp]),
     "pilot_align_debug_normal_eq": (ct.c_int, [_vp, ct.POINTER(pilot_frame), ct.c_int, _vp, _vp, _vp]),
     "pilot_align_profile": (ct.c_int, [_vp, ct.POINTER(ct.c_double), ct.POINTER(ct.c_int), ct.POINTER(ct.c_int)]),
     "pilot_align_normal_eq_noalloc": (ct.c_int, [ct.POINTER(pilot_align_config), ct.POINTER(pilot_frame), ct.c_int,
@@ -513,6 +516,20 @@ def probe_gather(map_dev, dtype: int, samples: int = 1 << 24, stream=None) -> fl
     v = ct.c_double()
     check(load().pilot_probe_gather(ct.c_void_p(map_dev.data_ptr()), int(H), int(W), int(C), int(dtype),
                                     int(samples), ct.byref(v), Solver._stream(stream)))
+    return v.value
+
+
+def probe_gather_frame(points_dev, map_dev, ref_dev, dtype: int, fx: float, fy: float, cx: float, cy: float,
+                       poses32_dev, tile: int, stream=None) -> float:
+    """pilot_probe_gather_frame: the build pass' loads on a real frame at one level, no
+    arithmetic; returns (anchor, pose) units per second."""
+    H, W, C = map_dev.shape
+    N = points_dev.shape[-1]
+    M = poses32_dev.shape[0]
+    v = ct.c_double()
+    check(load().pilot_probe_gather_frame(_ptr(points_dev), int(N), _ptr(map_dev), _ptr(ref_dev), int(H), int(W),
+                                          int(C), int(dtype), float(fx), float(fy), float(cx), float(cy),
+                                          _ptr(poses32_dev), int(M), int(tile), ct.byref(v), Solver._stream(stream)))
     return v.value
 
 

@@ -1,5 +1,5 @@
-// Build pass: for one level, every (anchor tile, hypothesis) pair evaluates the photo
-// term of the objective and its normal equations at the hypothesis' candidate pose.
+// Build pass: for one level, every (anchor tile, hypothesis pair) evaluates the photo
+// term of the objective and its normal equations at the two hypotheses' candidate poses.
 //
 //   Eq. 1  r_j = f^q(pi(K_l, T, P_j)) - f^r(p_j)   (bilinear read of C channels)
 //   Eq. 2  cost += rho(w_j ||r_j||^2)              (Huber on the squared norm)
@@ -11,18 +11,23 @@
 // formed: per anchor only the 2x2 Gram matrix M = G^T G, b = G^T r and s = ||r||^2 are
 // summed over channels, then H_j = w A^T M A and g_j = w A^T b.
 //
-// Thread mapping.  A group of LP consecutive lanes works on LP anchors at a time, LP
-// chosen so that one 16-byte load per lane covers a whole tap (LP = C x element size /
-// 16, at most 8: 8 lanes for FP32 at C = 32, 4 for BF16, 2 for FP8), i.e. one L1
-// wavefront per anchor and tap.  Each lane projects one anchor and broadcasts its tap
-// offset and bilinear weights to the group; the group then reads the 4 taps and the
-// reference row of every anchor together (vector k of lane q holds channels
-// VW (q + k LP) .. + VW).  A butterfly reduce-scatter over the group
-// leaves in lane q the channel sums of anchor q, and each lane finishes its own anchor
-// (Huber weight, A, 21 + 6 sums) exactly once.  An invisible anchor's partial sums stay
-// in its own reduce-scatter slot and are discarded by its owner.  The CTA reduces the
-// lanes' sums in a fixed order: the result is deterministic and independent of the
-// grid shape.
+// Thread mapping.  A CTA holds two hypotheses over one anchor tile.  A group of LP
+// consecutive lanes reads one tap with one 16-byte load per lane (LP = C x element size /
+// 16, at most 8: 8 lanes for FP32 at C = 32, 4 for BF16, 2 for FP8), i.e. one L1 wavefront
+// per record and tap, where a record is one (anchor, hypothesis) pair.  A group works on
+// LP records at a time: LP/2 anchors under both hypotheses.  Each lane projects one record
+// (lane q: anchor q mod LP/2 under hypothesis q div LP/2) and broadcasts its tap offset and
+// bilinear weights to the group; the group then reads the 4 taps of every record and the
+// reference row of every anchor together -- once for both hypotheses (vector k of lane q
+// holds channels VW (q + k LP) .. + VW).  A butterfly reduce-scatter over the group leaves
+// in lane q the channel sums of record q, and each lane finishes its own record (Huber
+// weight, A, 21 + 6 sums) exactly once.  An invisible record's partial sums stay in its own
+// reduce-scatter slot and are discarded by its owner.  With one lane per record (LP = 1)
+// two lanes form a group, one per hypothesis, each reading its record alone.  The CTA
+// reduces the lanes of each hypothesis in a fixed order.  A hypothesis' sums do not depend
+// on which of the two slots it takes or on the other hypothesis (the lanes of the two
+// slots run the same anchors in the same order, and the reduction trees are mirror
+// images), so the result is deterministic and independent of the grid shape and pairing.
 #pragma once
 
 #include <cuda_bf16.h>
@@ -187,6 +192,18 @@ __device__ __forceinline__ float hsum(f2 v) {
     return lo + hi;
 }
 
+// Lanes per tap (LP), lanes per group (LG) and anchors per group batch (APB) for C channels
+// stored as DT.  A group takes LG records at a time: APB anchors under both hypotheses of the
+// CTA; the hypothesis of lane q is q / APB, so lane bit APB tells the two slots apart.
+template <pilot_dtype DT, int C> struct GroupShape {
+    static constexpr int VEC = Storage<DT>::VEC;              // channels per 16-byte vector
+    static constexpr int VW = (C < VEC) ? C : VEC;            // channels per vector load
+    static constexpr int LP = (C / VW < 8) ? C / VW : 8;      // lanes per tap
+    static constexpr int LG = LP > 1 ? LP : 2;                // lanes per group = records per batch
+    static constexpr int APB = LG / 2;                        // anchors per group batch
+    static constexpr int NV = C / LP / VW;                    // vector loads per lane and tap
+};
+
 // The level-specific inputs of the anchor loop.
 struct LevelView {
     const float* px;
@@ -208,40 +225,80 @@ __device__ __forceinline__ LevelView level_view(const BuildParams& p) {
                      p.H, p.W, p.fx, p.fy, p.cx, p.cy, p.huber};
 }
 
-// Accumulate anchors [j_begin, j_end) at pose P (12 FP32 values) into this lane's 29
-// sums.  Every thread of the CTA calls it with the same range; threads are grouped as
-// described at the top of the file.
+// Channel sums of one record over this lane's channels (vector k covers VW (q + k LP) ..
+// + VW): the 4 taps at t00 (row below at t00 + WC) against the reference values rr (already
+// loaded, shared by the two hypotheses of an anchor): bilinear value and in-cell gradient,
+// residual, and the six partial sums.
+template <pilot_dtype DT, int C, bool SCALED>
+__device__ __forceinline__ void record_partials(const typename Storage<DT>::T* t00, int WC, const float* rr,
+                                                float ax, float ay, int q, const float* qs, const float* rs,
+                                                float* p) {
+    using G = GroupShape<DT, C>;
+    constexpr int VW = G::VW, LP = G::LP, NV = G::NV;
+    const typename Storage<DT>::T* t10 = t00 + WC;
+    const f2 ax2 = pk(ax, ax), ay2 = pk(ay, ay), z2 = pk(0.f, 0.f);
+    ChanSums2 cs{z2, z2, z2, z2, z2, z2};
+#pragma unroll
+    for (int k = 0; k < NV; ++k) {
+        const int c = VW * (q + k * LP);
+        float a00[VW], a01[VW], a10[VW], a11[VW];
+        load_vec<DT, VW>(t00 + c, a00);
+        load_vec<DT, VW>(t00 + c + C, a01);
+        load_vec<DT, VW>(t10 + c, a10);
+        load_vec<DT, VW>(t10 + c + C, a11);
+        const float* r = rr + k * VW;
+#pragma unroll
+        for (int e = 0; e < VW; e += 2)
+            channel_pair<SCALED>(cs, pk(a00[e], a00[e + 1]), pk(a01[e], a01[e + 1]), pk(a10[e], a10[e + 1]),
+                                 pk(a11[e], a11[e + 1]), pk(r[e], r[e + 1]), ax2, ay2,
+                                 pk(qs[k * VW + e], qs[k * VW + e + 1]), pk(rs[k * VW + e], rs[k * VW + e + 1]));
+    }
+    p[0] = hsum(cs.s);
+    p[1] = hsum(cs.m00);
+    p[2] = hsum(cs.m01);
+    p[3] = hsum(cs.m11);
+    p[4] = hsum(cs.b0);
+    p[5] = hsum(cs.b1);
+}
+
+// Accumulate anchors [j_begin, j_end) under the CTA's two hypotheses into this lane's 29
+// sums (the lane's own hypothesis: q / APB).  P0, P1: the two poses (12 FP32 values each);
+// act0, act1: whether each slot has a pose to evaluate (an inactive slot's lanes finish
+// nothing).  Every thread of the CTA calls it with the same arguments; threads are grouped
+// as described at the top of the file.
 template <pilot_dtype DT, int C, bool SCALED, bool CONF, int NTHREADS>
-__device__ __forceinline__ void accumulate_anchors(const LevelView& v, const float* P, int j_begin,
-                                                   int j_end, float* acc) {
+__device__ __forceinline__ void accumulate_anchors(const LevelView& v, const float* P0, const float* P1, bool act0,
+                                                   bool act1, int j_begin, int j_end, float* acc) {
     using Elem = typename Storage<DT>::T;
-    constexpr int VEC = Storage<DT>::VEC;            // channels per 16-byte vector
-    constexpr int VW = (C < VEC) ? C : VEC;          // channels per vector load
-    constexpr int LP = (C / VW < 8) ? C / VW : 8;    // lanes per group = anchors per batch
+    using G = GroupShape<DT, C>;
+    constexpr int VW = G::VW, LP = G::LP, LG = G::LG, APB = G::APB, NV = G::NV;
     constexpr int CPL = C / LP;                      // channels per lane
-    constexpr int NV = CPL / VW;                     // vector loads per lane and tap
-    constexpr int GROUPS = NTHREADS / LP;
-    constexpr int BATCH = GROUPS * LP;
+    constexpr int GROUPS = NTHREADS / LG;
+    constexpr int ASTEP = GROUPS * APB;              // anchors per CTA batch
     static_assert(C % 4 == 0 && C >= 4 && C <= 64 && LP >= 1 && LP <= 8, "channels");
 
     const int tid = threadIdx.x;
     const int lane = tid & 31;
-    const int q = lane & (LP - 1);
-    const int grp = tid / LP;
-    const int src0 = lane & ~(LP - 1);
-    const unsigned gmask = (((1u << LP) - 1u) << src0);
+    const int q = lane & (LG - 1);
+    const int hyp = q / APB;                         // this lane's slot
+    const int qa = q % APB;                          // this lane's anchor in the batch
+    const int src0 = lane & ~(LG - 1);
+    const unsigned gmask = (((1u << LG) - 1u) << src0);
+    const int cq = LP > 1 ? q : 0;                   // channel block of this lane
 
+    const float* P = hyp ? P1 : P0;
+    const bool act = hyp ? act1 : act0;
     const float R00 = P[0], R01 = P[1], R02 = P[2], T0 = P[3];
     const float R10 = P[4], R11 = P[5], R12 = P[6], T1 = P[7];
     const float R20 = P[8], R21 = P[9], R22 = P[10], T2 = P[11];
 
-    // channels owned by this lane: vector k covers VW (q + k LP) .. + VW
+    // channels owned by this lane: vector k covers VW (cq + k LP) .. + VW
     float qs[CPL], rs[CPL];
 #pragma unroll
     for (int k = 0; k < NV; ++k)
 #pragma unroll
         for (int e = 0; e < VW; ++e) {
-            const int ch = VW * (q + k * LP) + e;
+            const int ch = VW * (cq + k * LP) + e;
             qs[k * VW + e] = SCALED ? __ldg(v.qscale + ch) : 1.0f;
             rs[k * VW + e] = SCALED ? __ldg(v.rscale + ch) : 1.0f;
         }
@@ -252,13 +309,13 @@ __device__ __forceinline__ void accumulate_anchors(const LevelView& v, const flo
     const float xmax = (float)(v.W - 1), ymax = (float)(v.H - 1);
     const float d2 = v.huber * v.huber;
 
-    for (int jb = j_begin + grp * LP; jb < j_end; jb += BATCH) {
-        // 1. every lane projects its own anchor jb + q
-        const int jo = jb + q;
+    for (int jb = j_begin + (tid / LG) * APB; jb < j_end; jb += ASTEP) {
+        // 1. every lane projects its own record: anchor jb + qa under its hypothesis
+        const int jo = jb + qa;
         bool vis = false;
         int off = 0;
         float ax = 0.f, ay = 0.f, x = 0.f, y = 0.f, z = 1.f, iz = 1.f, wq = 1.f;
-        if (jo < j_end && (!v.valid || v.valid[jo])) {
+        if (act && jo < j_end && (!v.valid || v.valid[jo])) {
             const float X = __ldg(v.px + jo), Y = __ldg(v.py + jo), Z = __ldg(v.pz + jo);
             // p = R P + t  (world -> camera)
             x = fmaf(R00, X, fmaf(R01, Y, fmaf(R02, Z, T0)));
@@ -280,96 +337,76 @@ __device__ __forceinline__ void accumulate_anchors(const LevelView& v, const flo
                         const float* cp = v.conf + r0 * v.W + c0;
                         const float c00 = __ldg(cp), c01 = __ldg(cp + 1);
                         const float c10 = __ldg(cp + v.W), c11 = __ldg(cp + v.W + 1);
-                        const float bq = c01 - c00, cq = c10 - c00, dq = (c11 - c10) - bq;
-                        wq = fmaf(ax, fmaf(dq, ay, bq), fmaf(ay, cq, c00));
+                        const float bq = c01 - c00, cq2 = c10 - c00, dq = (c11 - c10) - bq;
+                        wq = fmaf(ax, fmaf(dq, ay, bq), fmaf(ay, cq2, c00));
                     }
                 }
             }
         }
 
-        // 2. the group reads the taps of its LP anchors together, two at a time: anchors
-        //    t and t + LP/2 are read, then the first butterfly round (xor LP/2) keeps in
-        //    each lane only the half it owns, so only LP/2 partial records stay live
-        constexpr int HALF = (LP > 1) ? LP / 2 : 1;
-        float S[HALF][6];
+        float S[6];
+        if constexpr (LP == 1) {
+            // one lane per record: its own taps and reference row
+            float rr[C];
+            const Elem* fr = ref + (jo < j_end ? jo : j_begin) * C;
 #pragma unroll
-        for (int t = 0; t < HALF; ++t) {
-            float P2[2][6];
+            for (int k = 0; k < NV; ++k) load_vec<DT, VW>(fr + VW * k, rr + VW * k);
+            record_partials<DT, C, SCALED>(qry + off, WC, rr, ax, ay, 0, qs, rs, S);
+        } else {
+            // 2. the group reads its records two at a time: anchor t under both hypotheses
+            //    (records t and t + APB) with one read of the anchor's reference row; the
+            //    first butterfly round (xor APB) then keeps in each lane only the record of
+            //    its own slot, so only APB partial records stay live
+            float B[APB][6];
 #pragma unroll
-            for (int u = 0; u < ((LP > 1) ? 2 : 1); ++u) {
-                const int i = t + u * HALF;
-                int vi = (int)vis, oi = off;
-                float axi = ax, ayi = ay;
-                if constexpr (LP > 1) {
-                    vi = __shfl_sync(gmask, (int)vis, src0 + i);
-                    oi = __shfl_sync(gmask, off, src0 + i);
-                    axi = __shfl_sync(gmask, ax, src0 + i);
-                    ayi = __shfl_sync(gmask, ay, src0 + i);
+            for (int t = 0; t < APB; ++t) {
+                float rr[CPL];
+                const int ja = jb + t;
+                const Elem* fr = ref + (ja < j_end ? ja : j_begin) * C;
+#pragma unroll
+                for (int k = 0; k < NV; ++k) load_vec<DT, VW>(fr + VW * (q + k * LP), rr + k * VW);
+                float P2[2][6];
+#pragma unroll
+                for (int u = 0; u < 2; ++u) {
+                    const int i = t + u * APB;
+                    const int vi = __shfl_sync(gmask, (int)vis, src0 + i);
+                    const int oi = __shfl_sync(gmask, off, src0 + i);
+                    const float axi = __shfl_sync(gmask, ax, src0 + i);
+                    const float ayi = __shfl_sync(gmask, ay, src0 + i);
+                    record_partials<DT, C, SCALED>(qry + (vi ? oi : 0), WC, rr, axi, ayi, q, qs, rs, P2[u]);
                 }
-                const int ri = (vi ? jb + i : 0) * C;    // row 0 is a safe dummy
-                const Elem* t00 = qry + oi;
-                const Elem* t10 = t00 + WC;
-                const Elem* fr = ref + ri;
-                const f2 ax2 = pk(axi, axi), ay2 = pk(ayi, ayi), z2 = pk(0.f, 0.f);
-                ChanSums2 cs{z2, z2, z2, z2, z2, z2};
-#pragma unroll
-                for (int k = 0; k < NV; ++k) {
-                    const int c = VW * (q + k * LP);
-                    float a00[VW], a01[VW], a10[VW], a11[VW], rr[VW];
-                    load_vec<DT, VW>(t00 + c, a00);
-                    load_vec<DT, VW>(t00 + c + C, a01);
-                    load_vec<DT, VW>(t10 + c, a10);
-                    load_vec<DT, VW>(t10 + c + C, a11);
-                    load_vec<DT, VW>(fr + c, rr);
-#pragma unroll
-                    for (int e = 0; e < VW; e += 2)
-                        channel_pair<SCALED>(cs, pk(a00[e], a00[e + 1]), pk(a01[e], a01[e + 1]),
-                                             pk(a10[e], a10[e + 1]), pk(a11[e], a11[e + 1]),
-                                             pk(rr[e], rr[e + 1]), ax2, ay2,
-                                             pk(qs[k * VW + e], qs[k * VW + e + 1]),
-                                             pk(rs[k * VW + e], rs[k * VW + e + 1]));
-                }
-                P2[u][0] = hsum(cs.s);
-                P2[u][1] = hsum(cs.m00);
-                P2[u][2] = hsum(cs.m01);
-                P2[u][3] = hsum(cs.m11);
-                P2[u][4] = hsum(cs.b0);
-                P2[u][5] = hsum(cs.b1);
-            }
-            if constexpr (LP > 1) {
-                const bool upper = (q & HALF) != 0;
+                const bool upper = hyp != 0;
 #pragma unroll
                 for (int k = 0; k < 6; ++k) {
                     const float send = upper ? P2[0][k] : P2[1][k];
                     const float keep = upper ? P2[1][k] : P2[0][k];
-                    S[t][k] = keep + __shfl_xor_sync(gmask, send, HALF);
-                }
-            } else {
-#pragma unroll
-                for (int k = 0; k < 6; ++k) S[t][k] = P2[0][k];
-            }
-        }
-
-        // 3. remaining butterfly rounds: afterwards S[0] of lane q holds anchor q's sums
-#pragma unroll
-        for (int half = HALF / 2; half >= 1; half >>= 1) {
-            const bool upper = (q & half) != 0;
-#pragma unroll
-            for (int t = 0; t < half; ++t) {
-#pragma unroll
-                for (int k = 0; k < 6; ++k) {
-                    const float send = upper ? S[t][k] : S[t + half][k];
-                    const float keep = upper ? S[t + half][k] : S[t][k];
-                    S[t][k] = keep + __shfl_xor_sync(gmask, send, half);
+                    B[t][k] = keep + __shfl_xor_sync(gmask, send, APB);
                 }
             }
+            // 3. remaining butterfly rounds over the anchors: afterwards B[0] of lane q holds
+            //    record q's sums
+#pragma unroll
+            for (int half = APB / 2; half >= 1; half >>= 1) {
+                const bool upper = (q & half) != 0;
+#pragma unroll
+                for (int t = 0; t < half; ++t) {
+#pragma unroll
+                    for (int k = 0; k < 6; ++k) {
+                        const float send = upper ? B[t][k] : B[t + half][k];
+                        const float keep = upper ? B[t + half][k] : B[t][k];
+                        B[t][k] = keep + __shfl_xor_sync(gmask, send, half);
+                    }
+                }
+            }
+#pragma unroll
+            for (int k = 0; k < 6; ++k) S[k] = B[0][k];
         }
 
-        // 4. each lane finishes its own anchor: Huber weight, A = d(u,v)/dp [I | -[p]x],
+        // 4. each lane finishes its own record: Huber weight, A = d(u,v)/dp [I | -[p]x],
         //    H += w A^T M A, g += w A^T b
         if (vis) {
-            const float s = S[0][0], m00 = S[0][1], m01 = S[0][2], m11 = S[0][3];
-            const float b0 = S[0][4], b1 = S[0][5];
+            const float s = S[0], m00 = S[1], m01 = S[2], m11 = S[3];
+            const float b0 = S[4], b1 = S[5];
             const float w = (v.weight ? __ldg(v.weight + jo) : 1.0f) * wq;
             const float sw = w * s;
             float rho, drho;
@@ -428,109 +465,143 @@ __device__ __forceinline__ void accumulate_anchors(const LevelView& v, const flo
     }
 }
 
-// Fixed-order CTA reduction of the lanes' 29 sums; thread t < kAcc returns sum t (0 pads).
-template <int NTHREADS>
-__device__ __forceinline__ float cta_reduce(float* acc, float (*red)[kAcc]) {
+// Fixed-order CTA reduction of the lanes' 29 sums, per hypothesis slot: the lanes of a slot
+// are reduced by a butterfly over every lane bit but the slot bit (APB), then the warps in
+// order.  Thread t < 2 kAcc returns sum t mod kAcc of slot t / kAcc (0 pads).
+template <int NTHREADS, int APB>
+__device__ __forceinline__ float cta_reduce_pair(float* acc, float (*red)[2][kAcc]) {
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
 #pragma unroll
     for (int off = 1; off < 32; off <<= 1) {
+        if (off == APB) continue;
 #pragma unroll
         for (int i = 0; i < kNumSums; ++i) acc[i] += __shfl_xor_sync(0xffffffffu, acc[i], off);
     }
-    if (lane == 0) {
+    if (lane == 0 || lane == APB) {
 #pragma unroll
-        for (int i = 0; i < kNumSums; ++i) red[warp][i] = acc[i];
+        for (int i = 0; i < kNumSums; ++i) red[warp][lane == APB][i] = acc[i];
     }
     __syncthreads();
     float v = 0.f;
-    if (tid < kNumSums) {
+    if (tid < 2 * kAcc && (tid % kAcc) < kNumSums) {
 #pragma unroll
-        for (int w = 0; w < NTHREADS / 32; ++w) v += red[w][tid];
+        for (int w = 0; w < NTHREADS / 32; ++w) v += red[w][tid / kAcc][tid % kAcc];
     }
     return v;
+}
+
+// The CTA's hypothesis pair: slots 2 blockIdx.y and 2 blockIdx.y + 1 of the active list (the
+// second absent when the count is odd).
+struct PairSlots {
+    int slot[2];
+    int hyp[2];
+    bool cand[2];
+    int n;                                           // 1 or 2
+};
+
+__device__ __forceinline__ PairSlots pair_slots(const BuildParams& p) {
+    PairSlots s;
+    s.n = min(2, p.n_active - 2 * (int)blockIdx.y);
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        s.slot[h] = 2 * blockIdx.y + (h < s.n ? h : 0);
+        s.hyp[h] = p.active_idx[s.slot[h]];
+        s.cand[h] = h < s.n && p.state[s.hyp[h]].has_cand;
+    }
+    return s;
 }
 
 template <pilot_dtype DT, int C, bool SCALED, bool CONF>
 __global__ void __launch_bounds__(kBuildThreads, 2)
 build_kernel(const BuildParams p) {
-    __shared__ float red[kBuildThreads / 32][kAcc];
-    const int slot = blockIdx.y;
-    const int hyp = p.active_idx[slot];
-    float* out = p.partial + ((size_t)slot * p.n_tiles + blockIdx.x) * kAcc;
-    if (!p.state[hyp].has_cand) return;            // uniform over the CTA
+    __shared__ float red[kBuildThreads / 32][2][kAcc];
+    const PairSlots ps = pair_slots(p);
+    if (!ps.cand[0] && !ps.cand[1]) return;          // uniform over the CTA
     float acc[kNumSums];
 #pragma unroll
     for (int i = 0; i < kNumSums; ++i) acc[i] = 0.f;
     const int j0 = blockIdx.x * p.tile;
-    accumulate_anchors<DT, C, SCALED, CONF, kBuildThreads>(level_view(p), p.pose32 + 12 * hyp, j0,
-                                                     min(j0 + p.tile, p.N), acc);
-    const float v = cta_reduce<kBuildThreads>(acc, red);
-    if (threadIdx.x < kAcc) out[threadIdx.x] = v;
+    accumulate_anchors<DT, C, SCALED, CONF, kBuildThreads>(level_view(p), p.pose32 + 12 * ps.hyp[0],
+                                                           p.pose32 + 12 * ps.hyp[1], ps.cand[0], ps.cand[1], j0,
+                                                           min(j0 + p.tile, p.N), acc);
+    const float v = cta_reduce_pair<kBuildThreads, GroupShape<DT, C>::APB>(acc, red);
+    const int h = threadIdx.x / kAcc;
+    if (threadIdx.x < 2 * kAcc && h < ps.n && ps.cand[h])
+        p.partial[((size_t)ps.slot[h] * p.n_tiles + blockIdx.x) * kAcc + threadIdx.x % kAcc] = v;
 }
 
 // The same pass with the per-hypothesis FP64 step fused in: the CTA that takes the last
-// ticket of its hypothesis sums the tile records (FP64, 8 chains per value, fixed order)
-// and runs lm_step.  A hypothesis without a candidate runs its step in tile 0's CTA.
+// ticket of its pair sums the tile records of both hypotheses (FP64, 8 chains per value,
+// fixed order) and runs lm_step for them on warps 0 and 1.  A pair with no candidate runs
+// its steps in tile 0's CTA.
 template <pilot_dtype DT, int C, bool SCALED, bool CONF>
 __global__ void __launch_bounds__(kBuildThreads, 2)
 build_fused_kernel(const FusedBuildParams fp) {
     const BuildParams& p = fp.b;
-    __shared__ float red[kBuildThreads / 32][kAcc];
-    __shared__ double part[8][kAcc];
-    __shared__ double E[kAcc];
+    __shared__ float red[kBuildThreads / 32][2][kAcc];
+    __shared__ double part[2][8][kAcc];
+    __shared__ double E[2][kAcc];
     __shared__ int s_last;
-    const int slot = blockIdx.y;
-    const int hyp = p.active_idx[slot];
-    const int tid = threadIdx.x;
-    if (!p.state[hyp].has_cand) {                  // uniform over the CTA
-        if (blockIdx.x == 0 && tid < 32) lm_step(fp.ep, slot, E, &part[0][0], *fp.min_valid, tid);
+    const PairSlots ps = pair_slots(p);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    if (!ps.cand[0] && !ps.cand[1]) {                // uniform over the CTA
+        if (blockIdx.x == 0 && warp < ps.n) lm_step(fp.ep, ps.slot[warp], E[warp], &part[warp][0][0], *fp.min_valid, lane);
         return;
     }
     float acc[kNumSums];
 #pragma unroll
     for (int i = 0; i < kNumSums; ++i) acc[i] = 0.f;
     const int j0 = blockIdx.x * p.tile;
-    accumulate_anchors<DT, C, SCALED, CONF, kBuildThreads>(level_view(p), p.pose32 + 12 * hyp, j0,
-                                                     min(j0 + p.tile, p.N), acc);
-    const float v = cta_reduce<kBuildThreads>(acc, red);
+    accumulate_anchors<DT, C, SCALED, CONF, kBuildThreads>(level_view(p), p.pose32 + 12 * ps.hyp[0],
+                                                           p.pose32 + 12 * ps.hyp[1], ps.cand[0], ps.cand[1], j0,
+                                                           min(j0 + p.tile, p.N), acc);
+    const float v = cta_reduce_pair<kBuildThreads, GroupShape<DT, C>::APB>(acc, red);
+    const int hv = tid / kAcc, iv = tid % kAcc;     // slot and sum this thread holds (tid < 64)
     if (p.n_tiles == 1) {
         // the only tile: its record is the sum (0 + x is what the 8-chain sum gives), no
         // round trip through the partial buffer and the ticket
-        if (tid < kAcc) E[tid] = 0.0 + (double)v;
+        if (tid < 2 * kAcc) E[hv][iv] = 0.0 + (double)v;
         __syncthreads();
-        if (tid < 32) lm_step(fp.ep, slot, E, &part[0][0], *fp.min_valid, tid);
+        if (warp < ps.n) lm_step(fp.ep, ps.slot[warp], E[warp], &part[warp][0][0], *fp.min_valid, lane);
         return;
     }
-    float* out = p.partial + ((size_t)slot * p.n_tiles + blockIdx.x) * kAcc;
-    if (tid < kAcc) out[tid] = v;
+    if (tid < 2 * kAcc && hv < ps.n && ps.cand[hv])
+        p.partial[((size_t)ps.slot[hv] * p.n_tiles + blockIdx.x) * kAcc + iv] = v;
     __threadfence();
     __syncthreads();
-    if (tid == 0) s_last = (atomicAdd(fp.tickets + slot, 1u) == (unsigned)(p.n_tiles - 1));
+    if (tid == 0) s_last = (atomicAdd(fp.tickets + blockIdx.y, 1u) == (unsigned)(p.n_tiles - 1));
     __syncthreads();
     if (!s_last) return;
     __threadfence();
-    const int vi = tid & 31, c = tid >> 5;
-    const float* src = p.partial + (size_t)slot * p.n_tiles * kAcc + vi;
-    double a = 0.0;
-    for (int t = c; t < p.n_tiles; t += 8) a += (double)__ldcg(src + (size_t)t * kAcc);
-    part[c][vi] = a;
+    // 8 chains per slot and value: thread (h, c, i) sums tiles c, c + 8, ... of sum i of slot h
+    {
+        const int h = tid >> 7, c = (tid >> 4) & 7;
+        for (int ii = tid & 15; ii < kAcc; ii += 16) {
+            double a = 0.0;
+            if (h < ps.n && ps.cand[h]) {
+                const float* src = p.partial + (size_t)ps.slot[h] * p.n_tiles * kAcc + ii;
+                for (int t = c; t < p.n_tiles; t += 8) a += (double)__ldcg(src + (size_t)t * kAcc);
+            }
+            part[h][c][ii] = a;
+        }
+    }
     __syncthreads();
-    if (tid < kAcc) {
+    if (tid < 2 * kAcc) {
         double sum = 0.0;
 #pragma unroll
-        for (int k = 0; k < 8; ++k) sum += part[k][tid];
-        E[tid] = sum;
+        for (int k = 0; k < 8; ++k) sum += part[hv][k][iv];
+        E[hv][iv] = sum;
     }
     __syncthreads();
-    if (tid < 32) {                                // the warp-cooperative FP64 step
-        lm_step(fp.ep, slot, E, &part[0][0], *fp.min_valid, tid);
-        if (tid == 0) fp.tickets[slot] = 0u;
+    if (warp < ps.n) {                               // the warp-cooperative FP64 steps
+        lm_step(fp.ep, ps.slot[warp], E[warp], &part[warp][0][0], *fp.min_valid, lane);
     }
+    if (tid == 0) fp.tickets[blockIdx.y] = 0u;
 }
 
 template <pilot_dtype DT, int C>
 cudaError_t launch_build_typed(const BuildParams& p, cudaStream_t s) {
-    dim3 grid(p.n_tiles, p.n_active);
+    dim3 grid(p.n_tiles, (p.n_active + 1) / 2);
     if (p.qscale && p.conf)
         build_kernel<DT, C, true, true><<<grid, kBuildThreads, 0, s>>>(p);
     else if (p.qscale)
@@ -544,7 +615,7 @@ cudaError_t launch_build_typed(const BuildParams& p, cudaStream_t s) {
 
 template <pilot_dtype DT, int C>
 cudaError_t launch_build_fused_typed(const FusedBuildParams& p, cudaStream_t s) {
-    dim3 grid(p.b.n_tiles, p.b.n_active);
+    dim3 grid(p.b.n_tiles, (p.b.n_active + 1) / 2);
     if (p.b.qscale && p.b.conf)
         build_fused_kernel<DT, C, true, true><<<grid, kBuildThreads, 0, s>>>(p);
     else if (p.b.qscale)

@@ -467,7 +467,7 @@ __global__ void round_advance_kernel(const BatchHeader* hdr, FrameDesc* frames, 
             f.flags = 0;
         }
         fr_job[i + 1] = fr_job[i] + f.n_active;
-        fr_item[i + 1] = fr_item[i] + f.n_active * items_per_job(f.N, tile, tpi);
+        fr_item[i + 1] = fr_item[i] + frame_items(f.n_active, f.N, tile, tpi);
     }
 }
 

@@ -34,6 +34,12 @@ __host__ __device__ inline int items_per_job(int N, int tile, int tpi) {
     const int tiles = N > 0 ? (N + tile - 1) / tile : 1;
     return (tiles + tpi - 1) / tpi;
 }
+
+// Work items of a frame of N anchors with n_jobs jobs: the jobs are taken in pairs (a work
+// item covers both jobs of a pair, as a build-pass CTA holds two hypotheses).
+__host__ __device__ inline int frame_items(int n_jobs, int N, int tile, int tpi) {
+    return (n_jobs + 1) / 2 * items_per_job(N, tile, tpi);
+}
 constexpr int kBuildThreads = 256;
 constexpr float kZNear = 0.1f;
 
@@ -106,12 +112,12 @@ struct EpilogueParams {
     double* eval_out;          // kEpiEval: [slot][29]
 };
 
-// A build pass whose last CTA per hypothesis runs the FP64 LM step itself (the CTA that
-// takes the last ticket of its hypothesis sums the tile records and calls lm_step).
+// A build pass whose last CTA per hypothesis pair runs the FP64 LM steps itself (the CTA
+// that takes the last ticket of its pair sums the tile records and calls lm_step for both).
 struct FusedBuildParams {
     BuildParams b;
     EpilogueParams ep;
-    unsigned* tickets;         // [n_active], zero between launches
+    unsigned* tickets;         // [(n_active + 1) / 2], one per hypothesis pair, zero between launches
     const double* min_valid;
 };
 
@@ -155,8 +161,9 @@ struct BatchHeader {
 // frame) and work items are numbered frame after frame in list order: listed frame i is
 // frames[fr_list[i]]; its jobs are fr_job[i] .. fr_job[i + 1] - 1 (its active slots in
 // order) and its items fr_item[i] .. fr_item[i + 1] - 1, items_per_job(N) consecutive items
-// per job, each covering tiles_per_item anchor tiles.  Tile t of the job whose first item is
-// q keeps its record at partial[q * tiles_per_item + t].
+// per pair of jobs (2p, 2p + 1), each covering tiles_per_item anchor tiles of both.  Tile t
+// of job 2p + h, whose pair's first item is q, keeps its record at
+// partial[(q * tiles_per_item + t) * 2 + h].
 struct LevelArgs {
     const BatchHeader* header;
     const FrameDesc* frames;

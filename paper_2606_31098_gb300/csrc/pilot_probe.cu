@@ -8,6 +8,10 @@
 //                       covering a whole tap (so each load instruction touches one line per
 //                       group).  Random pixels give no reuse between samples, so this is the
 //                       L2-to-SM gather rate of the map's layout.
+//   pilot_probe_gather_frame  the build pass' loads with the locality of a real frame:
+//                       the same grid (anchor tiles x poses) and lane groups, anchors
+//                       projected under real poses, 4 taps and the reference row of every
+//                       (anchor, pose), no arithmetic: the gather ceiling of that pattern.
 #include <cuda_runtime.h>
 
 #include "pilot_internal.cuh"
@@ -75,6 +79,57 @@ __global__ void gather_probe_kernel(const uint4* map, int H, int W, long long sa
         for (int u = 0; u < 2; ++u)
 #pragma unroll
             for (int k = 0; k < 4; ++k) acc ^= v[u][k][0] ^ v[u][k][1];
+    }
+    if (acc == 0x9e3779b9u) atomicXor(&g_probe_sink, acc);
+}
+
+// The build pass' own access pattern without its arithmetic: grid (anchor tiles x poses),
+// 256 threads, groups of LP lanes; each lane projects one anchor under its CTA's pose and
+// publishes the tap offset to the group (shuffles), then the group reads the 4 taps and the
+// reference row of each of its LP anchors with NV 16-byte loads per lane and tap (row 0 for
+// an anchor that is not visible, as the build pass does).  Loaded words are XOR-folded.
+template <int LP, int NV>
+__global__ void __launch_bounds__(256) frame_gather_probe_kernel(const float* pts, int N, const uint4* map,
+                                                                 const uint4* ref, int H, int W, float fx,
+                                                                 float fy, float cx, float cy,
+                                                                 const float* poses, int tile) {
+    constexpr int V = LP * NV;                 // 16-byte vectors per tap (= per reference row)
+    const float* P = poses + 12 * blockIdx.y;
+    const float R00 = P[0], R01 = P[1], R02 = P[2], T0 = P[3], R10 = P[4], R11 = P[5], R12 = P[6], T1 = P[7];
+    const float R20 = P[8], R21 = P[9], R22 = P[10], T2 = P[11];
+    const int lane = threadIdx.x & 31, q = lane & (LP - 1), src0 = lane & ~(LP - 1);
+    const unsigned gmask = (((1u << LP) - 1u) << src0);
+    const int j0 = blockIdx.x * tile, j1 = min(j0 + tile, N);
+    const size_t row = (size_t)W * V;
+    unsigned acc = 0;
+    for (int jb = j0 + (int)(threadIdx.x / LP) * LP; jb < j1; jb += 256) {
+        const int jo = jb + q;
+        int off = -1;
+        if (jo < j1) {
+            const float X = __ldg(pts + jo), Y = __ldg(pts + N + jo), Z = __ldg(pts + 2 * N + jo);
+            const float x = fmaf(R00, X, fmaf(R01, Y, fmaf(R02, Z, T0)));
+            const float y = fmaf(R10, X, fmaf(R11, Y, fmaf(R12, Z, T1)));
+            const float z = fmaf(R20, X, fmaf(R21, Y, fmaf(R22, Z, T2)));
+            if (z > kZNear) {
+                const float iz = 1.0f / z;
+                const float xs = fmaf(fx * x, iz, cx) - 0.5f, ys = fmaf(fy * y, iz, cy) - 0.5f;
+                if (xs >= 0.f && xs <= (float)(W - 1) && ys >= 0.f && ys <= (float)(H - 1))
+                    off = min((int)ys, H - 2) * W + min((int)xs, W - 2);
+            }
+        }
+#pragma unroll
+        for (int i = 0; i < LP; ++i) {
+            const int oi = LP > 1 ? __shfl_sync(gmask, off, src0 + i) : off;
+            const uint4* t00 = map + (size_t)(oi >= 0 ? oi : 0) * V;
+            const uint4* fr = ref + (size_t)(oi >= 0 ? jb + i : 0) * V;
+#pragma unroll
+            for (int k = 0; k < NV; ++k) {
+                const int c = q + k * LP;
+                const uint4 a = __ldg(t00 + c), b = __ldg(t00 + V + c), d = __ldg(t00 + row + c);
+                const uint4 e = __ldg(t00 + row + V + c), r = __ldg(fr + c);
+                acc ^= a.x ^ a.w ^ b.y ^ b.z ^ d.x ^ d.w ^ e.y ^ e.z ^ r.x ^ r.w;
+            }
+        }
     }
     if (acc == 0x9e3779b9u) atomicXor(&g_probe_sink, acc);
 }
@@ -172,6 +227,44 @@ pilot_status pilot_probe_gather(const void* map, int H, int W, int C, pilot_dtyp
     e = time_launch(go, s, &ms);
     if (e != cudaSuccess) return probe_fail(PILOT_ECUDA, cudaGetErrorString(e));
     *gbps = (double)samples * 4.0 * tap / (ms * 1e-3) / 1e9;
+    return PILOT_OK;
+}
+
+pilot_status pilot_probe_gather_frame(const float* points, int N, const void* map, const void* ref, int H, int W,
+                                      int C, pilot_dtype dtype, double fx, double fy, double cx, double cy,
+                                      const float* poses32, int M, int tile, double* units_per_s, void* stream) {
+    if (!points || !map || !ref || !poses32 || !units_per_s) return probe_fail(PILOT_EINVAL, "NULL argument");
+    if (N < 1 || M < 1 || M > 65535 || tile < 1) return probe_fail(PILOT_EINVAL, "N, M and tile must be positive, M <= 65535");
+    if (H < 2 || W < 2) return probe_fail(PILOT_EINVAL, "map must be at least 2 x 2");
+    if (reinterpret_cast<uintptr_t>(map) % 16 || reinterpret_cast<uintptr_t>(ref) % 16)
+        return probe_fail(PILOT_EINVAL, "map and ref must be 16-byte aligned");
+    const int elem = dtype == PILOT_F32 ? 4 : (dtype == PILOT_FP8E4M3 ? 1 : 2);
+    const int vec = C * elem / 16;               // 16-byte vectors per tap
+    if (C * elem % 16 || vec < 1 || vec > 16 || (vec & (vec - 1)))
+        return probe_fail(PILOT_EINVAL, "a tap (C x element size) must be 16 .. 256 bytes, a power of two");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const dim3 grid((N + tile - 1) / tile, M);
+    const float f[4] = {(float)fx, (float)fy, (float)cx, (float)cy};
+    const uint4* mp = static_cast<const uint4*>(map);
+    const uint4* rp = static_cast<const uint4*>(ref);
+    auto go = [&]() {
+#define PILOT_FRAME_PROBE(LP, NV)                                                                             \
+    frame_gather_probe_kernel<LP, NV><<<grid, 256, 0, s>>>(points, N, mp, rp, H, W, f[0], f[1], f[2], f[3], \
+                                                           poses32, tile)
+        switch (vec) {
+            case 1: PILOT_FRAME_PROBE(1, 1); break;
+            case 2: PILOT_FRAME_PROBE(2, 1); break;
+            case 4: PILOT_FRAME_PROBE(4, 1); break;
+            case 8: PILOT_FRAME_PROBE(8, 1); break;
+            default: PILOT_FRAME_PROBE(8, 2); break;
+        }
+#undef PILOT_FRAME_PROBE
+        return cudaGetLastError();
+    };
+    float ms = 0.f;
+    const cudaError_t e = time_launch(go, s, &ms);
+    if (e != cudaSuccess) return probe_fail(PILOT_ECUDA, cudaGetErrorString(e));
+    *units_per_s = (double)N * (double)M / (ms * 1e-3);
     return PILOT_OK;
 }
 

@@ -712,9 +712,11 @@ pilot_status pilot_align_create(const pilot_align_config* cfg_in, pilot_align_ha
     }
     ALLOC(h->state, sizeof(HypState) * M);
     ALLOC(h->pose32, sizeof(float) * 12 * M);
-    // tile records: plain form [slot][tile]; batched form [job_item * tiles_per_item + tile],
-    // which rounds each job's tiles up to whole work items
-    ALLOC(h->partial, sizeof(float) * kAcc * M * ((size_t)h->max_tiles + kItemAnchors / kMinTile));
+    // tile records: plain form [slot][tile]; batched form [(pair_item * tiles_per_item + tile)
+    // * 2 + h], which rounds each pair's tiles up to whole work items and a frame's odd last
+    // job up to a pair
+    ALLOC(h->partial, sizeof(float) * kAcc * (M + (size_t)cfg.max_frames) *
+                          ((size_t)h->max_tiles + kItemAnchors / kMinTile));
     ALLOC(h->active[0], sizeof(int) * M);
     ALLOC(h->active[1], sizeof(int) * M);
     ALLOC(h->Tin, sizeof(double) * 12 * M);
@@ -1063,7 +1065,7 @@ pilot_status pilot_align_solve_batch(pilot_align_handle* h, const pilot_frame* f
             nactive[(size_t)level * lay.max_frames + i] = cur[i];
             list[oi] = i;
             jobs[oi + 1] = jobs[oi] + cur[i];
-            items[oi + 1] = items[oi] + cur[i] * items_per_job(frames[i].N, sc.tile, tpi);
+            items[oi + 1] = items[oi] + frame_items(cur[i], frames[i].N, sc.tile, tpi);
         }
         hdr->n_listed[level] = n;
         for (int i = 0; i < n; ++i) {

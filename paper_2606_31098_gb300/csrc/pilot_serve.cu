@@ -405,7 +405,7 @@ void write_round(pilot_server* s) {
         d.quota = r->quota;
         list[nl] = r->slot;
         jobs[nl + 1] = jobs[nl] + r->n_active;
-        items[nl + 1] = items[nl] + r->n_active * items_per_job(f.N, kPlainTile, tiles_per_item(kPlainTile));
+        items[nl + 1] = items[nl] + frame_items(r->n_active, f.N, kPlainTile, tiles_per_item(kPlainTile));
         ++nl;
     }
     hdr->n_listed[0] = nl;
@@ -544,8 +544,8 @@ pilot_status pilot_serve_create(const pilot_align_config* cfg_in, size_t hbm_bud
         return bad("level counters");
     if ((e = cudaMalloc((void**)&s->pose32, sizeof(float) * 12 * H)) != cudaSuccess) return bad("candidates");
     if ((e = cudaMalloc((void**)&s->job_meta, sizeof(unsigned) * H)) != cudaSuccess) return bad("job table");
-    if ((e = cudaMalloc((void**)&s->partial,
-                        sizeof(float) * kAcc * H * (max_tiles + tiles_per_item(kPlainTile)))) != cudaSuccess)
+    if ((e = cudaMalloc((void**)&s->partial, sizeof(float) * kAcc * (H + (size_t)max_slots) *
+                                                 (max_tiles + tiles_per_item(kPlainTile)))) != cudaSuccess)
         return bad("tile records");
     if ((e = cudaMalloc((void**)&s->desc_dev, s->desc_bytes)) != cudaSuccess) return bad("descriptors");
     if ((e = cudaMallocHost((void**)&s->desc_host, s->desc_bytes)) != cudaSuccess) return bad("descriptor staging");

@@ -62,6 +62,24 @@ def fp32_pose(T):
     return np.asarray(T, np.float64).astype(np.float32).astype(np.float64)
 
 
+def oracle_normal_eq(frame, oo, level, T, **kw):
+    """The oracle's normal equations split the way the path evaluates them (step A2): the
+    photo term at the FP32 rounding of the pose, the FP64 prior terms (Eq. 3-6) at the
+    FP64 pose itself.  Where the laser point lies on a steep DSM edge the range residual
+    moves measurably between the two poses, so one pose for both would not be the
+    quantity the path computes."""
+    T = np.asarray(T, np.float64)
+    total64 = O.evaluate(frame, oo, level, T, **kw)
+    H64, g64, c64, _ = O.photo_terms(frame, oo, level, T, **kw)
+    H32, g32, c32, n32 = O.photo_terms(frame, oo, level, fp32_pose(T), **kw)
+    out = np.empty(29)
+    out[:21] = H32 + (total64[:21] - H64)
+    out[21:27] = g32 + (total64[21:27] - g64)
+    out[27] = c32 + (total64[27] - c64)
+    out[28] = n32
+    return out
+
+
 # worst errors seen in this process, under the bounds asserted and under the residual-based
 # scales sqrt(H_aa cost) and cost (reported by test_normal_equation_error_scales)
 WORST = {"H": 0.0, "g": 0.0, "cost": 0.0, "g_residual_scale": 0.0, "cost_residual_scale": 0.0}

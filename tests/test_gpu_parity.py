@@ -17,7 +17,7 @@ from paper_2606_31098_gb300 import scenes as S
 
 from gpu_support import (assert_normal_eq_close, assert_pose_close, assert_selection_agrees,
                          assert_solutions_agree, boundary_mask, converged, device_frame, fp32_pose,
-                         pose_errors, require_cuda, to_oracle_opts)
+                         oracle_normal_eq, pose_errors, require_cuda, to_oracle_opts)
 
 pytestmark = pytest.mark.gpu
 
@@ -36,7 +36,8 @@ def random_poses(T_ref, n, seed, trans=3.0, rot_deg=2.0):
 
 def check_normal_eq(frame, opts, levels, poses):
     """Normal equations of the GPU (at the FP64 poses, which its build pass rounds to
-    FP32) against the oracle evaluated at those FP32-rounded poses."""
+    FP32) against the oracle's photo term at those FP32-rounded poses plus its prior terms
+    at the FP64 poses."""
     poses32 = [fp32_pose(T) for T in poses]
     valid = boundary_mask(frame, levels, poses32)
     fm = frame.replace(point_valid=valid)
@@ -47,8 +48,8 @@ def check_normal_eq(frame, opts, levels, poses):
     w = fm.point_weight.astype(np.float64)
     for level in levels:
         gpu = solver.normal_eq(fa, level, np.array(poses))
-        for m, T in enumerate(poses32):
-            ora = O.evaluate(fm, oo, level, T)
+        for m, T in enumerate(poses):
+            ora = oracle_normal_eq(fm, oo, level, T)
             worst = np.maximum(worst, assert_normal_eq_close(gpu[m], ora, what=f"level {level} pose {m}",
                                                              F=float(ora[28]) * max(w.max(), 1.0)))
     solver.close()

@@ -15,7 +15,8 @@ from paper_2606_31098_gb300 import binding as B
 from paper_2606_31098_gb300 import scenes as S
 
 from gpu_support import (assert_normal_eq_close, assert_selection_agrees, assert_solutions_agree,
-                         boundary_mask, fp32_pose, pose_errors, require_cuda, to_oracle_opts)
+                         boundary_mask, fp32_pose, oracle_normal_eq, pose_errors, require_cuda,
+                         to_oracle_opts)
 from precision_support import (BF16, F16, FP8, dequantize, encode_bf16_rne, encode_e4m3_satfinite,
                                to_numpy_bits)
 
@@ -79,8 +80,8 @@ def test_normal_equations_on_quantised_storage(torch, dt, _):
     oo = to_oracle_opts(B.Options())
     for level in (0, 1, 2):
         gpu = solver.normal_eq(fa, level, np.array(poses))
-        for m, T in enumerate(poses32):
-            assert_normal_eq_close(gpu[m], O.evaluate(fdeq, oo, level, T), what=f"level {level} pose {m}")
+        for m, T in enumerate(poses):
+            assert_normal_eq_close(gpu[m], oracle_normal_eq(fdeq, oo, level, T), what=f"level {level} pose {m}")
 
 
 @pytest.mark.parametrize("dt,_", DTYPES)

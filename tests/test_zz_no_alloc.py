@@ -15,12 +15,11 @@ run every other test first; it also passes on its own in a fresh process.
 import numpy as np
 import pytest
 
-from oracle import oracle as O
 from paper_2606_31098_gb300 import binding as B
 from paper_2606_31098_gb300 import scenes as S
 
-from gpu_support import (assert_normal_eq_close, boundary_mask, device_frame, fp32_pose, require_cuda,
-                         to_oracle_opts)
+from gpu_support import (assert_normal_eq_close, boundary_mask, device_frame, fp32_pose, oracle_normal_eq,
+                         require_cuda, to_oracle_opts)
 
 pytestmark = pytest.mark.gpu
 
@@ -92,8 +91,8 @@ def test_noalloc_matches_the_oracle(torch):
     fa = device_frame(f, poses)
     for level in (0, 2):
         got = noalloc(torch, opts, fa, level, poses)
-        for m, T in enumerate(poses32):
-            assert_normal_eq_close(got[m], O.evaluate(f, oo, level, T), what=f"level {level} pose {m}")
+        for m, T in enumerate(poses):
+            assert_normal_eq_close(got[m], oracle_normal_eq(f, oo, level, T), what=f"level {level} pose {m}")
 
 
 def test_noalloc_rejects_sizes_beyond_its_scratch(torch):
