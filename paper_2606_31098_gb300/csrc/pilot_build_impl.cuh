@@ -309,14 +309,31 @@ __device__ __forceinline__ void accumulate_anchors(const LevelView& v, const flo
     const float xmax = (float)(v.W - 1), ymax = (float)(v.H - 1);
     const float d2 = v.huber * v.huber;
 
-    for (int jb = j_begin + (tid / LG) * APB; jb < j_end; jb += ASTEP) {
+    // the anchor coordinates of the next batch are read one batch ahead, so that their load
+    // latency overlaps the current batch's gathers
+    const int jfirst = j_begin + (tid / LG) * APB;
+    float nX = 0.f, nY = 0.f, nZ = 0.f;
+    bool nok = false;
+    if (jfirst + qa < j_end) {
+        const int j = jfirst + qa;
+        nok = act && (!v.valid || v.valid[j]);
+        nX = __ldg(v.px + j), nY = __ldg(v.py + j), nZ = __ldg(v.pz + j);
+    }
+    for (int jb = jfirst; jb < j_end; jb += ASTEP) {
         // 1. every lane projects its own record: anchor jb + qa under its hypothesis
         const int jo = jb + qa;
+        const float X = nX, Y = nY, Z = nZ;
+        const bool ok = nok && jo < j_end;
+        nok = false;
+        if (jo + ASTEP < j_end) {
+            const int j = jo + ASTEP;
+            nok = act && (!v.valid || v.valid[j]);
+            nX = __ldg(v.px + j), nY = __ldg(v.py + j), nZ = __ldg(v.pz + j);
+        }
         bool vis = false;
         int off = 0;
         float ax = 0.f, ay = 0.f, x = 0.f, y = 0.f, z = 1.f, iz = 1.f, wq = 1.f;
-        if (act && jo < j_end && (!v.valid || v.valid[jo])) {
-            const float X = __ldg(v.px + jo), Y = __ldg(v.py + jo), Z = __ldg(v.pz + jo);
+        if (ok) {
             // p = R P + t  (world -> camera)
             x = fmaf(R00, X, fmaf(R01, Y, fmaf(R02, Z, T0)));
             y = fmaf(R10, X, fmaf(R11, Y, fmaf(R12, Z, T1)));
