@@ -259,6 +259,25 @@ typedef struct {
 pilot_status pilot_crop_reference(const pilot_map* map, const pilot_crop_params* params, float* points,
                                   unsigned char* valid, float* rgb, double* geometry, void* stream);
 
+/* Geo-anchor sampling from a reference crop (Supp. "TDOM/DSM Reference Crop": the valid
+ * geo-anchors are sampled from the crop).  Draws min(n_select, number of valid pixels) of the
+ * pixels whose valid byte is non-zero, uniformly without replacement: pixel j gets the key
+ * (upper 32 bits of the (j+1)-th output of the SplitMix64 generator seeded with `seed`) * 2^32
+ * + j and the valid pixels with the smallest keys are taken -- integer arithmetic only, so the
+ * draw is exact and repeatable.  SplitMix64 (Steele, Lea, Flood, OOPSLA 2014): state +=
+ * 0x9E3779B97F4A7C15; z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9; z = (z ^ (z >> 27)) *
+ * 0x94D049BB133111EB; output z ^ (z >> 31).  DEVICE pointers, owned by the caller:
+ *   valid       n_pixels bytes (a crop's valid mask)
+ *   points      3 x n_pixels FP32 SoA (a crop's geo-anchors), read only when out_points is set
+ *   out_idx     n_select ints: the selected pixel indices in increasing order
+ *   out_points  3 x n_select FP32 SoA (row stride n_select) or NULL: the selected anchors
+ *   out_count   1 int: the number selected
+ * Entries of out_idx / out_points past *out_count are left as they were.  Asynchronous on
+ * `stream` (one CTA); allocates nothing.  EINVAL on negative sizes or missing pointers. */
+pilot_status pilot_sample_anchors(const unsigned char* valid, const float* points, int n_pixels, int n_select,
+                                  unsigned long long seed, int* out_idx, float* out_points, int* out_count,
+                                  void* stream);
+
 /* ---------------------------------------------------------------- sequential tracking
  * Pieces of the online loop (Supp. "Runtime Analysis": map preparation and localisation run
  * as two asynchronous stages; Sec. V-A: failure recovery).  Poses are [R | t] world ->
@@ -310,11 +329,12 @@ pilot_status pilot_probe_gather(const void* map, int H, int W, int C, pilot_dtyp
 
 /* Gather ceiling of the build pass' access pattern on a real frame (the paper has no
  * counterpart; a roofline probe).  Runs the build pass' loads without its arithmetic on
- * the same grid (ceil(N / tile) anchor tiles x M poses, 256 threads): every (anchor, pose)
- * projects the anchor (Eq. 1, level intrinsics fx, fy, cx, cy in pixels of this map, corner
- * convention) and reads its 4 taps and its reference row, 16-byte loads by lane groups as
- * the build pass issues them, so the cache reuse between neighbouring anchors is the
- * frame's own.  DEVICE pointers: points 3 x N FP32 SoA; map H x W x C NHWC and ref N x C in
+ * the same grid (ceil(N / tile) anchor tiles x tiles of the build pass' number of poses per
+ * CTA, 256 threads, its lane layout): every (anchor, pose) projects the anchor (Eq. 1, level
+ * intrinsics fx, fy, cx, cy in pixels of this map, corner convention) and reads its 4 taps,
+ * and every anchor's reference row is read once for the CTA's poses, 16-byte loads by lane
+ * groups as the build pass issues them, so the cache reuse between neighbouring anchors is
+ * the frame's own.  Two batches of anchors are in flight per step.  DEVICE pointers: points 3 x N FP32 SoA; map H x W x C NHWC and ref N x C in
  * `dtype` (16-byte aligned; C x element size a power of two from 16 to 256 bytes); poses32
  * M x 12 FP32 [R | t] world -> camera.  Times one launch after a warm-up one on `stream`
  * (synchronous) and returns the (anchor, pose) units per second in *units_per_s. */

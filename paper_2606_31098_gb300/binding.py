@@ -69,6 +69,7 @@ SIGNATURES = {
     "pilot_align_set_schedule": (ct.c_int, [_vp, _vp, ct.c_int, ct.c_int, _vp]),
     "pilot_align_selftest_barrier_timeout": (ct.c_int, [_vp, ct.c_double, ct.POINTER(ct.c_double), _vp]),
     "pilot_crop_reference": (ct.c_int, [_vp, _vp, _vp, _vp, _vp, _vp, _vp]),
+    "pilot_sample_anchors": (ct.c_int, [_vp, _vp, ct.c_int, ct.c_int, ct.c_ulonglong, _vp, _vp, _vp, _vp]),
     "pilot_pose_predict": (ct.c_int, [_vp, _vp, ct.c_int, _vp]),
     "pilot_pose_reorigin": (ct.c_int, [_vp, ct.c_double, ct.c_double, _vp]),
     "pilot_seed_hypotheses": (ct.c_int, [_vp, _vp, _vp]),
@@ -444,6 +445,24 @@ def crop_reference(m: MapArgs, p: pilot_crop_params, with_rgb: bool = True, out:
                    geometry=torch.empty(28, dtype=torch.float64, device=dev))
     check(load().pilot_crop_reference(ct.byref(m.c), ct.byref(p), _ptr(out["points"]), _ptr(out["valid"]),
                                       _ptr(out["rgb"]), _ptr(out["geometry"]), Solver._stream(stream)))
+    return out
+
+
+def sample_anchors(valid_dev, points_dev, n_select: int, seed: int, out: dict | None = None, stream=None) -> dict:
+    """pilot_sample_anchors on a crop's device valid mask (n,) u8 and geo-anchors (3, n) f32:
+    returns device tensors idx (n_select,) i32, points (3, n_select) f32 and count (1,) i32
+    (allocated here unless `out` is given).  Asynchronous on `stream`."""
+    import torch
+    n = int(valid_dev.numel())
+    if out is None:
+        dev = valid_dev.device
+        out = dict(idx=torch.full((n_select,), -1, dtype=torch.int32, device=dev),
+                   points=torch.zeros((3, n_select), dtype=torch.float32, device=dev),
+                   count=torch.zeros(1, dtype=torch.int32, device=dev))
+    check(load().pilot_sample_anchors(_ptr(valid_dev), _ptr(points_dev), n, int(n_select),
+                                      ct.c_ulonglong(int(seed) & 0xFFFFFFFFFFFFFFFF), _ptr(out["idx"]),
+                                      _ptr(out["points"]) if points_dev is not None else None, _ptr(out["count"]),
+                                      Solver._stream(stream)))
     return out
 
 

@@ -11,23 +11,25 @@
 // formed: per anchor only the 2x2 Gram matrix M = G^T G, b = G^T r and s = ||r||^2 are
 // summed over channels, then H_j = w A^T M A and g_j = w A^T b.
 //
-// Thread mapping.  A CTA holds two hypotheses over one anchor tile.  A group of LP
-// consecutive lanes reads one tap with one 16-byte load per lane (LP = C x element size /
-// 16, at most 8: 8 lanes for FP32 at C = 32, 4 for BF16, 2 for FP8), i.e. one L1 wavefront
-// per record and tap, where a record is one (anchor, hypothesis) pair.  A group works on
-// LP records at a time: LP/2 anchors under both hypotheses.  Each lane projects one record
-// (lane q: anchor q mod LP/2 under hypothesis q div LP/2) and broadcasts its tap offset and
-// bilinear weights to the group; the group then reads the 4 taps of every record and the
-// reference row of every anchor together -- once for both hypotheses (vector k of lane q
-// holds channels VW (q + k LP) .. + VW).  A butterfly reduce-scatter over the group leaves
-// in lane q the channel sums of record q, and each lane finishes its own record (Huber
-// weight, A, 21 + 6 sums) exactly once.  An invisible record's partial sums stay in its own
-// reduce-scatter slot and are discarded by its owner.  With one lane per record (LP = 1)
-// two lanes form a group, one per hypothesis, each reading its record alone.  The CTA
-// reduces the lanes of each hypothesis in a fixed order.  A hypothesis' sums do not depend
-// on which of the two slots it takes or on the other hypothesis (the lanes of the two
-// slots run the same anchors in the same order, and the reduction trees are mirror
-// images), so the result is deterministic and independent of the grid shape and pairing.
+// Thread mapping.  A CTA holds kHypTile (HT) hypotheses over one anchor tile.  A group of
+// LP consecutive lanes reads one tap with one 16-byte load per lane (LP = C x element size
+// / 16, at most 8: 8 lanes for FP32 at C = 32, 4 for BF16, 2 for FP8), i.e. one L1 wavefront
+// per record and tap, where a record is one (anchor, hypothesis) pair.  A group works on LP
+// records at a time: APB anchors under HG = min(HT, LP) hypotheses (APB HG = LP); with
+// LP < HT, HT / HG neighbouring groups take the same anchors under the other hypotheses.
+// Each lane projects one record (lane q of the group: anchor q mod APB under the group's
+// hypothesis q div APB) and broadcasts its tap offset and bilinear weights to the group; the
+// group then reads the 4 taps of every record and the reference row of every anchor
+// together -- once for all the hypotheses of the CTA (vector k of lane q holds channels
+// VW (q + k LP) .. + VW).  A butterfly reduce-scatter over the group leaves in lane q the
+// channel sums of record q, and each lane finishes its own record (Huber weight, A, 21 + 6
+// sums) exactly once.  An invisible record's partial sums stay in its own reduce-scatter
+// slot and are discarded by its owner.  The hypothesis slot of a lane is read from lane bits
+// log2 APB .. log2 (APB HT) - 1; the CTA reduces the lanes of each slot over the other lane
+// bits, then the warps, in a fixed order.  A hypothesis' sums do not depend on which slot
+// it takes or on the other hypotheses (the lanes of all slots run the same anchors in the
+// same order, and the reduction trees are translates of one another), so the result is
+// deterministic and independent of the grid shape and of how hypotheses are grouped.
 #pragma once
 
 #include <cuda_bf16.h>
@@ -192,16 +194,25 @@ __device__ __forceinline__ float hsum(f2 v) {
     return lo + hi;
 }
 
-// Lanes per tap (LP), lanes per group (LG) and anchors per group batch (APB) for C channels
-// stored as DT.  A group takes LG records at a time: APB anchors under both hypotheses of the
-// CTA; the hypothesis of lane q is q / APB, so lane bit APB tells the two slots apart.
+// Lane layout of the build pass for C channels stored as DT (see the top of the file): LP
+// lanes per tap = records per group batch, HG hypotheses per group, NS = kHypTile / HG
+// groups over the same anchors, APB anchors per group batch.  The slot of lane l is
+// (l / APB) mod kHypTile.
 template <pilot_dtype DT, int C> struct GroupShape {
     static constexpr int VEC = Storage<DT>::VEC;              // channels per 16-byte vector
     static constexpr int VW = (C < VEC) ? C : VEC;            // channels per vector load
     static constexpr int LP = (C / VW < 8) ? C / VW : 8;      // lanes per tap
-    static constexpr int LG = LP > 1 ? LP : 2;                // lanes per group = records per batch
-    static constexpr int APB = LG / 2;                        // anchors per group batch
+    static constexpr int HG = LP < kHypTile ? LP : kHypTile;  // hypotheses per group
+    static constexpr int NS = kHypTile / HG;                  // groups over the same anchors
+    static constexpr int APB = LP / HG;                       // anchors per group batch
     static constexpr int NV = C / LP / VW;                    // vector loads per lane and tap
+    static_assert(APB * kHypTile <= 32, "a warp holds every slot of an anchor");
+};
+
+// The CTA's hypotheses: their FP32 poses and whether each slot has one to evaluate.
+struct SlotPoses {
+    const float* p[kHypTile];
+    bool act[kHypTile];
 };
 
 // The level-specific inputs of the anchor loop.
@@ -261,44 +272,48 @@ __device__ __forceinline__ void record_partials(const typename Storage<DT>::T* t
     p[5] = hsum(cs.b1);
 }
 
-// Accumulate anchors [j_begin, j_end) under the CTA's two hypotheses into this lane's 29
-// sums (the lane's own hypothesis: q / APB).  P0, P1: the two poses (12 FP32 values each);
-// act0, act1: whether each slot has a pose to evaluate (an inactive slot's lanes finish
-// nothing).  Every thread of the CTA calls it with the same arguments; threads are grouped
-// as described at the top of the file.
+// Accumulate anchors [j_begin, j_end) under the CTA's kHypTile hypotheses into this lane's
+// 29 sums (the lane's own slot, see GroupShape).  sp: the slots' poses (12 FP32 values each)
+// and whether each has a pose to evaluate (an inactive slot's lanes finish nothing).  Every
+// thread of the CTA calls it with the same arguments; threads are grouped as described at
+// the top of the file.
 template <pilot_dtype DT, int C, bool SCALED, bool CONF, int NTHREADS>
-__device__ __forceinline__ void accumulate_anchors(const LevelView& v, const float* P0, const float* P1, bool act0,
-                                                   bool act1, int j_begin, int j_end, float* acc) {
+__device__ __forceinline__ void accumulate_anchors(const LevelView& v, const SlotPoses& sp, int j_begin, int j_end,
+                                                   float* acc) {
     using Elem = typename Storage<DT>::T;
     using G = GroupShape<DT, C>;
-    constexpr int VW = G::VW, LP = G::LP, LG = G::LG, APB = G::APB, NV = G::NV;
+    constexpr int VW = G::VW, LP = G::LP, HG = G::HG, NS = G::NS, APB = G::APB, NV = G::NV;
     constexpr int CPL = C / LP;                      // channels per lane
-    constexpr int GROUPS = NTHREADS / LG;
-    constexpr int ASTEP = GROUPS * APB;              // anchors per CTA batch
+    constexpr int ASTEP = NTHREADS / (LP * NS) * APB;   // anchors per CTA batch
     static_assert(C % 4 == 0 && C >= 4 && C <= 64 && LP >= 1 && LP <= 8, "channels");
 
     const int tid = threadIdx.x;
     const int lane = tid & 31;
-    const int q = lane & (LG - 1);
-    const int hyp = q / APB;                         // this lane's slot
+    const int q = lane & (LP - 1);
+    const int slot = (lane / APB) % kHypTile;        // this lane's hypothesis slot
     const int qa = q % APB;                          // this lane's anchor in the batch
-    const int src0 = lane & ~(LG - 1);
-    const unsigned gmask = (((1u << LG) - 1u) << src0);
-    const int cq = LP > 1 ? q : 0;                   // channel block of this lane
+    const int src0 = lane & ~(LP - 1);
+    const unsigned gmask = LP > 1 ? (((1u << LP) - 1u) << src0) : (1u << lane);
 
-    const float* P = hyp ? P1 : P0;
-    const bool act = hyp ? act1 : act0;
+    const float* P = sp.p[0];
+    bool act = sp.act[0];
+#pragma unroll
+    for (int h = 1; h < kHypTile; ++h)
+        if (slot == h) {
+            P = sp.p[h];
+            act = sp.act[h];
+        }
     const float R00 = P[0], R01 = P[1], R02 = P[2], T0 = P[3];
     const float R10 = P[4], R11 = P[5], R12 = P[6], T1 = P[7];
     const float R20 = P[8], R21 = P[9], R22 = P[10], T2 = P[11];
 
-    // channels owned by this lane: vector k covers VW (cq + k LP) .. + VW
+    // channels owned by this lane: vector k covers VW (q + k LP) .. + VW
     float qs[CPL], rs[CPL];
 #pragma unroll
     for (int k = 0; k < NV; ++k)
 #pragma unroll
         for (int e = 0; e < VW; ++e) {
-            const int ch = VW * (cq + k * LP) + e;
+            const int ch = VW * (q + k * LP) + e;
             qs[k * VW + e] = SCALED ? __ldg(v.qscale + ch) : 1.0f;
             rs[k * VW + e] = SCALED ? __ldg(v.rscale + ch) : 1.0f;
         }
@@ -311,7 +326,7 @@ __device__ __forceinline__ void accumulate_anchors(const LevelView& v, const flo
 
     // the anchor coordinates of the next batch are read one batch ahead, so that their load
     // latency overlaps the current batch's gathers
-    const int jfirst = j_begin + (tid / LG) * APB;
+    const int jfirst = j_begin + (tid / (LP * NS)) * APB;
     float nX = 0.f, nY = 0.f, nZ = 0.f;
     bool nok = false;
     if (jfirst + qa < j_end) {
@@ -370,40 +385,56 @@ __device__ __forceinline__ void accumulate_anchors(const LevelView& v, const flo
             for (int k = 0; k < NV; ++k) load_vec<DT, VW>(fr + VW * k, rr + VW * k);
             record_partials<DT, C, SCALED>(qry + off, WC, rr, ax, ay, 0, qs, rs, S);
         } else {
-            // 2. the group reads its records two at a time: anchor t under both hypotheses
-            //    (records t and t + APB) with one read of the anchor's reference row; the
-            //    first butterfly round (xor APB) then keeps in each lane only the record of
-            //    its own slot, so only APB partial records stay live
-            float B[APB][6];
+            // 2. the group reads its records two at a time: records t and t + LP/2, one
+            //    anchor (t mod APB) under two of the group's hypotheses, against one read of
+            //    the anchor's reference row (with four hypotheses per group, the rows are read
+            //    once per batch and kept for both record pairs of an anchor); the first
+            //    butterfly round (xor LP/2) keeps in each lane only the record it owns, so
+            //    only LP/2 partial records stay live
+            constexpr int HALF = LP / 2;
+            float rra[HG > 2 ? APB : 1][CPL];
+            if constexpr (HG > 2) {
 #pragma unroll
-            for (int t = 0; t < APB; ++t) {
-                float rr[CPL];
-                const int ja = jb + t;
-                const Elem* fr = ref + (ja < j_end ? ja : j_begin) * C;
+                for (int a = 0; a < APB; ++a) {
+                    const int ja = jb + a;
+                    const Elem* fr = ref + (ja < j_end ? ja : j_begin) * C;
 #pragma unroll
-                for (int k = 0; k < NV; ++k) load_vec<DT, VW>(fr + VW * (q + k * LP), rr + k * VW);
+                    for (int k = 0; k < NV; ++k) load_vec<DT, VW>(fr + VW * (q + k * LP), rra[a] + k * VW);
+                }
+            }
+            float B[HALF][6];
+#pragma unroll
+            for (int t = 0; t < HALF; ++t) {
+                float rrt[CPL];
+                const float* rr = rra[HG > 2 ? t % APB : 0];
+                if constexpr (HG <= 2) {
+                    const int ja = jb + t;
+                    const Elem* fr = ref + (ja < j_end ? ja : j_begin) * C;
+#pragma unroll
+                    for (int k = 0; k < NV; ++k) load_vec<DT, VW>(fr + VW * (q + k * LP), rrt + k * VW);
+                    rr = rrt;
+                }
                 float P2[2][6];
 #pragma unroll
                 for (int u = 0; u < 2; ++u) {
-                    const int i = t + u * APB;
+                    const int i = t + u * HALF;
                     const int vi = __shfl_sync(gmask, (int)vis, src0 + i);
                     const int oi = __shfl_sync(gmask, off, src0 + i);
                     const float axi = __shfl_sync(gmask, ax, src0 + i);
                     const float ayi = __shfl_sync(gmask, ay, src0 + i);
                     record_partials<DT, C, SCALED>(qry + (vi ? oi : 0), WC, rr, axi, ayi, q, qs, rs, P2[u]);
                 }
-                const bool upper = hyp != 0;
+                const bool upper = (q & HALF) != 0;
 #pragma unroll
                 for (int k = 0; k < 6; ++k) {
                     const float send = upper ? P2[0][k] : P2[1][k];
                     const float keep = upper ? P2[1][k] : P2[0][k];
-                    B[t][k] = keep + __shfl_xor_sync(gmask, send, APB);
+                    B[t][k] = keep + __shfl_xor_sync(gmask, send, HALF);
                 }
             }
-            // 3. remaining butterfly rounds over the anchors: afterwards B[0] of lane q holds
-            //    record q's sums
+            // 3. remaining butterfly rounds: afterwards B[0] of lane q holds record q's sums
 #pragma unroll
-            for (int half = APB / 2; half >= 1; half >>= 1) {
+            for (int half = HALF / 2; half >= 1; half >>= 1) {
                 const bool upper = (q & half) != 0;
 #pragma unroll
                 for (int t = 0; t < half; ++t) {
@@ -483,107 +514,122 @@ __device__ __forceinline__ void accumulate_anchors(const LevelView& v, const flo
 }
 
 // Fixed-order CTA reduction of the lanes' 29 sums, per hypothesis slot: the lanes of a slot
-// are reduced by a butterfly over every lane bit but the slot bit (APB), then the warps in
-// order.  Thread t < 2 kAcc returns sum t mod kAcc of slot t / kAcc (0 pads).
+// are reduced by a butterfly over every lane bit but the slot bits (APB .. APB kHypTile / 2),
+// then the warps in order.  Thread t < kHypTile kAcc returns sum t mod kAcc of slot t / kAcc
+// (0 pads).
 template <int NTHREADS, int APB>
-__device__ __forceinline__ float cta_reduce_pair(float* acc, float (*red)[2][kAcc]) {
+__device__ __forceinline__ float cta_reduce_slots(float* acc, float (*red)[kHypTile][kAcc]) {
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
 #pragma unroll
     for (int off = 1; off < 32; off <<= 1) {
-        if (off == APB) continue;
+        if (off >= APB && off < APB * kHypTile) continue;
 #pragma unroll
         for (int i = 0; i < kNumSums; ++i) acc[i] += __shfl_xor_sync(0xffffffffu, acc[i], off);
     }
-    if (lane == 0 || lane == APB) {
+    if (lane % APB == 0 && lane < APB * kHypTile) {
 #pragma unroll
-        for (int i = 0; i < kNumSums; ++i) red[warp][lane == APB][i] = acc[i];
+        for (int i = 0; i < kNumSums; ++i) red[warp][lane / APB][i] = acc[i];
     }
     __syncthreads();
     float v = 0.f;
-    if (tid < 2 * kAcc && (tid % kAcc) < kNumSums) {
+    if (tid < kHypTile * kAcc && (tid % kAcc) < kNumSums) {
 #pragma unroll
         for (int w = 0; w < NTHREADS / 32; ++w) v += red[w][tid / kAcc][tid % kAcc];
     }
     return v;
 }
 
-// The CTA's hypothesis pair: slots 2 blockIdx.y and 2 blockIdx.y + 1 of the active list (the
-// second absent when the count is odd).
-struct PairSlots {
-    int slot[2];
-    int hyp[2];
-    bool cand[2];
-    int n;                                           // 1 or 2
+// The CTA's hypotheses: slots kHypTile blockIdx.y + h of the active list, h < n.
+struct TileSlots {
+    int slot[kHypTile];
+    int hyp[kHypTile];
+    bool cand[kHypTile];
+    int n;                                           // 1 .. kHypTile
 };
 
-__device__ __forceinline__ PairSlots pair_slots(const BuildParams& p) {
-    PairSlots s;
-    s.n = min(2, p.n_active - 2 * (int)blockIdx.y);
+__device__ __forceinline__ TileSlots tile_slots(const BuildParams& p) {
+    TileSlots s;
+    s.n = min(kHypTile, p.n_active - kHypTile * (int)blockIdx.y);
 #pragma unroll
-    for (int h = 0; h < 2; ++h) {
-        s.slot[h] = 2 * blockIdx.y + (h < s.n ? h : 0);
+    for (int h = 0; h < kHypTile; ++h) {
+        s.slot[h] = kHypTile * blockIdx.y + (h < s.n ? h : 0);
         s.hyp[h] = p.active_idx[s.slot[h]];
         s.cand[h] = h < s.n && p.state[s.hyp[h]].has_cand;
     }
     return s;
 }
 
+__device__ __forceinline__ SlotPoses slot_poses(const BuildParams& p, const TileSlots& ts) {
+    SlotPoses sp;
+#pragma unroll
+    for (int h = 0; h < kHypTile; ++h) {
+        sp.p[h] = p.pose32 + 12 * ts.hyp[h];
+        sp.act[h] = ts.cand[h];
+    }
+    return sp;
+}
+
+__device__ __forceinline__ bool any_cand(const TileSlots& ts) {
+    bool a = false;
+#pragma unroll
+    for (int h = 0; h < kHypTile; ++h) a = a || ts.cand[h];
+    return a;
+}
+
 template <pilot_dtype DT, int C, bool SCALED, bool CONF>
 __global__ void __launch_bounds__(kBuildThreads, 2)
 build_kernel(const BuildParams p) {
-    __shared__ float red[kBuildThreads / 32][2][kAcc];
-    const PairSlots ps = pair_slots(p);
-    if (!ps.cand[0] && !ps.cand[1]) return;          // uniform over the CTA
+    __shared__ float red[kBuildThreads / 32][kHypTile][kAcc];
+    const TileSlots ts = tile_slots(p);
+    if (!any_cand(ts)) return;                       // uniform over the CTA
     float acc[kNumSums];
 #pragma unroll
     for (int i = 0; i < kNumSums; ++i) acc[i] = 0.f;
     const int j0 = blockIdx.x * p.tile;
-    accumulate_anchors<DT, C, SCALED, CONF, kBuildThreads>(level_view(p), p.pose32 + 12 * ps.hyp[0],
-                                                           p.pose32 + 12 * ps.hyp[1], ps.cand[0], ps.cand[1], j0,
+    accumulate_anchors<DT, C, SCALED, CONF, kBuildThreads>(level_view(p), slot_poses(p, ts), j0,
                                                            min(j0 + p.tile, p.N), acc);
-    const float v = cta_reduce_pair<kBuildThreads, GroupShape<DT, C>::APB>(acc, red);
+    const float v = cta_reduce_slots<kBuildThreads, GroupShape<DT, C>::APB>(acc, red);
     const int h = threadIdx.x / kAcc;
-    if (threadIdx.x < 2 * kAcc && h < ps.n && ps.cand[h])
-        p.partial[((size_t)ps.slot[h] * p.n_tiles + blockIdx.x) * kAcc + threadIdx.x % kAcc] = v;
+    if (threadIdx.x < kHypTile * kAcc && h < ts.n && ts.cand[h])
+        p.partial[((size_t)ts.slot[h] * p.n_tiles + blockIdx.x) * kAcc + threadIdx.x % kAcc] = v;
 }
 
 // The same pass with the per-hypothesis FP64 step fused in: the CTA that takes the last
-// ticket of its pair sums the tile records of both hypotheses (FP64, 8 chains per value,
-// fixed order) and runs lm_step for them on warps 0 and 1.  A pair with no candidate runs
-// its steps in tile 0's CTA.
+// ticket of its hypothesis tile sums the tile records of its hypotheses (FP64, 8 chains per
+// value, fixed order) and runs lm_step for hypothesis h on warp h.  A tile of hypotheses with
+// no candidate runs its steps in tile 0's CTA.
 template <pilot_dtype DT, int C, bool SCALED, bool CONF>
 __global__ void __launch_bounds__(kBuildThreads, 2)
 build_fused_kernel(const FusedBuildParams fp) {
     const BuildParams& p = fp.b;
-    __shared__ float red[kBuildThreads / 32][2][kAcc];
-    __shared__ double part[2][8][kAcc];
-    __shared__ double E[2][kAcc];
+    __shared__ float red[kBuildThreads / 32][kHypTile][kAcc];
+    __shared__ double part[kHypTile][8][kAcc];
+    __shared__ double E[kHypTile][kAcc];
     __shared__ int s_last;
-    const PairSlots ps = pair_slots(p);
+    const TileSlots ts = tile_slots(p);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    if (!ps.cand[0] && !ps.cand[1]) {                // uniform over the CTA
-        if (blockIdx.x == 0 && warp < ps.n) lm_step(fp.ep, ps.slot[warp], E[warp], &part[warp][0][0], *fp.min_valid, lane);
+    if (!any_cand(ts)) {                             // uniform over the CTA
+        if (blockIdx.x == 0 && warp < ts.n) lm_step(fp.ep, ts.slot[warp], E[warp], &part[warp][0][0], *fp.min_valid, lane);
         return;
     }
     float acc[kNumSums];
 #pragma unroll
     for (int i = 0; i < kNumSums; ++i) acc[i] = 0.f;
     const int j0 = blockIdx.x * p.tile;
-    accumulate_anchors<DT, C, SCALED, CONF, kBuildThreads>(level_view(p), p.pose32 + 12 * ps.hyp[0],
-                                                           p.pose32 + 12 * ps.hyp[1], ps.cand[0], ps.cand[1], j0,
+    accumulate_anchors<DT, C, SCALED, CONF, kBuildThreads>(level_view(p), slot_poses(p, ts), j0,
                                                            min(j0 + p.tile, p.N), acc);
-    const float v = cta_reduce_pair<kBuildThreads, GroupShape<DT, C>::APB>(acc, red);
-    const int hv = tid / kAcc, iv = tid % kAcc;     // slot and sum this thread holds (tid < 64)
+    const float v = cta_reduce_slots<kBuildThreads, GroupShape<DT, C>::APB>(acc, red);
+    const int hv = tid / kAcc, iv = tid % kAcc;     // slot and sum this thread holds (tid < kHypTile kAcc)
     if (p.n_tiles == 1) {
         // the only tile: its record is the sum (0 + x is what the 8-chain sum gives), no
         // round trip through the partial buffer and the ticket
-        if (tid < 2 * kAcc) E[hv][iv] = 0.0 + (double)v;
+        if (tid < kHypTile * kAcc) E[hv][iv] = 0.0 + (double)v;
         __syncthreads();
-        if (warp < ps.n) lm_step(fp.ep, ps.slot[warp], E[warp], &part[warp][0][0], *fp.min_valid, lane);
+        if (warp < ts.n) lm_step(fp.ep, ts.slot[warp], E[warp], &part[warp][0][0], *fp.min_valid, lane);
         return;
     }
-    if (tid < 2 * kAcc && hv < ps.n && ps.cand[hv])
-        p.partial[((size_t)ps.slot[hv] * p.n_tiles + blockIdx.x) * kAcc + iv] = v;
+    if (tid < kHypTile * kAcc && hv < ts.n && ts.cand[hv])
+        p.partial[((size_t)ts.slot[hv] * p.n_tiles + blockIdx.x) * kAcc + iv] = v;
     __threadfence();
     __syncthreads();
     if (tid == 0) s_last = (atomicAdd(fp.tickets + blockIdx.y, 1u) == (unsigned)(p.n_tiles - 1));
@@ -592,33 +638,34 @@ build_fused_kernel(const FusedBuildParams fp) {
     __threadfence();
     // 8 chains per slot and value: thread (h, c, i) sums tiles c, c + 8, ... of sum i of slot h
     {
-        const int h = tid >> 7, c = (tid >> 4) & 7;
-        for (int ii = tid & 15; ii < kAcc; ii += 16) {
+        constexpr int kTPC = kBuildThreads / (kHypTile * 8);     // threads per (slot, chain)
+        const int h = tid / (8 * kTPC), c = (tid / kTPC) & 7;
+        for (int ii = tid % kTPC; ii < kAcc; ii += kTPC) {
             double a = 0.0;
-            if (h < ps.n && ps.cand[h]) {
-                const float* src = p.partial + (size_t)ps.slot[h] * p.n_tiles * kAcc + ii;
+            if (h < ts.n && ts.cand[h]) {
+                const float* src = p.partial + (size_t)ts.slot[h] * p.n_tiles * kAcc + ii;
                 for (int t = c; t < p.n_tiles; t += 8) a += (double)__ldcg(src + (size_t)t * kAcc);
             }
             part[h][c][ii] = a;
         }
     }
     __syncthreads();
-    if (tid < 2 * kAcc) {
+    if (tid < kHypTile * kAcc) {
         double sum = 0.0;
 #pragma unroll
         for (int k = 0; k < 8; ++k) sum += part[hv][k][iv];
         E[hv][iv] = sum;
     }
     __syncthreads();
-    if (warp < ps.n) {                               // the warp-cooperative FP64 steps
-        lm_step(fp.ep, ps.slot[warp], E[warp], &part[warp][0][0], *fp.min_valid, lane);
+    if (warp < ts.n) {                               // the warp-cooperative FP64 steps
+        lm_step(fp.ep, ts.slot[warp], E[warp], &part[warp][0][0], *fp.min_valid, lane);
     }
     if (tid == 0) fp.tickets[blockIdx.y] = 0u;
 }
 
 template <pilot_dtype DT, int C>
 cudaError_t launch_build_typed(const BuildParams& p, cudaStream_t s) {
-    dim3 grid(p.n_tiles, (p.n_active + 1) / 2);
+    dim3 grid(p.n_tiles, (p.n_active + kHypTile - 1) / kHypTile);
     if (p.qscale && p.conf)
         build_kernel<DT, C, true, true><<<grid, kBuildThreads, 0, s>>>(p);
     else if (p.qscale)
@@ -632,7 +679,7 @@ cudaError_t launch_build_typed(const BuildParams& p, cudaStream_t s) {
 
 template <pilot_dtype DT, int C>
 cudaError_t launch_build_fused_typed(const FusedBuildParams& p, cudaStream_t s) {
-    dim3 grid(p.b.n_tiles, (p.b.n_active + 1) / 2);
+    dim3 grid(p.b.n_tiles, (p.b.n_active + kHypTile - 1) / kHypTile);
     if (p.b.qscale && p.b.conf)
         build_fused_kernel<DT, C, true, true><<<grid, kBuildThreads, 0, s>>>(p);
     else if (p.b.qscale)

@@ -35,10 +35,18 @@ __host__ __device__ inline int items_per_job(int N, int tile, int tpi) {
     return (tiles + tpi - 1) / tpi;
 }
 
-// Work items of a frame of N anchors with n_jobs jobs: the jobs are taken in pairs (a work
-// item covers both jobs of a pair, as a build-pass CTA holds two hypotheses).
+#ifndef PILOT_HYP_TILE
+#define PILOT_HYP_TILE 4
+#endif
+// Hypotheses a build-pass CTA holds over one anchor tile (2 or 4): the reference row of an
+// anchor is read once for all of them.
+constexpr int kHypTile = PILOT_HYP_TILE;
+static_assert(kHypTile == 2 || kHypTile == 4, "hypothesis tile");
+
+// Work items of a frame of N anchors with n_jobs jobs: the jobs are taken kHypTile at a time
+// (a work item covers all jobs of its tile, as a build-pass CTA holds kHypTile hypotheses).
 __host__ __device__ inline int frame_items(int n_jobs, int N, int tile, int tpi) {
-    return (n_jobs + 1) / 2 * items_per_job(N, tile, tpi);
+    return (n_jobs + kHypTile - 1) / kHypTile * items_per_job(N, tile, tpi);
 }
 constexpr int kBuildThreads = 256;
 constexpr float kZNear = 0.1f;
@@ -112,12 +120,13 @@ struct EpilogueParams {
     double* eval_out;          // kEpiEval: [slot][29]
 };
 
-// A build pass whose last CTA per hypothesis pair runs the FP64 LM steps itself (the CTA
-// that takes the last ticket of its pair sums the tile records and calls lm_step for both).
+// A build pass whose last CTA per hypothesis tile runs the FP64 LM steps itself (the CTA
+// that takes the last ticket of its tile sums the tile records and calls lm_step for each
+// of its hypotheses).
 struct FusedBuildParams {
     BuildParams b;
     EpilogueParams ep;
-    unsigned* tickets;         // [(n_active + 1) / 2], one per hypothesis pair, zero between launches
+    unsigned* tickets;         // one per hypothesis tile of the launch, zero between launches
     const double* min_valid;
 };
 
@@ -161,9 +170,9 @@ struct BatchHeader {
 // frame) and work items are numbered frame after frame in list order: listed frame i is
 // frames[fr_list[i]]; its jobs are fr_job[i] .. fr_job[i + 1] - 1 (its active slots in
 // order) and its items fr_item[i] .. fr_item[i + 1] - 1, items_per_job(N) consecutive items
-// per pair of jobs (2p, 2p + 1), each covering tiles_per_item anchor tiles of both.  Tile t
-// of job 2p + h, whose pair's first item is q, keeps its record at
-// partial[(q * tiles_per_item + t) * 2 + h].
+// per tile of kHypTile jobs (jobs kHypTile p .. kHypTile p + kHypTile - 1), each covering
+// tiles_per_item anchor tiles of all of them.  Tile t of job kHypTile p + h, whose job tile's
+// first item is q, keeps its record at partial[(q * tiles_per_item + t) * kHypTile + h].
 struct LevelArgs {
     const BatchHeader* header;
     const FrameDesc* frames;

@@ -56,27 +56,27 @@ __device__ __forceinline__ bool grid_sync(unsigned long long* sync, unsigned* er
 // Batched form: one persistent (cooperative) launch per level for a whole batch of frames.
 // The level's LM iterations run in lockstep over all jobs (a job = one hypothesis of one
 // frame): in iteration k the CTAs claim the work items (runs of up to tiles_per_item
-// consecutive anchor tiles of one pair of jobs -- jobs 2p and 2p + 1 of a frame, the pair
-// the plain form's CTAs hold) from one counter, and write each tile's FP32 records exactly
-// as build_fused_kernel does (same thread mapping, same sums); after a grid barrier each
-// job's FP64 step runs on one warp (all lanes), on the tile records summed in the plain
-// form's 8-chain FP64 order, and writes the job's next candidate; a second barrier ends the
+// consecutive anchor tiles of one tile of kHypTile jobs of a frame, the hypotheses a plain
+// form's CTA holds) from one counter, and write each tile's FP32 records exactly as
+// build_fused_kernel does (same thread mapping, same sums); after a grid barrier each job's
+// FP64 step runs on one warp (all lanes), on the tile records summed in the plain form's
+// 8-chain FP64 order, and writes the job's next candidate; a second barrier ends the
 // iteration.  A frame's result is therefore bitwise the one its plain solve gives, whatever
 // else is in the batch; the items balance the gathers over all CTAs, and the FP64 steps of
-// all jobs run at once, one per warp.  Tile t of job 2p + h, whose pair's first item is q,
-// keeps its record at partial[(q tiles_per_item + t) 2 + h].
+// all jobs run at once, one per warp.  Tile t of job kHypTile p + h, whose job tile's first
+// item is q, keeps its record at partial[(q tiles_per_item + t) kHypTile + h].
 template <pilot_dtype DT, int C, bool SCALED, bool CONF>
 __global__ void __launch_bounds__(kBuildThreads, 2)
 level_persistent_kernel(const LevelArgs a) {
     constexpr int kWarps = kBuildThreads / 32;
     constexpr unsigned kEval = 0x80000000u;          // job_meta: "has a pose to evaluate" bit
-    __shared__ float red[kWarps][2][kAcc];
+    __shared__ float red[kWarps][kHypTile][kAcc];
     __shared__ double E[kWarps][kAcc];
     __shared__ double Wsh[kWarps][128];         // FP64 step scratch, one block per warp
-    __shared__ float pose[2][12];
+    __shared__ float pose[kHypTile][12];
     __shared__ long long s_item;
     __shared__ int s_frame, s_job, s_njobs, s_first, s_t0;
-    __shared__ unsigned s_meta[2];
+    __shared__ unsigned s_meta[kHypTile];
     // frame tables, staged when the launch lists few frames
     __shared__ int s_fitem[kSmemFrames + 1], s_fjob[kSmemFrames + 1], s_flist[kSmemFrames], s_fipj[kSmemFrames];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -138,27 +138,34 @@ level_persistent_kernel(const LevelArgs a) {
                     const int i = find(true, item);
                     const int ipj = fipj(i);
                     const int local = (int)(item - fitem(i));
-                    const int pair = local / ipj;
+                    const int jt = local / ipj;      // job tile within the frame
                     s_frame = flist(i);
-                    s_job = fjob(i) + 2 * pair;
-                    s_njobs = min(2, fjob(i + 1) - s_job);
-                    s_first = fitem(i) + pair * ipj;
-                    s_t0 = (local - pair * ipj) * tpi;
+                    s_job = fjob(i) + kHypTile * jt;
+                    s_njobs = min(kHypTile, fjob(i + 1) - s_job);
+                    s_first = fitem(i) + jt * ipj;
+                    s_t0 = (local - jt * ipj) * tpi;
                 }
             }
             __syncthreads();
             if (s_item >= n_items) break;
             const int job = s_job;
-            if (tid < 24) {
+            if (tid < 12 * kHypTile) {
                 const int h = tid / 12;
                 pose[h][tid % 12] = __ldcg(a.pose32 + 12 * (size_t)(job + (h < s_njobs ? h : 0)) + tid % 12);
             }
-            if (tid < 2) s_meta[tid] = tid < s_njobs ? __ldcg(a.job_meta + job + tid) : 0u;
+            if (tid < kHypTile) s_meta[tid] = tid < s_njobs ? __ldcg(a.job_meta + job + tid) : 0u;
             __syncthreads();
             const FrameDesc* fd = a.frames + s_frame;
             const int level = a.level >= 0 ? a.level : fd->level;
-            const bool act0 = (s_meta[0] & kEval) != 0, act1 = (s_meta[1] & kEval) != 0;
-            if (k <= a.iters[level] && (act0 || act1)) {
+            SlotPoses sp;
+            bool any = false;
+#pragma unroll
+            for (int h = 0; h < kHypTile; ++h) {
+                sp.p[h] = pose[h];
+                sp.act[h] = (s_meta[h] & kEval) != 0;
+                any = any || sp.act[h];
+            }
+            if (k <= a.iters[level] && any) {
                 const LevelView v{fd->px, fd->py, fd->pz, fd->weight, fd->valid, fd->qry[level], fd->ref[level],
                                   fd->qscale[level], fd->rscale[level], fd->conf[level], fd->H[level], fd->W[level],
                                   fd->fx[level], fd->fy[level], fd->cx[level], fd->cy[level], a.huber};
@@ -169,11 +176,10 @@ level_persistent_kernel(const LevelArgs a) {
 #pragma unroll
                     for (int i = 0; i < kNumSums; ++i) acc[i] = 0.f;
                     const int j0 = t * a.tile;
-                    accumulate_anchors<DT, C, SCALED, CONF, kBuildThreads>(v, pose[0], pose[1], act0, act1, j0,
-                                                                           min(j0 + a.tile, fd->N), acc);
-                    const float val = cta_reduce_pair<kBuildThreads, GroupShape<DT, C>::APB>(acc, red);
-                    if (tid < 2 * kAcc && tid / kAcc < s_njobs)
-                        a.partial[(((size_t)s_first * tpi + t) * 2 + tid / kAcc) * kAcc + tid % kAcc] = val;
+                    accumulate_anchors<DT, C, SCALED, CONF, kBuildThreads>(v, sp, j0, min(j0 + a.tile, fd->N), acc);
+                    const float val = cta_reduce_slots<kBuildThreads, GroupShape<DT, C>::APB>(acc, red);
+                    if (tid < kHypTile * kAcc && tid / kAcc < s_njobs)
+                        a.partial[(((size_t)s_first * tpi + t) * kHypTile + tid / kAcc) * kAcc + tid % kAcc] = val;
                 }
             }
             __syncthreads();
@@ -193,12 +199,12 @@ level_persistent_kernel(const LevelArgs a) {
             if (evaluated && lane < kNumSums) {
                 const int n_t = fd->N > 0 ? (fd->N + a.tile - 1) / a.tile : 1;
                 const int jl = job - fjob(i);
-                const int first = fitem(i) + (jl >> 1) * fipj(i);
-                const float* src = a.partial + ((size_t)first * tpi * 2 + (jl & 1)) * kAcc + lane;
+                const int first = fitem(i) + (jl / kHypTile) * fipj(i);
+                const float* src = a.partial + ((size_t)first * tpi * kHypTile + jl % kHypTile) * kAcc + lane;
                 double sum = 0.0;
                 for (int c = 0; c < 8; ++c) {
                     double part = 0.0;
-                    for (int t = c; t < n_t; t += 8) part += (double)__ldcg(src + (size_t)t * 2 * kAcc);
+                    for (int t = c; t < n_t; t += 8) part += (double)__ldcg(src + (size_t)t * kHypTile * kAcc);
                     sum += part;
                 }
                 E[warp][lane] = sum;

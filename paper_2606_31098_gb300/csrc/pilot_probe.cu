@@ -83,30 +83,35 @@ __global__ void gather_probe_kernel(const uint4* map, int H, int W, long long sa
     if (acc == 0x9e3779b9u) atomicXor(&g_probe_sink, acc);
 }
 
-// The build pass' own access pattern without its arithmetic: grid (anchor tiles x poses),
-// 256 threads, groups of LP lanes; each lane projects one anchor under its CTA's pose and
-// publishes the tap offset to the group (shuffles), then the group reads the 4 taps and the
-// reference row of each of its LP anchors with NV 16-byte loads per lane and tap (row 0 for
-// an anchor that is not visible, as the build pass does).  Loaded words are XOR-folded.
+// The build pass' own access pattern without its arithmetic: grid (anchor tiles x tiles of
+// kHypTile poses), 256 threads, the build pass' lane layout (LP lanes per tap; a group takes
+// APB anchors under HG poses at a time, NS groups over the same anchors): each lane projects
+// one (anchor, pose) record and publishes the tap offset to its group (shuffles), then the
+// group reads the reference row of each of its anchors once and the 4 taps of each record,
+// NV 16-byte loads per lane and tap (row 0 for a record that is not visible, as the build
+// pass does).  Two batches are in flight per step.  Loaded words are XOR-folded.
 template <int LP, int NV>
 __global__ void __launch_bounds__(256) frame_gather_probe_kernel(const float* pts, int N, const uint4* map,
                                                                  const uint4* ref, int H, int W, float fx,
                                                                  float fy, float cx, float cy,
-                                                                 const float* poses, int tile) {
+                                                                 const float* poses, int M, int tile) {
+    constexpr int HG = LP < kHypTile ? LP : kHypTile, NS = kHypTile / HG, APB = LP / HG;
     constexpr int V = LP * NV;                 // 16-byte vectors per tap (= per reference row)
-    const float* P = poses + 12 * blockIdx.y;
+    constexpr int ASTEP = 256 / (LP * NS) * APB;
+    const int lane = threadIdx.x & 31, q = lane & (LP - 1), src0 = lane & ~(LP - 1);
+    const int slot = (lane / APB) % kHypTile, qa = q % APB;
+    const unsigned gmask = LP > 1 ? (((1u << LP) - 1u) << src0) : (1u << lane);
+    const float* P = poses + 12 * min(kHypTile * (int)blockIdx.y + slot, M - 1);
     const float R00 = P[0], R01 = P[1], R02 = P[2], T0 = P[3], R10 = P[4], R11 = P[5], R12 = P[6], T1 = P[7];
     const float R20 = P[8], R21 = P[9], R22 = P[10], T2 = P[11];
-    const int lane = threadIdx.x & 31, q = lane & (LP - 1), src0 = lane & ~(LP - 1);
-    const unsigned gmask = (((1u << LP) - 1u) << src0);
     const int j0 = blockIdx.x * tile, j1 = min(j0 + tile, N);
     const size_t row = (size_t)W * V;
     unsigned acc = 0;
-    for (int jb = j0 + (int)(threadIdx.x / LP) * LP; jb < j1; jb += 256) {
-        const int jo = jb + q;
+    // tap offset of anchor j under this lane's pose (-1: not visible)
+    auto project = [&](int j) {
         int off = -1;
-        if (jo < j1) {
-            const float X = __ldg(pts + jo), Y = __ldg(pts + N + jo), Z = __ldg(pts + 2 * N + jo);
+        if (j < j1) {
+            const float X = __ldg(pts + j), Y = __ldg(pts + N + j), Z = __ldg(pts + 2 * N + j);
             const float x = fmaf(R00, X, fmaf(R01, Y, fmaf(R02, Z, T0)));
             const float y = fmaf(R10, X, fmaf(R11, Y, fmaf(R12, Z, T1)));
             const float z = fmaf(R20, X, fmaf(R21, Y, fmaf(R22, Z, T2)));
@@ -117,17 +122,33 @@ __global__ void __launch_bounds__(256) frame_gather_probe_kernel(const float* pt
                     off = min((int)ys, H - 2) * W + min((int)xs, W - 2);
             }
         }
+        return off;
+    };
+    for (int jb = j0 + (int)(threadIdx.x / (LP * NS)) * APB; jb < j1; jb += 2 * ASTEP) {
+        const int offA = project(jb + qa), offB = project(jb + ASTEP + qa);
 #pragma unroll
-        for (int i = 0; i < LP; ++i) {
-            const int oi = LP > 1 ? __shfl_sync(gmask, off, src0 + i) : off;
-            const uint4* t00 = map + (size_t)(oi >= 0 ? oi : 0) * V;
-            const uint4* fr = ref + (size_t)(oi >= 0 ? jb + i : 0) * V;
+        for (int b = 0; b < 2; ++b) {
+            const int off = b ? offB : offA, jbb = jb + ASTEP * b;
 #pragma unroll
-            for (int k = 0; k < NV; ++k) {
-                const int c = q + k * LP;
-                const uint4 a = __ldg(t00 + c), b = __ldg(t00 + V + c), d = __ldg(t00 + row + c);
-                const uint4 e = __ldg(t00 + row + V + c), r = __ldg(fr + c);
-                acc ^= a.x ^ a.w ^ b.y ^ b.z ^ d.x ^ d.w ^ e.y ^ e.z ^ r.x ^ r.w;
+            for (int a = 0; a < APB; ++a) {
+                const uint4* fr = ref + (size_t)(jbb + a < j1 ? jbb + a : j0) * V;
+#pragma unroll
+                for (int k = 0; k < NV; ++k) {
+                    const uint4 r = __ldg(fr + q + k * LP);
+                    acc ^= r.x ^ r.w;
+                }
+            }
+#pragma unroll
+            for (int i = 0; i < LP; ++i) {
+                const int oi = LP > 1 ? __shfl_sync(gmask, off, src0 + i) : off;
+                const uint4* t00 = map + (size_t)(oi >= 0 ? oi : 0) * V;
+#pragma unroll
+                for (int k = 0; k < NV; ++k) {
+                    const int c = q + k * LP;
+                    const uint4 x0 = __ldg(t00 + c), x1 = __ldg(t00 + V + c), x2 = __ldg(t00 + row + c);
+                    const uint4 x3 = __ldg(t00 + row + V + c);
+                    acc ^= x0.x ^ x0.w ^ x1.y ^ x1.z ^ x2.x ^ x2.w ^ x3.y ^ x3.z;
+                }
             }
         }
     }
@@ -243,14 +264,14 @@ pilot_status pilot_probe_gather_frame(const float* points, int N, const void* ma
     if (C * elem % 16 || vec < 1 || vec > 16 || (vec & (vec - 1)))
         return probe_fail(PILOT_EINVAL, "a tap (C x element size) must be 16 .. 256 bytes, a power of two");
     cudaStream_t s = static_cast<cudaStream_t>(stream);
-    const dim3 grid((N + tile - 1) / tile, M);
+    const dim3 grid((N + tile - 1) / tile, (M + kHypTile - 1) / kHypTile);
     const float f[4] = {(float)fx, (float)fy, (float)cx, (float)cy};
     const uint4* mp = static_cast<const uint4*>(map);
     const uint4* rp = static_cast<const uint4*>(ref);
     auto go = [&]() {
 #define PILOT_FRAME_PROBE(LP, NV)                                                                             \
     frame_gather_probe_kernel<LP, NV><<<grid, 256, 0, s>>>(points, N, mp, rp, H, W, f[0], f[1], f[2], f[3], \
-                                                           poses32, tile)
+                                                           poses32, M, tile)
         switch (vec) {
             case 1: PILOT_FRAME_PROBE(1, 1); break;
             case 2: PILOT_FRAME_PROBE(2, 1); break;
@@ -264,7 +285,8 @@ pilot_status pilot_probe_gather_frame(const float* points, int N, const void* ma
     float ms = 0.f;
     const cudaError_t e = time_launch(go, s, &ms);
     if (e != cudaSuccess) return probe_fail(PILOT_ECUDA, cudaGetErrorString(e));
-    *units_per_s = (double)N * (double)M / (ms * 1e-3);
+    // every CTA evaluates kHypTile poses (a short last tile repeats the last pose)
+    *units_per_s = (double)N * (double)grid.y * kHypTile / (ms * 1e-3);
     return PILOT_OK;
 }
 

@@ -712,10 +712,10 @@ pilot_status pilot_align_create(const pilot_align_config* cfg_in, pilot_align_ha
     }
     ALLOC(h->state, sizeof(HypState) * M);
     ALLOC(h->pose32, sizeof(float) * 12 * M);
-    // tile records: plain form [slot][tile]; batched form [(pair_item * tiles_per_item + tile)
-    // * 2 + h], which rounds each pair's tiles up to whole work items and a frame's odd last
-    // job up to a pair
-    ALLOC(h->partial, sizeof(float) * kAcc * (M + (size_t)cfg.max_frames) *
+    // tile records: plain form [slot][tile]; batched form [(tile_item * tiles_per_item + tile)
+    // * kHypTile + h], which rounds each job tile's anchor tiles up to whole work items and a
+    // frame's jobs up to whole job tiles
+    ALLOC(h->partial, sizeof(float) * kAcc * (M + (size_t)(kHypTile - 1) * cfg.max_frames) *
                           ((size_t)h->max_tiles + kItemAnchors / kMinTile));
     ALLOC(h->active[0], sizeof(int) * M);
     ALLOC(h->active[1], sizeof(int) * M);

@@ -544,7 +544,7 @@ pilot_status pilot_serve_create(const pilot_align_config* cfg_in, size_t hbm_bud
         return bad("level counters");
     if ((e = cudaMalloc((void**)&s->pose32, sizeof(float) * 12 * H)) != cudaSuccess) return bad("candidates");
     if ((e = cudaMalloc((void**)&s->job_meta, sizeof(unsigned) * H)) != cudaSuccess) return bad("job table");
-    if ((e = cudaMalloc((void**)&s->partial, sizeof(float) * kAcc * (H + (size_t)max_slots) *
+    if ((e = cudaMalloc((void**)&s->partial, sizeof(float) * kAcc * (H + (size_t)(kHypTile - 1) * max_slots) *
                                                  (max_tiles + tiles_per_item(kPlainTile)))) != cudaSuccess)
         return bad("tile records");
     if ((e = cudaMalloc((void**)&s->desc_dev, s->desc_bytes)) != cudaSuccess) return bad("descriptors");
