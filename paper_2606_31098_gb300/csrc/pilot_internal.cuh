@@ -38,10 +38,10 @@ __host__ __device__ inline int items_per_job(int N, int tile, int tpi) {
 #ifndef PILOT_HYP_TILE
 #define PILOT_HYP_TILE 4
 #endif
-// Hypotheses a build-pass CTA holds over one anchor tile (2 or 4): the reference row of an
+// Hypotheses a build-pass CTA holds over one anchor tile (2, 4 or 8): the reference row of an
 // anchor is read once for all of them.
 constexpr int kHypTile = PILOT_HYP_TILE;
-static_assert(kHypTile == 2 || kHypTile == 4, "hypothesis tile");
+static_assert(kHypTile == 2 || kHypTile == 4 || kHypTile == 8, "hypothesis tile");
 
 // Work items of a frame of N anchors with n_jobs jobs: the jobs are taken kHypTile at a time
 // (a work item covers all jobs of its tile, as a build-pass CTA holds kHypTile hypotheses).

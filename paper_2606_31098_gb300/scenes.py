@@ -355,6 +355,47 @@ def _ray_to_dsm(C, d, dsm, x0, y0, gsd, step=0.05, s_max=5000.0, pointwise=False
     return 0.5 * (lo + hi)
 
 
+def _rays_to_dsm(Cs, ds, dsm, x0, y0, gsd, step=0.25, s_max=5000.0):
+    """_ray_to_dsm for many rays at once (Cs, ds: (K, 3)): each ray starts where it drops
+    below the map's highest cell (no crossing before that), marches in lockstep with the
+    others, then bisects to 1e-9 m.  Bilinear DSM between cell centres, clamped to the raster."""
+    Cs, ds = np.asarray(Cs, np.float64), np.asarray(ds, np.float64)
+    H, W = dsm.shape
+    D = dsm.astype(np.float64)
+
+    def above(idx, s_arr):
+        p = Cs[idx] + s_arr[:, None] * ds[idx]
+        c = np.clip((p[:, 0] - x0) / gsd - 0.5, 0.0, W - 1.0)
+        r = np.clip((p[:, 1] - y0) / gsd - 0.5, 0.0, H - 1.0)
+        c0 = np.minimum(c.astype(np.int64), W - 2)
+        r0 = np.minimum(r.astype(np.int64), H - 2)
+        ax, ay = c - c0, r - r0
+        h = ((1 - ay) * ((1 - ax) * D[r0, c0] + ax * D[r0, c0 + 1]) + ay * ((1 - ax) * D[r0 + 1, c0] + ax * D[r0 + 1, c0 + 1]))
+        return p[:, 2] - h
+
+    K = Cs.shape[0]
+    lo = np.maximum((Cs[:, 2] - float(D.max()) - 1.0) / np.maximum(-ds[:, 2], 1e-12), 0.0)
+    hi = np.full(K, np.nan)
+    todo = np.arange(K)
+    while todo.size:
+        s_new = lo[todo] + step
+        f = above(todo, s_new)
+        hit = f <= 0
+        hi[todo[hit]] = s_new[hit]
+        lo[todo[~hit]] = s_new[~hit]
+        todo = todo[~hit & (s_new < s_max)]
+    if np.isnan(hi).any():
+        raise ValueError("a ray does not reach the surface")
+    lo = hi - step
+    idx = np.arange(K)
+    while np.max(hi - lo) > 1e-9:
+        mid = 0.5 * (lo + hi)
+        up = above(idx, mid) > 0
+        lo = np.where(up, mid, lo)
+        hi = np.where(up, hi, mid)
+    return 0.5 * (lo + hi)
+
+
 # ------------------------------------------------------------------------- frames
 
 def make_frame(cfg: SceneConfig, seed: int) -> Frame:
@@ -382,7 +423,7 @@ def make_frame(cfg: SceneConfig, seed: int) -> Frame:
     C_gt = target - dist * d
     T_gt = look_pose(C_gt, yaw, pitch)
 
-    qry, refs = [], []
+    qry, refs, seen = [], [], []
     valid = np.ones(points.shape[1], bool)
     for lvl, (H, W) in enumerate(cfg.levels):
         qry.append(_make_feature_map(H, W, cfg.channels, cfg, r_lev[lvl]))
@@ -391,21 +432,33 @@ def make_frame(cfg: SceneConfig, seed: int) -> Frame:
         u, v, z = project_gt(points, T_gt, cfg.f0 * s, cx0 * s, cy0 * s)
         vis = (z > 0.1) & (u - 0.5 >= 0) & (u - 0.5 <= W - 1) & (v - 0.5 >= 0) & (v - 0.5 <= H - 1)
         valid &= vis
+        seen.append(vis)
         f = read_map(qry[lvl], u, v)
         f += cfg.ref_noise * r_ref.standard_normal(f.shape)
         refs.append(f.astype(np.float32))
-    for f in refs:
-        f[~valid] = 0.0
     if cfg.n_anchors > 0:
-        # sample geo-anchors among the crop cells seen at every level (Sec. V-A: the
-        # refinement runs on a fixed number of valid anchors drawn from the crop)
-        cand = np.flatnonzero(valid)
-        if cand.size < cfg.n_anchors:
-            raise ValueError(f"only {cand.size} valid crop cells for {cfg.n_anchors} anchors")
-        keep = np.sort(np.random.default_rng(kids[6]).choice(cand, cfg.n_anchors, replace=False))
+        # geo-anchors drawn from the whole crop, blind to the ground truth (Sec. V-A: the
+        # refinement runs on a fixed number of anchors drawn from the crop's valid pixels --
+        # every cell of a synthetic crop is one): an anchor the query does not see at a level
+        # gets a random unit descriptor there, as a real network's reference descriptor of a
+        # pixel outside the query view would match nothing
+        r_anc = np.random.default_rng(kids[6])
+        keep = np.sort(r_anc.choice(points.shape[1], cfg.n_anchors, replace=False))
         points = np.ascontiguousarray(points[:, keep])
-        valid = valid[keep]
-        refs = [np.ascontiguousarray(f[keep]) for f in refs]
+        valid = np.ones(keep.size, bool)
+        out = []
+        for f, vis in zip(refs, seen):
+            f = np.ascontiguousarray(f[keep])
+            unseen = ~vis[keep]
+            rnd = r_anc.standard_normal((int(unseen.sum()), f.shape[1]))
+            f[unseen] = (rnd / np.linalg.norm(rnd, axis=1, keepdims=True)).astype(np.float32)
+            out.append(f)
+        refs = out
+        n_seen_all = int(np.logical_and.reduce([vis[keep] for vis in seen]).sum())
+    else:
+        for f in refs:
+            f[~valid] = 0.0
+        n_seen_all = int(valid.sum())
 
     # hypotheses
     M = cfg.n_hyps
@@ -456,7 +509,7 @@ def make_frame(cfg: SceneConfig, seed: int) -> Frame:
                  use_range=cfg.use_range, range_m=float(rng_meas), w_range=cfg.w_range,
                  dsm=dsm, dsm_x0=x0, dsm_y0=y0, dsm_gsd=gsd, seed=seed,
                  meta=dict(alt=alt, pitch_deg=float(np.rad2deg(pitch)), yaw_deg=float(np.rad2deg(yaw)),
-                           range_true=float(rng_true), crop_side=S,
+                           range_true=float(rng_true), crop_side=S, n_seen_all_levels=n_seen_all,
                            T_prior=prior if cfg.hyp_mode == "grid" else None))
 
 
@@ -654,45 +707,44 @@ def query_bank(tc: TrackConfig, seed: int) -> list:
 
 
 def track_inputs(gmap: GlobalMap, tc: TrackConfig, bank: list, t: int, T_gt_world: np.ndarray,
-                 crop_points: np.ndarray, crop_valid: np.ndarray, origin, seed: int) -> Frame:
+                 crop_points: np.ndarray, crop_valid: np.ndarray, origin, seed: int, anchor_idx) -> Frame:
     """Frame t of a sequence from its reference crop (the stand-in for the feature network:
     reference descriptors are the query features at the anchors' ground-truth projections).
 
-    crop_points (3, S^2) are the crop's anchors as offsets from `origin` (ox, oy); anchors
-    seen with a 1-pixel margin at every level under the ground truth are eligible, and the
-    tc.n_anchors of them with the smallest seeded per-pixel keys are kept (so an anchor's
-    selection does not depend on the others).  With probability tc.degrade_prob the frame's
-    reference descriptors are replaced by random unit vectors (a visual failure).  Poses
-    and the DSM are crop-local; T_hyps is a placeholder the tracker replaces by its seeds."""
+    crop_points (3, S^2) are the crop's anchors as offsets from `origin` (ox, oy);
+    anchor_idx are the crop pixels drawn as geo-anchors (by the geo-anchor sampler, from the
+    crop's valid mask, blind to the ground truth).  An anchor the query sees at a level under
+    the ground truth (1-pixel margin) gets the query feature there plus noise; any other gets
+    a random unit descriptor at that level (a real network's descriptor of a pixel outside
+    the query view matches nothing).  With probability tc.degrade_prob the frame's reference
+    descriptors are all random unit vectors (a visual failure).  Poses and the DSM are
+    crop-local; T_hyps is a placeholder the tracker replaces by its seeds."""
     ss = np.random.SeedSequence([seed, t]).spawn(4)
     r_key, r_ref, r_sens, r_deg = (np.random.default_rng(k) for k in ss)
     ox, oy = float(origin[0]), float(origin[1])
     R, tw = pose_parts(T_gt_world)
     T_loc = np.hstack([R, (tw + R @ np.array([ox, oy, 0.0]))[:, None]]).ravel()
     qry = bank[t % len(bank)]
-    pts = np.asarray(crop_points, np.float32)
-    ok = np.asarray(crop_valid).astype(bool).copy()
+    keep = np.asarray(anchor_idx, np.int64)
+    if keep.size == 0:
+        raise ValueError(f"frame {t}: no geo-anchor drawn from the crop")
+    pts = np.asarray(crop_points, np.float32)[:, keep]
     H0, W0 = tc.levels[0]
     cx0, cy0 = W0 / 2.0, H0 / 2.0
-    uv = []
+    refs = []
+    degraded = bool(r_deg.random() < tc.degrade_prob) or t in tc.degraded_frames
+    seen_all = np.ones(keep.size, bool)
     for lvl, (H, W) in enumerate(tc.levels):
         s = 2.0 ** -lvl
         u, v, z = project_gt(pts, T_loc, tc.f0 * s, cx0 * s, cy0 * s)
-        ok &= (z > 0.1) & (u - 0.5 >= 1.0) & (u - 0.5 <= W - 2.0) & (v - 0.5 >= 1.0) & (v - 0.5 <= H - 2.0)
-        uv.append((u, v))
-    keys = r_key.random(pts.shape[1])
-    cand = np.flatnonzero(ok)
-    keep = np.sort(cand[np.argsort(keys[cand], kind="stable")[:tc.n_anchors]])
-    if keep.size == 0:
-        raise ValueError(f"frame {t}: no crop anchor is seen at the ground truth")
-    refs = []
-    degraded = bool(r_deg.random() < tc.degrade_prob) or t in tc.degraded_frames
-    for lvl in range(len(tc.levels)):
-        u, v = uv[lvl]
-        f = read_map(qry[lvl], u[keep], v[keep]) + tc.ref_noise * r_ref.standard_normal((keep.size, tc.channels))
-        if degraded:
-            f = r_ref.standard_normal(f.shape)
-            f /= np.linalg.norm(f, axis=1, keepdims=True)
+        seen = (z > 0.1) & (u - 0.5 >= 1.0) & (u - 0.5 <= W - 2.0) & (v - 0.5 >= 1.0) & (v - 0.5 <= H - 2.0)
+        seen_all &= seen
+        f = np.empty((keep.size, tc.channels))
+        if seen.any():
+            f[seen] = read_map(qry[lvl], u[seen], v[seen]) + tc.ref_noise * r_ref.standard_normal((int(seen.sum()), tc.channels))
+        rnd_rows = ~seen if not degraded else np.ones(keep.size, bool)
+        rnd = r_ref.standard_normal((int(rnd_rows.sum()), tc.channels))
+        f[rnd_rows] = rnd / np.linalg.norm(rnd, axis=1, keepdims=True)
         refs.append(f.astype(np.float32))
     g_cam = R @ GRAVITY_WORLD
     a = np.cross(g_cam, _unit(r_sens))
@@ -702,14 +754,14 @@ def track_inputs(gmap: GlobalMap, tc: TrackConfig, bank: list, t: int, T_gt_worl
     d = R[2]                                         # optical axis in the world
     rng_true = _ray_to_dsm(C_loc, d, gmap.dsm, gmap.x0 - ox, gmap.y0 - oy, gmap.gsd, step=tc.ray_step, pointwise=True)
     rng_meas = rng_true + tc.range_noise * r_sens.standard_normal()
-    sub = np.ascontiguousarray(pts[:, keep])
+    sub = np.ascontiguousarray(pts)
     return Frame(points=sub, point_valid=np.ones(keep.size, np.uint8),
                  point_weight=np.ones(keep.size, np.float32), ref_feat=refs, qry_feat=qry,
                  fx=tc.f0, fy=tc.f0, cx=cx0, cy=cy0, T_hyps=T_loc.reshape(1, 12).copy(), T_gt=T_loc,
                  use_gravity=True, gravity_cam=g_meas, gravity_world=GRAVITY_WORLD.copy(), w_grav=tc.w_grav,
                  use_range=True, range_m=float(rng_meas), w_range=tc.w_range,
                  dsm=gmap.dsm, dsm_x0=gmap.x0 - ox, dsm_y0=gmap.y0 - oy, dsm_gsd=gmap.gsd,
-                 seed=seed, meta=dict(t=t, degraded=degraded, origin=(ox, oy), n_eligible=int(cand.size)))
+                 seed=seed, meta=dict(t=t, degraded=degraded, origin=(ox, oy), n_seen_all_levels=int(seen_all.sum())))
 
 
 class SyntheticNetwork:
@@ -725,7 +777,7 @@ class SyntheticNetwork:
 
     def frame(self, t: int, crop: dict) -> Frame:
         return track_inputs(self.gmap, self.tc, self.bank, t, self.gt[t], crop["points"], crop["valid"],
-                            crop["origin"], self.seed)
+                            crop["origin"], self.seed, crop["anchor_idx"])
 
     def __call__(self, t: int, crop: dict):
         import torch
@@ -738,3 +790,138 @@ class SyntheticNetwork:
         arrays = dict(points=to(f.points), point_weight=to(f.point_weight), point_valid=to(f.point_valid),
                       ref_feat=[to(r) for r in f.ref_feat], qry_feat=self._qdev[b])
         return f, arrays
+
+
+# ------------------------------------------------------------- serving workload (streams)
+
+@dataclass
+class StreamConfig:
+    """Recipe of the serving workload: UAV streams over one global map, each a smooth
+    trajectory at `rate_hz` (Poisson jitter on arrival, mean 1 / rate_hz), altitude and pitch
+    drawn per stream, heading rate at most `yaw_rate_deg_s`, ground speed `speed`; per frame
+    a reference crop of side U{crop_sides} around the previous estimate (every valid crop
+    pixel a geo-anchor), hypotheses on a grid around it, BF16 features (the query pyramids of
+    a bank, used in turn; reference descriptors the query features at the anchors'
+    ground-truth projections plus noise, random unit vectors for anchors the query does not
+    see), gravity and range priors as the frame recipe."""
+
+    n_frames: int = 300
+    rate_hz: float = 30.0
+    speed: float = 10.0                              # m/s
+    yaw_rate_deg_s: float = 10.0                     # largest heading rate
+    altitude: tuple = (100.0, 300.0)
+    pitch_deg: tuple = (30.0, 70.0)
+    crop_sides: tuple = (128, 192, 256, 320, 384)
+    grids: tuple = ((2, 4), (3, 4), (2, 9), (3, 7), (4, 5), (3, 9), (4, 7), (4, 9))   # (n_xy, n_yaw): M = 16 .. 144
+    xy_span: float = 10.0                            # grid half-width, metres
+    yaw_span_deg: float = 5.0                        # grid half-width, degrees
+    levels: tuple = ((480, 640), (240, 320), (120, 160))
+    f0: float = 600.0
+    channels: int = 32
+    query_bank: int = 4
+    ref_noise: float = 0.01
+    gravity_noise_deg: float = 0.2
+    range_noise: float = 0.1
+    w_grav: float = 1e2
+    w_range: float = 1e1
+
+
+def stream_trajectory(gmap: GlobalMap, sc: StreamConfig, seed: int) -> np.ndarray:
+    """(n_frames, 12) ground-truth world->camera poses of one seeded stream: constant
+    altitude U(altitude) and pitch U(pitch), heading rate a sinusoid of amplitude up to
+    yaw_rate_deg_s, ground speed `speed`, starting well inside the map."""
+    rng = np.random.default_rng(seed)
+    n, dt = sc.n_frames, 1.0 / sc.rate_hz
+    tt = np.arange(n) * dt
+    alt = rng.uniform(*sc.altitude)
+    pitch = np.deg2rad(rng.uniform(*sc.pitch_deg))
+    amp = np.deg2rad(rng.uniform(0.3, 1.0) * sc.yaw_rate_deg_s)
+    w, ph = rng.uniform(0.2, 1.0), rng.uniform(0, 2 * np.pi)
+    yaw = rng.uniform(0, 2 * np.pi) + np.concatenate([[0.0], np.cumsum(amp * np.sin(w * tt[:-1] + ph) * dt)])
+    half = gmap.dsm.shape[0] * gmap.gsd / 2.0
+    xy = np.zeros((n, 2))
+    margin = min(900.0, 0.5 * half)                  # the crops stay on the map
+    xy[0] = rng.uniform(-half + margin, half - margin, 2)
+    for k in range(1, n):
+        xy[k] = xy[k - 1] + sc.speed * dt * np.array([np.cos(yaw[k - 1]), np.sin(yaw[k - 1])])
+    return np.array([look_pose(np.array([xy[k, 0], xy[k, 1], alt]), yaw[k], pitch) for k in range(n)])
+
+
+def stream_sensors(gmap: GlobalMap, sc: StreamConfig, gt: np.ndarray, seed: int) -> list:
+    """Per frame of a stream: (measured gravity in the camera frame, measured laser range
+    along the optical axis), from the ground truth with the recipe's noise."""
+    rng = np.random.default_rng(seed)
+    Cs = np.array([camera_centre(T) for T in gt])
+    ds = np.array([pose_parts(T)[0][2] for T in gt])            # optical axes in the world
+    rng_true = _rays_to_dsm(Cs, ds, gmap.dsm, gmap.x0, gmap.y0, gmap.gsd)
+    out = []
+    for T, r_t in zip(gt, rng_true):
+        R, _ = pose_parts(T)
+        g_cam = R @ GRAVITY_WORLD
+        a = np.cross(g_cam, _unit(rng))
+        a /= np.linalg.norm(a)
+        g_meas = Rotation.from_rotvec(a * np.deg2rad(sc.gravity_noise_deg)).as_matrix() @ g_cam
+        out.append((g_meas, float(r_t + sc.range_noise * rng.standard_normal())))
+    return out
+
+
+def stream_frame_shape(sc: StreamConfig, stream: int, t: int) -> tuple:
+    """(crop side, n_xy, n_yaw) of frame t of a stream, seeded by (stream, t)."""
+    rng = np.random.default_rng([9_000_000 + stream, t])
+    side = int(sc.crop_sides[rng.integers(0, len(sc.crop_sides))])
+    n_xy, n_yaw = sc.grids[rng.integers(0, len(sc.grids))]
+    return side, int(n_xy), int(n_yaw)
+
+
+class StreamNetwork:
+    """The feature network's stand-in for the serving workload, on the device: a bank of
+    query pyramids (FP32 for sampling, BF16 for the solver) and, for a crop, the reference
+    descriptors of every anchor at every level -- the bank pyramid read bilinearly at the
+    anchor's ground-truth projection (pixel i covers [i, i + 1), read at array coordinate
+    pixel - 1/2) plus N(0, ref_noise) noise where the query sees it (1-pixel margin), a random
+    unit vector elsewhere -- drawn from a device generator seeded per frame."""
+
+    def __init__(self, sc: StreamConfig, seed: int, device: str = "cuda"):
+        import torch
+        self.torch, self.sc, self.device = torch, sc, device
+        cfg = SceneConfig(levels=sc.levels, channels=sc.channels)
+        ss = np.random.SeedSequence(seed).spawn(sc.query_bank * len(sc.levels))
+        self.bank32, self.bank_nchw = [], []
+        for b in range(sc.query_bank):
+            lv, lc = [], []
+            for l, (H, W) in enumerate(sc.levels):
+                m = _make_feature_map(H, W, sc.channels, cfg, np.random.default_rng(ss[b * len(sc.levels) + l]))
+                t = torch.from_numpy(np.ascontiguousarray(m, np.float32)).to(device)
+                lv.append(t)
+                lc.append(t.permute(2, 0, 1).unsqueeze(0).contiguous())
+            self.bank32.append(lv)
+            self.bank_nchw.append(lc)
+
+    def descriptors(self, b: int, points, T_local: np.ndarray, seed: int) -> list:
+        """Per level (N, C) FP32 device reference descriptors of the anchors `points` (3, N)
+        (device, crop-local) under the crop-local ground truth T_local, with pyramid b."""
+        torch = self.torch
+        sc = self.sc
+        g = torch.Generator(device=self.device)
+        g.manual_seed(int(seed) & 0x7FFFFFFFFFFFFFFF)
+        T = torch.as_tensor(np.asarray(T_local, np.float64).reshape(3, 4), dtype=torch.float64, device=self.device)
+        p = T[:, :3] @ points.double() + T[:, 3:]
+        x, y, z = p[0], p[1], p[2]
+        H0, W0 = sc.levels[0]
+        out = []
+        for l, (H, W) in enumerate(sc.levels):
+            s = 2.0 ** -l
+            zz = torch.where(z > 0.1, z, torch.ones_like(z))
+            u = sc.f0 * s * x / zz + W0 / 2.0 * s
+            v = sc.f0 * s * y / zz + H0 / 2.0 * s
+            seen = (z > 0.1) & (u - 0.5 >= 1.0) & (u - 0.5 <= W - 2.0) & (v - 0.5 >= 1.0) & (v - 0.5 <= H - 2.0)
+            gx = (2.0 * (u - 0.5) / (W - 1) - 1.0).float()
+            gy = (2.0 * (v - 0.5) / (H - 1) - 1.0).float()
+            grid = torch.stack([gx, gy], dim=-1).view(1, 1, -1, 2)
+            f = torch.nn.functional.grid_sample(self.bank_nchw[b][l], grid, mode="bilinear", align_corners=True)
+            f = f.view(sc.channels, -1).t()
+            f = f + sc.ref_noise * torch.randn(f.shape, generator=g, device=self.device)
+            rnd = torch.randn(f.shape, generator=g, device=self.device)
+            rnd = rnd / rnd.norm(dim=1, keepdim=True)
+            out.append(torch.where(seen[:, None], f, rnd).contiguous())
+        return out

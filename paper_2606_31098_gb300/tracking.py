@@ -63,6 +63,13 @@ class CropSettings:
     s_min: float = 0.0
     s_step: float = 0.25
     n_samples: int = 8000
+    n_anchors: int = 500          # geo-anchors drawn from each crop's valid pixels
+    anchor_seed: int = 0          # base seed of the draws (frame t: frame_anchor_seed(anchor_seed, t))
+
+
+def frame_anchor_seed(base: int, t: int) -> int:
+    """Seed of frame t's geo-anchor draw (a distinct SplitMix64 stream per frame)."""
+    return (int(base) * 1000003 + int(t) + 1) & 0xFFFFFFFFFFFFFFFF
 
 
 @dataclass
@@ -106,10 +113,14 @@ class SequentialTracker:
         # two crop slots (the one being localised and the one being prepared), each with a
         # page-locked host copy for the network
         self.slots = []
+        n = crop.n_anchors
         for _ in range(2):
             d = dict(points=torch.empty((3, S * S), dtype=torch.float32, device=dev),
                      valid=torch.empty(S * S, dtype=torch.uint8, device=dev), rgb=None,
-                     geometry=torch.empty(28, dtype=torch.float64, device=dev))
+                     geometry=torch.empty(28, dtype=torch.float64, device=dev),
+                     idx=torch.empty(n, dtype=torch.int32, device=dev),
+                     anchors=torch.empty((3, n), dtype=torch.float32, device=dev),
+                     count=torch.empty(1, dtype=torch.int32, device=dev))
             h = {k: torch.empty(v.shape, dtype=v.dtype, pin_memory=True) for k, v in d.items() if v is not None}
             self.slots.append((d, h))
         self.seeds = torch.empty((self.M, 12), dtype=torch.float64, device=dev)
@@ -126,8 +137,9 @@ class SequentialTracker:
         return lookahead_crop_pose(t, self.state.history, self._initial)
 
     # ------------------------------------------------------------------ crops
-    def _crop(self, T, slot: int) -> dict:
-        """Crop around T into `slot` on the map-preparation stream; waits for it and returns
+    def _crop(self, T, slot: int, t: int) -> dict:
+        """Crop around T into `slot` on the map-preparation stream and draw frame t's
+        geo-anchors from its valid pixels (pilot_sample_anchors); waits for it and returns
         the host copies with the device time."""
         torch = self.torch
         d, h = self.slots[slot]
@@ -138,6 +150,8 @@ class SequentialTracker:
         with torch.cuda.stream(self.map_stream):
             e0.record(self.map_stream)
             B.crop_reference(self.map, p, with_rgb=False, out=d, stream=self.map_stream)
+            B.sample_anchors(d["valid"], d["points"], c.n_anchors, frame_anchor_seed(c.anchor_seed, t),
+                             out=dict(idx=d["idx"], points=d["anchors"], count=d["count"]), stream=self.map_stream)
             for k in h:
                 h[k].copy_(d[k], non_blocking=True)
             e1.record(self.map_stream)
@@ -145,8 +159,10 @@ class SequentialTracker:
         g = h["geometry"].numpy()
         if g[27] != 1.0:
             raise CropFailure("the reference crop failed (a corner ray never met the DSM)")
+        n = int(h["count"].numpy()[0])
         return dict(points=h["points"].numpy(), valid=h["valid"].numpy(), origin=(float(g[9]), float(g[10])),
-                    geometry=g.copy(), crop_ms=e0.elapsed_time(e1), slot=slot)
+                    anchor_idx=h["idx"].numpy()[:n].astype(np.int64).copy(), geometry=g.copy(),
+                    crop_ms=e0.elapsed_time(e1), slot=slot)
 
     def _start_prepare(self, t_next: int):
         T = self._lookahead_pose(t_next)
@@ -155,7 +171,7 @@ class SequentialTracker:
 
         def work():
             try:
-                box["crop"] = self._crop(T, slot)
+                box["crop"] = self._crop(T, slot, t_next)
             except Exception as ex:      # surfaced when the crop is taken
                 box["error"] = ex
         th = threading.Thread(target=work, daemon=True)
@@ -202,7 +218,7 @@ class SequentialTracker:
                 self._slot = crop["slot"]
             else:
                 crop_pose = prior.copy()
-                crop = self._crop(crop_pose, self._slot)
+                crop = self._crop(crop_pose, self._slot, t)
         except CropFailure:
             # no reference for this frame: the prior stands as its estimate
             self._next_given = None

@@ -138,3 +138,37 @@ def test_submit_errors(torch):
         server.wait(t)
     server.close()
     tiny.close()
+
+
+def test_served_stream_frames_equal_their_alone_solve(torch):
+    """Serving workload frames (a device crop around the stream's estimate, grid hypotheses,
+    BF16 features; serving.StreamClient.prepare) from four streams are in the server
+    together; each result equals pilot_align_solve of the same frame alone, bitwise."""
+    from paper_2606_31098_gb300 import serving as SV
+    from paper_2606_31098_gb300 import tracking as TK
+    g = S.make_global_map(side=2048, seed=31, n_hills=256, n_boxes=512)
+    sc = S.StreamConfig(n_frames=4)
+    net = S.StreamNetwork(sc, 5)
+    dsm = torch.as_tensor(g.dsm, device="cuda")
+    H0, W0 = sc.levels[0]
+    cam = TK.Camera(sc.f0, sc.f0, W0 / 2.0, H0 / 2.0, W0, H0)
+    server = B.Server(B.Options(max_points=384 * 384, max_hyps=4 * 144), 8 << 30, max_slots=8)
+    client = SV.StreamClient(server, g, dsm, sc, net, cam)
+    prepared = []
+    for sid in range(4):
+        gt = S.stream_trajectory(g, sc, 100 + sid)
+        st = SV.StreamState(gt, S.stream_sensors(g, sc, gt, 200 + sid), np.zeros(sc.n_frames), gt[0].copy())
+        prep = client.prepare(sid, st, 1)
+        assert prep is not None
+        prepared.append(prep)
+    tickets = [server.submit(fa) for fa, _, _ in prepared]
+    served = [server.wait(tk)[0] for tk in tickets]
+    server.close()
+    solver = B.Solver(B.Options(max_points=384 * 384, max_hyps=144))
+    for (fa, origin, keep), r in zip(prepared, served):
+        alone = solver.solve(fa)
+        np.testing.assert_array_equal(r.T_cw, alone.T_cw)
+        np.testing.assert_array_equal(r.cost, alone.cost)
+        np.testing.assert_array_equal(r.status, alone.status)
+        assert r.best == alone.best and r.best >= 0
+    solver.close()

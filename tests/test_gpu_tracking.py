@@ -17,6 +17,7 @@ import pytest
 
 from oracle import crop as OC
 from oracle import oracle as O
+from oracle import sampler as OS
 from oracle import tracking as TR
 from paper_2606_31098_gb300 import binding as B
 from paper_2606_31098_gb300 import scenes as S
@@ -76,7 +77,8 @@ def oracle_log(world, mode):
                       tc.ray_samples, tc.crop_side)
         r = OC.crop(om, p, with_rgb=False)
         assert r["ok"]
-        f = S.track_inputs(g, tc, bank, t, gt[t], r["points"], r["valid"], r["origin"], 77)
+        idx = OS.sample_anchors(r["valid"], tc.n_anchors, TK.frame_anchor_seed(0, t))
+        f = S.track_inputs(g, tc, bank, t, gt[t], r["points"], r["valid"], r["origin"], 77, idx)
         hyps = np.array([TR.to_local(h, r["origin"]) for h in TR.seed_grid(prior, GRID_XY, GRID_YAW)])
         o = O.solve(f.replace(T_hyps=hyps), oo)
         return TR.to_world(o.T_cw[o.best], r["origin"]), None
