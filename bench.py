@@ -41,9 +41,10 @@ MEASURED_PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
 BUILD_SRC = os.path.join(ROOT, "paper_2606_31098_gb300", "csrc", "pilot_build_impl.cuh")
 FP32_LANES_PER_SM = 128
 # DRAM bytes (read + write) per (anchor, hypothesis) unit of the FP32 build pass at C = 32,
-# from one ncu capture of a coarse-level launch (dram__bytes_read.sum + dram__bytes_write.sum
-# over its units), valid for the kernel source with this SHA-256 prefix; None otherwise.
-BUILD_TRAFFIC = {"src_sha256_16": None, "dram_bytes_per_unit": None}
+# from one ncu capture of a finest-level launch of the full frame (dram__bytes_read.sum +
+# dram__bytes_write.sum = 15 055 104 B over its 2 097 152 units; a coarse-level launch: 4.86 B
+# per unit), valid for the kernel source with this SHA-256 prefix; None otherwise.
+BUILD_TRAFFIC = {"src_sha256_16": "148b7ee765d4d3dd", "dram_bytes_per_unit": 7.179}
 
 
 def flops_per_unit(C: int) -> int:
@@ -82,6 +83,8 @@ def parse():
                     help="profiling entry point: only the reference-crop timing, printed as one JSON line")
     ap.add_argument("--batched-only", action="store_true",
                     help="profiling entry point: only the batched-form timings, printed as one JSON line")
+    ap.add_argument("--served-only", action="store_true",
+                    help="profiling entry point: only the served-form stream sweep, printed as one JSON line")
     ap.add_argument("--paper-schedule-only", action="store_true",
                     help="profiling entry point: only the plain paper-schedule solve (3 warm-up + 20 timed "
                          "solves of one frame), printed as one JSON line")
@@ -241,26 +244,23 @@ def make_frames(S, specs):
         return pool.starmap(S.make_frame, specs)
 
 
-def batched_and_served(args, B, S, torch, world, stream, served_too: bool = True):
+def batched_and_served(args, B, S, torch, world, stream, served_too: bool = True, gmap=None):
     """The batched form (one persistent launch per level under a CUDA graph) on BF16
-    storage, and the served form.
+    storage, and the served form (served_streams).
 
     * uneven32_bf16: 32 independently generated scenes, crop sides drawn uniformly from
       {128, 192, 256, 384}^2 anchors, 16-144 hypotheses each, 3 levels, priors on.
     * crop256: 8 independently generated 256^2-anchor frames (64 hypotheses): the plain
       form solving them one at a time in FP32 and in BF16, and the batched BF16 form
       solving all 8 in one batch -- the comparison the metric is quoted on."""
-    import threading
     rng = np.random.default_rng(12345)
     sides_all = (128, 192, 256, 384)
     sides = [int(sides_all[k]) for k in rng.integers(0, 4, 32)]
     hyps = [int(m) for m in rng.integers(16, 145, 32)]
     specs = [(S.SceneConfig(crop_side=sd, n_hyps=m), S.frame_seed(3, 5000 + i)) for i, (sd, m) in enumerate(zip(sides, hyps))]
     specs += [(S.config_full_frame(), S.frame_seed(3, 6000 + i)) for i in range(8)]
-    if served_too:
-        specs += [(S.SceneConfig(crop_side=s_, n_hyps=144), S.frame_seed(3, 7000 + i)) for i, s_ in enumerate(sides_all)]
     frames = make_frames(S, specs)
-    uneven_frames, f256, distinct = frames[:32], frames[32:40], frames[40:]
+    uneven_frames, f256 = frames[:32], frames[32:40]
     flush = torch.empty(512 * 1024 * 1024, dtype=torch.uint8, device="cuda")
 
     def bf16_args(f):
@@ -288,7 +288,7 @@ def batched_and_served(args, B, S, torch, world, stream, served_too: bool = True
         return world * units / (sum(ts) / 1e3), sum(ts) / reps, sched
 
     def time_plain(fas, reps):
-        solver = B.Solver(B.Options(max_points=max(fa.N for fa in fas), max_hyps=max(fa.M for fa in fas)))
+        solver = B.Solver(B.Options(max_points=max(fa.c.N for fa in fas), max_hyps=max(fa.M for fa in fas)))
         if args.pin_schedule:
             tile, streams = (int(v) for v in args.pin_schedule.split(":"))
             solver.set_schedule(fas[:1], batched=False, tile=tile, streams=streams)
@@ -313,7 +313,11 @@ def batched_and_served(args, B, S, torch, world, stream, served_too: bool = True
 
     uneven = [bf16_args(f) for f in uneven_frames]
     v_uneven, ms_uneven, sc_uneven = time_batch(uneven, 3)
+    v_uneven_plain_bf16, _ = time_plain(uneven, 1)
     del uneven
+    uneven32 = [B.FrameArgs(f, B.device_arrays(f), is_device=True) for f in uneven_frames]
+    v_uneven_plain_f32, _ = time_plain(uneven32, 1)
+    del uneven32
     a256_bf16 = [bf16_args(f) for f in f256]
     a256_f32 = [B.FrameArgs(f, B.device_arrays(f), is_device=True) for f in f256]
     v_plain_f32, sc_pf = time_plain(a256_f32, 2)
@@ -322,7 +326,9 @@ def batched_and_served(args, B, S, torch, world, stream, served_too: bool = True
     del a256_f32
     batched = {"uneven32_bf16": {"value": v_uneven, "unit": UNIT, "ms_per_batch": ms_uneven, "frames": 32,
                                  "distinct_scenes": 32, "crops": "128^2..384^2 (uniform over 4 sides)",
-                                 "hypotheses": "16..144", "schedule": sc_uneven},
+                                 "hypotheses": "16..144", "schedule": sc_uneven,
+                                 "plain_bf16_same_frames": v_uneven_plain_bf16,
+                                 "plain_f32_same_frames": v_uneven_plain_f32},
                "crop256": {"frames": 8, "distinct_scenes": 8, "hypotheses": 64, "unit": UNIT,
                            "plain_f32": v_plain_f32, "plain_bf16": v_plain_bf16, "batched_bf16": v_256,
                            "ms_per_batch_bf16": ms_256, "schedules": {"plain_f32": sc_pf, "plain_bf16": sc_pb,
@@ -330,100 +336,51 @@ def batched_and_served(args, B, S, torch, world, stream, served_too: bool = True
 
     if not served_too:
         return batched, {}
-    # served form: host (page-locked) BF16 frames staged by the server per request
-    dev = [B.quantized_device_arrays(f, B.BF16) for f in distinct]
+    return batched, served_streams(B, S, torch, gmap)
 
-    def entry(k, m, arrays):
-        a = dict(arrays[k])
-        a["T_cw"] = a["T_cw"][:m].contiguous()
-        return B.FrameArgs(distinct[k], a, is_device=a["points"].is_cuda, dtype=B.BF16)
 
-    host = []
-    for d in dev:
-        h = {}
-        for k, v in d.items():
-            if isinstance(v, list):
-                h[k] = [x.cpu().pin_memory() for x in v]
-            else:
-                h[k] = v.cpu().pin_memory()
-        host.append(h)
-    sweep, sweep_paper = [], []
+def served_streams(B, S, torch, g, counts=(1, 4, 16, 64), duration: float = 4.0, seed: int = 8_000_000):
+    """The served form on the serving workload: UAV streams at 30 Hz (exponential
+    inter-arrival, mean 33 ms) over one 4096^2 map at 0.5 m, each a smooth trajectory
+    (altitude 100-300 m, pitch 30-70 deg, heading rate up to 10 deg/s, 10 m/s); per frame a
+    device crop of 128^2 .. 384^2 anchors around the stream's previous estimate, a grid of
+    16-144 hypotheses around it, BF16 features, submitted to one server with a 16 GiB arena
+    (admission by slots, hypotheses and arena memory); the newest arrived frame of a stream
+    is taken when its previous result returns.  Swept over stream counts; each point
+    `duration` s of arrivals.  Reports the sustainable rate and arrival-to-result latency."""
+    from paper_2606_31098_gb300 import serving as SV
+    from paper_2606_31098_gb300 import tracking as TK
+    sc = S.StreamConfig(n_frames=int(duration * 30.0) + 30)
+    n_max = max(counts)
+    inputs = []
+    for s_ in range(n_max):
+        gt = S.stream_trajectory(g, sc, seed + s_)
+        inputs.append((gt, S.stream_sensors(g, sc, gt, seed + 1000 + s_)))
+    net = S.StreamNetwork(sc, seed + 99)
+    dsm_dev = torch.as_tensor(g.dsm, device="cuda")
+    H0, W0 = sc.levels[0]
+    cam = TK.Camera(sc.f0, sc.f0, W0 / 2.0, H0 / 2.0, W0, H0)
+    rng = np.random.default_rng(seed)
+    arrivals = []
+    for _ in range(n_max):
+        a = rng.uniform(0.0, 1.0 / sc.rate_hz) + np.concatenate([[0.0], np.cumsum(rng.exponential(1.0 / sc.rate_hz, sc.n_frames - 1))])
+        arrivals.append(a)
     budget = 16 << 30
-    # 10 iterations per level, then the paper's 2 / 3 / 4 (coarse to fine)
-    sweep_levels = []
-    for iters, streams, out, lpr in [((10, 10, 10, 0), 2, sweep, 1), ((10, 10, 10, 0), 8, sweep, 1),
-                                     ((10, 10, 10, 0), 64, sweep, 1), ((4, 3, 2, 0), 8, sweep_paper, 1),
-                                     ((4, 3, 2, 0), 64, sweep_paper, 1), ((10, 10, 10, 0), 2, sweep_levels, 3),
-                                     ((4, 3, 2, 0), 8, sweep_levels, 3), ((10, 10, 10, 0), 2, sweep_levels, 0),
-                                     ((4, 3, 2, 0), 8, sweep_levels, 0)]:
+    out = {"workload": "UAV streams at 30 Hz over a 4096^2 map at 0.5 m, per-frame device crop 128^2..384^2 "
+                       "anchors around the previous estimate, 16-144 grid hypotheses, BF16, 3 levels",
+           "hbm_budget_bytes": budget, "max_slots": 64, "duration_s_per_point": duration, "sweep": []}
+    for iters, ns in [((10, 10, 10, 0), c) for c in counts] + [((4, 3, 2, 0), n_max)]:
         server = B.Server(B.Options(iters=iters, max_points=384 * 384, max_hyps=64 * 144), budget, max_slots=64)
-        server.set_levels_per_round(lpr)
-        duration = 3.0
-        arrivals = []
-        for s_ in range(streams):
-            t = rng.exponential(1 / 30.0)
-            while t < duration:
-                arrivals.append(t)
-                t += rng.exponential(1 / 30.0)
-        arrivals.sort()
-        reqs = [entry(int(rng.integers(0, 4)), int(rng.integers(16, 145)), host) for _ in arrivals]
-        tickets, rejected = [], 0
-        lat, units, done_t = [], 0, []
-        lock = threading.Lock()
-        stop = [False]
-
-        def poller():
-            while True:
-                with lock:
-                    pend = list(tickets)
-                    fin = stop[0]
-                if fin and not pend:
-                    return
-                for tk in pend:
-                    ok, r, l_ = server.poll(tk)
-                    if ok:
-                        with lock:
-                            tickets.remove(tk)
-                            lat.append(l_)
-                            done_t.append(time.perf_counter())
-                        nonlocal_units[0] += r.hyp_iters
-                time.sleep(0.0005)
-
-        nonlocal_units = [0]
-        th = threading.Thread(target=poller)
-        th.start()
-        t0 = time.perf_counter()
-        for a, fa in zip(arrivals, reqs):
-            dt = t0 + a - time.perf_counter()
-            if dt > 0:
-                time.sleep(dt)
-            try:
-                tk = server.submit(fa)
-                with lock:
-                    tickets.append(tk)
-            except B.PilotError as e:
-                if e.status != B.PILOT_EBUSY:
-                    raise
-                rejected += 1
-        with lock:
-            stop[0] = True
-        th.join()
-        span = (max(done_t) - t0) if done_t else 1.0
-        st = server.stats()
+        client = SV.StreamClient(server, g, dsm_dev, sc, net, cam)
+        streams = [SV.StreamState(inputs[s][0], inputs[s][1], arrivals[s], inputs[s][0][0].copy()) for s in range(ns)]
+        st = client.run(streams, duration)
+        st["iters"] = list(iters[:3])
+        st.update({k: v for k, v in server.stats().items() if k in ("rounds", "peak_active", "arena_bytes_peak")})
         server.close()
-        out.append({"streams": streams, "iters": list(iters[:3]), "levels_per_round": lpr,
-                    "offered_fps": len(arrivals) / duration,
-                      "completed_fps": len(lat) / span, "rejected_ebusy": rejected,
-                      "hyp_iter_per_s": nonlocal_units[0] / span,
-                      "p50_ms": float(np.percentile(lat, 50)) if lat else None,
-                      "p99_ms": float(np.percentile(lat, 99)) if lat else None,
-                      "peak_active": st["peak_active"], "rounds": st["rounds"]})
-    served = {"sweep": sweep, "sweep_paper_iterations": sweep_paper, "sweep_levels_per_round": sweep_levels,
-              "hbm_budget_bytes": budget,
-              "max_slots": 64, "storage": "bf16",
-              "arrivals": "30 Hz per stream, exponential inter-arrival (mean 33 ms), 3 s",
-              "frames": "host page-locked BF16 frames, crops 128^2..384^2, 16..144 hypotheses"}
-    return batched, served
+        out["sweep"].append(st)
+        if ns == n_max and iters[0] == 10:
+            out["config5"] = st
+    return out
 
 
 def paper_schedule_form(args, B, S, torch, world, stream):
@@ -523,12 +480,12 @@ def seeding_form(B, S, n_frames: int = 24):
     return out
 
 
-def crop_form(B, S, torch, stream):
+def crop_form(B, S, torch, stream, g=None):
     """The TDOM/DSM reference crop (Supp. "TDOM/DSM Reference Crop") on the serving workload's
     map (4096 x 4096 cells at 0.5 m): device time per crop (corner-ray footprint with 8000
     samples of 0.25 m per ray, homography, warp and geo-anchor lift) for 256^2 and 384^2 crops,
     over 16 seeded pose priors."""
-    g = S.make_global_map(side=4096, seed=31)
+    g = S.make_global_map(side=4096, seed=31) if g is None else g
     dm = B.MapArgs(torch.as_tensor(g.dsm, device="cuda"), torch.as_tensor(g.tdom, device="cuda"), g.x0, g.y0, g.gsd)
     priors = [S.crop_prior(g, k) for k in range(16)]
     out = {"map": "4096 x 4096 cells at 0.5 m (TDOM RGB + DSM)", "ray_samples": 8000, "ray_step_m": 0.25,
@@ -665,6 +622,10 @@ def run_ours(args):
         out, _, _ = crop_form(B, S, torch, torch.cuda.current_stream())
         print(json.dumps({"form": "crop", **out}), flush=True)
         return 0
+    if args.served_only:
+        out = served_streams(B, S, torch, S.make_global_map(side=4096, seed=31))
+        print(json.dumps({"form": "served", **out}), flush=True)
+        return 0
     if args.batched_only:
         out, _ = batched_and_served(args, B, S, torch, world, torch.cuda.current_stream(), served_too=False)
         print(json.dumps({"form": "batched", **out}), flush=True)
@@ -796,14 +757,15 @@ def run_ours(args):
                 "gather_bytes_per_unit": tap_bytes, "units_per_launch": units_per_launch,
                 "avg_launch_ms": avg_launch_ms, "launches": build_n, "concurrent_launches": parts,
                 "achieved_basis": "build-pass units of the timed solves / their device time",
-                "traffic_basis": "ncu dram bytes per unit of a coarse launch x units per launch (None: not "
-                                 "measured for this kernel source)",
+                "traffic_basis": "ncu dram bytes per unit of a finest-level launch (cold cache) x units per "
+                                 "launch (None: not measured for this kernel source)",
                 "hbm_GBps_measured": (load_peaks() or {}).get("hbm_gbs"),
                 "fma_probe_TFLOPs": probe_fma, "gather_random_pixels_GBps": probe_gather}
 
-    batched, served = batched_and_served(args, B, S, torch, world, stream) if not args.no_forms else ({}, {})
+    gmap = S.make_global_map(side=4096, seed=31) if not args.no_forms else None
+    batched, served = batched_and_served(args, B, S, torch, world, stream, gmap=gmap) if not args.no_forms else ({}, {})
     paper = paper_schedule_form(args, B, S, torch, world, stream) if not args.no_forms else {}
-    crop, crop_map, crop_priors = crop_form(B, S, torch, stream) if not args.no_forms else ({}, None, None)
+    crop, crop_map, crop_priors = crop_form(B, S, torch, stream, gmap) if not args.no_forms else ({}, None, None)
     seeding = seeding_form(B, S) if not args.no_forms else {}
     tracking = tracking_form(B, S, crop_map) if not args.no_forms else {}
 
@@ -864,6 +826,11 @@ def run_ours(args):
                     "equal_accuracy_forms": ["f32", "bf16", "f16"],
                     "accuracy_basis": "selected pose within 1e-3 deg / 1 mm of the FP64 oracle on every one of 256 "
                                       "seeds (tests/test_gpu_precision_sweep.py); FP8-E4M3 storage is not (p99 22 mm)"}
+        u32 = batched["uneven32_bf16"]
+        headline["uneven32"] = {"frames": 32, "batched_bf16": u32["value"], "plain_bf16": u32["plain_bf16_same_frames"],
+                                "plain_f32": u32["plain_f32_same_frames"],
+                                "batched_bf16_over_plain_f32": u32["value"] / u32["plain_f32_same_frames"],
+                                "batched_bf16_over_plain_bf16": u32["value"] / u32["plain_bf16_same_frames"]}
         if served.get("config5"):
             headline["served_config5"] = {k: served["config5"].get(k) for k in
                                           ("hyp_iter_per_s", "p50_ms", "p99_ms", "completed_fps", "offered_fps")}

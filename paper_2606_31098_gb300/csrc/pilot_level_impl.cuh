@@ -54,17 +54,18 @@ __device__ __forceinline__ bool grid_sync(unsigned long long* sync, unsigned* er
 }
 
 // Batched form: one persistent (cooperative) launch per level for a whole batch of frames.
-// The level's LM iterations run in lockstep over all jobs (a job = one hypothesis of one
-// frame): in iteration k the CTAs claim the work items (runs of up to tiles_per_item
-// consecutive anchor tiles of one tile of kHypTile jobs of a frame, the hypotheses a plain
-// form's CTA holds) from one counter, and write each tile's FP32 records exactly as
-// build_fused_kernel does (same thread mapping, same sums); after a grid barrier each job's
-// FP64 step runs on one warp (all lanes), on the tile records summed in the plain form's
-// 8-chain FP64 order, and writes the job's next candidate; a second barrier ends the
-// iteration.  A frame's result is therefore bitwise the one its plain solve gives, whatever
-// else is in the batch; the items balance the gathers over all CTAs, and the FP64 steps of
-// all jobs run at once, one per warp.  Tile t of job kHypTile p + h, whose job tile's first
-// item is q, keeps its record at partial[(q tiles_per_item + t) kHypTile + h].
+// The level's LM iterations run in step over all jobs (a job = one hypothesis of one frame),
+// in two halves offset by half an iteration (see the phase loop).  For iteration k of a half,
+// the CTAs claim its work items (runs of up to tiles_per_item consecutive anchor tiles of one
+// tile of kHypTile jobs of a frame, the hypotheses a plain form's CTA holds) from one counter
+// and write each tile's FP32 records exactly as build_fused_kernel does (same thread mapping,
+// same sums); in the next phase, while the other half gathers, each of its jobs' FP64 step
+// runs on one warp (all lanes), on the tile records summed in the plain form's 8-chain FP64
+// order, and writes the job's next candidate.  A frame's result is therefore bitwise the one
+// its plain solve gives, whatever else is in the batch; the items balance the gathers over
+// all CTAs, and the FP64 steps of half the jobs run at once, one per warp, beside the other
+// half's gathers.  Tile t of job kHypTile p + h, whose job tile's first item is q, keeps its
+// record at partial[(q tiles_per_item + t) kHypTile + h].
 template <pilot_dtype DT, int C, bool SCALED, bool CONF>
 __global__ void __launch_bounds__(kBuildThreads, 2)
 level_persistent_kernel(const LevelArgs a) {
@@ -127,94 +128,143 @@ level_persistent_kernel(const LevelArgs a) {
         a.job_meta[job] = (unsigned)hyp | kEval;
     }
     if (!grid_sync(a.sync, a.error, gen, a.barrier_timeout_ns, a.barrier_extra)) return;
-    const unsigned long long round = (unsigned long long)n_items + gridDim.x;   // claims per iteration
-    for (int k = 0; k <= a.k_max; ++k) {
-        // gather: the work items of iteration k, claimed one at a time
-        for (;;) {
-            if (tid == 0) {
-                const long long item = (long long)(atomicAdd(a.sync, 1ull) - (unsigned long long)k * round);
-                s_item = item;
-                if (item < n_items) {
-                    const int i = find(true, item);
-                    const int ipj = fipj(i);
-                    const int local = (int)(item - fitem(i));
-                    const int jt = local / ipj;      // job tile within the frame
-                    s_frame = flist(i);
-                    s_job = fjob(i) + kHypTile * jt;
-                    s_njobs = min(kHypTile, fjob(i + 1) - s_job);
-                    s_first = fitem(i) + jt * ipj;
-                    s_t0 = (local - jt * ipj) * tpi;
-                }
-            }
-            __syncthreads();
-            if (s_item >= n_items) break;
-            const int job = s_job;
-            if (tid < 12 * kHypTile) {
-                const int h = tid / 12;
-                pose[h][tid % 12] = __ldcg(a.pose32 + 12 * (size_t)(job + (h < s_njobs ? h : 0)) + tid % 12);
-            }
-            if (tid < kHypTile) s_meta[tid] = tid < s_njobs ? __ldcg(a.job_meta + job + tid) : 0u;
-            __syncthreads();
-            const FrameDesc* fd = a.frames + s_frame;
-            const int level = a.level >= 0 ? a.level : fd->level;
-            SlotPoses sp;
-            bool any = false;
-#pragma unroll
-            for (int h = 0; h < kHypTile; ++h) {
-                sp.p[h] = pose[h];
-                sp.act[h] = (s_meta[h] & kEval) != 0;
-                any = any || sp.act[h];
-            }
-            if (k <= a.iters[level] && any) {
-                const LevelView v{fd->px, fd->py, fd->pz, fd->weight, fd->valid, fd->qry[level], fd->ref[level],
-                                  fd->qscale[level], fd->rscale[level], fd->conf[level], fd->H[level], fd->W[level],
-                                  fd->fx[level], fd->fy[level], fd->cx[level], fd->cy[level], a.huber};
-                const int n_t = fd->N > 0 ? (fd->N + a.tile - 1) / a.tile : 1;
-                const int t1 = min(s_t0 + tpi, n_t);
-                for (int t = s_t0; t < t1; ++t) {
-                    float acc[kNumSums];
-#pragma unroll
-                    for (int i = 0; i < kNumSums; ++i) acc[i] = 0.f;
-                    const int j0 = t * a.tile;
-                    accumulate_anchors<DT, C, SCALED, CONF, kBuildThreads>(v, sp, j0, min(j0 + a.tile, fd->N), acc);
-                    const float val = cta_reduce_slots<kBuildThreads, GroupShape<DT, C>::APB>(acc, red);
-                    if (tid < kHypTile * kAcc && tid / kAcc < s_njobs)
-                        a.partial[(((size_t)s_first * tpi + t) * kHypTile + tid / kAcc) * kAcc + tid % kAcc] = val;
-                }
-            }
-            __syncthreads();
+    // The jobs are split into two halves at a job-tile boundary near the middle of the items:
+    // A = jobs [0, JA) with items [0, IA), B = the rest.  Each phase gathers one half while
+    // the FP64 steps of the other half (for the iteration it gathered in the previous phase)
+    // run on their warps, so the steps overlap gathers:
+    //   phase 0: gather A(0);  phase 2k+1: gather B(k), step A(k);  phase 2k+2: gather A(k+1),
+    //   step B(k);  ...  the last phase steps B(k_max).  A grid barrier ends every phase.
+    // Each job's records and FP64 step are those of the lockstep schedule, so the results are
+    // unchanged; only the order in which the GPU runs them differs.
+    // The split pays when the gathers of a half outlast an FP64 step and a half's steps
+    // occupy only part of the warps; when the steps dominate (few anchors per hypothesis,
+    // e.g. the paper's 500-anchor schedule) it would put two step latencies in every
+    // iteration, so it is only made for at least kSplitUnits anchor-hypothesis units per
+    // iteration and at most one job per warp.
+    __shared__ int s_IA, s_JA;
+    if (tid == 0) {
+        int IA = n_items, JA = n_jobs;
+        const int target = (n_items + 1) / 2;
+        long long units = 0;
+        for (int i = 0; i < n_fr; ++i) units += (long long)a.frames[flist(i)].N * (fjob(i + 1) - fjob(i));
+        if (target < n_items && units >= kSplitUnits && n_jobs <= n_warps) {
+            const int i = find(true, target);
+            const int ipj = fipj(i);
+            const int jt = (target - fitem(i) + ipj - 1) / ipj;    // round up to a job tile
+            IA = fitem(i) + jt * ipj;
+            JA = min(fjob(i) + jt * kHypTile, fjob(i + 1));
         }
-        if (!grid_sync(a.sync, a.error, gen, a.barrier_timeout_ns, a.barrier_extra)) return;
-        // FP64 steps: job j on global warp j (mod the warp count), all 32 lanes
-        for (int job = blockIdx.x * kWarps + warp; job < n_jobs; job += n_warps) {
-            const int i = find(false, job);
-            const int f = flist(i);
-            const FrameDesc* fd = a.frames + f;
-            const int level = a.level >= 0 ? a.level : fd->level;
-            const int iters = a.iters[level];
-            if (k > iters) continue;
-            const unsigned meta = __ldcg(a.job_meta + job);
-            const int hyp = (int)(meta & ~kEval);
-            const bool evaluated = (meta & kEval) != 0;
-            if (evaluated && lane < kNumSums) {
-                const int n_t = fd->N > 0 ? (fd->N + a.tile - 1) / a.tile : 1;
-                const int jl = job - fjob(i);
-                const int first = fitem(i) + (jl / kHypTile) * fipj(i);
-                const float* src = a.partial + ((size_t)first * tpi * kHypTile + jl % kHypTile) * kAcc + lane;
-                double sum = 0.0;
-                for (int c = 0; c < 8; ++c) {
-                    double part = 0.0;
-                    for (int t = c; t < n_t; t += 8) part += (double)__ldcg(src + (size_t)t * kHypTile * kAcc);
-                    sum += part;
+        s_IA = IA;
+        s_JA = JA;
+    }
+    __syncthreads();
+    const int IA = s_IA, JA = s_JA;
+    // claims made before the current phase: a gathering phase takes one claim per item of its
+    // half plus one unsuccessful claim per CTA
+    unsigned long long base = 0;
+    for (int ph = 0; ph <= 2 * a.k_max + 2; ++ph) {
+        // FP64 steps of the half gathered in the previous phase: job j on global warp j (mod
+        // the warp count), all 32 lanes
+        if (ph >= 1) {
+            const int k = (ph - 1) / 2;
+            const int jlo = (ph & 1) ? 0 : JA, jhi = (ph & 1) ? JA : n_jobs;
+            for (int job = jlo + blockIdx.x * kWarps + warp; job < jhi; job += n_warps) {
+                const int i = find(false, job);
+                const int f = flist(i);
+                const FrameDesc* fd = a.frames + f;
+                const int level = a.level >= 0 ? a.level : fd->level;
+                const int iters = a.iters[level];
+                if (k > iters) continue;
+                const unsigned meta = __ldcg(a.job_meta + job);
+                const int hyp = (int)(meta & ~kEval);
+                const bool evaluated = (meta & kEval) != 0;
+                if (evaluated && lane < kNumSums) {
+                    const int n_t = fd->N > 0 ? (fd->N + a.tile - 1) / a.tile : 1;
+                    const int jl = job - fjob(i);
+                    const int first = fitem(i) + (jl / kHypTile) * fipj(i);
+                    const float* src = a.partial + ((size_t)first * tpi * kHypTile + jl % kHypTile) * kAcc + lane;
+                    double sum = 0.0;
+                    for (int c = 0; c < 8; ++c) {
+                        double part = 0.0;
+                        for (int t = c; t < n_t; t += 8) part += (double)__ldcg(src + (size_t)t * kHypTile * kAcc);
+                        sum += part;
+                    }
+                    E[warp][lane] = sum;
                 }
-                E[warp][lane] = sum;
+                __syncwarp();
+                HypState& st = a.state[hyp];
+                lm_update(st, k == 0 ? kEpiInit : kEpiStep, k < iters, a.damping_mode, fd->prior, E[warp], Wsh[warp],
+                          a.min_valid[f], a.pose32 + 12 * (size_t)job, nullptr, lane);
+                if (lane == 0) a.job_meta[job] = (unsigned)hyp | (st.has_cand ? kEval : 0u);
+                __syncwarp();
             }
-            __syncwarp();
-            HypState& st = a.state[hyp];
-            lm_update(st, k == 0 ? kEpiInit : kEpiStep, k < iters, a.damping_mode, fd->prior, E[warp], Wsh[warp],
-                      a.min_valid[f], a.pose32 + 12 * (size_t)job, nullptr, lane);
-            if (lane == 0) a.job_meta[job] = (unsigned)hyp | (st.has_cand ? kEval : 0u);
-            __syncwarp();
+        }
+        // gathers of one half at iteration k, its work items claimed one at a time
+        if (ph <= 2 * a.k_max + 1) {
+            const int k = ph / 2;
+            const int ilo = (ph & 1) ? IA : 0, ihi = (ph & 1) ? n_items : IA;
+            for (;;) {
+                if (tid == 0) {
+                    long long item = ilo + (long long)(atomicAdd(a.sync, 1ull) - base);
+                    if (item < ilo) {              // cannot happen: the counts above are exact
+                        atomicExch(a.error, 1u);
+                        item = ihi;
+                    }
+                    s_item = item;
+                    if (item < ihi) {
+                        const int i = find(true, item);
+                        const int ipj = fipj(i);
+                        const int local = (int)(item - fitem(i));
+                        const int jt = local / ipj;      // job tile within the frame
+                        s_frame = flist(i);
+                        s_job = fjob(i) + kHypTile * jt;
+                        s_njobs = min(kHypTile, fjob(i + 1) - s_job);
+                        s_first = fitem(i) + jt * ipj;
+                        s_t0 = (local - jt * ipj) * tpi;
+                    }
+                }
+                __syncthreads();
+                if (s_item >= ihi) break;
+                const int job = s_job;
+                if (tid < 12 * kHypTile) {
+                    const int h = tid / 12;
+                    pose[h][tid % 12] = __ldcg(a.pose32 + 12 * (size_t)(job + (h < s_njobs ? h : 0)) + tid % 12);
+                }
+                if (tid < kHypTile) s_meta[tid] = tid < s_njobs ? __ldcg(a.job_meta + job + tid) : 0u;
+                __syncthreads();
+                const FrameDesc* fd = a.frames + s_frame;
+                const int level = a.level >= 0 ? a.level : fd->level;
+                SlotPoses sp;
+                bool any = false;
+#pragma unroll
+                for (int h = 0; h < kHypTile; ++h) {
+                    sp.p[h] = pose[h];
+                    sp.act[h] = (s_meta[h] & kEval) != 0;
+                    any = any || sp.act[h];
+                }
+                if (k <= a.iters[level] && any) {
+                    const LevelView v{fd->px, fd->py, fd->pz, fd->weight, fd->valid, fd->qry[level], fd->ref[level],
+                                      fd->qscale[level], fd->rscale[level], fd->conf[level], fd->H[level],
+                                      fd->W[level], fd->fx[level], fd->fy[level], fd->cx[level], fd->cy[level],
+                                      a.huber};
+                    const int n_t = fd->N > 0 ? (fd->N + a.tile - 1) / a.tile : 1;
+                    const int t1 = min(s_t0 + tpi, n_t);
+                    for (int t = s_t0; t < t1; ++t) {
+                        float acc[kNumSums];
+#pragma unroll
+                        for (int i = 0; i < kNumSums; ++i) acc[i] = 0.f;
+                        const int j0 = t * a.tile;
+                        accumulate_anchors<DT, C, SCALED, CONF, kBuildThreads>(v, sp, j0, min(j0 + a.tile, fd->N),
+                                                                               acc);
+                        const float val = cta_reduce_slots<kBuildThreads, GroupShape<DT, C>::APB>(acc, red);
+                        if (tid < kHypTile * kAcc && tid / kAcc < s_njobs)
+                            a.partial[(((size_t)s_first * tpi + t) * kHypTile + tid / kAcc) * kAcc + tid % kAcc] =
+                                val;
+                    }
+                }
+                __syncthreads();
+            }
+            base += (unsigned long long)(ihi - ilo) + gridDim.x;
         }
         if (!grid_sync(a.sync, a.error, gen, a.barrier_timeout_ns, a.barrier_extra)) return;
     }

@@ -54,7 +54,10 @@ class StreamClient:
         self.map = B.MapArgs(dsm_dev, None, gmap.x0, gmap.y0, gmap.gsd)
         self.ray_step, self.ray_samples, self.win = ray_step, ray_samples, dsm_window
         self.bank16 = [[B.quantize_features(q, B.BF16)[0] for q in pyr] for pyr in network.bank32]
-        self.stream = torch.cuda.current_stream()
+        torch.cuda.synchronize()
+        # frames are prepared on a high-priority stream, so that their small kernels are
+        # dispatched ahead of the server's queued level launches
+        self.stream = torch.cuda.Stream(priority=-1)
 
     def _dsm_window(self, T_prev: np.ndarray, origin):
         """A window of the global DSM for the range prior: win x win cells centred where the
@@ -77,32 +80,48 @@ class StreamClient:
     def prepare(self, sid: int, st: StreamState, t: int):
         """Frame t of stream sid around the stream's current estimate: (FrameArgs, origin,
         keep-alive) or None when the crop fails."""
+        return self.prepare_batch([(sid, st, t)])[0]
+
+    def prepare_batch(self, jobs: list) -> list:
+        """prepare() for several (stream id, state, frame) at once, with one host wait for all
+        the crops' geometry and one before the frames are handed to the server."""
         from . import scenes as S
+        torch = self.torch
         sc, cam = self.sc, self.cam
-        side, n_xy, n_yaw = S.stream_frame_shape(sc, sid, t)
-        prior = st.estimate
-        p = B.crop_params(prior, cam.fx, cam.fy, cam.cx, cam.cy, cam.img_w, cam.img_h, 0.0, self.ray_step,
-                          self.ray_samples, side)
-        crop = B.crop_reference(self.map, p, with_rgb=False, stream=self.stream)
-        geo = crop["geometry"].cpu().numpy()
-        if geo[27] != 1.0:
-            return None
-        ox, oy = float(geo[9]), float(geo[10])
-        T_gt_local = B.pose_reorigin(st.gt[t], ox, oy)
-        b = t % len(self.bank16)
-        refs32 = self.net.descriptors(b, crop["points"], T_gt_local, seed=(sid << 20) + t)
-        refs16 = [B.quantize_features(r, B.BF16)[0] for r in refs32]
-        seeds = B.seed_hypotheses(B.seed_params(prior, grid_values(n_xy, sc.xy_span),
-                                                grid_values(n_yaw, sc.yaw_span_deg), (ox, oy)))
-        dsm, wx0, wy0 = self._dsm_window(prior, (ox, oy))
-        g_cam, rng = st.sensors[t]
-        scal = SimpleNamespace(fx=cam.fx, fy=cam.fy, cx=cam.cx, cy=cam.cy, use_gravity=True, gravity_cam=g_cam,
-                               gravity_world=np.array([0.0, 0.0, -1.0]), w_grav=sc.w_grav, use_range=True,
-                               range_m=rng, w_range=sc.w_range, dsm_x0=wx0 - ox, dsm_y0=wy0 - oy,
-                               dsm_gsd=self.gmap.gsd)
-        arrays = dict(points=crop["points"], point_valid=crop["valid"], point_weight=None, ref_feat=refs16,
-                      qry_feat=self.bank16[b], T_cw=seeds, dsm=dsm)
-        return B.FrameArgs(scal, arrays, is_device=True, dtype=B.BF16), (ox, oy), (crop, refs32)
+        out = []
+        with torch.cuda.stream(self.stream):
+            crops = []
+            for sid, st, t in jobs:
+                side, n_xy, n_yaw = S.stream_frame_shape(sc, sid, t)
+                p = B.crop_params(st.estimate, cam.fx, cam.fy, cam.cx, cam.cy, cam.img_w, cam.img_h, 0.0,
+                                  self.ray_step, self.ray_samples, side)
+                crop = B.crop_reference(self.map, p, with_rgb=False, stream=self.stream)
+                crops.append((crop, (n_xy, n_yaw)))
+            geos = torch.stack([c["geometry"] for c, _ in crops]).cpu().numpy()   # one wait for all
+            for (sid, st, t), (crop, (n_xy, n_yaw)), geo in zip(jobs, crops, geos):
+                if geo[27] != 1.0:
+                    out.append(None)
+                    continue
+                ox, oy = float(geo[9]), float(geo[10])
+                prior = st.estimate
+                T_gt_local = B.pose_reorigin(st.gt[t], ox, oy)
+                b = t % len(self.bank16)
+                refs32 = self.net.descriptors(b, crop["points"], T_gt_local, seed=(sid << 20) + t)
+                refs16 = [B.quantize_features(r, B.BF16, stream=self.stream)[0] for r in refs32]
+                seeds = B.seed_hypotheses(B.seed_params(prior, grid_values(n_xy, sc.xy_span),
+                                                        grid_values(n_yaw, sc.yaw_span_deg), (ox, oy)),
+                                          stream=self.stream)
+                dsm, wx0, wy0 = self._dsm_window(prior, (ox, oy))
+                g_cam, rng = st.sensors[t]
+                scal = SimpleNamespace(fx=cam.fx, fy=cam.fy, cx=cam.cx, cy=cam.cy, use_gravity=True,
+                                       gravity_cam=g_cam, gravity_world=np.array([0.0, 0.0, -1.0]),
+                                       w_grav=sc.w_grav, use_range=True, range_m=rng, w_range=sc.w_range,
+                                       dsm_x0=wx0 - ox, dsm_y0=wy0 - oy, dsm_gsd=self.gmap.gsd)
+                arrays = dict(points=crop["points"], point_valid=crop["valid"], point_weight=None,
+                              ref_feat=refs16, qry_feat=self.bank16[b], T_cw=seeds, dsm=dsm)
+                out.append((B.FrameArgs(scal, arrays, is_device=True, dtype=B.BF16), (ox, oy), (crop, refs32)))
+        self.stream.synchronize()          # the server stages the frames on its own stream
+        return out
 
     def run(self, streams: list, duration_s: float, poll_s: float = 0.0005) -> dict:
         """Serve `streams` for duration_s seconds of arrivals (then drain the frames in the
@@ -114,6 +133,24 @@ class StreamClient:
         while True:
             now = time.perf_counter() - t0
             active = False
+            # the newest arrived frame of every stream with nothing in the server, prepared
+            # together
+            due = []
+            for sid, st in enumerate(streams):
+                if st.in_flight is not None or now > duration_s:
+                    continue
+                k = int(np.searchsorted(st.arrivals, now, side="right")) - 1
+                if st.next_t <= k < len(st.arrivals) and (sid not in pending or pending[sid][0] != k):
+                    due.append((sid, st, k))
+            if due:
+                for (sid, st, k), prep in zip(due, self.prepare_batch(due)):
+                    dropped += k - st.next_t        # frames next_t .. k - 1 (any older prepared one among them)
+                    if prep is None:
+                        crop_failed += 1
+                        st.next_t = k + 1
+                        pending.pop(sid, None)
+                        continue
+                    pending[sid] = (k, prep)
             for sid, st in enumerate(streams):
                 if st.in_flight is not None:
                     active = True
@@ -139,14 +176,8 @@ class StreamClient:
                     active = active or k < len(st.arrivals)
                     continue
                 active = True
-                if sid not in pending or pending[sid][0] != k:
-                    dropped += k - st.next_t
-                    prep = self.prepare(sid, st, k)
-                    if prep is None:
-                        crop_failed += 1
-                        st.next_t = k + 1
-                        continue
-                    pending[sid] = (k, prep)
+                if sid not in pending:
+                    continue
                 k, (fa, origin, keep) = pending[sid]
                 try:
                     tk = self.server.submit(fa)
