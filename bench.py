@@ -375,7 +375,11 @@ def served_streams(B, S, torch, g, counts=(1, 4, 16, 64), duration: float = 4.0,
         streams = [SV.StreamState(inputs[s][0], inputs[s][1], arrivals[s], inputs[s][0][0].copy()) for s in range(ns)]
         st = client.run(streams, duration)
         st["iters"] = list(iters[:3])
-        st.update({k: v for k, v in server.stats().items() if k in ("rounds", "peak_active", "arena_bytes_peak")})
+        ss = server.stats()
+        st.update({k: v for k, v in ss.items() if k in ("rounds", "peak_active", "arena_bytes_peak")})
+        # fraction of the run the server's rounds occupied the device / its worker
+        st["round_device_busy"] = ss["round_device_ms"] / (1e3 * st["span_s"])
+        st["round_wall_busy"] = ss["round_wall_ms"] / (1e3 * st["span_s"])
         server.close()
         out["sweep"].append(st)
         if ns == n_max and iters[0] == 10:
@@ -813,27 +817,28 @@ def run_ours(args):
             OC.crop(om, op)
             cpu["crop_256_ms"] = 1e3 * (time.perf_counter() - t0)
 
+    # kept short and printed last: the headline comparison of the forms, rates rounded
     headline = None
     if batched:
-        c256 = batched["crop256"]
-        headline = {"comparison": "hyp*iter/s on the same 8 seeded 256^2-anchor frames (C=32, 64 hypotheses, 3 levels "
-                                  "x 10 iterations): batched BF16 form vs the plain single-frame FP32 form (the "
-                                  "metric's denominator) and the plain BF16 form",
-                    "plain_f32": c256["plain_f32"], "plain_bf16": c256["plain_bf16"],
-                    "batched_bf16": c256["batched_bf16"],
-                    "batched_bf16_over_plain_f32": c256["batched_bf16"] / c256["plain_f32"],
-                    "batched_bf16_over_plain_bf16": c256["batched_bf16"] / c256["plain_bf16"],
-                    "equal_accuracy_forms": ["f32", "bf16", "f16"],
-                    "accuracy_basis": "selected pose within 1e-3 deg / 1 mm of the FP64 oracle on every one of 256 "
-                                      "seeds (tests/test_gpu_precision_sweep.py); FP8-E4M3 storage is not (p99 22 mm)"}
-        u32 = batched["uneven32_bf16"]
-        headline["uneven32"] = {"frames": 32, "batched_bf16": u32["value"], "plain_bf16": u32["plain_bf16_same_frames"],
-                                "plain_f32": u32["plain_f32_same_frames"],
-                                "batched_bf16_over_plain_f32": u32["value"] / u32["plain_f32_same_frames"],
-                                "batched_bf16_over_plain_bf16": u32["value"] / u32["plain_bf16_same_frames"]}
+        c256, u32 = batched["crop256"], batched["uneven32_bf16"]
+        r = lambda x: int(round(x))
+        headline = {"what": "hyp*iter/s, batched BF16 form vs plain FP32 (the metric's form) and plain BF16, same frames",
+                    "equal_accuracy": "f32, bf16, f16 (selected pose within 1e-3 deg / 1 mm of the FP64 oracle on 256 of "
+                                      "256 seeds); not fp8e4m3",
+                    "crop256_x8": {"plain_f32": r(c256["plain_f32"]), "plain_bf16": r(c256["plain_bf16"]),
+                                   "batched_bf16": r(c256["batched_bf16"]),
+                                   "vs_plain_f32": round(c256["batched_bf16"] / c256["plain_f32"], 3),
+                                   "vs_plain_bf16": round(c256["batched_bf16"] / c256["plain_bf16"], 3)},
+                    "uneven_x32": {"plain_f32": r(u32["plain_f32_same_frames"]),
+                                   "plain_bf16": r(u32["plain_bf16_same_frames"]), "batched_bf16": r(u32["value"]),
+                                   "vs_plain_f32": round(u32["value"] / u32["plain_f32_same_frames"], 3),
+                                   "vs_plain_bf16": round(u32["value"] / u32["plain_bf16_same_frames"], 3)}}
         if served.get("config5"):
-            headline["served_config5"] = {k: served["config5"].get(k) for k in
-                                          ("hyp_iter_per_s", "p50_ms", "p99_ms", "completed_fps", "offered_fps")}
+            c5 = served["config5"]
+            headline["served_64_streams"] = {"hyp_iter_per_s": r(c5["hyp_iter_per_s"]),
+                                             "completed_fps": round(c5["completed_fps"], 1),
+                                             "offered_fps": round(c5["offered_fps"], 1),
+                                             "p50_ms": round(c5["p50_ms"], 1), "p99_ms": round(c5["p99_ms"], 1)}
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -849,13 +854,13 @@ def run_ours(args):
                         "d2h_bytes_per_step": int(d2h), "ms_per_step": e2e_ms / args.steps},
                 "gpu_launches": int(launches),
                 "roofline": roofline,
-                "headline": headline,
                 "precision_forms": precision, "confidence_form": confidence,
                 "batched_form": batched,
                 "served_form": served, "paper_schedule_form": paper, "crop_form": crop,
                 "seeding_ablation": seeding, "tracking_form": tracking,
                 "clocks": clk,
-                "cpu_baseline": cpu}
+                "cpu_baseline": cpu,
+                "headline": headline}
         print(json.dumps(line), flush=True)
     solver.close()
     if world > 1:

@@ -429,9 +429,14 @@ void pilot_align_destroy(pilot_align_handle* h);
  * maps, each given on every level or on none (fixed by the first frame). */
 typedef struct pilot_server pilot_server;
 
+/* Counters since create.  round_device_ms: device time of all rounds (CUDA events around
+ * each round's graph on the server's stream); round_wall_ms: host time from each round's
+ * launch to its completion.  Wall time outside rounds is spent admitting and staging frames
+ * or waiting for work. */
 typedef struct {
     long long rounds, admitted, completed, pending, active, peak_active;
     long long arena_bytes_in_use, arena_bytes_peak;
+    double round_device_ms, round_wall_ms;
 } pilot_serve_stats;
 
 /* cfg: solver options (max_hyps bounds the hypotheses of all admitted frames together);

@@ -118,7 +118,8 @@ def _schedule_dict(sc: pilot_schedule) -> dict:
 
 class pilot_serve_stats(ct.Structure):
     _fields_ = [(n, ct.c_longlong) for n in ("rounds", "admitted", "completed", "pending", "active",
-                                             "peak_active", "arena_bytes_in_use", "arena_bytes_peak")]
+                                             "peak_active", "arena_bytes_in_use", "arena_bytes_peak")] + \
+               [(n, ct.c_double) for n in ("round_device_ms", "round_wall_ms")]
 
 
 def load(path: str = LIB_PATH):

@@ -402,9 +402,19 @@ __device__ __forceinline__ void accumulate_anchors(const LevelView& v, const Slo
                     for (int k = 0; k < NV; ++k) load_vec<DT, VW>(fr + VW * (q + k * LP), rra[a] + k * VW);
                 }
             }
-            float B[HALF][6];
+            // one butterfly step: lane keeps the record of its half and adds the partner's
+            auto combine = [&](float* lo, const float* hi, int half) {
+                const bool upper = (q & half) != 0;
 #pragma unroll
-            for (int t = 0; t < HALF; ++t) {
+                for (int k = 0; k < 6; ++k) {
+                    const float send = upper ? lo[k] : hi[k];
+                    const float keep = upper ? hi[k] : lo[k];
+                    lo[k] = keep + __shfl_xor_sync(gmask, send, half);
+                }
+            };
+            // record pair t: records t and t + HALF (one anchor, two hypotheses) against one
+            // reference read, then the first butterfly round
+            auto pair = [&](int t, float* Bt) {
                 float rrt[CPL];
                 const float* rr = rra[HG > 2 ? t % APB : 0];
                 if constexpr (HG <= 2) {
@@ -418,33 +428,36 @@ __device__ __forceinline__ void accumulate_anchors(const LevelView& v, const Slo
 #pragma unroll
                 for (int u = 0; u < 2; ++u) {
                     const int i = t + u * HALF;
-                    const int vi = __shfl_sync(gmask, (int)vis, src0 + i);
-                    const int oi = __shfl_sync(gmask, off, src0 + i);
+                    // the tap offset carries visibility: -1 when the record is not visible
+                    const int oi = __shfl_sync(gmask, vis ? off : -1, src0 + i);
                     const float axi = __shfl_sync(gmask, ax, src0 + i);
                     const float ayi = __shfl_sync(gmask, ay, src0 + i);
-                    record_partials<DT, C, SCALED>(qry + (vi ? oi : 0), WC, rr, axi, ayi, q, qs, rs, P2[u]);
+                    record_partials<DT, C, SCALED>(qry + (oi >= 0 ? oi : 0), WC, rr, axi, ayi, q, qs, rs, P2[u]);
                 }
-                const bool upper = (q & HALF) != 0;
+                combine(P2[0], P2[1], HALF);
 #pragma unroll
-                for (int k = 0; k < 6; ++k) {
-                    const float send = upper ? P2[0][k] : P2[1][k];
-                    const float keep = upper ? P2[1][k] : P2[0][k];
-                    B[t][k] = keep + __shfl_xor_sync(gmask, send, HALF);
-                }
-            }
-            // 3. remaining butterfly rounds: afterwards B[0] of lane q holds record q's sums
+                for (int k = 0; k < 6; ++k) Bt[k] = P2[0][k];
+            };
+            float B[HALF][6];
+            if constexpr (HALF == 4) {
+                // the pairs in the order 0, 2, 1, 3: the second round combines (0, 2) and
+                // (1, 3) as soon as both exist, so fewer partial records stay live (the same
+                // additions as the round-by-round order)
+                pair(0, B[0]);
+                pair(2, B[2]);
+                combine(B[0], B[2], 2);
+                pair(1, B[1]);
+                pair(3, B[3]);
+                combine(B[1], B[3], 2);
+                combine(B[0], B[1], 1);
+            } else {
 #pragma unroll
-            for (int half = HALF / 2; half >= 1; half >>= 1) {
-                const bool upper = (q & half) != 0;
+                for (int t = 0; t < HALF; ++t) pair(t, B[t]);
+                // remaining butterfly rounds: afterwards B[0] of lane q holds record q's sums
 #pragma unroll
-                for (int t = 0; t < half; ++t) {
+                for (int half = HALF / 2; half >= 1; half >>= 1)
 #pragma unroll
-                    for (int k = 0; k < 6; ++k) {
-                        const float send = upper ? B[t][k] : B[t + half][k];
-                        const float keep = upper ? B[t + half][k] : B[t][k];
-                        B[t][k] = keep + __shfl_xor_sync(gmask, send, half);
-                    }
-                }
+                    for (int t = 0; t < half; ++t) combine(B[t], B[t + half], half);
             }
 #pragma unroll
             for (int k = 0; k < 6; ++k) S[k] = B[0][k];

@@ -177,6 +177,8 @@ struct pilot_server {
     std::unordered_map<uint64_t, std::unique_ptr<Request>> reqs;
     uint64_t next_ticket = 1;
     long long rounds = 0, admitted = 0, completed = 0, peak_active = 0;
+    cudaEvent_t ev_begin = nullptr, ev_end = nullptr;  // bracket each round on the stream
+    double round_device_ms = 0, round_wall_ms = 0;
 };
 
 namespace {
@@ -196,6 +198,8 @@ void release_buffers(pilot_server* s) {
     if (s->desc_host) cudaFreeHost(s->desc_host);
     cudaFree(s->res_dev);
     if (s->res_host) cudaFreeHost(s->res_host);
+    if (s->ev_begin) cudaEventDestroy(s->ev_begin);
+    if (s->ev_end) cudaEventDestroy(s->ev_end);
     if (s->stream) cudaStreamDestroy(s->stream);
 }
 
@@ -485,10 +489,18 @@ void worker_main(pilot_server* s) {
         }
         write_round(s);
         lock.unlock();
-        cudaError_t e = cudaGraphLaunch(s->gexec, s->stream);
+        const double t0 = now_ms();
+        cudaError_t e = cudaEventRecord(s->ev_begin, s->stream);
+        if (e == cudaSuccess) e = cudaGraphLaunch(s->gexec, s->stream);
+        if (e == cudaSuccess) e = cudaEventRecord(s->ev_end, s->stream);
         if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+        float dev_ms = 0.f;
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&dev_ms, s->ev_begin, s->ev_end);
+        const double t1 = now_ms();
         lock.lock();
         ++s->rounds;
+        s->round_device_ms += dev_ms;
+        s->round_wall_ms += t1 - t0;
         const unsigned* barrier_error = reinterpret_cast<const unsigned*>(
             s->res_host + ResultLayout::make(s->cfg.max_hyps).bytes + sizeof(int) * (size_t)s->max_slots);
         if (e != cudaSuccess) {
@@ -552,6 +564,8 @@ pilot_status pilot_serve_create(const pilot_align_config* cfg_in, size_t hbm_bud
     if ((e = cudaMalloc((void**)&s->res_dev, s->res_bytes)) != cudaSuccess) return bad("results");
     if ((e = cudaMallocHost((void**)&s->res_host, s->res_bytes)) != cudaSuccess) return bad("result staging");
     if ((e = cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking)) != cudaSuccess) return bad("stream");
+    if ((e = cudaEventCreate(&s->ev_begin)) != cudaSuccess) return bad("round events");
+    if ((e = cudaEventCreate(&s->ev_end)) != cudaSuccess) return bad("round events");
     s->arena_alloc.reset(hbm_budget);
     s->hyp_alloc.reset(H);
     for (int i = max_slots - 1; i >= 0; --i) s->free_slots.push_back(i);
@@ -664,6 +678,8 @@ pilot_status pilot_serve_get_stats(pilot_server* s, pilot_serve_stats* out) {
     out->peak_active = s->peak_active;
     out->arena_bytes_in_use = (long long)s->arena_alloc.in_use();
     out->arena_bytes_peak = (long long)s->arena_alloc.peak();
+    out->round_device_ms = s->round_device_ms;
+    out->round_wall_ms = s->round_wall_ms;
     return PILOT_OK;
 }
 

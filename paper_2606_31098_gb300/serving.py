@@ -128,6 +128,7 @@ class StreamClient:
         server); returns the statistics of the completed frames."""
         t0 = time.perf_counter()
         lat, srv_lat, units, dropped, crop_failed, rejected = [], [], 0, 0, 0, 0
+        prep_s = 0.0                          # host time spent preparing frames
         errs = []
         pending = {}                          # sid -> prepared frame waiting for admission
         while True:
@@ -143,7 +144,10 @@ class StreamClient:
                 if st.next_t <= k < len(st.arrivals) and (sid not in pending or pending[sid][0] != k):
                     due.append((sid, st, k))
             if due:
-                for (sid, st, k), prep in zip(due, self.prepare_batch(due)):
+                tp = time.perf_counter()
+                prepared = self.prepare_batch(due)
+                prep_s += time.perf_counter() - tp
+                for (sid, st, k), prep in zip(due, prepared):
                     dropped += k - st.next_t        # frames next_t .. k - 1 (any older prepared one among them)
                     if prep is None:
                         crop_failed += 1
@@ -196,9 +200,10 @@ class StreamClient:
         n_done = len(lat)
         offered = sum(int(np.searchsorted(st.arrivals, duration_s, side="right")) for st in streams)
         pct = lambda a, q: float(np.percentile(a, q)) if a else None
-        return {"streams": len(streams), "duration_s": duration_s, "offered_frames": offered,
+        return {"streams": len(streams), "duration_s": duration_s, "span_s": span, "offered_frames": offered,
                 "completed_frames": n_done, "dropped_frames": dropped, "crop_failed": crop_failed,
                 "ebusy_retries": rejected, "offered_fps": offered / duration_s, "completed_fps": n_done / span,
                 "hyp_iter_per_s": units / span, "p50_ms": pct(lat, 50), "p99_ms": pct(lat, 99),
                 "server_p50_ms": pct(srv_lat, 50), "server_p99_ms": pct(srv_lat, 99),
+                "client_prepare_busy": prep_s / span,
                 "median_error_m": float(np.median(errs)) if errs else None}
