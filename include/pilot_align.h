@@ -470,6 +470,15 @@ pilot_status pilot_serve_wait(pilot_server* s, uint64_t ticket, pilot_result* re
  * or for n outside [0, 4]. */
 pilot_status pilot_serve_set_levels_per_round(pilot_server* s, int levels);
 
+/* SMs' worth of CTA slots the rounds' persistent launches leave unused (0 by default: every
+ * slot).  A round holds the slots it takes for its whole duration, so work the clients enqueue
+ * on other streams of the device (crops, feature extraction, seeding) waits for the round to
+ * end unless some slots are left free; with n > 0 it runs beside the rounds, at the price of
+ * about n / SM count of the rounds' throughput.  Outputs are the same bitwise (the work is
+ * claimed dynamically; the reduction order does not depend on the grid).  Only before the
+ * first pilot_serve_submit; EINVAL otherwise or for n outside [0, SM count). */
+pilot_status pilot_serve_set_reserved_sms(pilot_server* s, int n_sms);
+
 pilot_status pilot_serve_get_stats(pilot_server* s, pilot_serve_stats* out);
 
 /* Stops the worker after its current round and releases everything; tickets not yet

@@ -92,6 +92,7 @@ SIGNATURES = {
                                     ct.POINTER(ct.c_double)]),
     "pilot_serve_wait": (ct.c_int, [_vp, ct.c_uint64, ct.POINTER(pilot_result), ct.POINTER(ct.c_double), ct.c_int]),
     "pilot_serve_set_levels_per_round": (ct.c_int, [_vp, ct.c_int]),
+    "pilot_serve_set_reserved_sms": (ct.c_int, [_vp, ct.c_int]),
     "pilot_serve_get_stats": (ct.c_int, [_vp, _vp]),
     "pilot_serve_destroy": (None, [_vp]),
 }
@@ -607,6 +608,11 @@ class Server:
     def set_levels_per_round(self, levels: int):
         """pilot_serve_set_levels_per_round (before the first submit; 0 = chosen per frame by size)."""
         check(load().pilot_serve_set_levels_per_round(self.h, int(levels)))
+
+    def set_reserved_sms(self, n_sms: int):
+        """pilot_serve_set_reserved_sms (before the first submit): CTA slots of n_sms SMs left
+        free of the rounds, for client work on other streams."""
+        check(load().pilot_serve_set_reserved_sms(self.h, int(n_sms)))
 
     def submit(self, fa: FrameArgs) -> int:
         """Queue a frame; returns its ticket (raises PilotError, status PILOT_EBUSY, when the

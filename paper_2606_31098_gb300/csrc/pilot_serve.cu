@@ -166,6 +166,7 @@ struct pilot_server {
     int C = 0, L = 0;
     int variant = 0;           // kVariantScaled | kVariantConf, shared by every served frame
     int levels_per_round = 1;  // pyramid levels each admitted frame advances per round; 0: by size
+    int reserved_sms = 0;      // SMs' worth of CTA slots the round's persistent launch leaves free
     std::thread worker;
     std::mutex mu;
     std::condition_variable cv_work, cv_done;
@@ -257,7 +258,10 @@ cudaError_t capture_round(pilot_server* s) {
     cudaError_t e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, s->device);
     if (e == cudaSuccess) e = level_occupancy_query(s->dt, s->C, s->variant, &per_sm);
     if (e != cudaSuccess) return e;
-    s->grid = sms * (per_sm > 0 ? per_sm : 1);
+    // the round's persistent launch takes every CTA slot but those of reserved_sms SMs, so
+    // that the clients' work on other streams (crops, feature extraction, seeding) runs
+    // beside a round instead of waiting for it; the results do not depend on the grid
+    s->grid = std::max(1, sms - s->reserved_sms) * (per_sm > 0 ? per_sm : 1);
     const BatchHeader* hdr = reinterpret_cast<const BatchHeader*>(s->desc_dev);
     const FrameDesc* frames = reinterpret_cast<const FrameDesc*>(s->desc_dev + s->off_frames);
     if ((e = cudaStreamBeginCapture(s->stream, cudaStreamCaptureModeThreadLocal)) != cudaSuccess) return e;
@@ -664,6 +668,18 @@ pilot_status pilot_serve_set_levels_per_round(pilot_server* s, int levels) {
     std::unique_lock<std::mutex> lock(s->mu);
     if (s->key_set) return sfail(PILOT_EINVAL, "set levels_per_round before the first frame is submitted");
     s->levels_per_round = levels;
+    return PILOT_OK;
+}
+
+pilot_status pilot_serve_set_reserved_sms(pilot_server* s, int n_sms) {
+    if (!s) return sfail(PILOT_EINVAL, "server is NULL");
+    int sms = 0;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, s->device) != cudaSuccess)
+        return sfail(PILOT_ECUDA, "SM count query failed");
+    if (n_sms < 0 || n_sms >= sms) return sfail(PILOT_EINVAL, "reserved SMs must be in [0, SM count)");
+    std::unique_lock<std::mutex> lock(s->mu);
+    if (s->key_set) return sfail(PILOT_EINVAL, "set reserved SMs before the first frame is submitted");
+    s->reserved_sms = n_sms;
     return PILOT_OK;
 }
 

@@ -879,13 +879,17 @@ class StreamNetwork:
     descriptors of every anchor at every level -- the bank pyramid read bilinearly at the
     anchor's ground-truth projection (pixel i covers [i, i + 1), read at array coordinate
     pixel - 1/2) plus N(0, ref_noise) noise where the query sees it (1-pixel margin), a random
-    unit vector elsewhere -- drawn from a device generator seeded per frame."""
+    unit vector elsewhere.  The noise and the unit vectors are rows of two fixed device banks
+    read from an offset drawn per frame and level from the frame's seed, so a frame's
+    descriptors are the same whether it is described alone or with others."""
+
+    BANK_ROWS = 1 << 18              # at least the largest crop (384^2 anchors) + offsets
 
     def __init__(self, sc: StreamConfig, seed: int, device: str = "cuda"):
         import torch
         self.torch, self.sc, self.device = torch, sc, device
         cfg = SceneConfig(levels=sc.levels, channels=sc.channels)
-        ss = np.random.SeedSequence(seed).spawn(sc.query_bank * len(sc.levels))
+        ss = np.random.SeedSequence(seed).spawn(sc.query_bank * len(sc.levels) + 1)
         self.bank32, self.bank_nchw = [], []
         for b in range(sc.query_bank):
             lv, lc = [], []
@@ -896,32 +900,73 @@ class StreamNetwork:
                 lc.append(t.permute(2, 0, 1).unsqueeze(0).contiguous())
             self.bank32.append(lv)
             self.bank_nchw.append(lc)
+        g = torch.Generator(device=device)
+        g.manual_seed(int(ss[-1].generate_state(1)[0]))
+        self.noise = torch.randn((self.BANK_ROWS, sc.channels), generator=g, device=device)
+        u = torch.randn((self.BANK_ROWS, sc.channels), generator=g, device=device)
+        self.unit = u / u.norm(dim=1, keepdim=True)
+
+    def _offsets(self, seed: int, n: int) -> np.ndarray:
+        """Per level the (noise, unit) bank rows where a frame of n anchors starts."""
+        r = np.random.default_rng(int(seed) & 0x7FFFFFFFFFFFFFFF)
+        return r.integers(0, self.BANK_ROWS - n + 1, size=(len(self.sc.levels), 2))
 
     def descriptors(self, b: int, points, T_local: np.ndarray, seed: int) -> list:
         """Per level (N, C) FP32 device reference descriptors of the anchors `points` (3, N)
         (device, crop-local) under the crop-local ground truth T_local, with pyramid b."""
+        return self.descriptors_batch([(b, points, T_local, seed)])[0]
+
+    def descriptors_batch(self, items: list) -> list:
+        """descriptors() for several (b, points, T_local, seed) at once: the frames of one
+        pyramid are concatenated and described by one sequence of device operations per
+        level; the results equal descriptors() frame by frame, bitwise (every operation is
+        per anchor).  Returns, per item, its per-level (N, C) tensors (views of one tensor per
+        pyramid and level)."""
         torch = self.torch
         sc = self.sc
-        g = torch.Generator(device=self.device)
-        g.manual_seed(int(seed) & 0x7FFFFFFFFFFFFFFF)
-        T = torch.as_tensor(np.asarray(T_local, np.float64).reshape(3, 4), dtype=torch.float64, device=self.device)
-        p = T[:, :3] @ points.double() + T[:, 3:]
-        x, y, z = p[0], p[1], p[2]
         H0, W0 = sc.levels[0]
-        out = []
-        for l, (H, W) in enumerate(sc.levels):
-            s = 2.0 ** -l
-            zz = torch.where(z > 0.1, z, torch.ones_like(z))
-            u = sc.f0 * s * x / zz + W0 / 2.0 * s
-            v = sc.f0 * s * y / zz + H0 / 2.0 * s
-            seen = (z > 0.1) & (u - 0.5 >= 1.0) & (u - 0.5 <= W - 2.0) & (v - 0.5 >= 1.0) & (v - 0.5 <= H - 2.0)
-            gx = (2.0 * (u - 0.5) / (W - 1) - 1.0).float()
-            gy = (2.0 * (v - 0.5) / (H - 1) - 1.0).float()
-            grid = torch.stack([gx, gy], dim=-1).view(1, 1, -1, 2)
-            f = torch.nn.functional.grid_sample(self.bank_nchw[b][l], grid, mode="bilinear", align_corners=True)
-            f = f.view(sc.channels, -1).t()
-            f = f + sc.ref_noise * torch.randn(f.shape, generator=g, device=self.device)
-            rnd = torch.randn(f.shape, generator=g, device=self.device)
-            rnd = rnd / rnd.norm(dim=1, keepdim=True)
-            out.append(torch.where(seen[:, None], f, rnd).contiguous())
+        out = [None] * len(items)
+        for b in sorted({it[0] for it in items}):
+            idx = [i for i, it in enumerate(items) if it[0] == b]
+            counts = [int(items[i][1].shape[1]) for i in idx]
+            n_all = sum(counts)
+            P = torch.cat([items[i][1] for i in idx], dim=1).double()
+            # per-frame pose rows and bank offsets in pinned host blocks, copied without waiting
+            # for the stream (a pageable copy would wait for the server's running round)
+            L = len(sc.levels)
+            hT = torch.empty((len(idx), 12), dtype=torch.float64, pin_memory=True)
+            hO = torch.empty((len(idx), 2 * L), dtype=torch.int64, pin_memory=True)
+            hN = torch.empty(len(idx), dtype=torch.int64, pin_memory=True)
+            start = 0
+            for k, i in enumerate(idx):
+                hT[k] = torch.from_numpy(np.asarray(items[i][2], np.float64).ravel())
+                hO[k] = torch.from_numpy((self._offsets(items[i][3], counts[k]) - start).ravel())
+                hN[k] = counts[k]
+                start += counts[k]
+            fi = torch.repeat_interleave(torch.arange(len(idx), device=self.device),
+                                         hN.to(self.device, non_blocking=True), output_size=n_all)
+            T = hT.to(self.device, non_blocking=True)[fi]          # (n_all, 12): the anchor's frame pose
+            O = hO.to(self.device, non_blocking=True)[fi]          # (n_all, 2L): its bank row shifts
+            x, y, z = (T[:, 4 * r] * P[0] + T[:, 4 * r + 1] * P[1] + T[:, 4 * r + 2] * P[2] + T[:, 4 * r + 3]
+                       for r in range(3))
+            pos = torch.arange(n_all, device=self.device)
+            per_level = []
+            for l, (H, W) in enumerate(sc.levels):
+                s = 2.0 ** -l
+                zz = torch.where(z > 0.1, z, torch.ones_like(z))
+                u = sc.f0 * s * x / zz + W0 / 2.0 * s
+                v = sc.f0 * s * y / zz + H0 / 2.0 * s
+                seen = (z > 0.1) & (u - 0.5 >= 1.0) & (u - 0.5 <= W - 2.0) & (v - 0.5 >= 1.0) & (v - 0.5 <= H - 2.0)
+                gx = (2.0 * (u - 0.5) / (W - 1) - 1.0).float()
+                gy = (2.0 * (v - 0.5) / (H - 1) - 1.0).float()
+                grid = torch.stack([gx, gy], dim=-1).view(1, 1, -1, 2)
+                f = torch.nn.functional.grid_sample(self.bank_nchw[b][l], grid, mode="bilinear", align_corners=True)
+                f = f.view(sc.channels, -1).t()
+                rn = pos + O[:, 2 * l]
+                ru = pos + O[:, 2 * l + 1]
+                f = f + sc.ref_noise * self.noise[rn]
+                per_level.append(torch.where(seen[:, None], f, self.unit[ru]).contiguous())
+            parts = [torch.split(t, counts) for t in per_level]
+            for k, i in enumerate(idx):
+                out[i] = [parts[l][k] for l in range(L)]
         return out

@@ -7,7 +7,10 @@ the frame's features from the network (`StreamNetwork`, the feature extractor's 
 stores them as BF16 (pilot_quantize_features), writes the hypothesis grid around the
 previous estimate (pilot_seed_hypotheses), and submits the frame; the server admits it when
 a slot, hypothesis room and arena memory are free and runs it with whatever else it is
-serving.  A stream has at most one frame in the server: when its result arrives, the
+serving.  The frames due at one time are prepared together (one network pass per query
+pyramid for all of them) on a high-priority stream; a server that leaves a few SMs outside
+its rounds (pilot_serve_set_reserved_sms) lets this work run beside a round instead of after
+it, as the paper's map-preparation and localisation threads run side by side.  A stream has at most one frame in the server: when its result arrives, the
 client takes the stream's newest arrived frame and drops the ones that arrived meanwhile
 (a tracker keeps the latest image), so latency stays bounded under overload and the
 completed rate is the sustainable one.  This module only orders the library calls and
@@ -98,15 +101,23 @@ class StreamClient:
                 crop = B.crop_reference(self.map, p, with_rgb=False, stream=self.stream)
                 crops.append((crop, (n_xy, n_yaw)))
             geos = torch.stack([c["geometry"] for c, _ in crops]).cpu().numpy()   # one wait for all
-            for (sid, st, t), (crop, (n_xy, n_yaw)), geo in zip(jobs, crops, geos):
-                if geo[27] != 1.0:
+            # the frames whose crop succeeded, described together by the network
+            keep = [k for k, geo in enumerate(geos) if geo[27] == 1.0]
+            items = []
+            for k in keep:
+                sid, st, t = jobs[k]
+                ox, oy = float(geos[k][9]), float(geos[k][10])
+                items.append((t % len(self.bank16), crops[k][0]["points"], B.pose_reorigin(st.gt[t], ox, oy),
+                              (sid << 20) + t))
+            described = dict(zip(keep, self.net.descriptors_batch(items)))
+            for k, ((sid, st, t), (crop, (n_xy, n_yaw)), geo) in enumerate(zip(jobs, crops, geos)):
+                if k not in described:
                     out.append(None)
                     continue
                 ox, oy = float(geo[9]), float(geo[10])
                 prior = st.estimate
-                T_gt_local = B.pose_reorigin(st.gt[t], ox, oy)
                 b = t % len(self.bank16)
-                refs32 = self.net.descriptors(b, crop["points"], T_gt_local, seed=(sid << 20) + t)
+                refs32 = described[k]
                 refs16 = [B.quantize_features(r, B.BF16, stream=self.stream)[0] for r in refs32]
                 seeds = B.seed_hypotheses(B.seed_params(prior, grid_values(n_xy, sc.xy_span),
                                                         grid_values(n_yaw, sc.yaw_span_deg), (ox, oy)),

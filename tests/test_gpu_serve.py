@@ -69,6 +69,28 @@ def test_several_levels_per_round_equal_plain_solves(torch, levels):
     server.close()
 
 
+@pytest.mark.parametrize("reserved", [8, 100])
+def test_reserved_sms_leave_results_unchanged(torch, reserved):
+    """Rounds that leave CTA slots free for client work (a smaller persistent grid) give the
+    plain solves' outputs bitwise, with the two-half schedule (the 256^2 frame with 130
+    hypotheses is above its 2^23-unit threshold at the coarse level) and without."""
+    frames = uneven_frames(sides=(40, 256, 30), hyps=(9, 130, 5), base=1170)
+    fas = args_for(frames)
+    opts = B.Options(iters=(3, 4, 2, 0), keep_top_k=(0, 3, 4, 0))
+    plain = [B.Solver(opts).solve(fa) for fa in fas]
+    server = B.Server(opts, BUDGET, max_slots=4)
+    with pytest.raises(B.PilotError, match="reserved SMs"):
+        server.set_reserved_sms(-1)
+    server.set_reserved_sms(reserved)
+    tickets = [server.submit(fa) for fa in fas]
+    for i, t in enumerate(tickets):
+        res, _ = server.wait(t)
+        assert_same(res, plain[i], what=f"frame {i}, {reserved} SMs reserved")
+    with pytest.raises(B.PilotError, match="before the first frame"):
+        server.set_reserved_sms(0)
+    server.close()
+
+
 def test_result_alone_equals_result_in_the_mix(torch):
     frames = uneven_frames(sides=(48, 66, 35), hyps=(5, 3, 6), base=1200)
     fas = args_for(frames, B.BF16)
@@ -172,3 +194,27 @@ def test_served_stream_frames_equal_their_alone_solve(torch):
         np.testing.assert_array_equal(r.status, alone.status)
         assert r.best == alone.best and r.best >= 0
     solver.close()
+
+
+def test_stream_descriptors_batched_equal_one_by_one(torch):
+    """The network stand-in describes the frames prepared together in one pass per pyramid;
+    each frame's descriptors equal its own one-frame pass bitwise."""
+    sc = S.StreamConfig(n_frames=4)
+    net = S.StreamNetwork(sc, 7)
+    gen = torch.Generator(device="cuda")
+    gen.manual_seed(3)
+    items = []
+    for k, n in enumerate((500, 1300, 64, 900)):
+        pts = torch.rand((3, n), generator=gen, device="cuda") * 200.0 - 100.0
+        pts[2] = pts[2] * 0.1
+        T = np.eye(3, 4)
+        T[:, 3] = (5.0 * k, -3.0, 250.0)
+        items.append((k % 2, pts, T.ravel(), 1000 + k))
+    both = net.descriptors_batch(items)
+    for (b, pts, T, seed), got in zip(items, both):
+        one = net.descriptors(b, pts, T, seed)
+        assert len(one) == len(got) == len(sc.levels)
+        for a, c in zip(one, got):
+            assert a.shape == (pts.shape[1], sc.channels)
+            assert torch.equal(a, c)
+
