@@ -101,7 +101,10 @@ typedef struct {
 /* One query frame.  All pointers are owned by the caller and are either all device
  * pointers (is_device = 1) or all host pointers (is_device = 0; the solver copies them to
  * its workspace).  Every coordinate is in one local metric frame (e.g. centred on the
- * crop); x east, y north, z up; gravity points along -z in the world. */
+ * crop); x east, y north, z up; gravity points along -z in the world.  Feature pointers
+ * (ref_feat, qry_feat) are 32-byte aligned for a device frame (the maps are read with loads
+ * of up to 32 bytes) and 16-byte aligned for a host frame; scale pointers 16-byte aligned;
+ * EINVAL otherwise. */
 typedef struct {
     int is_device;
     int N;                          /* anchors (geo-anchors P_j, Supp. geo-anchor lift) */
@@ -332,10 +335,13 @@ pilot_status pilot_probe_gather(const void* map, int H, int W, int C, pilot_dtyp
  * the same grid (ceil(N / tile) anchor tiles x tiles of the build pass' number of poses per
  * CTA, 256 threads, its lane layout): every (anchor, pose) projects the anchor (Eq. 1, level
  * intrinsics fx, fy, cx, cy in pixels of this map, corner convention) and reads its 4 taps,
- * and every anchor's reference row is read once for the CTA's poses, 16-byte loads by lane
- * groups as the build pass issues them, so the cache reuse between neighbouring anchors is
- * the frame's own.  Two batches of anchors are in flight per step.  DEVICE pointers: points 3 x N FP32 SoA; map H x W x C NHWC and ref N x C in
- * `dtype` (16-byte aligned; C x element size a power of two from 16 to 256 bytes); poses32
+ * and every anchor's reference row is read once for the CTA's poses, with the build pass'
+ * loads by lane groups for maps without per-channel scales (32 bytes per lane for FP32 and
+ * 16-bit taps of 32 bytes or more, 16 otherwise),
+ * so the cache reuse between neighbouring anchors is the frame's own.  Two batches of anchors
+ * are in flight per step.  DEVICE pointers: points 3 x N FP32 SoA; map H x W x C NHWC and ref
+ * N x C in `dtype` (aligned to that load width; C x element size a power of two from 16 to
+ * 256 bytes); poses32
  * M x 12 FP32 [R | t] world -> camera.  Times one launch after a warm-up one on `stream`
  * (synchronous) and returns the (anchor, pose) units per second in *units_per_s. */
 pilot_status pilot_probe_gather_frame(const float* points, int N, const void* map, const void* ref, int H, int W,

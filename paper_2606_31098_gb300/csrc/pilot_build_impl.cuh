@@ -1,5 +1,5 @@
-// Build pass: for one level, every (anchor tile, hypothesis pair) evaluates the photo
-// term of the objective and its normal equations at the two hypotheses' candidate poses.
+// Build pass: for one level, every (anchor tile, tile of hypotheses) evaluates the photo
+// term of the objective and its normal equations at the hypotheses' candidate poses.
 //
 //   Eq. 1  r_j = f^q(pi(K_l, T, P_j)) - f^r(p_j)   (bilinear read of C channels)
 //   Eq. 2  cost += rho(w_j ||r_j||^2)              (Huber on the squared norm)
@@ -12,9 +12,10 @@
 // summed over channels, then H_j = w A^T M A and g_j = w A^T b.
 //
 // Thread mapping.  A CTA holds kHypTile (HT) hypotheses over one anchor tile.  A group of
-// LP consecutive lanes reads one tap with one 16-byte load per lane (LP = C x element size
-// / 16, at most 8: 8 lanes for FP32 at C = 32, 4 for BF16, 2 for FP8), i.e. one L1 wavefront
-// per record and tap, where a record is one (anchor, hypothesis) pair.  A group works on LP
+// LP consecutive lanes reads one tap with one load per lane, 32 bytes for FP32 and 16-bit
+// maps and 16 bytes for FP8 and for maps with per-channel scales (LP = C x element size /
+// load width, at most 8: 4 lanes for FP32 at C = 32, 2 for BF16, 2 for FP8), i.e. one L1
+// wavefront per record and tap, where a record is one (anchor, hypothesis) pair.  A group works on LP
 // records at a time: APB anchors under HG = min(HT, LP) hypotheses (APB HG = LP); with
 // LP < HT, HT / HG neighbouring groups take the same anchors under the other hypotheses.
 // Each lane projects one record (lane q of the group: anchor q mod APB under the group's
@@ -42,24 +43,36 @@
 namespace pilot {
 
 template <pilot_dtype DT> struct Storage;
-template <> struct Storage<PILOT_F32> { using T = float; static constexpr int VEC = 4; };
-template <> struct Storage<PILOT_BF16> { using T = uint16_t; static constexpr int VEC = 8; };
-template <> struct Storage<PILOT_F16> { using T = uint16_t; static constexpr int VEC = 8; };
+template <> struct Storage<PILOT_F32> { using T = float; static constexpr int VEC = 8; };   // 32-byte loads
+template <> struct Storage<PILOT_BF16> { using T = uint16_t; static constexpr int VEC = 16; };  // 32-byte loads
+template <> struct Storage<PILOT_F16> { using T = uint16_t; static constexpr int VEC = 16; };
 template <> struct Storage<PILOT_FP8E4M3> { using T = uint8_t; static constexpr int VEC = 16; };
 
-// Load W (4, 8 or 16) consecutive channels at p and widen them to FP32 (one 4-, 8- or
-// 16-byte load).
+// Load W (4, 8 or 16) consecutive channels at p and widen them to FP32 (one load of W
+// elements: 4 to 16 bytes for the narrow types, 16 or 32 bytes for FP32).
 template <pilot_dtype DT, int W>
 __device__ __forceinline__ void load_vec(const typename Storage<DT>::T* p, float* out) {
     static_assert(W == 4 || W == 8 || W == 16, "vector width");
     if constexpr (DT == PILOT_F32) {
-        static_assert(W == 4, "FP32 vectors are 4 wide");
-        const float4 v = __ldg(reinterpret_cast<const float4*>(p));
-        out[0] = v.x; out[1] = v.y; out[2] = v.z; out[3] = v.w;
-    } else if constexpr (DT == PILOT_BF16 || DT == PILOT_F16) {
-        static_assert(W <= 8, "16-bit vectors are at most 8 wide");
-        uint32_t w[W / 2];
+        static_assert(W <= 8, "FP32 vectors are at most 8 wide");
         if constexpr (W == 8) {
+            // one 256-bit load (32-byte aligned: device feature pointers are validated for it)
+            asm("ld.global.nc.v8.f32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+                : "=f"(out[0]), "=f"(out[1]), "=f"(out[2]), "=f"(out[3]), "=f"(out[4]), "=f"(out[5]),
+                  "=f"(out[6]), "=f"(out[7])
+                : "l"(p));
+        } else {
+            const float4 v = __ldg(reinterpret_cast<const float4*>(p));
+            out[0] = v.x; out[1] = v.y; out[2] = v.z; out[3] = v.w;
+        }
+    } else if constexpr (DT == PILOT_BF16 || DT == PILOT_F16) {
+        uint32_t w[W / 2];
+        if constexpr (W == 16) {
+            // one 256-bit load (32-byte aligned: device feature pointers are validated for it)
+            asm("ld.global.nc.v8.u32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+                : "=r"(w[0]), "=r"(w[1]), "=r"(w[2]), "=r"(w[3]), "=r"(w[4]), "=r"(w[5]), "=r"(w[6]), "=r"(w[7])
+                : "l"(p));
+        } else if constexpr (W == 8) {
             const uint4 r = __ldg(reinterpret_cast<const uint4*>(p));
             w[0] = r.x; w[1] = r.y; w[2] = r.z; w[3] = r.w;
         } else {
@@ -197,9 +210,10 @@ __device__ __forceinline__ float hsum(f2 v) {
 // Lane layout of the build pass for C channels stored as DT (see the top of the file): LP
 // lanes per tap = records per group batch, HG hypotheses per group, NS = kHypTile / HG
 // groups over the same anchors, APB anchors per group batch.  The slot of lane l is
-// (l / APB) mod kHypTile.
-template <pilot_dtype DT, int C> struct GroupShape {
-    static constexpr int VEC = Storage<DT>::VEC;              // channels per 16-byte vector
+// (l / APB) mod kHypTile.  Maps with per-channel scales keep 16-byte loads: the wider lane
+// share of channels would hold twice the scale registers and spill.
+template <pilot_dtype DT, int C, bool SCALED> struct GroupShape {
+    static constexpr int VEC = SCALED ? 16 / (int)sizeof(typename Storage<DT>::T) : Storage<DT>::VEC;  // per load
     static constexpr int VW = (C < VEC) ? C : VEC;            // channels per vector load
     static constexpr int LP = (C / VW < 8) ? C / VW : 8;      // lanes per tap
     static constexpr int HG = LP < kHypTile ? LP : kHypTile;  // hypotheses per group
@@ -244,7 +258,7 @@ template <pilot_dtype DT, int C, bool SCALED>
 __device__ __forceinline__ void record_partials(const typename Storage<DT>::T* t00, int WC, const float* rr,
                                                 float ax, float ay, int q, const float* qs, const float* rs,
                                                 float* p) {
-    using G = GroupShape<DT, C>;
+    using G = GroupShape<DT, C, SCALED>;
     constexpr int VW = G::VW, LP = G::LP, NV = G::NV;
     const typename Storage<DT>::T* t10 = t00 + WC;
     const f2 ax2 = pk(ax, ax), ay2 = pk(ay, ay), z2 = pk(0.f, 0.f);
@@ -281,7 +295,7 @@ template <pilot_dtype DT, int C, bool SCALED, bool CONF, int NTHREADS>
 __device__ __forceinline__ void accumulate_anchors(const LevelView& v, const SlotPoses& sp, int j_begin, int j_end,
                                                    float* acc) {
     using Elem = typename Storage<DT>::T;
-    using G = GroupShape<DT, C>;
+    using G = GroupShape<DT, C, SCALED>;
     constexpr int VW = G::VW, LP = G::LP, HG = G::HG, NS = G::NS, APB = G::APB, NV = G::NV;
     constexpr int CPL = C / LP;                      // channels per lane
     constexpr int ASTEP = NTHREADS / (LP * NS) * APB;   // anchors per CTA batch
@@ -601,7 +615,7 @@ build_kernel(const BuildParams p) {
     const int j0 = blockIdx.x * p.tile;
     accumulate_anchors<DT, C, SCALED, CONF, kBuildThreads>(level_view(p), slot_poses(p, ts), j0,
                                                            min(j0 + p.tile, p.N), acc);
-    const float v = cta_reduce_slots<kBuildThreads, GroupShape<DT, C>::APB>(acc, red);
+    const float v = cta_reduce_slots<kBuildThreads, GroupShape<DT, C, SCALED>::APB>(acc, red);
     const int h = threadIdx.x / kAcc;
     if (threadIdx.x < kHypTile * kAcc && h < ts.n && ts.cand[h])
         p.partial[((size_t)ts.slot[h] * p.n_tiles + blockIdx.x) * kAcc + threadIdx.x % kAcc] = v;
@@ -631,7 +645,7 @@ build_fused_kernel(const FusedBuildParams fp) {
     const int j0 = blockIdx.x * p.tile;
     accumulate_anchors<DT, C, SCALED, CONF, kBuildThreads>(level_view(p), slot_poses(p, ts), j0,
                                                            min(j0 + p.tile, p.N), acc);
-    const float v = cta_reduce_slots<kBuildThreads, GroupShape<DT, C>::APB>(acc, red);
+    const float v = cta_reduce_slots<kBuildThreads, GroupShape<DT, C, SCALED>::APB>(acc, red);
     const int hv = tid / kAcc, iv = tid % kAcc;     // slot and sum this thread holds (tid < kHypTile kAcc)
     if (p.n_tiles == 1) {
         // the only tile: its record is the sum (0 + x is what the 8-chain sum gives), no

@@ -256,7 +256,7 @@ level_persistent_kernel(const LevelArgs a) {
                         const int j0 = t * a.tile;
                         accumulate_anchors<DT, C, SCALED, CONF, kBuildThreads>(v, sp, j0, min(j0 + a.tile, fd->N),
                                                                                acc);
-                        const float val = cta_reduce_slots<kBuildThreads, GroupShape<DT, C>::APB>(acc, red);
+                        const float val = cta_reduce_slots<kBuildThreads, GroupShape<DT, C, SCALED>::APB>(acc, red);
                         if (tid < kHypTile * kAcc && tid / kAcc < s_njobs)
                             a.partial[(((size_t)s_first * tpi + t) * kHypTile + tid / kAcc) * kAcc + tid % kAcc] =
                                 val;

@@ -83,20 +83,40 @@ __global__ void gather_probe_kernel(const uint4* map, int H, int W, long long sa
     if (acc == 0x9e3779b9u) atomicXor(&g_probe_sink, acc);
 }
 
+// One vector of VB bytes (16 or 32, the build pass' load width) read through the read-only
+// path, folded to one word.
+template <int VB> struct ProbeVec;
+template <> struct ProbeVec<16> {
+    static __device__ __forceinline__ unsigned fold(const unsigned char* p) {
+        const uint4 v = __ldg(reinterpret_cast<const uint4*>(p));
+        return v.x ^ v.w;
+    }
+};
+template <> struct ProbeVec<32> {
+    static __device__ __forceinline__ unsigned fold(const unsigned char* p) {
+        unsigned w[8];
+        asm("ld.global.nc.v8.u32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+            : "=r"(w[0]), "=r"(w[1]), "=r"(w[2]), "=r"(w[3]), "=r"(w[4]), "=r"(w[5]), "=r"(w[6]), "=r"(w[7])
+            : "l"(p));
+        return w[0] ^ w[7];
+    }
+};
+
 // The build pass' own access pattern without its arithmetic: grid (anchor tiles x tiles of
 // kHypTile poses), 256 threads, the build pass' lane layout (LP lanes per tap; a group takes
 // APB anchors under HG poses at a time, NS groups over the same anchors): each lane projects
 // one (anchor, pose) record and publishes the tap offset to its group (shuffles), then the
 // group reads the reference row of each of its anchors once and the 4 taps of each record,
-// NV 16-byte loads per lane and tap (row 0 for a record that is not visible, as the build
+// NV loads of VB bytes per lane and tap (row 0 for a record that is not visible, as the build
 // pass does).  Two batches are in flight per step.  Loaded words are XOR-folded.
-template <int LP, int NV>
-__global__ void __launch_bounds__(256) frame_gather_probe_kernel(const float* pts, int N, const uint4* map,
-                                                                 const uint4* ref, int H, int W, float fx,
+template <int LP, int NV, int VB>
+__global__ void __launch_bounds__(256) frame_gather_probe_kernel(const float* pts, int N, const unsigned char* map,
+                                                                 const unsigned char* ref, int H, int W, float fx,
                                                                  float fy, float cx, float cy,
                                                                  const float* poses, int M, int tile) {
+    using PV = ProbeVec<VB>;
     constexpr int HG = LP < kHypTile ? LP : kHypTile, NS = kHypTile / HG, APB = LP / HG;
-    constexpr int V = LP * NV;                 // 16-byte vectors per tap (= per reference row)
+    constexpr int V = LP * NV;                 // vectors per tap (= per reference row)
     constexpr int ASTEP = 256 / (LP * NS) * APB;
     const int lane = threadIdx.x & 31, q = lane & (LP - 1), src0 = lane & ~(LP - 1);
     const int slot = (lane / APB) % kHypTile, qa = q % APB;
@@ -105,7 +125,7 @@ __global__ void __launch_bounds__(256) frame_gather_probe_kernel(const float* pt
     const float R00 = P[0], R01 = P[1], R02 = P[2], T0 = P[3], R10 = P[4], R11 = P[5], R12 = P[6], T1 = P[7];
     const float R20 = P[8], R21 = P[9], R22 = P[10], T2 = P[11];
     const int j0 = blockIdx.x * tile, j1 = min(j0 + tile, N);
-    const size_t row = (size_t)W * V;
+    const size_t row = (size_t)W * V * VB;     // bytes per map row
     unsigned acc = 0;
     // tap offset of anchor j under this lane's pose (-1: not visible)
     auto project = [&](int j) {
@@ -131,23 +151,19 @@ __global__ void __launch_bounds__(256) frame_gather_probe_kernel(const float* pt
             const int off = b ? offB : offA, jbb = jb + ASTEP * b;
 #pragma unroll
             for (int a = 0; a < APB; ++a) {
-                const uint4* fr = ref + (size_t)(jbb + a < j1 ? jbb + a : j0) * V;
+                const unsigned char* fr = ref + (size_t)(jbb + a < j1 ? jbb + a : j0) * V * VB;
 #pragma unroll
-                for (int k = 0; k < NV; ++k) {
-                    const uint4 r = __ldg(fr + q + k * LP);
-                    acc ^= r.x ^ r.w;
-                }
+                for (int k = 0; k < NV; ++k) acc ^= PV::fold(fr + (size_t)(q + k * LP) * VB);
             }
 #pragma unroll
             for (int i = 0; i < LP; ++i) {
                 const int oi = LP > 1 ? __shfl_sync(gmask, off, src0 + i) : off;
-                const uint4* t00 = map + (size_t)(oi >= 0 ? oi : 0) * V;
+                const unsigned char* t00 = map + (size_t)(oi >= 0 ? oi : 0) * V * VB;
 #pragma unroll
                 for (int k = 0; k < NV; ++k) {
-                    const int c = q + k * LP;
-                    const uint4 x0 = __ldg(t00 + c), x1 = __ldg(t00 + V + c), x2 = __ldg(t00 + row + c);
-                    const uint4 x3 = __ldg(t00 + row + V + c);
-                    acc ^= x0.x ^ x0.w ^ x1.y ^ x1.z ^ x2.x ^ x2.w ^ x3.y ^ x3.z;
+                    const size_t c = (size_t)(q + k * LP) * VB;
+                    acc ^= PV::fold(t00 + c) ^ PV::fold(t00 + V * VB + c) ^ PV::fold(t00 + row + c) ^
+                           PV::fold(t00 + row + V * VB + c);
                 }
             }
         }
@@ -257,27 +273,39 @@ pilot_status pilot_probe_gather_frame(const float* points, int N, const void* ma
     if (!points || !map || !ref || !poses32 || !units_per_s) return probe_fail(PILOT_EINVAL, "NULL argument");
     if (N < 1 || M < 1 || M > 65535 || tile < 1) return probe_fail(PILOT_EINVAL, "N, M and tile must be positive, M <= 65535");
     if (H < 2 || W < 2) return probe_fail(PILOT_EINVAL, "map must be at least 2 x 2");
-    if (reinterpret_cast<uintptr_t>(map) % 16 || reinterpret_cast<uintptr_t>(ref) % 16)
-        return probe_fail(PILOT_EINVAL, "map and ref must be 16-byte aligned");
     const int elem = dtype == PILOT_F32 ? 4 : (dtype == PILOT_FP8E4M3 ? 1 : 2);
-    const int vec = C * elem / 16;               // 16-byte vectors per tap
+    // the build pass' load width for maps without per-channel scales: 32 bytes for FP32 and
+    // 16-bit taps of 32 bytes or more, else 16
+    const int vb = (dtype != PILOT_FP8E4M3 && C * elem >= 32) ? 32 : 16;
+    if (reinterpret_cast<uintptr_t>(map) % vb || reinterpret_cast<uintptr_t>(ref) % vb)
+        return probe_fail(PILOT_EINVAL, "map and ref must be aligned to the load width (16 or 32 bytes)");
+    const int vec = C * elem / vb;               // vectors per tap
     if (C * elem % 16 || vec < 1 || vec > 16 || (vec & (vec - 1)))
         return probe_fail(PILOT_EINVAL, "a tap (C x element size) must be 16 .. 256 bytes, a power of two");
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     const dim3 grid((N + tile - 1) / tile, (M + kHypTile - 1) / kHypTile);
     const float f[4] = {(float)fx, (float)fy, (float)cx, (float)cy};
-    const uint4* mp = static_cast<const uint4*>(map);
-    const uint4* rp = static_cast<const uint4*>(ref);
+    const unsigned char* mp = static_cast<const unsigned char*>(map);
+    const unsigned char* rp = static_cast<const unsigned char*>(ref);
     auto go = [&]() {
-#define PILOT_FRAME_PROBE(LP, NV)                                                                             \
-    frame_gather_probe_kernel<LP, NV><<<grid, 256, 0, s>>>(points, N, mp, rp, H, W, f[0], f[1], f[2], f[3], \
-                                                           poses32, M, tile)
-        switch (vec) {
-            case 1: PILOT_FRAME_PROBE(1, 1); break;
-            case 2: PILOT_FRAME_PROBE(2, 1); break;
-            case 4: PILOT_FRAME_PROBE(4, 1); break;
-            case 8: PILOT_FRAME_PROBE(8, 1); break;
-            default: PILOT_FRAME_PROBE(8, 2); break;
+#define PILOT_FRAME_PROBE(LP, NV, VB)                                                                             \
+    frame_gather_probe_kernel<LP, NV, VB><<<grid, 256, 0, s>>>(points, N, mp, rp, H, W, f[0], f[1], f[2], f[3], \
+                                                               poses32, M, tile)
+        if (vb == 32) {
+            switch (vec) {
+                case 1: PILOT_FRAME_PROBE(1, 1, 32); break;
+                case 2: PILOT_FRAME_PROBE(2, 1, 32); break;
+                case 4: PILOT_FRAME_PROBE(4, 1, 32); break;
+                default: PILOT_FRAME_PROBE(8, 1, 32); break;
+            }
+        } else {
+            switch (vec) {
+                case 1: PILOT_FRAME_PROBE(1, 1, 16); break;
+                case 2: PILOT_FRAME_PROBE(2, 1, 16); break;
+                case 4: PILOT_FRAME_PROBE(4, 1, 16); break;
+                case 8: PILOT_FRAME_PROBE(8, 1, 16); break;
+                default: PILOT_FRAME_PROBE(8, 2, 16); break;
+            }
         }
 #undef PILOT_FRAME_PROBE
         return cudaGetLastError();

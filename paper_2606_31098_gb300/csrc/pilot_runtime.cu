@@ -123,8 +123,11 @@ pilot_status validate_frame(const pilot_align_config& c, const pilot_frame* f) {
             return fail(PILOT_EINVAL, "level %d map has 2^31 or more elements", l);
         if (!f->qry_feat[l]) return fail(PILOT_EINVAL, "qry_feat[%d] is NULL", l);
         if (f->N > 0 && !f->ref_feat[l]) return fail(PILOT_EINVAL, "ref_feat[%d] is NULL", l);
-        if (!aligned(f->qry_feat[l], 16) || (f->ref_feat[l] && !aligned(f->ref_feat[l], 16)))
-            return fail(PILOT_EINVAL, "level %d feature pointers must be 16-byte aligned", l);
+        // device maps are read with loads of up to 32 bytes; host frames are staged into
+        // the solver's own (aligned) buffers
+        const size_t fa = f->is_device ? 32 : 16;
+        if (!aligned(f->qry_feat[l], fa) || (f->ref_feat[l] && !aligned(f->ref_feat[l], fa)))
+            return fail(PILOT_EINVAL, "level %d feature pointers must be %d-byte aligned", l, (int)fa);
         if ((f->qry_scale[l] && !aligned(f->qry_scale[l], 16)) || (f->ref_scale[l] && !aligned(f->ref_scale[l], 16)))
             return fail(PILOT_EINVAL, "level %d scale pointers must be 16-byte aligned", l);
         if (f->qry_conf[l] && !aligned(f->qry_conf[l], 4))

@@ -77,6 +77,22 @@ def test_validate_rejects_malformed_frames(lib, mutation, needle):
     assert needle in msg
 
 
+def test_device_feature_pointers_need_32_byte_alignment(lib):
+    """Device maps are read with loads of up to 32 bytes; host frames are staged into the
+    solver's own buffers and need only 16.  Validation reads no memory, so the pointer
+    values alone are checked here."""
+    f, arrs = small_host_frame()
+    for is_device, ok in ((1, False), (0, True)):
+        fa = B.FrameArgs(f, arrs, is_device=False)
+        fa.c.is_device = is_device
+        fa.c.qry_feat[0] = (fa.c.qry_feat[0] // 32) * 32 + 16     # 16- but not 32-byte aligned
+        st, msg = B.validate(B.Options(), fa)
+        if ok:
+            assert st == B.PILOT_OK, msg
+        else:
+            assert st == B.PILOT_EINVAL and "32-byte aligned" in msg
+
+
 @pytest.mark.parametrize("field,value", [("lambda0", -1.0), ("damping_mode", 3), ("huber_photo", -0.1),
                                          ("min_valid_frac", 1.5), ("max_channels", 12), ("gate_range", -1.0),
                                          ("gate_grav", float("nan"))])
