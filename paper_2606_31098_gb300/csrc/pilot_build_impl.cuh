@@ -291,7 +291,9 @@ __device__ __forceinline__ void record_partials(const typename Storage<DT>::T* t
 // and whether each has a pose to evaluate (an inactive slot's lanes finish nothing).  Every
 // thread of the CTA calls it with the same arguments; threads are grouped as described at
 // the top of the file.
-template <pilot_dtype DT, int C, bool SCALED, bool CONF, int NTHREADS>
+// PREFETCH: read the next batch's anchor coordinates one batch ahead (four more registers
+// through the loop; the sums are the same either way).
+template <pilot_dtype DT, int C, bool SCALED, bool CONF, int NTHREADS, bool PREFETCH = true>
 __device__ __forceinline__ void accumulate_anchors(const LevelView& v, const SlotPoses& sp, int j_begin, int j_end,
                                                    float* acc) {
     using Elem = typename Storage<DT>::T;
@@ -338,12 +340,12 @@ __device__ __forceinline__ void accumulate_anchors(const LevelView& v, const Slo
     const float xmax = (float)(v.W - 1), ymax = (float)(v.H - 1);
     const float d2 = v.huber * v.huber;
 
-    // the anchor coordinates of the next batch are read one batch ahead, so that their load
-    // latency overlaps the current batch's gathers
+    // with PREFETCH the anchor coordinates of the next batch are read one batch ahead, so
+    // that their load latency overlaps the current batch's gathers
     const int jfirst = j_begin + (tid / (LP * NS)) * APB;
     float nX = 0.f, nY = 0.f, nZ = 0.f;
     bool nok = false;
-    if (jfirst + qa < j_end) {
+    if (PREFETCH && jfirst + qa < j_end) {
         const int j = jfirst + qa;
         nok = act && (!v.valid || v.valid[j]);
         nX = __ldg(v.px + j), nY = __ldg(v.py + j), nZ = __ldg(v.pz + j);
@@ -351,13 +353,18 @@ __device__ __forceinline__ void accumulate_anchors(const LevelView& v, const Slo
     for (int jb = jfirst; jb < j_end; jb += ASTEP) {
         // 1. every lane projects its own record: anchor jb + qa under its hypothesis
         const int jo = jb + qa;
-        const float X = nX, Y = nY, Z = nZ;
-        const bool ok = nok && jo < j_end;
-        nok = false;
-        if (jo + ASTEP < j_end) {
-            const int j = jo + ASTEP;
-            nok = act && (!v.valid || v.valid[j]);
-            nX = __ldg(v.px + j), nY = __ldg(v.py + j), nZ = __ldg(v.pz + j);
+        float X = nX, Y = nY, Z = nZ;
+        bool ok = nok && jo < j_end;
+        if constexpr (PREFETCH) {
+            nok = false;
+            if (jo + ASTEP < j_end) {
+                const int j = jo + ASTEP;
+                nok = act && (!v.valid || v.valid[j]);
+                nX = __ldg(v.px + j), nY = __ldg(v.py + j), nZ = __ldg(v.pz + j);
+            }
+        } else if (jo < j_end) {
+            ok = act && (!v.valid || v.valid[jo]);
+            X = __ldg(v.px + jo), Y = __ldg(v.py + jo), Z = __ldg(v.pz + jo);
         }
         bool vis = false;
         int off = 0;

@@ -75,32 +75,39 @@ level_persistent_kernel(const LevelArgs a) {
     __shared__ double E[kWarps][kAcc];
     __shared__ double Wsh[kWarps][128];         // FP64 step scratch, one block per warp
     __shared__ float pose[kHypTile][12];
-    __shared__ long long s_item;
-    __shared__ int s_frame, s_job, s_njobs, s_first, s_t0;
     __shared__ unsigned s_meta[kHypTile];
+    // the claimed work item: its frame, first record slot, tile range and job tile (s_item < 0:
+    // none left in this phase)
+    __shared__ long long s_item;
+    __shared__ int s_frame, s_level, s_job, s_njobs, s_first, s_t0, s_t1, s_run;
+    // CTA-uniform loop state, kept here and read where it is used: held in registers it would
+    // live through the anchor loop and push the loop's own values into local memory
+    __shared__ int s_nfr, s_items, s_jobs, s_IA, s_JA;
+    __shared__ unsigned long long s_base;
     // frame tables, staged when the launch lists few frames
     __shared__ int s_fitem[kSmemFrames + 1], s_fjob[kSmemFrames + 1], s_flist[kSmemFrames], s_fipj[kSmemFrames];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int n_fr = a.header->n_listed[a.list_index];
     const int tpi = a.tiles_per_item;
-    const bool staged = n_fr <= kSmemFrames;
-    if (staged)
-        for (int i = tid; i <= n_fr; i += kBuildThreads) {
+    if (tid == 0) s_nfr = a.header->n_listed[a.list_index];
+    __syncthreads();
+    if (s_nfr <= kSmemFrames)
+        for (int i = tid; i <= s_nfr; i += kBuildThreads) {
             s_fitem[i] = a.fr_item[i];
             s_fjob[i] = a.fr_job[i];
-            if (i < n_fr) {
+            if (i < s_nfr) {
                 s_flist[i] = a.fr_list[i];
                 s_fipj[i] = items_per_job(a.frames[s_flist[i]].N, a.tile, tpi);
             }
         }
     __syncthreads();
-    auto fitem = [&](int i) { return staged ? s_fitem[i] : a.fr_item[i]; };
-    auto fjob = [&](int i) { return staged ? s_fjob[i] : a.fr_job[i]; };
-    auto flist = [&](int i) { return staged ? s_flist[i] : a.fr_list[i]; };
-    auto fipj = [&](int i) { return staged ? s_fipj[i] : items_per_job(a.frames[a.fr_list[i]].N, a.tile, tpi); };
+    auto staged = [&]() { return s_nfr <= kSmemFrames; };
+    auto fitem = [&](int i) { return staged() ? s_fitem[i] : a.fr_item[i]; };
+    auto fjob = [&](int i) { return staged() ? s_fjob[i] : a.fr_job[i]; };
+    auto flist = [&](int i) { return staged() ? s_flist[i] : a.fr_list[i]; };
+    auto fipj = [&](int i) { return staged() ? s_fipj[i] : items_per_job(a.frames[a.fr_list[i]].N, a.tile, tpi); };
     // listed frame holding x: last i < n_fr with table(i) <= x (empty frames are skipped)
     auto find = [&](bool items, long long x) {
-        int lo = 0, hi = n_fr - 1;
+        int lo = 0, hi = s_nfr - 1;
         while (lo < hi) {
             const int mid = (lo + hi + 1) >> 1;
             if ((items ? fitem(mid) : fjob(mid)) <= x) lo = mid;
@@ -108,14 +115,17 @@ level_persistent_kernel(const LevelArgs a) {
         }
         return lo;
     };
-    const int n_items = fitem(n_fr), n_jobs = fjob(n_fr);
-    const int n_warps = gridDim.x * kWarps;
+    if (tid == 0) {
+        s_items = fitem(s_nfr);
+        s_jobs = fjob(s_nfr);
+    }
+    __syncthreads();
     unsigned gen = 0;
     // level start of every job: its hypothesis, LM state and FP32 start pose (pose32 and
     // job_meta are indexed by job within this launch).  Job j's state is only ever read and
     // written by global warp j (mod the warp count; lane 0 here, all lanes in the steps below),
     // so one SM's L1 sees all its accesses; other CTAs read pose32 and job_meta from L2.
-    for (int job = blockIdx.x * kWarps + warp; job < n_jobs; job += n_warps) {
+    for (int job = blockIdx.x * kWarps + warp; job < s_jobs; job += gridDim.x * kWarps) {
         if (lane != 0) continue;
         const int i = find(false, job);
         const FrameDesc* fd = a.frames + flist(i);
@@ -141,13 +151,13 @@ level_persistent_kernel(const LevelArgs a) {
     // e.g. the paper's 500-anchor schedule) it would put two step latencies in every
     // iteration, so it is only made for at least kSplitUnits anchor-hypothesis units per
     // iteration and at most one job per warp.
-    __shared__ int s_IA, s_JA;
     if (tid == 0) {
+        const int n_items = s_items, n_jobs = s_jobs;
         int IA = n_items, JA = n_jobs;
         const int target = (n_items + 1) / 2;
         long long units = 0;
-        for (int i = 0; i < n_fr; ++i) units += (long long)a.frames[flist(i)].N * (fjob(i + 1) - fjob(i));
-        if (target < n_items && units >= kSplitUnits && n_jobs <= n_warps) {
+        for (int i = 0; i < s_nfr; ++i) units += (long long)a.frames[flist(i)].N * (fjob(i + 1) - fjob(i));
+        if (target < n_items && units >= kSplitUnits && n_jobs <= (int)gridDim.x * kWarps) {
             const int i = find(true, target);
             const int ipj = fipj(i);
             const int jt = (target - fitem(i) + ipj - 1) / ipj;    // round up to a job tile
@@ -156,19 +166,18 @@ level_persistent_kernel(const LevelArgs a) {
         }
         s_IA = IA;
         s_JA = JA;
+        // claims made before the current phase: a gathering phase takes one claim per item of
+        // its half plus one unsuccessful claim per CTA
+        s_base = 0;
     }
     __syncthreads();
-    const int IA = s_IA, JA = s_JA;
-    // claims made before the current phase: a gathering phase takes one claim per item of its
-    // half plus one unsuccessful claim per CTA
-    unsigned long long base = 0;
     for (int ph = 0; ph <= 2 * a.k_max + 2; ++ph) {
         // FP64 steps of the half gathered in the previous phase: job j on global warp j (mod
         // the warp count), all 32 lanes
         if (ph >= 1) {
             const int k = (ph - 1) / 2;
-            const int jlo = (ph & 1) ? 0 : JA, jhi = (ph & 1) ? JA : n_jobs;
-            for (int job = jlo + blockIdx.x * kWarps + warp; job < jhi; job += n_warps) {
+            const int jlo = (ph & 1) ? 0 : s_JA, jhi = (ph & 1) ? s_JA : s_jobs;
+            for (int job = jlo + blockIdx.x * kWarps + warp; job < jhi; job += gridDim.x * kWarps) {
                 const int i = find(false, job);
                 const int f = flist(i);
                 const FrameDesc* fd = a.frames + f;
@@ -201,39 +210,41 @@ level_persistent_kernel(const LevelArgs a) {
         }
         // gathers of one half at iteration k, its work items claimed one at a time
         if (ph <= 2 * a.k_max + 1) {
-            const int k = ph / 2;
-            const int ilo = (ph & 1) ? IA : 0, ihi = (ph & 1) ? n_items : IA;
             for (;;) {
                 if (tid == 0) {
-                    long long item = ilo + (long long)(atomicAdd(a.sync, 1ull) - base);
+                    const int k = ph / 2;
+                    const int ilo = (ph & 1) ? s_IA : 0, ihi = (ph & 1) ? s_items : s_IA;
+                    long long item = ilo + (long long)(atomicAdd(a.sync, 1ull) - s_base);
                     if (item < ilo) {              // cannot happen: the counts above are exact
                         atomicExch(a.error, 1u);
                         item = ihi;
                     }
-                    s_item = item;
+                    s_item = item < ihi ? item : -1;
                     if (item < ihi) {
                         const int i = find(true, item);
                         const int ipj = fipj(i);
                         const int local = (int)(item - fitem(i));
                         const int jt = local / ipj;      // job tile within the frame
-                        s_frame = flist(i);
+                        const FrameDesc* fd = a.frames + flist(i);
+                        const int level = a.level >= 0 ? a.level : fd->level;
                         s_job = fjob(i) + kHypTile * jt;
                         s_njobs = min(kHypTile, fjob(i + 1) - s_job);
                         s_first = fitem(i) + jt * ipj;
                         s_t0 = (local - jt * ipj) * tpi;
+                        s_t1 = min(s_t0 + tpi, fd->N > 0 ? (fd->N + a.tile - 1) / a.tile : 1);
+                        s_run = k <= a.iters[level];
+                        s_frame = flist(i);
+                        s_level = level;
                     }
                 }
                 __syncthreads();
-                if (s_item >= ihi) break;
-                const int job = s_job;
+                if (s_item < 0) break;
                 if (tid < 12 * kHypTile) {
                     const int h = tid / 12;
-                    pose[h][tid % 12] = __ldcg(a.pose32 + 12 * (size_t)(job + (h < s_njobs ? h : 0)) + tid % 12);
+                    pose[h][tid % 12] = __ldcg(a.pose32 + 12 * (size_t)(s_job + (h < s_njobs ? h : 0)) + tid % 12);
                 }
-                if (tid < kHypTile) s_meta[tid] = tid < s_njobs ? __ldcg(a.job_meta + job + tid) : 0u;
+                if (tid < kHypTile) s_meta[tid] = tid < s_njobs ? __ldcg(a.job_meta + s_job + tid) : 0u;
                 __syncthreads();
-                const FrameDesc* fd = a.frames + s_frame;
-                const int level = a.level >= 0 ? a.level : fd->level;
                 SlotPoses sp;
                 bool any = false;
 #pragma unroll
@@ -242,29 +253,33 @@ level_persistent_kernel(const LevelArgs a) {
                     sp.act[h] = (s_meta[h] & kEval) != 0;
                     any = any || sp.act[h];
                 }
-                if (k <= a.iters[level] && any) {
+                if (s_run && any) {
+                    const FrameDesc* fd = a.frames + s_frame;
+                    const int level = s_level;
                     const LevelView v{fd->px, fd->py, fd->pz, fd->weight, fd->valid, fd->qry[level], fd->ref[level],
                                       fd->qscale[level], fd->rscale[level], fd->conf[level], fd->H[level],
                                       fd->W[level], fd->fx[level], fd->fy[level], fd->cx[level], fd->cy[level],
                                       a.huber};
-                    const int n_t = fd->N > 0 ? (fd->N + a.tile - 1) / a.tile : 1;
-                    const int t1 = min(s_t0 + tpi, n_t);
-                    for (int t = s_t0; t < t1; ++t) {
+                    for (int t = s_t0; t < s_t1; ++t) {
                         float acc[kNumSums];
 #pragma unroll
                         for (int i = 0; i < kNumSums; ++i) acc[i] = 0.f;
                         const int j0 = t * a.tile;
-                        accumulate_anchors<DT, C, SCALED, CONF, kBuildThreads>(v, sp, j0, min(j0 + a.tile, fd->N),
-                                                                               acc);
+                        // no anchor prefetch for the narrow types: the frame's level inputs
+                        // already take the registers that kernel parameters cost the plain form
+                        accumulate_anchors<DT, C, SCALED, CONF, kBuildThreads, DT == PILOT_F32>(
+                            v, sp, j0, min(j0 + a.tile, fd->N), acc);
                         const float val = cta_reduce_slots<kBuildThreads, GroupShape<DT, C, SCALED>::APB>(acc, red);
                         if (tid < kHypTile * kAcc && tid / kAcc < s_njobs)
                             a.partial[(((size_t)s_first * tpi + t) * kHypTile + tid / kAcc) * kAcc + tid % kAcc] =
                                 val;
+                        // the next tile's reduction reuses red: wait until every slot's sums are read
+                        if (t + 1 < s_t1) __syncthreads();
                     }
                 }
                 __syncthreads();
             }
-            base += (unsigned long long)(ihi - ilo) + gridDim.x;
+            if (tid == 0) s_base += (unsigned long long)((ph & 1) ? s_items - s_IA : s_IA) + gridDim.x;
         }
         if (!grid_sync(a.sync, a.error, gen, a.barrier_timeout_ns, a.barrier_extra)) return;
     }
