@@ -270,17 +270,18 @@ __device__ __forceinline__ void store_pose32(float* dst, const double* T) {
 static __device__ __noinline__ void lm_update(HypState& st, int mode, int solve_next, int damping_mode,
                                               const PriorParams& prior, double* E, double* W,
                                               double min_valid, float* cand32, double* eval_out, int lane) {
-    // every read of the state is issued here, before any write, as one round trip
-    const int has_cand = st.has_cand;
-    const double cost0 = st.cost;
-    const double lambda0 = st.lambda;
+    // every read of the state is issued here, before any write, as one round trip, from L2:
+    // the persistent level kernel may step a hypothesis on another SM than the last time
+    const int has_cand = __ldcg(&st.has_cand);
+    const double cost0 = __ldcg(&st.cost);
+    const double lambda0 = __ldcg(&st.lambda);
     const double* Tsrc = (mode == kEpiStep) ? st.Tc : st.T;
     double Tev[12];
 #pragma unroll
-    for (int i = 0; i < 12; ++i) Tev[i] = Tsrc[i];
-    const double Hg_own = lane < 21 ? st.H[lane] : (lane < 27 ? st.g[lane - 21] : 0.0);
-    const double T_own = lane < 12 ? st.T[lane] : 0.0;
-    const double Tc_own = lane < 12 ? st.Tc[lane] : 0.0;
+    for (int i = 0; i < 12; ++i) Tev[i] = __ldcg(Tsrc + i);
+    const double Hg_own = lane < 21 ? __ldcg(st.H + lane) : (lane < 27 ? __ldcg(st.g + lane - 21) : 0.0);
+    const double T_own = lane < 12 ? __ldcg(st.T + lane) : 0.0;
+    const double Tc_own = lane < 12 ? __ldcg(st.Tc + lane) : 0.0;
     const bool evaluated = (mode == kEpiStep) ? (has_cand != 0) : true;
     if (evaluated) {
         if (prior.use_gravity) add_gravity(prior, Tev, E, lane);

@@ -44,6 +44,12 @@ __host__ __device__ inline int items_per_job(int N, int tile, int tpi) {
 constexpr int kHypTile = PILOT_HYP_TILE;
 static_assert(kHypTile == 2 || kHypTile == 4 || kHypTile == 8, "hypothesis tile");
 
+// Words of one of the level kernel's per-job-tile flag arrays (indexed by a job tile's first
+// work item) for at most max_hyps jobs in max_frames frames of at most max_tiles anchor tiles.
+inline size_t level_flag_words(int max_hyps, int max_frames, int max_tiles) {
+    return ((size_t)max_hyps / kHypTile + (size_t)max_frames + 1) * ((size_t)max_tiles + 1);
+}
+
 // Work items of a frame of N anchors with n_jobs jobs: the jobs are taken kHypTile at a time
 // (a work item covers all jobs of its tile, as a build-pass CTA holds kHypTile hypotheses).
 __host__ __device__ inline int frame_items(int n_jobs, int N, int tile, int tpi) {
@@ -187,6 +193,8 @@ struct LevelArgs {
     unsigned* job_meta;        // [job] hypothesis index | 0x80000000 when it has a pose to evaluate
     float* partial;            // tile records
     unsigned long long* sync;  // [0] item claims, [1] barrier arrivals, [2] barrier generations; zero before the launch
+    unsigned* tile_done;       // per job tile, at its first item: items completed (all iterations); zero before the launch
+    unsigned* tile_ready;      // per job tile, at its first item: iterations whose FP64 steps are published; zero before the launch
     unsigned* error;           // set to 1 when a barrier wait gives up
     unsigned long long barrier_timeout_ns;   // longest barrier wait
     int barrier_extra;         // 0; > 0 only in the failure self-test (a barrier that cannot complete)

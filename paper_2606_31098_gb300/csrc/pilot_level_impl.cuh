@@ -14,6 +14,16 @@ __device__ __forceinline__ unsigned long long global_ns() {
     return t;
 }
 
+__device__ __forceinline__ unsigned ld_acquire_gpu(const unsigned* p) {
+    unsigned v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ void st_release_gpu(unsigned* p, unsigned v) {
+    asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
 // Grid-wide barrier of the persistent level kernel (cooperative launch: all CTAs resident).
 // sync[1] counts arrivals over all generations, sync[2] is the number of completed
 // generations; a generation completes when gridDim.x + extra CTAs have arrived (extra is 0
@@ -82,7 +92,7 @@ level_persistent_kernel(const LevelArgs a) {
     __shared__ int s_frame, s_level, s_job, s_njobs, s_first, s_t0, s_t1, s_run;
     // CTA-uniform loop state, kept here and read where it is used: held in registers it would
     // live through the anchor loop and push the loop's own values into local memory
-    __shared__ int s_nfr, s_items, s_jobs, s_IA, s_JA;
+    __shared__ int s_nfr, s_items, s_jobs, s_IA, s_JA, s_flow, s_k, s_ipj, s_last;
     __shared__ unsigned long long s_base;
     // frame tables, staged when the launch lists few frames
     __shared__ int s_fitem[kSmemFrames + 1], s_fjob[kSmemFrames + 1], s_flist[kSmemFrames], s_fipj[kSmemFrames];
@@ -157,6 +167,8 @@ level_persistent_kernel(const LevelArgs a) {
         const int target = (n_items + 1) / 2;
         long long units = 0;
         for (int i = 0; i < s_nfr; ++i) units += (long long)a.frames[flist(i)].N * (fjob(i + 1) - fjob(i));
+        // gather-heavy levels take the schedule without grid barriers (below)
+        s_flow = units >= kSplitUnits && a.tile_done != nullptr;
         if (target < n_items && units >= kSplitUnits && n_jobs <= (int)gridDim.x * kWarps) {
             const int i = find(true, target);
             const int ipj = fipj(i);
@@ -171,6 +183,137 @@ level_persistent_kernel(const LevelArgs a) {
         s_base = 0;
     }
     __syncthreads();
+    // Gather-heavy levels: the work items of every (iteration, job tile) are claimed in
+    // iteration-major order from one counter and no grid barrier is taken.  The CTA that
+    // completes a job tile's items of iteration k (counted in tile_done) runs the tile's FP64
+    // steps, job h on warp h as the plain form's last CTA does, then publishes k + 1 in
+    // tile_ready; an item of iteration k + 1 waits (bounded) until its tile has published k + 1.
+    // Records and steps are the lockstep schedule's, so the results are the same.  Progress:
+    // the earliest unfinished item in claim order never waits, since everything it depends on
+    // was claimed before it and is finished or held by a CTA that is working, not waiting (all
+    // CTAs are resident).  Items of iterations beyond a frame's count are claimed and skipped
+    // and touch no flag.
+    if (s_flow) {
+        for (;;) {
+            if (tid == 0) {
+                const long long g = (long long)atomicAdd(a.sync, 1ull);
+                const int n_items = s_items;
+                s_item = g < (long long)(a.k_max + 1) * n_items ? g : -1;
+                if (s_item >= 0) {
+                    const int k = (int)(g / n_items);
+                    const int local = (int)(g - (long long)k * n_items);
+                    const int i = find(true, local);
+                    const int ipj = fipj(i);
+                    const int loc = local - fitem(i);
+                    const int jt = loc / ipj;      // job tile within the frame
+                    const FrameDesc* fd = a.frames + flist(i);
+                    const int level = a.level >= 0 ? a.level : fd->level;
+                    s_k = k;
+                    s_run = k <= a.iters[level];
+                    s_job = fjob(i) + kHypTile * jt;
+                    s_njobs = min(kHypTile, fjob(i + 1) - s_job);
+                    s_first = fitem(i) + jt * ipj;
+                    s_ipj = ipj;
+                    s_t0 = (loc - jt * ipj) * tpi;
+                    s_t1 = min(s_t0 + tpi, fd->N > 0 ? (fd->N + a.tile - 1) / a.tile : 1);
+                    s_frame = flist(i);
+                    s_level = level;
+                    if (s_run && k > 0) {
+                        const unsigned long long t0 = global_ns();
+                        while (ld_acquire_gpu(a.tile_ready + s_first) < (unsigned)k) {
+                            if (__ldcg(a.error) != 0u || global_ns() - t0 > a.barrier_timeout_ns) {
+                                atomicExch(a.error, 1u);
+                                s_item = -1;
+                                break;
+                            }
+                            __nanosleep(128);
+                        }
+                    }
+                }
+            }
+            __syncthreads();
+            if (s_item < 0) return;
+            if (!s_run) {
+                __syncthreads();           // the shared item state is rewritten by the next claim
+                continue;
+            }
+            if (tid < 12 * kHypTile) {
+                const int h = tid / 12;
+                pose[h][tid % 12] = __ldcg(a.pose32 + 12 * (size_t)(s_job + (h < s_njobs ? h : 0)) + tid % 12);
+            }
+            if (tid < kHypTile) s_meta[tid] = tid < s_njobs ? __ldcg(a.job_meta + s_job + tid) : 0u;
+            __syncthreads();
+            SlotPoses sp;
+            bool any = false;
+#pragma unroll
+            for (int h = 0; h < kHypTile; ++h) {
+                sp.p[h] = pose[h];
+                sp.act[h] = (s_meta[h] & kEval) != 0;
+                any = any || sp.act[h];
+            }
+            if (any) {
+                const FrameDesc* fd = a.frames + s_frame;
+                const int level = s_level;
+                const LevelView v{fd->px, fd->py, fd->pz, fd->weight, fd->valid, fd->qry[level], fd->ref[level],
+                                  fd->qscale[level], fd->rscale[level], fd->conf[level], fd->H[level], fd->W[level],
+                                  fd->fx[level], fd->fy[level], fd->cx[level], fd->cy[level], a.huber};
+                for (int t = s_t0; t < s_t1; ++t) {
+                    float acc[kNumSums];
+#pragma unroll
+                    for (int i = 0; i < kNumSums; ++i) acc[i] = 0.f;
+                    const int j0 = t * a.tile;
+                    accumulate_anchors<DT, C, SCALED, CONF, kBuildThreads, DT == PILOT_F32>(
+                        v, sp, j0, min(j0 + a.tile, fd->N), acc);
+                    const float val = cta_reduce_slots<kBuildThreads, GroupShape<DT, C, SCALED>::APB>(acc, red);
+                    if (tid < kHypTile * kAcc && tid / kAcc < s_njobs)
+                        a.partial[(((size_t)s_first * tpi + t) * kHypTile + tid / kAcc) * kAcc + tid % kAcc] = val;
+                    if (t + 1 < s_t1) __syncthreads();
+                }
+            }
+            // count the item for its job tile; the CTA that completes the tile's iteration steps it
+            __syncthreads();
+            if (tid == 0) {
+                __threadfence();
+                const unsigned done = atomicAdd(a.tile_done + s_first, 1u) + 1u;
+                s_last = done == (unsigned)(s_k + 1) * (unsigned)s_ipj;
+                if (s_last) __threadfence();
+            }
+            __syncthreads();
+            if (s_last) {
+                if (warp < s_njobs) {
+                    const int job = s_job + warp;
+                    const FrameDesc* fd = a.frames + s_frame;
+                    const int iters = a.iters[s_level];
+                    const unsigned meta = __ldcg(a.job_meta + job);
+                    const int hyp = (int)(meta & ~kEval);
+                    const bool evaluated = (meta & kEval) != 0;
+                    if (evaluated && lane < kNumSums) {
+                        const int n_t = fd->N > 0 ? (fd->N + a.tile - 1) / a.tile : 1;
+                        const float* src = a.partial + ((size_t)s_first * tpi * kHypTile + warp) * kAcc + lane;
+                        double sum = 0.0;
+                        for (int c = 0; c < 8; ++c) {
+                            double part = 0.0;
+                            for (int t = c; t < n_t; t += 8) part += (double)__ldcg(src + (size_t)t * kHypTile * kAcc);
+                            sum += part;
+                        }
+                        E[warp][lane] = sum;
+                    }
+                    __syncwarp();
+                    HypState& st = a.state[hyp];
+                    lm_update(st, s_k == 0 ? kEpiInit : kEpiStep, s_k < iters, a.damping_mode, fd->prior, E[warp],
+                              Wsh[warp], a.min_valid[s_frame], a.pose32 + 12 * (size_t)job, nullptr, lane);
+                    if (lane == 0) a.job_meta[job] = (unsigned)hyp | (st.has_cand ? kEval : 0u);
+                    __syncwarp();
+                }
+                __syncthreads();
+                if (tid == 0) {
+                    __threadfence();
+                    st_release_gpu(a.tile_ready + s_first, (unsigned)s_k + 1u);
+                }
+            }
+            __syncthreads();               // the shared item state is rewritten by the next claim
+        }
+    }
     for (int ph = 0; ph <= 2 * a.k_max + 2; ++ph) {
         // FP64 steps of the half gathered in the previous phase: job j on global warp j (mod
         // the warp count), all 32 lanes

@@ -187,6 +187,8 @@ struct pilot_align_handle {
     double* bmin_valid = nullptr;
     unsigned long long* bsync = nullptr;   // per level: item claims, barrier arrivals, generations
     unsigned* bjob_meta = nullptr;         // per job of a level launch: hypothesis | evaluate bit
+    unsigned* bflags = nullptr;            // level kernel's per-job-tile flags: completed items, then published iterations
+    size_t bflag_words = 0;                // words of each of the two flag arrays
     cudaStream_t bstream = nullptr;
     // plain form, multi-stream schedule: extra streams, a fork event and their join events
     cudaStream_t pstream[kMaxStreams - 1] = {};
@@ -475,6 +477,7 @@ void release(pilot_align_handle* h) {
     cudaFree(h->bmin_valid);
     cudaFree(h->bsync);
     cudaFree(h->bjob_meta);
+    cudaFree(h->bflags);
     if (h->bstream) cudaStreamDestroy(h->bstream);
     for (int i = 0; i < kMaxStreams - 1; ++i) {
         if (h->pstream[i]) cudaStreamDestroy(h->pstream[i]);
@@ -553,6 +556,8 @@ pilot_status batch_alloc(pilot_align_handle* h) {
     PILOT_CUDA(cudaMalloc((void**)&h->bsync, sizeof(unsigned long long) * kSyncWords * PILOT_MAX_LEVELS),
                "batch level counters");
     PILOT_CUDA(cudaMalloc((void**)&h->bjob_meta, sizeof(unsigned) * (size_t)c.max_hyps), "batch job table");
+    h->bflag_words = level_flag_words(c.max_hyps, c.max_frames, h->max_tiles);
+    PILOT_CUDA(cudaMalloc((void**)&h->bflags, sizeof(unsigned) * 2 * h->bflag_words), "batch job tile flags");
     PILOT_CUDA(cudaStreamCreateWithFlags(&h->bstream, cudaStreamNonBlocking), "batch stream");
     return PILOT_OK;
 }
@@ -643,6 +648,8 @@ pilot_status capture_batch_graph(pilot_align_handle* h, pilot_dtype dt, int C, i
         a.job_meta = h->bjob_meta;
         a.partial = h->partial;
         a.sync = h->bsync + (size_t)level * kSyncWords;
+        a.tile_done = h->bflags;
+        a.tile_ready = h->bflags + h->bflag_words;
         a.error = error;
         a.barrier_timeout_ns = kBarrierTimeoutNs;
         a.barrier_extra = 0;
@@ -655,7 +662,8 @@ pilot_status capture_batch_graph(pilot_align_handle* h, pilot_dtype dt, int C, i
         a.damping_mode = c.damping_mode;
         a.huber = (float)c.huber_photo;
         a.lambda0 = c.lambda0;
-        e = launch_level(dt, C, variant, a, h->level_grid, s);
+        e = cudaMemsetAsync(h->bflags, 0, sizeof(unsigned) * 2 * h->bflag_words, s);
+        if (e == cudaSuccess) e = launch_level(dt, C, variant, a, h->level_grid, s);
         const int K = c.keep_top_k[level];
         if (e == cudaSuccess && level > 0 && K > 0)
             e = launch_batch_prune(hdr, frames, h->state, h->bactive, nactive + (size_t)level * lay.max_frames, K,

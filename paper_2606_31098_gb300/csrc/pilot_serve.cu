@@ -150,6 +150,8 @@ struct pilot_server {
     unsigned long long* sync = nullptr;   // level kernel: item claims, barrier arrivals, generations
     float* pose32 = nullptr;              // [job][12] FP32 poses to evaluate
     unsigned* job_meta = nullptr;         // [job] hypothesis | evaluate bit
+    unsigned* flags = nullptr;            // level kernel's per-job-tile flags: completed items, then published iterations
+    size_t flag_words = 0;                // words of each of the two flag arrays
     float* partial = nullptr;             // [work item][kAcc] tile records
     unsigned char* desc_dev = nullptr;
     unsigned char* desc_host = nullptr;
@@ -194,6 +196,7 @@ void release_buffers(pilot_server* s) {
     cudaFree(s->sync);
     cudaFree(s->pose32);
     cudaFree(s->job_meta);
+    cudaFree(s->flags);
     cudaFree(s->partial);
     cudaFree(s->desc_dev);
     if (s->desc_host) cudaFreeHost(s->desc_host);
@@ -285,6 +288,8 @@ cudaError_t capture_round(pilot_server* s) {
     a.job_meta = s->job_meta;
     a.partial = s->partial;
     a.sync = s->sync;
+    a.tile_done = s->flags;
+    a.tile_ready = s->flags + s->flag_words;
     a.error = error;
     a.barrier_timeout_ns = kBarrierTimeoutNs;
     a.barrier_extra = 0;
@@ -310,6 +315,7 @@ cudaError_t capture_round(pilot_server* s) {
             e = launch_round_advance(hdr, const_cast<FrameDesc*>(frames), a.fr_list, const_cast<int*>(a.fr_item),
                                      const_cast<int*>(a.fr_job), keep, a.tile, a.tiles_per_item, s->stream);
         if (e == cudaSuccess) e = cudaMemsetAsync(s->sync, 0, sizeof(unsigned long long) * kSyncWords, s->stream);
+        if (e == cudaSuccess) e = cudaMemsetAsync(s->flags, 0, sizeof(unsigned) * 2 * s->flag_words, s->stream);
         if (e == cudaSuccess) e = level_launch(s->dt, s->C, s->variant, a, s->grid, s->stream);
         if (e == cudaSuccess)
             e = launch_round_finish(hdr, frames, s->state, s->active, s->min_valid, s->res_dev, s->cfg.max_hyps,
@@ -560,6 +566,9 @@ pilot_status pilot_serve_create(const pilot_align_config* cfg_in, size_t hbm_bud
         return bad("level counters");
     if ((e = cudaMalloc((void**)&s->pose32, sizeof(float) * 12 * H)) != cudaSuccess) return bad("candidates");
     if ((e = cudaMalloc((void**)&s->job_meta, sizeof(unsigned) * H)) != cudaSuccess) return bad("job table");
+    s->flag_words = level_flag_words(cfg.max_hyps, max_slots, (int)max_tiles);
+    if ((e = cudaMalloc((void**)&s->flags, sizeof(unsigned) * 2 * s->flag_words)) != cudaSuccess)
+        return bad("job tile flags");
     if ((e = cudaMalloc((void**)&s->partial, sizeof(float) * kAcc * (H + (size_t)(kHypTile - 1) * max_slots) *
                                                  (max_tiles + tiles_per_item(kPlainTile)))) != cudaSuccess)
         return bad("tile records");

@@ -98,6 +98,21 @@ def test_full_size_uneven_batch(torch):
         assert er < 0.2 and et < 1.0, (i, er, et)
 
 
+def test_barrier_free_and_lockstep_levels_in_one_batch(torch):
+    """Two 256^2-anchor frames with 80 hypotheses each: the coarse level's 10.5 M anchor x
+    hypothesis units per iteration take the schedule without grid barriers, and after the
+    top-8 pruning the finer levels (1 M units) run in lockstep; the iteration counts differ per
+    level.  Every frame's outputs equal its plain solve bitwise."""
+    frames = [S.make_frame(S.SceneConfig(crop_side=256, n_hyps=80), S.frame_seed(3, 1050 + i)) for i in range(2)]
+    fas = args_for(frames, B.BF16)
+    opts = B.Options(max_points=256 * 256, max_hyps=160, iters=(3, 4, 2, 0), keep_top_k=(0, 8, 8, 0))
+    solver = B.Solver(opts)
+    batch = solver.solve_batch(fas)
+    for i, fa in enumerate(fas):
+        assert_same(batch[i], solver.solve(fa), what=f"frame {i}")
+    solver.close()
+
+
 def test_batched_crop_sizes_bf16_against_the_oracle(torch):
     """One BF16 frame of each crop size of the batched workload (128^2, 192^2, 256^2,
     384^2 anchors, C = 32, 3 levels, priors on), solved together in one batch and checked
