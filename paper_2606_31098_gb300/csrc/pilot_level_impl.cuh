@@ -76,9 +76,40 @@ __device__ __forceinline__ bool grid_sync(unsigned long long* sync, unsigned* er
 // all CTAs, and the FP64 steps of half the jobs run at once, one per warp, beside the other
 // half's gathers.  Tile t of job kHypTile p + h, whose job tile's first item is q, keeps its
 // record at partial[(q tiles_per_item + t) kHypTile + h].
-template <pilot_dtype DT, int C, bool SCALED, bool CONF>
+// One job's FP64 step in the schedule without grid barriers: its tile records (slot h of the
+// job tile whose first item is `first`) summed in the plain form's 8-chain FP64 order, then
+// lm_update; all 32 lanes of one warp.  Not inlined: the item loop that calls it keeps its own
+// registers for the anchor loop.
+static __device__ __noinline__ void flow_step(const LevelArgs& a, int job, int first, int frame, int level, int k,
+                                              int h, double* E, double* W) {
+    constexpr unsigned kEval = 0x80000000u;
+    const int lane = threadIdx.x & 31;
+    const FrameDesc* fd = a.frames + frame;
+    const int iters = a.iters[level];
+    const unsigned meta = __ldcg(a.job_meta + job);
+    const int hyp = (int)(meta & ~kEval);
+    if ((meta & kEval) != 0 && lane < kNumSums) {
+        const int n_t = fd->N > 0 ? (fd->N + a.tile - 1) / a.tile : 1;
+        const float* src = a.partial + ((size_t)first * a.tiles_per_item * kHypTile + h) * kAcc + lane;
+        double sum = 0.0;
+        for (int c = 0; c < 8; ++c) {
+            double part = 0.0;
+            for (int t = c; t < n_t; t += 8) part += (double)__ldcg(src + (size_t)t * kHypTile * kAcc);
+            sum += part;
+        }
+        E[lane] = sum;
+    }
+    __syncwarp();
+    HypState& st = a.state[hyp];
+    lm_update(st, k == 0 ? kEpiInit : kEpiStep, k < iters, a.damping_mode, fd->prior, E, W, a.min_valid[frame],
+              a.pose32 + 12 * (size_t)job, nullptr, lane);
+    if (lane == 0) a.job_meta[job] = (unsigned)hyp | (st.has_cand ? kEval : 0u);
+    __syncwarp();
+}
+
+template <pilot_dtype DT, int C, bool SCALED, bool CONF, bool FLOW>
 __global__ void __launch_bounds__(kBuildThreads, 2)
-level_persistent_kernel(const LevelArgs a) {
+level_persistent_kernel(const __grid_constant__ LevelArgs a) {
     constexpr int kWarps = kBuildThreads / 32;
     constexpr unsigned kEval = 0x80000000u;          // job_meta: "has a pose to evaluate" bit
     __shared__ float red[kWarps][kHypTile][kAcc];
@@ -92,7 +123,7 @@ level_persistent_kernel(const LevelArgs a) {
     __shared__ int s_frame, s_level, s_job, s_njobs, s_first, s_t0, s_t1, s_run;
     // CTA-uniform loop state, kept here and read where it is used: held in registers it would
     // live through the anchor loop and push the loop's own values into local memory
-    __shared__ int s_nfr, s_items, s_jobs, s_IA, s_JA, s_flow, s_k, s_ipj, s_last;
+    __shared__ int s_nfr, s_items, s_jobs, s_IA, s_JA, s_k, s_ipj, s_last;
     __shared__ unsigned long long s_base;
     // frame tables, staged when the launch lists few frames
     __shared__ int s_fitem[kSmemFrames + 1], s_fjob[kSmemFrames + 1], s_flist[kSmemFrames], s_fipj[kSmemFrames];
@@ -148,41 +179,6 @@ level_persistent_kernel(const LevelArgs a) {
         a.job_meta[job] = (unsigned)hyp | kEval;
     }
     if (!grid_sync(a.sync, a.error, gen, a.barrier_timeout_ns, a.barrier_extra)) return;
-    // The jobs are split into two halves at a job-tile boundary near the middle of the items:
-    // A = jobs [0, JA) with items [0, IA), B = the rest.  Each phase gathers one half while
-    // the FP64 steps of the other half (for the iteration it gathered in the previous phase)
-    // run on their warps, so the steps overlap gathers:
-    //   phase 0: gather A(0);  phase 2k+1: gather B(k), step A(k);  phase 2k+2: gather A(k+1),
-    //   step B(k);  ...  the last phase steps B(k_max).  A grid barrier ends every phase.
-    // Each job's records and FP64 step are those of the lockstep schedule, so the results are
-    // unchanged; only the order in which the GPU runs them differs.
-    // The split pays when the gathers of a half outlast an FP64 step and a half's steps
-    // occupy only part of the warps; when the steps dominate (few anchors per hypothesis,
-    // e.g. the paper's 500-anchor schedule) it would put two step latencies in every
-    // iteration, so it is only made for at least kSplitUnits anchor-hypothesis units per
-    // iteration and at most one job per warp.
-    if (tid == 0) {
-        const int n_items = s_items, n_jobs = s_jobs;
-        int IA = n_items, JA = n_jobs;
-        const int target = (n_items + 1) / 2;
-        long long units = 0;
-        for (int i = 0; i < s_nfr; ++i) units += (long long)a.frames[flist(i)].N * (fjob(i + 1) - fjob(i));
-        // gather-heavy levels take the schedule without grid barriers (below)
-        s_flow = units >= kSplitUnits && a.tile_done != nullptr;
-        if (target < n_items && units >= kSplitUnits && n_jobs <= (int)gridDim.x * kWarps) {
-            const int i = find(true, target);
-            const int ipj = fipj(i);
-            const int jt = (target - fitem(i) + ipj - 1) / ipj;    // round up to a job tile
-            IA = fitem(i) + jt * ipj;
-            JA = min(fjob(i) + jt * kHypTile, fjob(i + 1));
-        }
-        s_IA = IA;
-        s_JA = JA;
-        // claims made before the current phase: a gathering phase takes one claim per item of
-        // its half plus one unsuccessful claim per CTA
-        s_base = 0;
-    }
-    __syncthreads();
     // Gather-heavy levels: the work items of every (iteration, job tile) are claimed in
     // iteration-major order from one counter and no grid barrier is taken.  The CTA that
     // completes a job tile's items of iteration k (counted in tile_done) runs the tile's FP64
@@ -193,7 +189,7 @@ level_persistent_kernel(const LevelArgs a) {
     // was claimed before it and is finished or held by a CTA that is working, not waiting (all
     // CTAs are resident).  Items of iterations beyond a frame's count are claimed and skipped
     // and touch no flag.
-    if (s_flow) {
+    if constexpr (FLOW) {
         for (;;) {
             if (tid == 0) {
                 const long long g = (long long)atomicAdd(a.sync, 1ull);
@@ -280,16 +276,51 @@ level_persistent_kernel(const LevelArgs a) {
             }
             __syncthreads();
             if (s_last) {
-                if (warp < s_njobs) {
-                    const int job = s_job + warp;
-                    const FrameDesc* fd = a.frames + s_frame;
-                    const int iters = a.iters[s_level];
+                if (warp < s_njobs) flow_step(a, s_job + warp, s_first, s_frame, s_level, s_k, warp, E[warp], Wsh[warp]);
+                __syncthreads();
+                if (tid == 0) {
+                    __threadfence();
+                    st_release_gpu(a.tile_ready + s_first, (unsigned)s_k + 1u);
+                }
+            }
+            __syncthreads();               // the shared item state is rewritten by the next claim
+        }
+    } else {
+        // Lockstep phases (levels below kSplitUnits units per iteration, which the host does not
+        // give the flags of the schedule above): phase 2k gathers every job's items of
+        // iteration k, phase 2k + 1 steps every job (iteration k), a grid barrier ending each
+        // phase.  The loop is written for two halves A = jobs [0, JA) with items [0, IA) and B
+        // = the rest, stepping one half while the other gathers; here A is every job and B
+        // none, so B's gathers and steps are empty.
+        if (tid == 0) {
+            s_IA = s_items;
+            s_JA = s_jobs;
+            // claims made before the current phase: a gathering phase takes one claim per item of
+            // its half plus one unsuccessful claim per CTA
+            s_base = 0;
+        }
+        __syncthreads();
+        for (int ph = 0; ph <= 2 * a.k_max + 2; ++ph) {
+            // FP64 steps of the half gathered in the previous phase: job j on global warp j (mod
+            // the warp count), all 32 lanes
+            if (ph >= 1) {
+                const int k = (ph - 1) / 2;
+                const int jlo = (ph & 1) ? 0 : s_JA, jhi = (ph & 1) ? s_JA : s_jobs;
+                for (int job = jlo + blockIdx.x * kWarps + warp; job < jhi; job += gridDim.x * kWarps) {
+                    const int i = find(false, job);
+                    const int f = flist(i);
+                    const FrameDesc* fd = a.frames + f;
+                    const int level = a.level >= 0 ? a.level : fd->level;
+                    const int iters = a.iters[level];
+                    if (k > iters) continue;
                     const unsigned meta = __ldcg(a.job_meta + job);
                     const int hyp = (int)(meta & ~kEval);
                     const bool evaluated = (meta & kEval) != 0;
                     if (evaluated && lane < kNumSums) {
                         const int n_t = fd->N > 0 ? (fd->N + a.tile - 1) / a.tile : 1;
-                        const float* src = a.partial + ((size_t)s_first * tpi * kHypTile + warp) * kAcc + lane;
+                        const int jl = job - fjob(i);
+                        const int first = fitem(i) + (jl / kHypTile) * fipj(i);
+                        const float* src = a.partial + ((size_t)first * tpi * kHypTile + jl % kHypTile) * kAcc + lane;
                         double sum = 0.0;
                         for (int c = 0; c < 8; ++c) {
                             double part = 0.0;
@@ -300,137 +331,101 @@ level_persistent_kernel(const LevelArgs a) {
                     }
                     __syncwarp();
                     HypState& st = a.state[hyp];
-                    lm_update(st, s_k == 0 ? kEpiInit : kEpiStep, s_k < iters, a.damping_mode, fd->prior, E[warp],
-                              Wsh[warp], a.min_valid[s_frame], a.pose32 + 12 * (size_t)job, nullptr, lane);
+                    lm_update(st, k == 0 ? kEpiInit : kEpiStep, k < iters, a.damping_mode, fd->prior, E[warp], Wsh[warp],
+                              a.min_valid[f], a.pose32 + 12 * (size_t)job, nullptr, lane);
                     if (lane == 0) a.job_meta[job] = (unsigned)hyp | (st.has_cand ? kEval : 0u);
                     __syncwarp();
                 }
-                __syncthreads();
-                if (tid == 0) {
-                    __threadfence();
-                    st_release_gpu(a.tile_ready + s_first, (unsigned)s_k + 1u);
-                }
             }
-            __syncthreads();               // the shared item state is rewritten by the next claim
+            // gathers of one half at iteration k, its work items claimed one at a time
+            if (ph <= 2 * a.k_max + 1) {
+                for (;;) {
+                    if (tid == 0) {
+                        const int k = ph / 2;
+                        const int ilo = (ph & 1) ? s_IA : 0, ihi = (ph & 1) ? s_items : s_IA;
+                        long long item = ilo + (long long)(atomicAdd(a.sync, 1ull) - s_base);
+                        if (item < ilo) {              // cannot happen: the counts above are exact
+                            atomicExch(a.error, 1u);
+                            item = ihi;
+                        }
+                        s_item = item < ihi ? item : -1;
+                        if (item < ihi) {
+                            const int i = find(true, item);
+                            const int ipj = fipj(i);
+                            const int local = (int)(item - fitem(i));
+                            const int jt = local / ipj;      // job tile within the frame
+                            const FrameDesc* fd = a.frames + flist(i);
+                            const int level = a.level >= 0 ? a.level : fd->level;
+                            s_job = fjob(i) + kHypTile * jt;
+                            s_njobs = min(kHypTile, fjob(i + 1) - s_job);
+                            s_first = fitem(i) + jt * ipj;
+                            s_t0 = (local - jt * ipj) * tpi;
+                            s_t1 = min(s_t0 + tpi, fd->N > 0 ? (fd->N + a.tile - 1) / a.tile : 1);
+                            s_run = k <= a.iters[level];
+                            s_frame = flist(i);
+                            s_level = level;
+                        }
+                    }
+                    __syncthreads();
+                    if (s_item < 0) break;
+                    if (tid < 12 * kHypTile) {
+                        const int h = tid / 12;
+                        pose[h][tid % 12] = __ldcg(a.pose32 + 12 * (size_t)(s_job + (h < s_njobs ? h : 0)) + tid % 12);
+                    }
+                    if (tid < kHypTile) s_meta[tid] = tid < s_njobs ? __ldcg(a.job_meta + s_job + tid) : 0u;
+                    __syncthreads();
+                    SlotPoses sp;
+                    bool any = false;
+    #pragma unroll
+                    for (int h = 0; h < kHypTile; ++h) {
+                        sp.p[h] = pose[h];
+                        sp.act[h] = (s_meta[h] & kEval) != 0;
+                        any = any || sp.act[h];
+                    }
+                    if (s_run && any) {
+                        const FrameDesc* fd = a.frames + s_frame;
+                        const int level = s_level;
+                        const LevelView v{fd->px, fd->py, fd->pz, fd->weight, fd->valid, fd->qry[level], fd->ref[level],
+                                          fd->qscale[level], fd->rscale[level], fd->conf[level], fd->H[level],
+                                          fd->W[level], fd->fx[level], fd->fy[level], fd->cx[level], fd->cy[level],
+                                          a.huber};
+                        for (int t = s_t0; t < s_t1; ++t) {
+                            float acc[kNumSums];
+    #pragma unroll
+                            for (int i = 0; i < kNumSums; ++i) acc[i] = 0.f;
+                            const int j0 = t * a.tile;
+                            // no anchor prefetch for the narrow types: the frame's level inputs
+                            // already take the registers that kernel parameters cost the plain form
+                            accumulate_anchors<DT, C, SCALED, CONF, kBuildThreads, DT == PILOT_F32>(
+                                v, sp, j0, min(j0 + a.tile, fd->N), acc);
+                            const float val = cta_reduce_slots<kBuildThreads, GroupShape<DT, C, SCALED>::APB>(acc, red);
+                            if (tid < kHypTile * kAcc && tid / kAcc < s_njobs)
+                                a.partial[(((size_t)s_first * tpi + t) * kHypTile + tid / kAcc) * kAcc + tid % kAcc] =
+                                    val;
+                            // the next tile's reduction reuses red: wait until every slot's sums are read
+                            if (t + 1 < s_t1) __syncthreads();
+                        }
+                    }
+                    __syncthreads();
+                }
+                if (tid == 0) s_base += (unsigned long long)((ph & 1) ? s_items - s_IA : s_IA) + gridDim.x;
+            }
+            if (!grid_sync(a.sync, a.error, gen, a.barrier_timeout_ns, a.barrier_extra)) return;
         }
     }
-    for (int ph = 0; ph <= 2 * a.k_max + 2; ++ph) {
-        // FP64 steps of the half gathered in the previous phase: job j on global warp j (mod
-        // the warp count), all 32 lanes
-        if (ph >= 1) {
-            const int k = (ph - 1) / 2;
-            const int jlo = (ph & 1) ? 0 : s_JA, jhi = (ph & 1) ? s_JA : s_jobs;
-            for (int job = jlo + blockIdx.x * kWarps + warp; job < jhi; job += gridDim.x * kWarps) {
-                const int i = find(false, job);
-                const int f = flist(i);
-                const FrameDesc* fd = a.frames + f;
-                const int level = a.level >= 0 ? a.level : fd->level;
-                const int iters = a.iters[level];
-                if (k > iters) continue;
-                const unsigned meta = __ldcg(a.job_meta + job);
-                const int hyp = (int)(meta & ~kEval);
-                const bool evaluated = (meta & kEval) != 0;
-                if (evaluated && lane < kNumSums) {
-                    const int n_t = fd->N > 0 ? (fd->N + a.tile - 1) / a.tile : 1;
-                    const int jl = job - fjob(i);
-                    const int first = fitem(i) + (jl / kHypTile) * fipj(i);
-                    const float* src = a.partial + ((size_t)first * tpi * kHypTile + jl % kHypTile) * kAcc + lane;
-                    double sum = 0.0;
-                    for (int c = 0; c < 8; ++c) {
-                        double part = 0.0;
-                        for (int t = c; t < n_t; t += 8) part += (double)__ldcg(src + (size_t)t * kHypTile * kAcc);
-                        sum += part;
-                    }
-                    E[warp][lane] = sum;
-                }
-                __syncwarp();
-                HypState& st = a.state[hyp];
-                lm_update(st, k == 0 ? kEpiInit : kEpiStep, k < iters, a.damping_mode, fd->prior, E[warp], Wsh[warp],
-                          a.min_valid[f], a.pose32 + 12 * (size_t)job, nullptr, lane);
-                if (lane == 0) a.job_meta[job] = (unsigned)hyp | (st.has_cand ? kEval : 0u);
-                __syncwarp();
-            }
-        }
-        // gathers of one half at iteration k, its work items claimed one at a time
-        if (ph <= 2 * a.k_max + 1) {
-            for (;;) {
-                if (tid == 0) {
-                    const int k = ph / 2;
-                    const int ilo = (ph & 1) ? s_IA : 0, ihi = (ph & 1) ? s_items : s_IA;
-                    long long item = ilo + (long long)(atomicAdd(a.sync, 1ull) - s_base);
-                    if (item < ilo) {              // cannot happen: the counts above are exact
-                        atomicExch(a.error, 1u);
-                        item = ihi;
-                    }
-                    s_item = item < ihi ? item : -1;
-                    if (item < ihi) {
-                        const int i = find(true, item);
-                        const int ipj = fipj(i);
-                        const int local = (int)(item - fitem(i));
-                        const int jt = local / ipj;      // job tile within the frame
-                        const FrameDesc* fd = a.frames + flist(i);
-                        const int level = a.level >= 0 ? a.level : fd->level;
-                        s_job = fjob(i) + kHypTile * jt;
-                        s_njobs = min(kHypTile, fjob(i + 1) - s_job);
-                        s_first = fitem(i) + jt * ipj;
-                        s_t0 = (local - jt * ipj) * tpi;
-                        s_t1 = min(s_t0 + tpi, fd->N > 0 ? (fd->N + a.tile - 1) / a.tile : 1);
-                        s_run = k <= a.iters[level];
-                        s_frame = flist(i);
-                        s_level = level;
-                    }
-                }
-                __syncthreads();
-                if (s_item < 0) break;
-                if (tid < 12 * kHypTile) {
-                    const int h = tid / 12;
-                    pose[h][tid % 12] = __ldcg(a.pose32 + 12 * (size_t)(s_job + (h < s_njobs ? h : 0)) + tid % 12);
-                }
-                if (tid < kHypTile) s_meta[tid] = tid < s_njobs ? __ldcg(a.job_meta + s_job + tid) : 0u;
-                __syncthreads();
-                SlotPoses sp;
-                bool any = false;
-#pragma unroll
-                for (int h = 0; h < kHypTile; ++h) {
-                    sp.p[h] = pose[h];
-                    sp.act[h] = (s_meta[h] & kEval) != 0;
-                    any = any || sp.act[h];
-                }
-                if (s_run && any) {
-                    const FrameDesc* fd = a.frames + s_frame;
-                    const int level = s_level;
-                    const LevelView v{fd->px, fd->py, fd->pz, fd->weight, fd->valid, fd->qry[level], fd->ref[level],
-                                      fd->qscale[level], fd->rscale[level], fd->conf[level], fd->H[level],
-                                      fd->W[level], fd->fx[level], fd->fy[level], fd->cx[level], fd->cy[level],
-                                      a.huber};
-                    for (int t = s_t0; t < s_t1; ++t) {
-                        float acc[kNumSums];
-#pragma unroll
-                        for (int i = 0; i < kNumSums; ++i) acc[i] = 0.f;
-                        const int j0 = t * a.tile;
-                        // no anchor prefetch for the narrow types: the frame's level inputs
-                        // already take the registers that kernel parameters cost the plain form
-                        accumulate_anchors<DT, C, SCALED, CONF, kBuildThreads, DT == PILOT_F32>(
-                            v, sp, j0, min(j0 + a.tile, fd->N), acc);
-                        const float val = cta_reduce_slots<kBuildThreads, GroupShape<DT, C, SCALED>::APB>(acc, red);
-                        if (tid < kHypTile * kAcc && tid / kAcc < s_njobs)
-                            a.partial[(((size_t)s_first * tpi + t) * kHypTile + tid / kAcc) * kAcc + tid % kAcc] =
-                                val;
-                        // the next tile's reduction reuses red: wait until every slot's sums are read
-                        if (t + 1 < s_t1) __syncthreads();
-                    }
-                }
-                __syncthreads();
-            }
-            if (tid == 0) s_base += (unsigned long long)((ph & 1) ? s_items - s_IA : s_IA) + gridDim.x;
-        }
-        if (!grid_sync(a.sync, a.error, gen, a.barrier_timeout_ns, a.barrier_extra)) return;
-    }
+}
+
+// With per-job-tile flags (a.tile_done) the schedule without grid barriers, else lockstep.
+template <pilot_dtype DT, int C, bool SCALED, bool CONF>
+cudaError_t launch_level_kernel(const cudaLaunchConfig_t& cfg, const LevelArgs& a) {
+    return a.tile_done ? cudaLaunchKernelEx(&cfg, level_persistent_kernel<DT, C, SCALED, CONF, true>, a)
+                       : cudaLaunchKernelEx(&cfg, level_persistent_kernel<DT, C, SCALED, CONF, false>, a);
 }
 
 template <pilot_dtype DT, int C>
 cudaError_t launch_level_persistent_typed(int variant, const LevelArgs& a, int grid, cudaStream_t s) {
-    // cooperative: the grid barrier needs every CTA resident at once
+    // cooperative: every CTA resident at once (the lockstep schedule's grid barriers, the
+    // other schedule's waits on flags set by other CTAs)
     cudaLaunchConfig_t cfg{};
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeCooperative;
@@ -442,11 +437,10 @@ cudaError_t launch_level_persistent_typed(int variant, const LevelArgs& a, int g
     cfg.attrs = attr;
     cfg.numAttrs = 1;
     switch (variant) {
-        case 0: return cudaLaunchKernelEx(&cfg, level_persistent_kernel<DT, C, false, false>, a);
-        case kVariantScaled: return cudaLaunchKernelEx(&cfg, level_persistent_kernel<DT, C, true, false>, a);
-        case kVariantConf: return cudaLaunchKernelEx(&cfg, level_persistent_kernel<DT, C, false, true>, a);
-        case kVariantScaled | kVariantConf:
-            return cudaLaunchKernelEx(&cfg, level_persistent_kernel<DT, C, true, true>, a);
+        case 0: return launch_level_kernel<DT, C, false, false>(cfg, a);
+        case kVariantScaled: return launch_level_kernel<DT, C, true, false>(cfg, a);
+        case kVariantConf: return launch_level_kernel<DT, C, false, true>(cfg, a);
+        case kVariantScaled | kVariantConf: return launch_level_kernel<DT, C, true, true>(cfg, a);
         default: return cudaErrorInvalidValue;
     }
 }
@@ -464,20 +458,26 @@ cudaError_t launch_level_persistent_dtype(int C, int variant, const LevelArgs& a
     }
 }
 
+// CTAs per SM that both schedules' kernels can keep resident.
+template <pilot_dtype DT, int C, bool SCALED, bool CONF>
+cudaError_t occupancy_both(int* n) {
+    int n0 = 0, n1 = 0;
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+        &n0, level_persistent_kernel<DT, C, SCALED, CONF, false>, kBuildThreads, 0);
+    if (e == cudaSuccess)
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n1, level_persistent_kernel<DT, C, SCALED, CONF, true>,
+                                                          kBuildThreads, 0);
+    *n = n0 < n1 ? n0 : n1;
+    return e;
+}
+
 template <pilot_dtype DT, int C>
 cudaError_t occupancy_typed(int variant, int* n) {
     switch (variant) {
-        case 0: return cudaOccupancyMaxActiveBlocksPerMultiprocessor(n, level_persistent_kernel<DT, C, false, false>,
-                                                                     kBuildThreads, 0);
-        case kVariantScaled:
-            return cudaOccupancyMaxActiveBlocksPerMultiprocessor(n, level_persistent_kernel<DT, C, true, false>,
-                                                                 kBuildThreads, 0);
-        case kVariantConf:
-            return cudaOccupancyMaxActiveBlocksPerMultiprocessor(n, level_persistent_kernel<DT, C, false, true>,
-                                                                 kBuildThreads, 0);
-        case kVariantScaled | kVariantConf:
-            return cudaOccupancyMaxActiveBlocksPerMultiprocessor(n, level_persistent_kernel<DT, C, true, true>,
-                                                                 kBuildThreads, 0);
+        case 0: return occupancy_both<DT, C, false, false>(n);
+        case kVariantScaled: return occupancy_both<DT, C, true, false>(n);
+        case kVariantConf: return occupancy_both<DT, C, false, true>(n);
+        case kVariantScaled | kVariantConf: return occupancy_both<DT, C, true, true>(n);
         default: return cudaErrorInvalidValue;
     }
 }

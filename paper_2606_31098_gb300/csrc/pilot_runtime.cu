@@ -595,15 +595,16 @@ cudaError_t level_occupancy_query(pilot_dtype dt, int C, int variant, int* n) {
 
 namespace {
 
-long long graph_key(pilot_dtype dt, int C, int variant, int L, const pilot_schedule& sc) {
+// flow_mask bit l: level l runs the level kernel's schedule without grid barriers
+long long graph_key(pilot_dtype dt, int C, int variant, int L, const pilot_schedule& sc, int flow_mask) {
     return ((long long)dt << 44) | ((long long)C << 36) | ((long long)variant << 32) | ((long long)L << 28) |
-           ((long long)sc.tile << 8) | (long long)sc.ctas_per_sm;
+           ((long long)flow_mask << 22) | ((long long)sc.tile << 8) | (long long)sc.ctas_per_sm;
 }
 
 // Records the whole batched solve on h->bstream: descriptor upload, per-frame set-up,
 // one persistent launch per level (+ per-frame top-K), selection, result download.
 pilot_status capture_batch_graph(pilot_align_handle* h, pilot_dtype dt, int C, int variant, int L,
-                                 const pilot_schedule& sc) {
+                                 const pilot_schedule& sc, int flow_mask) {
     const pilot_align_config& c = h->cfg;
     const BatchLayout lay = BatchLayout::make(c.max_frames, c.max_hyps);
     int dev = 0, sms = 0, per_sm = 0;
@@ -648,8 +649,10 @@ pilot_status capture_batch_graph(pilot_align_handle* h, pilot_dtype dt, int C, i
         a.job_meta = h->bjob_meta;
         a.partial = h->partial;
         a.sync = h->bsync + (size_t)level * kSyncWords;
-        a.tile_done = h->bflags;
-        a.tile_ready = h->bflags + h->bflag_words;
+        // gather-heavy levels: the schedule without grid barriers (its per-job-tile flags)
+        const bool flow = (flow_mask >> level) & 1;
+        a.tile_done = flow ? h->bflags : nullptr;
+        a.tile_ready = flow ? h->bflags + h->bflag_words : nullptr;
         a.error = error;
         a.barrier_timeout_ns = kBarrierTimeoutNs;
         a.barrier_extra = 0;
@@ -662,7 +665,7 @@ pilot_status capture_batch_graph(pilot_align_handle* h, pilot_dtype dt, int C, i
         a.damping_mode = c.damping_mode;
         a.huber = (float)c.huber_photo;
         a.lambda0 = c.lambda0;
-        e = cudaMemsetAsync(h->bflags, 0, sizeof(unsigned) * 2 * h->bflag_words, s);
+        if (flow) e = cudaMemsetAsync(h->bflags, 0, sizeof(unsigned) * 2 * h->bflag_words, s);
         if (e == cudaSuccess) e = launch_level(dt, C, variant, a, h->level_grid, s);
         const int K = c.keep_top_k[level];
         if (e == cudaSuccess && level > 0 && K > 0)
@@ -681,7 +684,7 @@ pilot_status capture_batch_graph(pilot_align_handle* h, pilot_dtype dt, int C, i
     if (e2 != cudaSuccess) return cuda_fail(e2, "graph capture end");
     h->graph = g;
     PILOT_CUDA(cudaGraphInstantiate(&h->gexec, g, 0), "graph instantiate");
-    h->graph_key = graph_key(dt, C, variant, L, sc);
+    h->graph_key = graph_key(dt, C, variant, L, sc, flow_mask);
     return PILOT_OK;
 }
 
@@ -1065,6 +1068,7 @@ pilot_status pilot_align_solve_batch(pilot_align_handle* h, const pilot_frame* f
     const int tpi = tiles_per_item(sc.tile);
     std::vector<long long> hyp_iters(n, 0);
     std::vector<int> cur(n);
+    int flow_mask = 0;     // levels that run without grid barriers
     for (int i = 0; i < n; ++i) cur[i] = frames[i].M;
     for (int level = L - 1; level >= 0; --level) {
         int* list = fr_list + (size_t)level * lay.max_frames;
@@ -1079,15 +1083,18 @@ pilot_status pilot_align_solve_batch(pilot_align_handle* h, const pilot_frame* f
             items[oi + 1] = items[oi] + frame_items(cur[i], frames[i].N, sc.tile, tpi);
         }
         hdr->n_listed[level] = n;
+        long long units = 0;       // anchor x hypothesis units of one iteration of this level
+        for (int i = 0; i < n; ++i) units += (long long)frames[i].N * cur[i];
+        if (units >= kSplitUnits) flow_mask |= 1 << level;
         for (int i = 0; i < n; ++i) {
             hyp_iters[i] += (long long)cur[i] * c.iters_per_level[level];
             const int K = c.keep_top_k[level];
             if (level > 0 && K > 0 && K < cur[i]) cur[i] = K;
         }
     }
-    const long long key = graph_key(f0.feat_dtype, f0.C, variant, L, sc);
+    const long long key = graph_key(f0.feat_dtype, f0.C, variant, L, sc, flow_mask);
     if (!h->gexec || h->graph_key != key)
-        if ((st = capture_batch_graph(h, f0.feat_dtype, f0.C, variant, L, sc)) != PILOT_OK) return st;
+        if ((st = capture_batch_graph(h, f0.feat_dtype, f0.C, variant, L, sc, flow_mask)) != PILOT_OK) return st;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     PILOT_CUDA(cudaGraphLaunch(h->gexec, s), "batch graph launch");
     PILOT_CUDA(cudaStreamSynchronize(s), "batch solve");
