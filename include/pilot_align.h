@@ -203,17 +203,20 @@ pilot_status pilot_align_get_schedule(const pilot_align_handle* h, const pilot_f
 
 /* Batched form: solve n_frames independent frames (uneven N, M, map sizes, intrinsics,
  * priors) in one pass per pyramid level.  Each level is one persistent cooperative launch
- * that runs the level's LM iterations in lockstep over all (frame, hypothesis) jobs: per
- * iteration its CTAs claim work items (runs of anchor tiles of one job, frames with more
- * anchors first unless the schedule says otherwise) from one counter, then, after a grid
- * barrier, every job's FP64 step runs on one warp lane.  The launches, the per-frame top-K
+ * that runs the level's LM iterations over all (frame, hypothesis) jobs; its CTAs claim work
+ * items (runs of anchor tiles of one tile of jobs, frames with more anchors first unless the
+ * schedule says otherwise) from one counter.  A level with at least 2^23 anchor x hypothesis
+ * units per iteration takes the items of all iterations in iteration-major order without grid
+ * barriers: the CTA that completes a job tile's iteration runs its FP64 steps (one warp per
+ * job) and releases the tile's next iteration.  A smaller level runs in lockstep: every item
+ * of an iteration, a grid barrier, every job's FP64 step on one warp.  The launches, the per-frame top-K
  * and the selection are replayed from a CUDA graph captured on the first call (and again
  * when the storage type, C, L or schedule changes).
  * Requirements: every frame is a DEVICE frame; all frames share C, L, feat_dtype, the
  * presence of per-channel scales and of query confidence maps (each given on every level
  * or on none); n_frames <= max_frames; the hypotheses of all frames
- * together <= max_hyps, at most 8192 per frame.  PILOT_ETIMEOUT if a grid barrier wait
- * gave up (only when the device could not keep every CTA resident; results are then
+ * together <= max_hyps, at most 8192 per frame.  PILOT_ETIMEOUT if a grid barrier or flag
+ * wait gave up (only when the device could not keep every CTA resident; results are then
  * invalid).  results[i] receives frame i's outputs
  * exactly as pilot_align_solve would: with the same tile (both untuned, or tuned alike)
  * the reduction order is the same, so each frame's outputs are bitwise those of its own

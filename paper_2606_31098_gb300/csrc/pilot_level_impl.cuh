@@ -63,19 +63,18 @@ __device__ __forceinline__ bool grid_sync(unsigned long long* sync, unsigned* er
     return s_ok != 0;
 }
 
-// Batched form: one persistent (cooperative) launch per level for a whole batch of frames.
-// The level's LM iterations run in step over all jobs (a job = one hypothesis of one frame),
-// in two halves offset by half an iteration (see the phase loop).  For iteration k of a half,
-// the CTAs claim its work items (runs of up to tiles_per_item consecutive anchor tiles of one
-// tile of kHypTile jobs of a frame, the hypotheses a plain form's CTA holds) from one counter
-// and write each tile's FP32 records exactly as build_fused_kernel does (same thread mapping,
-// same sums); in the next phase, while the other half gathers, each of its jobs' FP64 step
-// runs on one warp (all lanes), on the tile records summed in the plain form's 8-chain FP64
-// order, and writes the job's next candidate.  A frame's result is therefore bitwise the one
-// its plain solve gives, whatever else is in the batch; the items balance the gathers over
-// all CTAs, and the FP64 steps of half the jobs run at once, one per warp, beside the other
-// half's gathers.  Tile t of job kHypTile p + h, whose job tile's first item is q, keeps its
-// record at partial[(q tiles_per_item + t) kHypTile + h].
+// Batched and served forms: one persistent (cooperative) launch per level for a whole batch
+// of frames, running the level's LM iterations over all jobs (a job = one hypothesis of one
+// frame).  The CTAs claim work items (runs of up to tiles_per_item consecutive anchor tiles of
+// one tile of kHypTile jobs of a frame, the hypotheses a plain form's CTA holds) from one
+// counter and write each tile's FP32 records exactly as build_fused_kernel does (same thread
+// mapping, same sums); each job's FP64 step runs on one warp (all lanes), on the tile records
+// summed in the plain form's 8-chain FP64 order, and writes the job's next candidate.  A
+// frame's result is therefore bitwise the one its plain solve gives, whatever else is in the
+// batch.  FLOW selects the schedule: without grid barriers (the items of all iterations in
+// iteration-major order, per-job-tile flags) or lockstep phases (below).  Tile t of job
+// kHypTile p + h, whose job tile's first item is q, keeps its record at
+// partial[(q tiles_per_item + t) kHypTile + h].
 // One job's FP64 step in the schedule without grid barriers: its tile records (slot h of the
 // job tile whose first item is `first`) summed in the plain form's 8-chain FP64 order, then
 // lm_update; all 32 lanes of one warp.  Not inlined: the item loop that calls it keeps its own
