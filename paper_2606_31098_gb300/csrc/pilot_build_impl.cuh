@@ -292,8 +292,10 @@ __device__ __forceinline__ void record_partials(const typename Storage<DT>::T* t
 // thread of the CTA calls it with the same arguments; threads are grouped as described at
 // the top of the file.
 // PREFETCH: read the next batch's anchor coordinates one batch ahead (four more registers
-// through the loop; the sums are the same either way).
-template <pilot_dtype DT, int C, bool SCALED, bool CONF, int NTHREADS, bool PREFETCH = true>
+// through the loop; the sums are the same either way).  FRESH_TID: read the thread index
+// through a volatile move, so that the lane layout derived from it is recomputed at each call
+// instead of being hoisted into an enclosing loop and held across that loop's function calls.
+template <pilot_dtype DT, int C, bool SCALED, bool CONF, int NTHREADS, bool PREFETCH = true, bool FRESH_TID = false>
 __device__ __forceinline__ void accumulate_anchors(const LevelView& v, const SlotPoses& sp, int j_begin, int j_end,
                                                    float* acc) {
     using Elem = typename Storage<DT>::T;
@@ -303,7 +305,8 @@ __device__ __forceinline__ void accumulate_anchors(const LevelView& v, const Slo
     constexpr int ASTEP = NTHREADS / (LP * NS) * APB;   // anchors per CTA batch
     static_assert(C % 4 == 0 && C >= 4 && C <= 64 && LP >= 1 && LP <= 8, "channels");
 
-    const int tid = threadIdx.x;
+    int tid = threadIdx.x;
+    if constexpr (FRESH_TID) asm volatile("mov.u32 %0, %%tid.x;" : "=r"(tid));
     const int lane = tid & 31;
     const int q = lane & (LP - 1);
     const int slot = (lane / APB) % kHypTile;        // this lane's hypothesis slot

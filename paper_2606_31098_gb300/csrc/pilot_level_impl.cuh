@@ -257,7 +257,7 @@ level_persistent_kernel(const __grid_constant__ LevelArgs a) {
 #pragma unroll
                     for (int i = 0; i < kNumSums; ++i) acc[i] = 0.f;
                     const int j0 = t * a.tile;
-                    accumulate_anchors<DT, C, SCALED, CONF, kBuildThreads, DT == PILOT_F32>(
+                    accumulate_anchors<DT, C, SCALED, CONF, kBuildThreads, DT == PILOT_F32, true>(
                         v, sp, j0, min(j0 + a.tile, fd->N), acc);
                     const float val = cta_reduce_slots<kBuildThreads, GroupShape<DT, C, SCALED>::APB>(acc, red);
                     if (tid < kHypTile * kAcc && tid / kAcc < s_njobs)
