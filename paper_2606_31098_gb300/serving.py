@@ -33,7 +33,7 @@ class StreamState:
     sensors: list                      # per frame (gravity in the camera frame, laser range)
     arrivals: np.ndarray               # arrival time of each frame, seconds from the start
     estimate: np.ndarray               # latest estimate (world); the first frame starts from its truth
-    next_t: int = 0
+    next_t: int = 0                    # first frame not yet accounted for (completed, dropped or failed)
     in_flight: tuple | None = None     # (ticket, t, arrival, keep-alive)
     done: list = field(default_factory=list)
 
@@ -159,7 +159,10 @@ class StreamClient:
                 prepared = self.prepare_batch(due)
                 prep_s += time.perf_counter() - tp
                 for (sid, st, k), prep in zip(due, prepared):
-                    dropped += k - st.next_t        # frames next_t .. k - 1 (any older prepared one among them)
+                    # frames next_t .. k - 1 are dropped (among them a prepared frame that was
+                    # waiting for admission); frame k is accounted for from here on
+                    dropped += k - st.next_t
+                    st.next_t = k
                     if prep is None:
                         crop_failed += 1
                         st.next_t = k + 1
