@@ -206,7 +206,7 @@ pilot_status pilot_align_get_schedule(const pilot_align_handle* h, const pilot_f
  * that runs the level's LM iterations over all (frame, hypothesis) jobs; its CTAs claim work
  * items (runs of anchor tiles of one tile of jobs, frames with more anchors first unless the
  * schedule says otherwise) from one counter.  A level with at least 2^23 anchor x hypothesis
- * units per iteration takes the items of all iterations in iteration-major order without grid
+ * units per iteration, or 4096 anchors per job on average, takes the items of all iterations in iteration-major order without grid
  * barriers: the CTA that completes a job tile's iteration runs its FP64 steps (one warp per
  * job) and releases the tile's next iteration.  A smaller level runs in lockstep: every item
  * of an iteration, a grid barrier, every job's FP64 step on one warp.  The launches, the per-frame top-K

@@ -25,7 +25,7 @@ constexpr int kSyncWords = 4;      // per persistent level launch: claims, arriv
 constexpr int kItemAnchors = 4096; // persistent level kernel: anchors per work item (whole tiles)
 constexpr int kMaxFrameHyps = 8192; // batched and served forms: hypotheses of one frame at most
 constexpr int kSmemFrames = 512;   // persistent level kernel: frame tables staged in shared memory up to this
-constexpr long long kSplitUnits = 8ll << 20;   // batched levels with at least this many anchor x hypothesis units per iteration run without grid barriers
+constexpr long long kSplitUnits = 8ll << 20;   // batched levels with at least this many anchor x hypothesis units per iteration (or kItemAnchors anchors per job) run without grid barriers
 
 // Tiles per work item of the persistent level kernel for a reduction tile of `tile` anchors.
 __host__ __device__ inline int tiles_per_item(int tile) { return tile >= kItemAnchors ? 1 : kItemAnchors / tile; }

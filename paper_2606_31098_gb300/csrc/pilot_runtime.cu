@@ -1083,9 +1083,16 @@ pilot_status pilot_align_solve_batch(pilot_align_handle* h, const pilot_frame* f
             items[oi + 1] = items[oi] + frame_items(cur[i], frames[i].N, sc.tile, tpi);
         }
         hdr->n_listed[level] = n;
-        long long units = 0;       // anchor x hypothesis units of one iteration of this level
-        for (int i = 0; i < n; ++i) units += (long long)frames[i].N * cur[i];
-        if (units >= kSplitUnits) flow_mask |= 1 << level;
+        // the schedule without grid barriers for levels with much gather work per iteration, or
+        // at least one work item of anchors per job on average (few steps per gather); the
+        // lockstep schedule where the FP64 steps dominate (e.g. 500 anchors per job)
+        long long units = 0, n_jobs = 0;   // anchor x hypothesis units and jobs of one iteration
+        for (int i = 0; i < n; ++i) {
+            units += (long long)frames[i].N * cur[i];
+            n_jobs += cur[i];
+        }
+        if (units >= kSplitUnits || (n_jobs > 0 && units >= (long long)kItemAnchors * n_jobs))
+            flow_mask |= 1 << level;
         for (int i = 0; i < n; ++i) {
             hyp_iters[i] += (long long)cur[i] * c.iters_per_level[level];
             const int K = c.keep_top_k[level];

@@ -99,13 +99,14 @@ def test_full_size_uneven_batch(torch):
 
 
 def test_barrier_free_and_lockstep_levels_in_one_batch(torch):
-    """Two 256^2-anchor frames with 80 hypotheses each: the coarse level's 10.5 M anchor x
+    """Two frames of 60^2 anchors with 1200 hypotheses each: the coarse level's 8.6 M anchor x
     hypothesis units per iteration take the schedule without grid barriers, and after the
-    top-8 pruning the finer levels (1 M units) run in lockstep; the iteration counts differ per
-    level.  Every frame's outputs equal its plain solve bitwise."""
-    frames = [S.make_frame(S.SceneConfig(crop_side=256, n_hyps=80), S.frame_seed(3, 1050 + i)) for i in range(2)]
+    top-8 pruning the finer levels (3600 anchors per job, under one 4096-anchor work item) run
+    in lockstep; the iteration counts differ per level.  Every frame's outputs equal its plain
+    solve bitwise."""
+    frames = [S.make_frame(S.SceneConfig(crop_side=60, n_hyps=1200), S.frame_seed(3, 1050 + i)) for i in range(2)]
     fas = args_for(frames, B.BF16)
-    opts = B.Options(max_points=256 * 256, max_hyps=160, iters=(3, 4, 2, 0), keep_top_k=(0, 8, 8, 0))
+    opts = B.Options(max_points=60 * 60, max_hyps=2400, iters=(3, 4, 2, 0), keep_top_k=(0, 8, 8, 0))
     solver = B.Solver(opts)
     batch = solver.solve_batch(fas)
     for i, fa in enumerate(fas):
