@@ -442,6 +442,7 @@ __global__ void round_advance_kernel(const BatchHeader* hdr, FrameDesc* frames, 
                                      int* fr_job, LevelKeep keep, int tile, int tpi) {
     if (blockIdx.x != 0 || threadIdx.x != 0) return;
     const int nl = hdr->n_listed[0];
+    if (hdr->tiles_per_item > 0) tpi = hdr->tiles_per_item;   // the round's own work-item size
     fr_item[0] = 0;
     fr_job[0] = 0;
     for (int i = 0; i < nl; ++i) {

@@ -171,6 +171,7 @@ struct BatchHeader {
     int n_frames;
     int n_listed[PILOT_MAX_LEVELS];   // frames listed for each level's persistent launch
     int total_hyps;
+    int tiles_per_item;               // > 0: work-item size of the launches over these tables; 0: LevelArgs'
 };
 
 // Persistent level kernel arguments.  A launch's jobs (one per active hypothesis of a listed

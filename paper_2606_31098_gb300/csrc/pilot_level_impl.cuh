@@ -80,7 +80,7 @@ __device__ __forceinline__ bool grid_sync(unsigned long long* sync, unsigned* er
 // lm_update; all 32 lanes of one warp.  Not inlined: the item loop that calls it keeps its own
 // registers for the anchor loop.
 static __device__ __noinline__ void flow_step(const LevelArgs& a, int job, int first, int frame, int level, int k,
-                                              int h, double* E, double* W) {
+                                              int h, int tpi, double* E, double* W) {
     constexpr unsigned kEval = 0x80000000u;
     const int lane = threadIdx.x & 31;
     const FrameDesc* fd = a.frames + frame;
@@ -89,7 +89,7 @@ static __device__ __noinline__ void flow_step(const LevelArgs& a, int job, int f
     const int hyp = (int)(meta & ~kEval);
     if ((meta & kEval) != 0 && lane < kNumSums) {
         const int n_t = fd->N > 0 ? (fd->N + a.tile - 1) / a.tile : 1;
-        const float* src = a.partial + ((size_t)first * a.tiles_per_item * kHypTile + h) * kAcc + lane;
+        const float* src = a.partial + ((size_t)first * tpi * kHypTile + h) * kAcc + lane;
         double sum = 0.0;
         for (int c = 0; c < 8; ++c) {
             double part = 0.0;
@@ -127,7 +127,8 @@ level_persistent_kernel(const __grid_constant__ LevelArgs a) {
     // frame tables, staged when the launch lists few frames
     __shared__ int s_fitem[kSmemFrames + 1], s_fjob[kSmemFrames + 1], s_flist[kSmemFrames], s_fipj[kSmemFrames];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int tpi = a.tiles_per_item;
+    // work-item size: the tables' own (served rounds choose it per round) or the launch's
+    const int tpi = a.header->tiles_per_item > 0 ? a.header->tiles_per_item : a.tiles_per_item;
     if (tid == 0) s_nfr = a.header->n_listed[a.list_index];
     __syncthreads();
     if (s_nfr <= kSmemFrames)
@@ -275,7 +276,8 @@ level_persistent_kernel(const __grid_constant__ LevelArgs a) {
             }
             __syncthreads();
             if (s_last) {
-                if (warp < s_njobs) flow_step(a, s_job + warp, s_first, s_frame, s_level, s_k, warp, E[warp], Wsh[warp]);
+                if (warp < s_njobs)
+                    flow_step(a, s_job + warp, s_first, s_frame, s_level, s_k, warp, tpi, E[warp], Wsh[warp]);
                 __syncthreads();
                 if (tid == 0) {
                     __threadfence();

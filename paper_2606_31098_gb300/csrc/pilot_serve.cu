@@ -375,6 +375,14 @@ void write_round(pilot_server* s) {
     memset(fds, 0, sizeof(FrameDesc) * (size_t)s->max_slots);
     std::vector<Request*> order = s->running;
     std::stable_sort(order.begin(), order.end(), [](Request* a, Request* b) { return a->src.N > b->src.N; });
+    // work items of one tile when the round's items of the default size would not give every
+    // CTA two (a light round: more, smaller items spread its gathers over the device); the
+    // records and their sums do not depend on it
+    int tpi = tiles_per_item(kPlainTile);
+    long long total_items = 0;
+    for (Request* r : order) total_items += frame_items(r->n_active, r->dev.N, kPlainTile, tpi);
+    if (total_items < 2ll * s->grid) tpi = 1;
+    hdr->tiles_per_item = tpi;
     int nl = 0;
     items[0] = jobs[0] = 0;
     for (Request* r : order) {
@@ -419,7 +427,7 @@ void write_round(pilot_server* s) {
         d.quota = r->quota;
         list[nl] = r->slot;
         jobs[nl + 1] = jobs[nl] + r->n_active;
-        items[nl + 1] = items[nl] + frame_items(r->n_active, f.N, kPlainTile, tiles_per_item(kPlainTile));
+        items[nl + 1] = items[nl] + frame_items(r->n_active, f.N, kPlainTile, tpi);
         ++nl;
     }
     hdr->n_listed[0] = nl;

@@ -91,6 +91,23 @@ def test_reserved_sms_leave_results_unchanged(torch, reserved):
     server.close()
 
 
+def test_light_and_heavy_rounds_equal_plain_solves(torch):
+    """A round's work items are one anchor tile when the round is light and four tiles
+    otherwise (three 256^2-anchor frames with 80 hypotheses each make 960 four-tile items, over
+    twice the grid); the records and their FP64 sums do not depend on it, so every frame equals
+    its plain solve bitwise either way, including a small frame served alone afterwards."""
+    frames = uneven_frames(sides=(256, 256, 256, 48), hyps=(80, 80, 80, 6), base=1180)
+    fas = args_for(frames, B.BF16)
+    opts = B.Options(iters=(3, 3, 2, 0), keep_top_k=(0, 8, 8, 0), max_hyps=256)
+    plain = [B.Solver(opts).solve(fa) for fa in fas]
+    server = B.Server(opts, BUDGET, max_slots=4)
+    tickets = [server.submit(fa) for fa in fas[:3]]
+    for i, t in enumerate(tickets):
+        assert_same(server.wait(t)[0], plain[i], what=f"frame {i} in a heavy round")
+    assert_same(server.wait(server.submit(fas[3]))[0], plain[3], what="small frame alone")
+    server.close()
+
+
 def test_result_alone_equals_result_in_the_mix(torch):
     frames = uneven_frames(sides=(48, 66, 35), hyps=(5, 3, 6), base=1200)
     fas = args_for(frames, B.BF16)
