@@ -362,6 +362,18 @@ pilot_status pilot_probe_gather_frame(const float* points, int N, const void* ma
 pilot_status pilot_align_selftest_barrier_timeout(pilot_align_handle* h, double timeout_ms, double* elapsed_ms,
                                                   void* stream);
 
+/* Failure-detection self-test of the batched form's schedule without grid barriers (the paper
+ * has no counterpart): solves the caller's n DEVICE frames (pilot_align_solve_batch's
+ * requirements) with every wait for a job tile's published iteration asking for one more
+ * than will ever be published, so the first waiting CTA gives up after timeout_ms (1 ..
+ * 10000) and sets the error word, and every later wait and barrier of the solve ends at once.
+ * Returns PILOT_OK when the solve reported the timeout (PILOT_ETIMEOUT) and ended (*elapsed_ms,
+ * may be NULL, receives its host wall time); PILOT_EINVAL when no level of the batch takes
+ * that schedule (fewer than 2^23 anchor x hypothesis units per iteration and fewer than 4096
+ * anchors per job).  The results are discarded; the handle stays usable.  Synchronous. */
+pilot_status pilot_align_selftest_flag_timeout(pilot_align_handle* h, const pilot_frame* frames, int n,
+                                               double timeout_ms, double* elapsed_ms, void* stream);
+
 /* Evaluate the normal equations of the total objective (Eq. 7, Eq. 8) at the given
  * poses on one level, without any LM step: out29 (HOST, M x 29 doubles) receives per
  * pose the 21 upper-triangle entries of J^T W J (row-major), the 6 entries of J^T W r,

@@ -68,6 +68,7 @@ SIGNATURES = {
     "pilot_align_get_schedule": (ct.c_int, [_vp, _vp, ct.c_int, ct.c_int, _vp]),
     "pilot_align_set_schedule": (ct.c_int, [_vp, _vp, ct.c_int, ct.c_int, _vp]),
     "pilot_align_selftest_barrier_timeout": (ct.c_int, [_vp, ct.c_double, ct.POINTER(ct.c_double), _vp]),
+    "pilot_align_selftest_flag_timeout": (ct.c_int, [_vp, _vp, ct.c_int, ct.c_double, ct.POINTER(ct.c_double), _vp]),
     "pilot_crop_reference": (ct.c_int, [_vp, _vp, _vp, _vp, _vp, _vp, _vp]),
     "pilot_sample_anchors": (ct.c_int, [_vp, _vp, ct.c_int, ct.c_int, ct.c_ulonglong, _vp, _vp, _vp, _vp]),
     "pilot_pose_predict": (ct.c_int, [_vp, _vp, ct.c_int, _vp]),
@@ -380,6 +381,14 @@ class Solver:
         ms = ct.c_double()
         check(load().pilot_align_selftest_barrier_timeout(self.h, float(timeout_ms), ct.byref(ms),
                                                           self._stream(stream)))
+        return ms.value
+
+    def selftest_flag_timeout(self, fas: list, timeout_ms: float, stream=None) -> float:
+        """pilot_align_selftest_flag_timeout on device frames: returns the solve's wall time (ms)."""
+        frames = self._frame_array(fas)
+        ms = ct.c_double()
+        check(load().pilot_align_selftest_flag_timeout(self.h, ct.cast(frames, _vp), len(fas), float(timeout_ms),
+                                                       ct.byref(ms), self._stream(stream)))
         return ms.value
 
     def set_schedule(self, fas: list, batched: bool, tile: int = 1024, ctas_per_sm: int = 0,

@@ -198,7 +198,7 @@ struct LevelArgs {
     unsigned* tile_ready;      // per job tile, at its first item: iterations whose FP64 steps are published; zero before the launch
     unsigned* error;           // set to 1 when a barrier wait gives up
     unsigned long long barrier_timeout_ns;   // longest barrier wait
-    int barrier_extra;         // 0; > 0 only in the failure self-test (a barrier that cannot complete)
+    int barrier_extra;         // 0; > 0 only in the failure self-tests: a grid barrier (lockstep) or a job tile's flag (barrier-free schedule) that cannot complete
     int level;                 // >= 0: every frame runs this level; -1: each its own level
     int list_index;            // which header->n_listed entry counts this launch's frames
     int iters[PILOT_MAX_LEVELS];

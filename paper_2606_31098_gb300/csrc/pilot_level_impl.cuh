@@ -178,7 +178,8 @@ level_persistent_kernel(const __grid_constant__ LevelArgs a) {
         store_pose32(a.pose32 + 12 * (size_t)job, st.T);
         a.job_meta[job] = (unsigned)hyp | kEval;
     }
-    if (!grid_sync(a.sync, a.error, gen, a.barrier_timeout_ns, a.barrier_extra)) return;
+    // (in the schedule without barriers the failure self-test's extra applies to the flags)
+    if (!grid_sync(a.sync, a.error, gen, a.barrier_timeout_ns, FLOW ? 0 : a.barrier_extra)) return;
     // Gather-heavy levels: the work items of every (iteration, job tile) are claimed in
     // iteration-major order from one counter and no grid barrier is taken.  The CTA that
     // completes a job tile's items of iteration k (counted in tile_done) runs the tile's FP64
@@ -216,7 +217,7 @@ level_persistent_kernel(const __grid_constant__ LevelArgs a) {
                     s_level = level;
                     if (s_run && k > 0) {
                         const unsigned long long t0 = global_ns();
-                        while (ld_acquire_gpu(a.tile_ready + s_first) < (unsigned)k) {
+                        while (ld_acquire_gpu(a.tile_ready + s_first) < (unsigned)(k + a.barrier_extra)) {
                             if (__ldcg(a.error) != 0u || global_ns() - t0 > a.barrier_timeout_ns) {
                                 atomicExch(a.error, 1u);
                                 s_item = -1;

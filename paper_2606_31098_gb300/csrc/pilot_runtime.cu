@@ -17,6 +17,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <chrono>
 #include <map>
 #include <string>
 #include <vector>
@@ -189,6 +190,7 @@ struct pilot_align_handle {
     unsigned* bjob_meta = nullptr;         // per job of a level launch: hypothesis | evaluate bit
     unsigned* bflags = nullptr;            // level kernel's per-job-tile flags: completed items, then published iterations
     size_t bflag_words = 0;                // words of each of the two flag arrays
+    double flag_selftest_ms = 0;           // > 0 during pilot_align_selftest_flag_timeout: unpublishable flags
     cudaStream_t bstream = nullptr;
     // plain form, multi-stream schedule: extra streams, a fork event and their join events
     cudaStream_t pstream[kMaxStreams - 1] = {};
@@ -595,10 +597,12 @@ cudaError_t level_occupancy_query(pilot_dtype dt, int C, int variant, int* n) {
 
 namespace {
 
-// flow_mask bit l: level l runs the level kernel's schedule without grid barriers
-long long graph_key(pilot_dtype dt, int C, int variant, int L, const pilot_schedule& sc, int flow_mask) {
-    return ((long long)dt << 44) | ((long long)C << 36) | ((long long)variant << 32) | ((long long)L << 28) |
-           ((long long)flow_mask << 22) | ((long long)sc.tile << 8) | (long long)sc.ctas_per_sm;
+// flow_mask bit l: level l runs the level kernel's schedule without grid barriers; selftest:
+// the graph of the flag self-test
+long long graph_key(pilot_dtype dt, int C, int variant, int L, const pilot_schedule& sc, int flow_mask,
+                    bool selftest) {
+    return ((long long)selftest << 62) | ((long long)dt << 44) | ((long long)C << 36) | ((long long)variant << 32) |
+           ((long long)L << 28) | ((long long)flow_mask << 22) | ((long long)sc.tile << 8) | (long long)sc.ctas_per_sm;
 }
 
 // Records the whole batched solve on h->bstream: descriptor upload, per-frame set-up,
@@ -656,6 +660,12 @@ pilot_status capture_batch_graph(pilot_align_handle* h, pilot_dtype dt, int C, i
         a.error = error;
         a.barrier_timeout_ns = kBarrierTimeoutNs;
         a.barrier_extra = 0;
+        if (flow && h->flag_selftest_ms > 0) {
+            // the flag self-test: every wait for a job tile's flag asks for one iteration more
+            // than will ever be published, and gives up after the test's timeout
+            a.barrier_extra = 1;
+            a.barrier_timeout_ns = (unsigned long long)(h->flag_selftest_ms * 1e6);
+        }
         a.level = level;
         a.list_index = level;
         for (int l = 0; l < PILOT_MAX_LEVELS; ++l) a.iters[l] = c.iters_per_level[l];
@@ -684,7 +694,7 @@ pilot_status capture_batch_graph(pilot_align_handle* h, pilot_dtype dt, int C, i
     if (e2 != cudaSuccess) return cuda_fail(e2, "graph capture end");
     h->graph = g;
     PILOT_CUDA(cudaGraphInstantiate(&h->gexec, g, 0), "graph instantiate");
-    h->graph_key = graph_key(dt, C, variant, L, sc, flow_mask);
+    h->graph_key = graph_key(dt, C, variant, L, sc, flow_mask, h->flag_selftest_ms > 0);
     return PILOT_OK;
 }
 
@@ -983,6 +993,34 @@ pilot_status pilot_align_selftest_barrier_timeout(pilot_align_handle* h, double 
     return PILOT_OK;
 }
 
+pilot_status pilot_align_selftest_flag_timeout(pilot_align_handle* h, const pilot_frame* frames, int n,
+                                               double timeout_ms, double* elapsed_ms, void* stream) {
+    if (!h || !frames || n < 1) return fail(PILOT_EINVAL, "handle or frames missing");
+    if (!(timeout_ms >= 1.0 && timeout_ms <= 10000.0)) return fail(PILOT_EINVAL, "timeout_ms must be in [1, 10000]");
+    if (n > h->cfg.max_frames) return fail(PILOT_EINVAL, "more frames than max_frames");
+    // results are discarded: one scratch record per hypothesis
+    long long total = 0;
+    for (int i = 0; i < n; ++i) total += frames[i].M > 0 ? frames[i].M : 0;
+    std::vector<double> T(12 * (size_t)total + 12), cost((size_t)total + 1);
+    std::vector<int> nv((size_t)total + 1), hs((size_t)total + 1), best(n);
+    std::vector<long long> hi(n);
+    std::vector<pilot_result> res(n);
+    size_t o = 0;
+    for (int i = 0; i < n; ++i) {
+        res[i] = pilot_result{T.data() + 12 * o, cost.data() + o, nv.data() + o, hs.data() + o, &best[i], &hi[i]};
+        o += frames[i].M > 0 ? frames[i].M : 0;
+    }
+    h->flag_selftest_ms = timeout_ms;
+    const auto t0 = std::chrono::steady_clock::now();
+    const pilot_status st = pilot_align_solve_batch(h, frames, n, res.data(), stream);
+    const double ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    h->flag_selftest_ms = 0;
+    if (elapsed_ms) *elapsed_ms = ms;
+    if (st == PILOT_ETIMEOUT) return PILOT_OK;
+    if (st != PILOT_OK) return st;
+    return fail(PILOT_ECUDA, "flag self-test: the unpublishable flag did not report its timeout");
+}
+
 pilot_status pilot_align_solve_batch(pilot_align_handle* h, const pilot_frame* frames, int n,
                                      pilot_result* results, void* stream) {
     if (!h || (n > 0 && (!frames || !results))) return fail(PILOT_EINVAL, "handle, frames or results is NULL");
@@ -1099,7 +1137,9 @@ pilot_status pilot_align_solve_batch(pilot_align_handle* h, const pilot_frame* f
             if (level > 0 && K > 0 && K < cur[i]) cur[i] = K;
         }
     }
-    const long long key = graph_key(f0.feat_dtype, f0.C, variant, L, sc, flow_mask);
+    if (h->flag_selftest_ms > 0 && flow_mask == 0)
+        return fail(PILOT_EINVAL, "flag self-test: no level of this batch runs without grid barriers");
+    const long long key = graph_key(f0.feat_dtype, f0.C, variant, L, sc, flow_mask, h->flag_selftest_ms > 0);
     if (!h->gexec || h->graph_key != key)
         if ((st = capture_batch_graph(h, f0.feat_dtype, f0.C, variant, L, sc, flow_mask)) != PILOT_OK) return st;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
@@ -1110,7 +1150,7 @@ pilot_status pilot_align_solve_batch(pilot_align_handle* h, const pilot_frame* f
     const unsigned char* r = h->bres_host;
     const int* best = reinterpret_cast<const int*>(r + rl.bytes);
     if (best[c.max_frames] != 0)
-        return fail(PILOT_ETIMEOUT, "batched solve: a level kernel's grid barrier timed out (results invalid)");
+        return fail(PILOT_ETIMEOUT, "batched solve: a level kernel's grid barrier or flag wait timed out (results invalid)");
     for (int i = 0; i < n; ++i) {
         const int o = fds[i].hyp_offset, M = frames[i].M;
         pilot_result& out = results[i];

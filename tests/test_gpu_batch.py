@@ -173,6 +173,26 @@ def test_barrier_timeout_is_reported_and_the_handle_stays_usable(torch):
         solver.selftest_barrier_timeout(0.5)
 
 
+def test_flag_wait_timeout_is_reported_and_the_handle_stays_usable(torch):
+    """Failure detection without a fault in the schedule without grid barriers: the waits for
+    a job tile's published iteration are bounded in time.  The self-test solves real frames
+    (70^2 and 72^2 anchors: over 4096 anchors per job, so that schedule) with flags that can
+    never be published; the first waiting CTA gives up after the timeout, the solve reports it,
+    and the handle stays usable (a batched solve afterwards still equals the plain solves)."""
+    fas = args_for(uneven_frames(sides=(70, 72), hyps=(4, 5), base=1660))
+    solver = B.Solver(B.Options())
+    ms = solver.selftest_flag_timeout(fas, 100.0)
+    assert 90.0 <= ms < 5000.0
+    batch = solver.solve_batch(fas)
+    for i, fa in enumerate(fas):
+        assert_same(batch[i], solver.solve(fa), what=f"frame {i}")
+    small = args_for(uneven_frames(sides=(30,), hyps=(2,), base=1670))
+    with pytest.raises(B.PilotError, match="without grid barriers"):
+        solver.selftest_flag_timeout(small, 100.0)
+    with pytest.raises(B.PilotError, match="timeout_ms"):
+        solver.selftest_flag_timeout(fas, 0.5)
+
+
 def test_autotuner_picks_a_schedule_that_keeps_the_results(torch):
     """pilot_align_autotune times the candidate schedules on the caller's frames and keeps
     the fastest for that frame shape; solves with the tuned schedule select the same pose
